@@ -1,0 +1,92 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This module holds no arithmetic of the lattice Boltzmann method: it only draws seeded
+random numbers and shapes them into the problem inputs that the paper's workloads use
+(porosity fields, perturbation fields, problem statements).  Both sides receive the same
+arrays from here; neither side's arithmetic lives here.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+FACES = ("x-", "x+", "y-", "y+", "z-", "z+")
+
+
+def gaussian_field(shape, seed: int, corr: float) -> np.ndarray:
+    """Zero-mean, unit-variance Gaussian random field on a [z][y][x] grid.
+
+    White noise from PCG64(seed), smoothed by a separable periodic Gaussian kernel of
+    standard deviation ``corr`` lattice spacings along each axis (FFT convolution), then
+    rescaled to unit variance.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = rng.standard_normal(shape)
+    out = np.fft.fftn(w)
+    for ax, n in enumerate(shape):
+        k = np.fft.fftfreq(n)
+        kern = np.exp(-0.5 * (2 * math.pi * k * corr) ** 2)
+        sh = [1] * len(shape)
+        sh[ax] = n
+        out = out * kern.reshape(sh)
+    f = np.real(np.fft.ifftn(out))
+    f -= f.mean()
+    sd = f.std()
+    return f / sd if sd > 0 else f
+
+
+def porosity_field(nx: int, ny: int, nz: int, seed: int = 20161110, mean: float = 0.6,
+                   std: float = 0.05, lo: float = 0.4, hi: float = 0.9,
+                   corr: float | None = None) -> np.ndarray:
+    """Heterogeneous porosity phi(x) [z][y][x]: Gaussian field, mean 0.6, std 0.05, clipped
+    to [0.4, 0.9]; correlation length L/16 with L the largest edge."""
+    if corr is None:
+        corr = max(nx, ny, nz) / 16.0
+    g = gaussian_field((nz, ny, nx), seed, corr)
+    return np.clip(mean + std * g, lo, hi)
+
+
+def uniform(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Seeded uniform random numbers (PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=shape)
+
+
+def random_macros(nx: int, ny: int, nz: int, seed: int, u_amp: float = 0.03,
+                  rho_amp: float = 0.01, T_lo: float = 0.0, T_hi: float = 1.0):
+    """Random density, velocity and temperature fields for single-step parity checks:
+    rho in 1 +- rho_amp, |u_a| <= u_amp, T in [T_lo, T_hi]; shapes [z][y][x] / [3][z][y][x]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rho = 1.0 + rho_amp * rng.uniform(-1, 1, size=(nz, ny, nx))
+    u = u_amp * rng.uniform(-1, 1, size=(3, nz, ny, nx))
+    T = rng.uniform(T_lo, T_hi, size=(nz, ny, nx))
+    return rho, u, T
+
+
+def cavity_problem(n: int, Ra: float, Da: float, phi: float, Pr: float = 1.0,
+                   F_phi: float = -1.0, J: float = 1.0, sigma: float = 1.0, **kw) -> dict:
+    """Porous cavity of Sec. 4.2: hot x-low wall (T=1), cold x-high wall (T=0), the other
+    four walls adiabatic, no-slip everywhere, gravity along -z, initial T = 0.5.
+    ``F_phi=-1`` selects Ergun's inertia coefficient (Eq. 6)."""
+    pb = dict(nx=n, ny=n, nz=n, mapping="cavity", Ra=Ra, Da=Da, Pr=Pr, J=J, sigma=sigma,
+              phi=phi, F_phi=F_phi, flow_bc=[1] * 6, heat_bc=[2, 2, 1, 1, 1, 1],
+              face_T=[1.0, 0.0, 0.0, 0.0, 0.0, 0.0], T_init=0.5, T0=0.5,
+              gravity_axis=2, gravity_sign=-1)
+    pb.update(kw)
+    return pb
+
+
+def channel_problem(nx: int, ny: int, nz: int, Re: float = 10.0, u0: float = 0.01,
+                    Pr: float = 0.71, Ri: float = 1.0, Da: float = 1e-3, phi: float = 0.7,
+                    F_phi: float = -1.0, **kw) -> dict:
+    """Porous channel: velocity inlet u0 at T=0 on x-low, convective outflow on x-high,
+    no-slip walls at y-low (T=0) and y-high (T=1), periodic in z, gravity along -y; the
+    channel height ny is the length scale of Re, Ri and Da."""
+    pb = dict(nx=nx, ny=ny, nz=nz, mapping="channel", Re=Re, u0=u0, Pr=Pr, Ri=Ri, Da=Da,
+              phi=phi, F_phi=F_phi, flow_bc=[2, 3, 1, 1, 0, 0], heat_bc=[2, 3, 2, 2, 0, 0],
+              face_T=[0.0, 0.0, 0.0, 1.0, 0.0, 0.0],
+              face_u=[(u0, 0.0, 0.0)] + [(0.0, 0.0, 0.0)] * 5,
+              T_init=0.0, T0=0.5, gravity_axis=1, gravity_sign=-1)
+    pb.update(kw)
+    return pb
