@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused D3Q19 + D3Q7 MRT stream-collide step on one GB300 (or N replicas).
+
+Workload: the mixed-convection porous channel, 256 x 64 x 64 sites, FP32 population storage
+and arithmetic (porosity 0.7, Da = 1e-3, Re = 10, Pr = 0.71, Ri = 1, u0 = 0.01, velocity
+inlet at T = 0, anchored convective outflow, walls at T = 1 / T = 0, periodic in z).  One
+bench step is one time step of the whole lattice.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead (a bounded
+z-slab of the channel per step, periodic in z like the full channel).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (D3Q19+D3Q7)"
+UNIT = "MLUPS"
+NX, NY, NZ = 256, 64, 64
+WORKLOAD = "porous mixed-convection channel 256x64x64, D3Q19+D3Q7 MRT, FP32"
+
+
+def _problem(nz=NZ):
+    from lbm_inputs import channel_problem
+
+    return channel_problem(NX, NY, nz)
+
+
+def _config(extra=None):
+    cfg = {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "phi": 0.7, "Da": 1e-3,
+           "Re": 10, "Pr": 0.71, "Ri": 1.0, "u0": 0.01, "storage": "fp32-deviation",
+           "scheme": "ping-pong pull",
+           "l2": "inputs larger than L2: two population copies of 218 MB vs 126 MB L2, no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _init_dist(ws):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo")
+    return dist
+
+
+def _max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---- clocks --------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---- CPU baseline: the oracle as it stands ------------------------------------------------------
+def _oracle_run(nz: int, steps: int, warmup: int):
+    import oracle
+
+    lp = oracle.map_problem(_problem(nz))
+    o = oracle.Oracle(lp)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return NX * NY * nz * steps / dt / 1e6, dt, oracle.max_threads()
+
+
+def cpu_baseline(budget_s: float = 10.0):
+    """The oracle on the host cores over a bounded sample: a z-slab of the channel (periodic
+    in z as the full channel) sized so that the timed steps take about budget_s."""
+    mlups1, dt1, cores = _oracle_run(8, 1, 0)
+    per_step_full = NX * NY * NZ / (mlups1 * 1e6)
+    steps = max(1, min(200, int(budget_s / per_step_full)))
+    mlups, dt, cores = _oracle_run(NZ, steps, 0)
+    return {"value": round(mlups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} time steps of the full {NX}x{NY}x{NZ} channel "
+                      f"({dt:.1f} s, FP64, OpenMP over z-planes)"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    budget = 120.0  # seconds for the whole --steps + --warmup run
+    mlups1, _, cores = _oracle_run(8, 1, 0)
+    per_site = 1.0 / (mlups1 * 1e6)
+    nz = int(budget / max(1, args.steps + args.warmup) / (per_site * NX * NY))
+    nz = max(1, min(NZ, nz))
+    mlups, dt, cores = _oracle_run(nz, args.steps, args.warmup)
+    sample = (f"each step: one time step of a {NX}x{NY}x{nz} z-slab of the channel "
+              f"(periodic in z), FP64 oracle, OpenMP over z-planes")
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config({"sample_nz": nz}),
+            "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- our arm ---------------------------------------------------------------------------------
+def run_ours(args):
+    ws, rank = _dist()
+    if ws > 1 and "LOCAL_RANK" in os.environ and "CUDA_VISIBLE_DEVICES" not in os.environ:
+        os.environ["CUDA_VISIBLE_DEVICES"] = os.environ["LOCAL_RANK"]  # one replica per GPU
+    import numpy as np
+    import torch
+
+    import paper_1611_03329_gb300 as gb
+
+    dist = _init_dist(ws)
+    gb.build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    pb = _problem()
+    ns = NX * NY * NZ
+    with torch.cuda.stream(stream):
+        lat = gb.Lattice(pb, stream=stream.cuda_stream)
+        lat.step(args.warmup)
+        lat.sync()
+
+        # ---- device-resident timing (the value) ----
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        _barrier(dist)
+        torch.cuda.synchronize()
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            start.record(stream)
+            lat.step(args.steps)
+            stop.record(stream)
+            stop.synchronize()
+        torch.cuda.synchronize()
+        _barrier(dist)
+        ms = start.elapsed_time(stop)
+        ms_max = _max_over_ranks(dist, ms)
+        mlups = ns * args.steps * ws / (ms_max * 1e-3) / 1e6
+        ru, rT = lat.residual()  # finite state after the run
+        m_dev, h_dev = lat.sums()
+
+        # ---- end to end through the host-buffer C ABI ----
+        n_e2e = max(1, min(args.steps, 50))
+        f, g = lat.populations()
+        fp = torch.from_numpy(f).pin_memory().numpy()
+        gp = torch.from_numpy(g).pin_memory().numpy()
+        rho_h = torch.empty((NZ, NY, NX), dtype=torch.float32).pin_memory().numpy()
+        u_h = torch.empty((3, NZ, NY, NX), dtype=torch.float32).pin_memory().numpy()
+        T_h = torch.empty((NZ, NY, NX), dtype=torch.float32).pin_memory().numpy()
+        for _ in range(3):
+            lat.set_populations(fp, gp)
+            lat.step(1)
+            lat.macros_into(rho_h, u_h, T_h)
+        _barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            lat.set_populations(fp, gp)
+            lat.step(1)
+            lat.macros_into(rho_h, u_h, T_h)
+        e2e_s = _max_over_ranks(dist, time.perf_counter() - t0)
+        e2e_mlups = ns * n_e2e * ws / e2e_s / 1e6
+    lat.close()
+
+    if rank != 0:
+        return 0
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    bytes_site = gb.algorithmic_bytes_per_site(pb)
+    kernel_ms = ms / args.steps  # one fused step kernel per time step
+    achieved = bytes_site * ns / (kernel_ms * 1e-3) / 1e9
+    cpu = cpu_baseline() if (ws == 1 and not args.no_cpu_baseline) else None
+    line = {
+        "metric": METRIC, "value": round(mlups, 2), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 6),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": _config({"parallelism": f"replicas{ws}" if ws > 1 else "single"}),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
+                     "kernel": "step_kernel<false,true> (fused stream-collide, outflow)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_mlups, 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(fp.nbytes + gp.nbytes),
+                "d2h_bytes_per_step": int(rho_h.nbytes + u_h.nbytes + T_h.nbytes),
+                "steps": n_e2e,
+                "path": "lbm_set_populations (pinned FP64 host) + lbm_step(1) + lbm_macros (pinned host)"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "state_check": {"residual_u": ru, "residual_T": rT, "mass_dev": m_dev,
+                        "heat_dev": h_dev},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

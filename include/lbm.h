@@ -1,0 +1,225 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) fused stream-collide library for the 3D
+ * double-distribution-function MRT lattice Boltzmann model of convection heat transfer in
+ * porous media at the REV scale (Liu & He, arXiv:1611.03329).
+ *
+ * One time step advances, at every lattice site, the D3Q19 MRT density populations f
+ * (Sec. 3.1.2, Eqs. 8-11 and 19-28, generalized non-Darcy force of Eq. 4) and the D3Q7 MRT
+ * temperature populations g (Sec. 3.2, Eqs. 33-43), streaming in pull form (Eqs. 10, 35)
+ * with halfway bounce-back walls, velocity inlets, anti-bounce-back Dirichlet walls and an
+ * anchored convective outflow.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an lbm_status; nothing throws across the ABI.  A CUDA failure is
+ *    sticky: once a call returns LBM_ECUDA the context only accepts lbm_destroy,
+ *    lbm_last_error and lbm_status_string.
+ *  - Field arrays are x-fastest: site s = x + nx*(y + ny*z); population arrays are
+ *    q-major, f[i*ns + s] with ns = nx*ny*nz and the velocity order of Eq. 19 (D3Q19) and
+ *    of the first seven columns of Eq. 12 (D3Q7).  Vector fields are [3][ns].
+ *  - "host" pointers are caller-owned CPU memory (pinned or pageable); the library copies
+ *    from or into them and keeps no reference.  "device" pointers are caller-owned GPU
+ *    memory on the context's device.  The context owns all of its own device memory.
+ *  - Work is queued on the stream given to lbm_create.  Calls that return results to host
+ *    memory synchronise that stream; lbm_step and the *_device calls do not.
+ *  - A context is not thread-safe; use one context per host thread or serialise.
+ *  - Faces are numbered x-low, x-high, y-low, y-high, z-low, z-high (0..5).
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* an argument or parameter is out of range; nothing was changed */
+    LBM_ENOMEM = 2,    /* device allocation failed; the context is unusable */
+    LBM_ECUDA = 3,     /* a CUDA call failed (sticky, see lbm_last_error) */
+    LBM_EUNSTABLE = 4, /* a reduction found NaN or Inf in the state */
+    LBM_ESTATE = 5     /* call not allowed in the context's current state */
+} lbm_status;
+
+/* Flow boundary kinds (per face). */
+enum {
+    LBM_FLOW_PERIODIC = 0, /* both faces of the axis must be periodic */
+    LBM_FLOW_WALL = 1,     /* resting no-slip wall, halfway bounce-back */
+    LBM_FLOW_VELOCITY = 2, /* moving wall / velocity inlet with face_u (bounce-back) */
+    LBM_FLOW_OUTFLOW = 3   /* convective outflow; x-high face only */
+};
+
+/* Thermal boundary kinds (per face). */
+enum {
+    LBM_HEAT_PERIODIC = 0,  /* must match a periodic flow face */
+    LBM_HEAT_ADIABATIC = 1, /* zero heat flux, bounce-back of g */
+    LBM_HEAT_DIRICHLET = 2, /* wall temperature face_T, anti-bounce-back of g */
+    LBM_HEAT_OUTFLOW = 3    /* convective outflow; only on an outflow face */
+};
+
+/* Mapping from the dimensionless problem statement to lattice units. */
+enum {
+    LBM_MAP_CAVITY = 0,  /* natural convection, Eq. 56 (Ra, Pr, Ma, J, sigma, Gamma) */
+    LBM_MAP_CHANNEL = 1, /* mixed convection, Eq. 51 (Re, u0, Pr, J, sigma, Gamma, Ri) */
+    LBM_MAP_LATTICE = 2  /* lattice units given directly (nu_e, alpha_f, gbeta) */
+};
+
+enum { LBM_STORE_FP32 = 0 }; /* populations stored as FP32 deviations from w_i rho0, w_i sigma T0 */
+
+/*
+ * Problem statement (Sec. 2, Eqs. 1-7, and the problem setups of Sec. 4).  Fill it with
+ * lbm_params_default() first; every field then holds the paper's default.
+ */
+typedef struct lbm_params {
+    int nx, ny, nz;  /* lattice sites per axis, each >= 1 (>= 3 along x with an outflow) */
+    int storage;     /* LBM_STORE_FP32 */
+    int mapping;     /* LBM_MAP_* */
+    double L;        /* characteristic length in lattice units; <= 0: nx (cavity,
+                        lattice) or ny (channel) -- the halfway walls make L = N */
+    double Ra, Da, Pr, J, sigma, Gamma, Ma; /* Eq. 7 and Eq. 56 (Ma = u_c / c_s) */
+    double Re, Ri, u0;                      /* channel: Eq. 51 with u1 = u0, H = L */
+    double dT;                              /* T_h - T_c (1) */
+    double T0, rho0, varpi;                 /* reference temperature (0.5), mean density
+                                               (1), D3Q7 parameter varpi in (0,1) (0.5) */
+    /* free relaxation rates of Sec. 4 (defaults 1.1, 1.1, 1.1, 1.1, 1.2, 1, 1.2, 1.2) */
+    double s_e, s_eps, s_q, s_pi, s_m, zeta_T, zeta_e, zeta_nu;
+    double nu_e, alpha_f, gbeta;     /* LBM_MAP_LATTICE: effective viscosity, fluid
+                                        diffusivity (<= 0: nu/Pr) and g*beta */
+    int gravity_axis;                /* 0, 1, 2 (z, Sec. 4.2) */
+    int gravity_sign;                /* -1: gravity points to -axis (hot fluid rises) */
+    double accel[3];                 /* external acceleration a of Eq. 5 */
+    int flow_bc[6];                  /* LBM_FLOW_* per face */
+    int heat_bc[6];                  /* LBM_HEAT_* per face */
+    double face_T[6];                /* Dirichlet wall temperatures */
+    double face_u[6][3];             /* velocity of LBM_FLOW_VELOCITY faces */
+    double T_init;                   /* initial uniform temperature */
+    double U_out;                    /* convective outflow speed; <= 0: u0 */
+} lbm_params;
+
+/*
+ * Lattice-unit parameters derived from an lbm_params (Eq. 32, Eq. 41, Eq. 51 or Eq. 56,
+ * Eq. 7) and the medium.  Read-only view for checks and logging.
+ */
+typedef struct lbm_lattice {
+    int nx, ny, nz;
+    double L, rho0, T0, sigma, varpi, dT;
+    double s[19];              /* diagonal of Lambda in the moment order of Eq. 20 (Eq. 22) */
+    double zeta_T, zeta_e, zeta_nu, zeta_alpha; /* Q of Eq. 38 (zeta_alpha of a uniform
+                                                   medium; per site with alpha_m >= 0) */
+    double s_nu, nu_e, nu, alpha_f, alpha_m, Gamma;
+    double gbeta, buoy[3], accel[3];   /* G = buoy (T - T0) + accel */
+    double phi, K, F_phi, phi_ref;     /* F_phi < 0: Ergun per site; K may be +inf */
+    int has_phi_field;
+    double U_out;
+} lbm_lattice;
+
+/* Fill p with the paper's defaults (Sec. 4: rho0 = 1, J = sigma = Gamma = 1, varpi = 1/2,
+ * the free relaxation rates above, Ma = 0.1, Pr = 1, T0 = 0.5, gravity -z) and all faces
+ * periodic.  Host only; never fails for a non-NULL p. */
+lbm_status lbm_params_default(lbm_params* p);
+
+/* Derive the lattice parameters of p without creating a context (host only, no GPU):
+ * Eq. 56 (cavity) or Eq. 51 read with 1/s_nu (channel) for s_nu, Eq. 32 for nu_e,
+ * nu = nu_e / J, alpha_f = nu / Pr, Eq. 41 for zeta_alpha, g beta from u_c = Ma c_s =
+ * sqrt(g beta dT L) (cavity) or Ri = g beta dT L / u0^2 (channel).  The medium is the
+ * default one (phi = 1, K = Da L^2 or +inf, F_phi = 0).  LBM_EINVAL on any invalid field. */
+lbm_status lbm_derive_lattice(const lbm_params* p, lbm_lattice* out);
+
+/* Create a context on the device of `stream` (a cudaStream_t; NULL: the calling thread's
+ * current device and a private non-blocking stream), queue its work on that stream,
+ * allocate the two population
+ * copies and initialise f = f_eq(rho0, u = 0), g = g_eq(T_init, u = 0) (Eqs. 24, 42).
+ * The medium starts as phi = 1, K = Da L^2 (Da > 0) or +inf, F_phi = 0.
+ * Errors: LBM_EINVAL (invalid params; *out untouched), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out);
+
+/* Release all device memory of the context (and its private stream).  NULL is a no-op. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Porous medium (Eq. 4, Eq. 6, Sec. 2).
+ *  phi_field : host, ns floats in (0,1), or NULL for the uniform porosity `phi` in (0,1].
+ *  K         : permeability; <= 0 selects Da L^2 (Eq. 7), +inf removes the Darcy and
+ *              Forchheimer drag.  With a field, K is the permeability at porosity phi_ref
+ *              and K(x) follows Kozeny-Carman, K ~ phi^3 / (1 - phi)^2 (Eq. 6).
+ *  F_phi     : Forchheimer inertia coefficient; < 0 selects Ergun's 1.75/sqrt(150 phi^3)
+ *              (Eq. 6, per site with a field); 0 is the Brinkman-extended Darcy model.
+ *  alpha_m   : matrix thermal diffusivity; < 0 keeps alpha_e = Gamma alpha_f, otherwise
+ *              alpha_e(x) = phi alpha_f + (1 - phi) alpha_m and zeta_alpha follows Eq. 41
+ *              per site.
+ *  phi_ref   : <= 0 selects the mean of phi_field (or phi).
+ * Takes effect from the next lbm_step; the populations are not touched.  Synchronises the
+ * stream.  Errors: LBM_EINVAL (out-of-range value; nothing changed), LBM_ECUDA. */
+lbm_status lbm_set_medium(lbm_ctx* ctx, const float* phi_field, double phi, double K,
+                          double F_phi, double alpha_m, double phi_ref);
+
+/* Advance nsteps >= 0 time steps: per site, pull streaming with the boundary rules
+ * (Eqs. 10, 35), T from Eq. 39, G from Eq. 5, u from Eqs. 27-28, F from Eq. 4, the D3Q19
+ * MRT collision with forcing in moment space (Eqs. 9, 21-23) and the D3Q7 MRT collision
+ * (Eqs. 34, 37-38, 43).  Asynchronous on the context's stream; launch errors are returned,
+ * execution errors surface at the next synchronising call.  LBM_EINVAL for nsteps < 0. */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Re-initialise the state to equilibrium (Eqs. 24 and 42) with rho = rho0 and, per site,
+ * T from T_field (host, ns doubles; NULL: T_uniform) and u from u_field (host, 3 x ns
+ * doubles; NULL: 0), using the current medium.  Resets the step counter.  Synchronises. */
+lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* T_field, const double* u_field,
+                                double T_uniform);
+
+/* Replace the stored post-collision populations f*(x, t-1), g*(x, t-1) (host, 19 x ns and
+ * 7 x ns doubles, full values, not deviations).  The outflow history is reset to the
+ * stored populations of the x-high column.  Synchronises. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g);
+
+/* Copy the stored post-collision populations to host (19 x ns and 7 x ns doubles, full
+ * values); either pointer may be NULL.  Synchronises. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* g);
+
+/* Macroscopic fields at the current time, computed from the streamed populations exactly
+ * as the step does: rho (Eq. 25), u (Eqs. 27-28), T (Eq. 39).  Host pointers: rho and T
+ * ns floats, u 3 x ns floats; any may be NULL.  Synchronises. */
+lbm_status lbm_macros(lbm_ctx* ctx, float* rho, float* u, float* T);
+
+/* Same as lbm_macros into device pointers; asynchronous on the context's stream. */
+lbm_status lbm_macros_device(lbm_ctx* ctx, float* rho, float* u, float* T);
+
+/* Wall Nusselt numbers of Eqs. 53-55 on a Dirichlet face: -d(theta)/dn at the halfway wall
+ * from the quadratic through the wall value and the first two nodes,
+ * Nu_local = L (8 T_w - 9 T_0 + T_1) / (3 dT) (positive = heat into the fluid), averaged
+ * over the second tangential axis into the profile along the first one (y for x-faces,
+ * x otherwise; Eq. 54), whose mean is Nu_3D (Eq. 55) and whose centre value is Nu_mp.
+ * FP64 accumulation on the device.  nu_avg, nu_profile (host, length of the first
+ * tangential axis) and nu_mp may each be NULL.  Synchronises.
+ * Errors: LBM_EINVAL (face not Dirichlet or normal extent < 2), LBM_EUNSTABLE (NaN). */
+lbm_status lbm_nusselt(lbm_ctx* ctx, int face, double* nu_avg, double* nu_profile,
+                       double* nu_mp);
+
+/* Totals of the stored populations, FP64 accumulation: mass_dev = sum_s sum_i f_i - ns rho0
+ * (mass, Eq. 25) and heat_dev = sum_s sum_i g_i - ns sigma T0 (heat, Eq. 39).
+ * Either pointer may be NULL.  Synchronises.  LBM_EUNSTABLE if a total is not finite. */
+lbm_status lbm_sums(lbm_ctx* ctx, double* mass_dev, double* heat_dev);
+
+/* Steady-state residual: r_u = ||u - u_prev||_2 / ||u||_2 and the same for T, against the
+ * fields saved by the previous call (FP64 accumulation); the first call after create or
+ * init returns +inf.  Synchronises.  LBM_EUNSTABLE if a field holds NaN or Inf. */
+lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
+
+/* Derived lattice parameters of the context, including the current medium. */
+lbm_status lbm_get_lattice(const lbm_ctx* ctx, lbm_lattice* out);
+
+/* Number of time steps taken since create / init. */
+long long lbm_steps_done(const lbm_ctx* ctx);
+
+/* Block the host until the context's stream is idle. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Text of the last error of the context (never NULL; "" when none).  Owned by ctx. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Static text for a status code. */
+const char* lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

@@ -1,0 +1,327 @@
+"""GB300 (sm_103a) library for the 3D DDF-MRT lattice Boltzmann model of convection heat
+transfer in porous media at the REV scale (Liu & He, arXiv:1611.03329).
+
+This module is a thin ctypes binding of the C ABI in ``include/lbm.h``: it marshals
+arguments and owns nothing but host buffers.  Every step of the computation runs in the
+CUDA library ``_lib/liblbm_gb300.so``; when that library is missing the binding raises
+instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+Q19, Q7 = 19, 7
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = range(6)
+FLOW_PERIODIC, FLOW_WALL, FLOW_VELOCITY, FLOW_OUTFLOW = range(4)
+HEAT_PERIODIC, HEAT_ADIABATIC, HEAT_DIRICHLET, HEAT_OUTFLOW = range(4)
+MAP_CAVITY, MAP_CHANNEL, MAP_LATTICE = range(3)
+_MAPPINGS = {"cavity": MAP_CAVITY, "channel": MAP_CHANNEL, "lattice": MAP_LATTICE}
+
+# Every symbol that include/lbm.h declares.
+ABI_SYMBOLS = (
+    "lbm_params_default", "lbm_derive_lattice", "lbm_create", "lbm_destroy", "lbm_set_medium",
+    "lbm_step", "lbm_init_equilibrium", "lbm_set_populations", "lbm_get_populations",
+    "lbm_macros", "lbm_macros_device", "lbm_nusselt", "lbm_sums", "lbm_residual",
+    "lbm_get_lattice", "lbm_steps_done", "lbm_sync", "lbm_last_error", "lbm_status_string",
+)
+
+
+class LbmParams(C.Structure):
+    """Mirror of ``lbm_params`` (include/lbm.h)."""
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("storage", C.c_int), ("mapping", C.c_int),
+        ("L", C.c_double),
+        ("Ra", C.c_double), ("Da", C.c_double), ("Pr", C.c_double), ("J", C.c_double),
+        ("sigma", C.c_double), ("Gamma", C.c_double), ("Ma", C.c_double),
+        ("Re", C.c_double), ("Ri", C.c_double), ("u0", C.c_double),
+        ("dT", C.c_double),
+        ("T0", C.c_double), ("rho0", C.c_double), ("varpi", C.c_double),
+        ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double), ("s_pi", C.c_double),
+        ("s_m", C.c_double), ("zeta_T", C.c_double), ("zeta_e", C.c_double),
+        ("zeta_nu", C.c_double),
+        ("nu_e", C.c_double), ("alpha_f", C.c_double), ("gbeta", C.c_double),
+        ("gravity_axis", C.c_int), ("gravity_sign", C.c_int),
+        ("accel", C.c_double * 3),
+        ("flow_bc", C.c_int * 6), ("heat_bc", C.c_int * 6),
+        ("face_T", C.c_double * 6), ("face_u", (C.c_double * 3) * 6),
+        ("T_init", C.c_double), ("U_out", C.c_double),
+    ]
+
+
+class LbmLattice(C.Structure):
+    """Mirror of ``lbm_lattice`` (include/lbm.h)."""
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("L", C.c_double), ("rho0", C.c_double), ("T0", C.c_double), ("sigma", C.c_double),
+        ("varpi", C.c_double), ("dT", C.c_double),
+        ("s", C.c_double * 19),
+        ("zeta_T", C.c_double), ("zeta_e", C.c_double), ("zeta_nu", C.c_double),
+        ("zeta_alpha", C.c_double),
+        ("s_nu", C.c_double), ("nu_e", C.c_double), ("nu", C.c_double), ("alpha_f", C.c_double),
+        ("alpha_m", C.c_double), ("Gamma", C.c_double),
+        ("gbeta", C.c_double), ("buoy", C.c_double * 3), ("accel", C.c_double * 3),
+        ("phi", C.c_double), ("K", C.c_double), ("F_phi", C.c_double), ("phi_ref", C.c_double),
+        ("has_phi_field", C.c_int),
+        ("U_out", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(path)
+        vp, dp, fp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)
+        pp = C.POINTER(LbmParams)
+        L.lbm_params_default.argtypes = [pp]
+        L.lbm_derive_lattice.argtypes = [pp, C.POINTER(LbmLattice)]
+        L.lbm_create.argtypes = [pp, vp, C.POINTER(vp)]
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_set_medium.argtypes = [vp, fp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.c_double]
+        L.lbm_step.argtypes = [vp, C.c_int]
+        L.lbm_init_equilibrium.argtypes = [vp, dp, dp, C.c_double]
+        L.lbm_set_populations.argtypes = [vp, dp, dp]
+        L.lbm_get_populations.argtypes = [vp, dp, dp]
+        L.lbm_macros.argtypes = [vp, fp, fp, fp]
+        L.lbm_macros_device.argtypes = [vp, vp, vp, vp]
+        L.lbm_nusselt.argtypes = [vp, C.c_int, dp, dp, dp]
+        L.lbm_sums.argtypes = [vp, dp, dp]
+        L.lbm_residual.argtypes = [vp, dp, dp]
+        L.lbm_get_lattice.argtypes = [vp, C.POINTER(LbmLattice)]
+        L.lbm_steps_done.argtypes = [vp]
+        L.lbm_steps_done.restype = C.c_longlong
+        L.lbm_sync.argtypes = [vp]
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_last_error.restype = C.c_char_p
+        L.lbm_status_string.argtypes = [C.c_int]
+        L.lbm_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def params_from_problem(pb: dict) -> LbmParams:
+    """Marshal a problem dictionary (the keys of ``lbm_params``) into the C struct."""
+    p = LbmParams()
+    lib().lbm_params_default(C.byref(p))
+    p.nx, p.ny, p.nz = int(pb["nx"]), int(pb["ny"]), int(pb["nz"])
+    p.mapping = _MAPPINGS[pb.get("mapping", "cavity")]
+    scalars = ("L", "Ra", "Pr", "J", "sigma", "Gamma", "Ma", "Re", "Ri", "u0", "dT", "T0",
+               "rho0", "varpi", "s_e", "s_eps", "s_q", "s_pi", "s_m", "zeta_T", "zeta_e",
+               "zeta_nu", "nu_e", "alpha_f", "gbeta", "T_init", "U_out")
+    for k in scalars:
+        if k in pb and pb[k] is not None:
+            setattr(p, k, float(pb[k]))
+    if pb.get("Da") is not None:
+        p.Da = float(pb["Da"])
+    if "T_init" not in pb:
+        p.T_init = p.T0
+    p.gravity_axis = int(pb.get("gravity_axis", 2))
+    p.gravity_sign = int(pb.get("gravity_sign", -1))
+    for a, v in enumerate(pb.get("accel", (0.0, 0.0, 0.0))):
+        p.accel[a] = float(v)
+    for f in range(6):
+        p.flow_bc[f] = int(pb.get("flow_bc", [0] * 6)[f])
+        p.heat_bc[f] = int(pb.get("heat_bc", [0] * 6)[f])
+        p.face_T[f] = float(pb.get("face_T", [0.0] * 6)[f])
+        fu = pb.get("face_u", [(0.0, 0.0, 0.0)] * 6)[f]
+        for a in range(3):
+            p.face_u[f][a] = float(fu[a])
+    return p
+
+
+def derive_lattice(pb: dict) -> dict:
+    """Lattice parameters of a problem (host only, no GPU needed)."""
+    out = LbmLattice()
+    st = lib().lbm_derive_lattice(C.byref(params_from_problem(pb)), C.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_derive_lattice: invalid problem")
+    return out.as_dict()
+
+
+class Lattice:
+    """One lattice on the current CUDA device, driven through the C ABI.
+
+    ``pb`` is a problem dictionary; its medium keys (phi, K, F_phi, alpha_m, phi_field,
+    phi_ref) go to ``lbm_set_medium``.  ``stream`` is a cudaStream_t handle (int) or None.
+    """
+
+    def __init__(self, pb: dict, stream: Optional[int] = None):
+        self.pb = dict(pb)
+        self.nx, self.ny, self.nz = int(pb["nx"]), int(pb["ny"]), int(pb["nz"])
+        self.shape = (self.nz, self.ny, self.nx)
+        self.ns = self.nx * self.ny * self.nz
+        self._h = C.c_void_p()
+        self._params = params_from_problem(pb)
+        st = lib().lbm_create(C.byref(self._params), C.c_void_p(stream or 0), C.byref(self._h))
+        if st != LBM_OK:
+            raise LbmError(st, f"lbm_create failed: {lib().lbm_status_string(st).decode()}")
+        self.set_medium(pb.get("phi_field"), pb.get("phi", 1.0), pb.get("K", 0.0),
+                        pb.get("F_phi", 0.0), pb.get("alpha_m", -1.0), pb.get("phi_ref", 0.0))
+
+    # -- plumbing
+    def _check(self, st: int, what: str):
+        if st != LBM_OK:
+            msg = lib().lbm_last_error(self._h).decode()
+            raise LbmError(st, f"{what}: {lib().lbm_status_string(st).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().lbm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # -- calls
+    def set_medium(self, phi_field=None, phi=1.0, K=0.0, F_phi=0.0, alpha_m=-1.0, phi_ref=0.0):
+        fptr = None
+        if phi_field is not None:
+            self._phi = np.ascontiguousarray(np.asarray(phi_field, dtype=np.float32).reshape(-1))
+            assert self._phi.size == self.ns
+            fptr = _fp(self._phi)
+        K = float(K) if K is not None else 0.0
+        self._check(lib().lbm_set_medium(self._h, fptr, float(phi), K, float(F_phi),
+                                         float(alpha_m), float(phi_ref)), "lbm_set_medium")
+
+    def step(self, n: int = 1):
+        self._check(lib().lbm_step(self._h, int(n)), "lbm_step")
+
+    def sync(self):
+        self._check(lib().lbm_sync(self._h), "lbm_sync")
+
+    @property
+    def steps(self) -> int:
+        return int(lib().lbm_steps_done(self._h))
+
+    def init_equilibrium(self, T=0.5, T_field=None, u_field=None):
+        tp = up = None
+        if T_field is not None:
+            self._tf = np.ascontiguousarray(T_field, dtype=np.float64).reshape(-1)
+            tp = _dp(self._tf)
+        if u_field is not None:
+            self._uf = np.ascontiguousarray(u_field, dtype=np.float64).reshape(-1)
+            up = _dp(self._uf)
+        self._check(lib().lbm_init_equilibrium(self._h, tp, up, float(T)), "lbm_init_equilibrium")
+
+    def set_populations(self, f: np.ndarray, g: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.size == Q19 * self.ns and g.size == Q7 * self.ns
+        self._check(lib().lbm_set_populations(self._h, _dp(f), _dp(g)), "lbm_set_populations")
+
+    def populations(self):
+        f = np.zeros((Q19,) + self.shape)
+        g = np.zeros((Q7,) + self.shape)
+        self._check(lib().lbm_get_populations(self._h, _dp(f), _dp(g)), "lbm_get_populations")
+        return f, g
+
+    def macros(self):
+        """(rho, u[3], T) as float32 arrays shaped [z][y][x]."""
+        rho = np.zeros(self.shape, np.float32)
+        u = np.zeros((3,) + self.shape, np.float32)
+        T = np.zeros(self.shape, np.float32)
+        self._check(lib().lbm_macros(self._h, _fp(rho), _fp(u), _fp(T)), "lbm_macros")
+        return rho, u, T
+
+    def macros_into(self, rho, u, T):
+        """Host-buffer variant writing into caller-owned float32 arrays (any may be None)."""
+        args = [None if a is None else _fp(a) for a in (rho, u, T)]
+        self._check(lib().lbm_macros(self._h, *args), "lbm_macros")
+
+    def macros_device(self, rho_ptr: int, u_ptr: int, T_ptr: int):
+        """Device-pointer variant (e.g. torch tensors' data_ptr()); asynchronous."""
+        self._check(lib().lbm_macros_device(self._h, C.c_void_p(rho_ptr or 0),
+                                            C.c_void_p(u_ptr or 0), C.c_void_p(T_ptr or 0)),
+                    "lbm_macros_device")
+
+    def nusselt(self, face: int):
+        """(Nu_3D, profile, Nu_mp) on a Dirichlet face (Eqs. 53-55)."""
+        axis = face // 2
+        n1 = self.ny if axis == 0 else self.nx
+        prof = np.zeros(n1)
+        avg, mp = C.c_double(), C.c_double()
+        self._check(lib().lbm_nusselt(self._h, int(face), C.byref(avg), _dp(prof), C.byref(mp)),
+                    "lbm_nusselt")
+        return avg.value, prof, mp.value
+
+    def sums(self):
+        m, h = C.c_double(), C.c_double()
+        self._check(lib().lbm_sums(self._h, C.byref(m), C.byref(h)), "lbm_sums")
+        return m.value, h.value
+
+    def residual(self):
+        ru, rT = C.c_double(), C.c_double()
+        self._check(lib().lbm_residual(self._h, C.byref(ru), C.byref(rT)), "lbm_residual")
+        return ru.value, rT.value
+
+    def lattice(self) -> dict:
+        out = LbmLattice()
+        self._check(lib().lbm_get_lattice(self._h, C.byref(out)), "lbm_get_lattice")
+        return out.as_dict()
+
+
+def medium_args(pb: dict) -> dict:
+    """The medium part of a problem dictionary with defaults made explicit."""
+    return dict(phi=pb.get("phi", 1.0), K=pb.get("K", 0.0), F_phi=pb.get("F_phi", 0.0),
+                alpha_m=pb.get("alpha_m", -1.0), phi_ref=pb.get("phi_ref", 0.0),
+                has_field=pb.get("phi_field") is not None)
+
+
+def algorithmic_bytes_per_site(pb: dict) -> int:
+    """Bytes one time step must move per site: 26 FP32 populations read and written, plus
+    the FP32 porosity of a heterogeneous medium."""
+    return 26 * 4 * 2 + (4 if pb.get("phi_field") is not None else 0)
+
+
+def nan_safe(x: float) -> float:
+    return x if math.isfinite(x) else float("nan")

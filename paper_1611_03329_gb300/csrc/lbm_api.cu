@@ -1,0 +1,696 @@
+// Host side of the C ABI declared in include/lbm.h: parameter mapping (Sec. 2, Sec. 4),
+// validation, device memory of a context and the launch sequence of each call.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+using lbm::KParams;
+
+struct lbm_ctx {
+    lbm_params prm;
+    lbm_lattice lat;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    long long ns = 0, sq = 0, nyz = 0;
+    float* pop[2] = {nullptr, nullptr};   // ping-pong population copies, 26 planes each
+    float* hist[2] = {nullptr, nullptr};  // outflow history, 6 x ny*nz
+    int cur = 0;
+    bool outflow = false;
+    float* phi_dev = nullptr;
+    KParams kp{};
+    double* partials = nullptr;  // reduction scratch
+    double* profile = nullptr;   // Nusselt profile scratch
+    double* dres = nullptr;      // small device results
+    double* hres = nullptr;      // pinned host mirror of dres
+    double* stage = nullptr;     // FP64 staging, 4 x ns doubles (lazy)
+    float* mac = nullptr;        // macro scratch, 9 x ns floats (lazy): two halves of (u, T)
+                                 // and one rho plane; half `snap` holds the residual snapshot
+    int snap = 0;
+    bool have_prev = false;
+    long long steps = 0;
+    lbm_status sticky = LBM_OK;
+    char err[512] = {0};
+};
+
+namespace {
+
+constexpr double kCs2 = 1.0 / 3.0;  // c_s^2 with c = 1
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+        if (s == LBM_ECUDA || s == LBM_ENOMEM) c->sticky = s;
+    }
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+bool rate_ok(double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; }
+
+// Relaxation rates of Sec. 4 where the caller left a non-positive value.
+double or_default(double v, double d) { return v > 0.0 ? v : d; }
+
+// Eq. 56 / Eq. 51 / lattice units -> lbm_lattice (default medium).  Returns an error text or
+// nullptr.
+const char* derive(const lbm_params* p, lbm_lattice* L) {
+    std::memset(L, 0, sizeof(*L));
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
+    double ns = (double)p->nx * p->ny * p->nz;
+    if (ns >= 2147483647.0) return "lattice too large (sites must fit in 31 bits)";
+    if (p->storage != LBM_STORE_FP32) return "unsupported storage";
+    if (!finite_pos(p->rho0)) return "rho0 must be > 0";
+    if (!(p->varpi > 0.0 && p->varpi < 1.0)) return "varpi must lie in (0, 1)";
+    if (!finite_pos(p->sigma)) return "sigma must be > 0";
+    if (!finite_pos(p->J)) return "J must be > 0";
+    if (!finite_pos(p->Gamma)) return "Gamma must be > 0";
+    if (!std::isfinite(p->T0)) return "T0 must be finite";
+    double dT = p->dT > 0.0 ? p->dT : 1.0;
+    L->nx = p->nx;
+    L->ny = p->ny;
+    L->nz = p->nz;
+    L->rho0 = p->rho0;
+    L->T0 = p->T0;
+    L->sigma = p->sigma;
+    L->varpi = p->varpi;
+    L->dT = dT;
+    double s_e = or_default(p->s_e, 1.1), s_eps = or_default(p->s_eps, 1.1);
+    double s_q = or_default(p->s_q, 1.1), s_pi = or_default(p->s_pi, 1.1);
+    double s_m = or_default(p->s_m, 1.2);
+    L->zeta_T = or_default(p->zeta_T, 1.0);
+    L->zeta_e = or_default(p->zeta_e, 1.2);
+    L->zeta_nu = or_default(p->zeta_nu, 1.2);
+    double inv_s_nu, Lc;
+    if (p->mapping == LBM_MAP_CAVITY) {
+        Lc = p->L > 0.0 ? p->L : p->nx;
+        if (!finite_pos(p->Ra) || !finite_pos(p->Pr) || !finite_pos(p->Ma))
+            return "cavity mapping needs Ra, Pr, Ma > 0";
+        // Eq. 56: 1/s_nu = 1/2 + Ma J L sqrt(3 Pr) / (c dt sqrt(Ra))
+        inv_s_nu = 0.5 + p->Ma * p->J * Lc * std::sqrt(3.0 * p->Pr) / std::sqrt(p->Ra);
+        L->nu_e = kCs2 * (inv_s_nu - 0.5);  // Eq. 32
+        L->nu = L->nu_e / p->J;             // J = nu_e / nu (Eq. 7)
+        L->alpha_f = L->nu / p->Pr;         // Pr = nu / alpha (Eq. 7)
+        double uc = p->Ma * std::sqrt(kCs2);  // u_c = Ma c_s = sqrt(g beta dT L)
+        L->gbeta = uc * uc / (dT * Lc);
+    } else if (p->mapping == LBM_MAP_CHANNEL) {
+        Lc = p->L > 0.0 ? p->L : p->ny;
+        if (!finite_pos(p->Re) || !finite_pos(p->u0) || !finite_pos(p->Pr))
+            return "channel mapping needs Re, u0, Pr > 0";
+        if (!(p->Ri >= 0.0) || !std::isfinite(p->Ri)) return "Ri must be >= 0";
+        // Eq. 51 with 1/s_nu on the left: nu_e = c_s^2 (1/s_nu - 1/2) = J H u0 / Re
+        inv_s_nu = 0.5 + p->J * Lc * p->u0 / (kCs2 * p->Re);
+        L->nu_e = kCs2 * (inv_s_nu - 0.5);
+        L->nu = L->nu_e / p->J;
+        L->alpha_f = L->nu / p->Pr;
+        L->gbeta = p->Ri * p->u0 * p->u0 / (dT * Lc);  // Ri = g beta dT H / u0^2
+    } else if (p->mapping == LBM_MAP_LATTICE) {
+        Lc = p->L > 0.0 ? p->L : p->nx;
+        if (!finite_pos(p->nu_e)) return "lattice mapping needs nu_e > 0";
+        inv_s_nu = 0.5 + p->nu_e / kCs2;
+        L->nu_e = p->nu_e;
+        L->nu = L->nu_e / p->J;
+        if (p->alpha_f > 0.0) {
+            L->alpha_f = p->alpha_f;
+        } else {
+            if (!finite_pos(p->Pr)) return "Pr must be > 0";
+            L->alpha_f = L->nu / p->Pr;
+        }
+        if (!std::isfinite(p->gbeta)) return "gbeta must be finite";
+        L->gbeta = p->gbeta;
+    } else {
+        return "unknown mapping";
+    }
+    L->L = Lc;
+    L->s_nu = 1.0 / inv_s_nu;
+    double sv[19] = {1.0,   s_e,    s_eps, 1.0,    s_q,    1.0,    s_q,    1.0,    s_q,   L->s_nu,
+                     s_pi,  L->s_nu, s_pi, L->s_nu, L->s_nu, L->s_nu, s_m, s_m, s_m};
+    std::memcpy(L->s, sv, sizeof(sv));
+    for (int k = 0; k < 19; ++k)
+        if (!rate_ok(L->s[k])) return "a D3Q19 relaxation rate lies outside (0, 2)";
+    if (!rate_ok(L->zeta_T) || !rate_ok(L->zeta_e) || !rate_ok(L->zeta_nu))
+        return "a D3Q7 relaxation rate lies outside (0, 2)";
+    L->Gamma = p->Gamma;
+    L->alpha_m = -1.0;
+    double csT2 = p->varpi / 3.0;
+    L->zeta_alpha = 1.0 / (0.5 + p->Gamma * L->alpha_f / (p->sigma * csT2));  // Eq. 41
+    if (!rate_ok(L->zeta_alpha)) return "zeta_alpha lies outside (0, 2)";
+    if (p->gravity_axis < 0 || p->gravity_axis > 2) return "gravity_axis must be 0, 1 or 2";
+    if (p->gravity_sign != 1 && p->gravity_sign != -1) return "gravity_sign must be +-1";
+    for (int a = 0; a < 3; ++a) {
+        L->buoy[a] = 0.0;
+        if (!std::isfinite(p->accel[a])) return "accel must be finite";
+        L->accel[a] = p->accel[a];
+    }
+    // G = -g beta (T - T0) with g pointing along gravity_sign * axis (Eq. 5)
+    L->buoy[p->gravity_axis] = -(double)p->gravity_sign * L->gbeta;
+    L->phi = 1.0;
+    L->K = p->Da > 0.0 ? p->Da * Lc * Lc : HUGE_VAL;  // Da = K / L^2 (Eq. 7)
+    L->F_phi = 0.0;
+    L->phi_ref = 1.0;
+    L->has_phi_field = 0;
+    L->U_out = p->U_out > 0.0 ? p->U_out : p->u0;
+
+    // boundaries
+    int n[3] = {p->nx, p->ny, p->nz};
+    for (int f = 0; f < 6; ++f) {
+        int fk = p->flow_bc[f], hk = p->heat_bc[f];
+        if (fk < 0 || fk > 3 || hk < 0 || hk > 3) return "unknown boundary kind";
+        if ((fk == LBM_FLOW_PERIODIC) != (hk == LBM_HEAT_PERIODIC))
+            return "a face must be periodic for both flow and heat, or for neither";
+        int other = f ^ 1;
+        if ((fk == LBM_FLOW_PERIODIC) != (p->flow_bc[other] == LBM_FLOW_PERIODIC))
+            return "periodic faces come in pairs";
+        if (fk == LBM_FLOW_OUTFLOW && f != 1) return "outflow only on the x-high face";
+        if (hk == LBM_HEAT_OUTFLOW && fk != LBM_FLOW_OUTFLOW)
+            return "thermal outflow needs a flow outflow face";
+        if (hk == LBM_HEAT_DIRICHLET && !std::isfinite(p->face_T[f]))
+            return "face temperature must be finite";
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(p->face_u[f][a])) return "face velocity must be finite";
+    }
+    if (p->flow_bc[1] == LBM_FLOW_OUTFLOW) {
+        if (n[0] < 3) return "an outflow needs nx >= 3";
+        if (!finite_pos(L->U_out)) return "outflow speed must be > 0";
+    }
+    if (!std::isfinite(p->T_init)) return "T_init must be finite";
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_params_default(lbm_params* p) {
+    if (!p) return LBM_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = p->ny = p->nz = 1;
+    p->storage = LBM_STORE_FP32;
+    p->mapping = LBM_MAP_CAVITY;
+    p->Ra = 1e3;
+    p->Pr = 1.0;
+    p->J = 1.0;
+    p->sigma = 1.0;
+    p->Gamma = 1.0;
+    p->Ma = 0.1;
+    p->dT = 1.0;
+    p->T0 = 0.5;
+    p->rho0 = 1.0;
+    p->varpi = 0.5;
+    p->s_e = p->s_eps = p->s_q = p->s_pi = 1.1;
+    p->s_m = 1.2;
+    p->zeta_T = 1.0;
+    p->zeta_e = p->zeta_nu = 1.2;
+    p->gravity_axis = 2;
+    p->gravity_sign = -1;
+    p->T_init = 0.5;
+    return LBM_OK;
+}
+
+lbm_status lbm_derive_lattice(const lbm_params* p, lbm_lattice* out) {
+    if (!p || !out) return LBM_EINVAL;
+    lbm_lattice L;
+    if (derive(p, &L)) return LBM_EINVAL;
+    *out = L;
+    return LBM_OK;
+}
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument";
+        case LBM_ENOMEM: return "out of device memory";
+        case LBM_ECUDA: return "CUDA error";
+        case LBM_EUNSTABLE: return "non-finite state";
+        case LBM_ESTATE: return "call not allowed in the current state";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : "null context"; }
+
+long long lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+}  // extern "C"
+
+namespace {
+
+// Per-launch parameter block from the lattice and the current medium.
+void fill_kparams(lbm_ctx* c) {
+    const lbm_params& p = c->prm;
+    const lbm_lattice& L = c->lat;
+    KParams& k = c->kp;
+    k = KParams{};
+    k.nx = p.nx;
+    k.ny = p.ny;
+    k.nz = p.nz;
+    k.ns = c->ns;
+    k.sq = c->sq;
+    for (int f = 0; f < 6; ++f) {
+        unsigned bit = 1u << f;
+        if (p.flow_bc[f] == LBM_FLOW_PERIODIC) k.per_mask |= bit;
+        if (p.flow_bc[f] == LBM_FLOW_WALL) k.wall_mask |= bit;
+        if (p.flow_bc[f] == LBM_FLOW_VELOCITY) k.vel_mask |= bit;
+        k.heat_kind[f] = p.heat_bc[f];
+        // anti-bounce-back term 2 omega_i sigma (T_w - T0) in deviation form, omega_i = varpi/6
+        k.heat_abb[f] = (float)(2.0 * (L.varpi / 6.0) * L.sigma * (p.face_T[f] - L.T0));
+        for (int a = 0; a < 3; ++a) k.face_u[f][a] = (float)p.face_u[f][a];
+    }
+    double U = L.U_out > 0.0 ? L.U_out : 0.0;
+    k.out_a = (float)(1.0 / (1.0 + U));
+    k.out_b = (float)(U / (1.0 + U));
+    k.rho0 = (float)L.rho0;
+    k.inv_rho0 = (float)(1.0 / L.rho0);
+    k.sigma = (float)L.sigma;
+    k.inv_sigma = (float)(1.0 / L.sigma);
+    k.T0 = (float)L.T0;
+    k.varpi = (float)L.varpi;
+    k.s_e = (float)L.s[1];
+    k.s_eps = (float)L.s[2];
+    k.s_q = (float)L.s[4];
+    k.s_nu = (float)L.s[9];
+    k.s_pi = (float)L.s[10];
+    k.s_m = (float)L.s[16];
+    k.zeta_e = (float)L.zeta_e;
+    k.zeta_nu = (float)L.zeta_nu;
+    k.zeta_alpha = (float)L.zeta_alpha;
+    for (int a = 0; a < 3; ++a) {
+        k.buoy[a] = (float)L.buoy[a];
+        k.accel[a] = (float)L.accel[a];
+    }
+    // uniform medium (Eq. 4, Eq. 28; Ergun's Eq. 6 when F_phi < 0)
+    double phi = L.phi, K = L.K;
+    double Fp = L.F_phi < 0.0 ? 1.75 / std::sqrt(150.0 * phi * phi * phi) : L.F_phi;
+    double c_darcy = std::isinf(K) ? 0.0 : phi * L.nu / K;
+    double c_forch = std::isinf(K) ? 0.0 : phi * Fp / std::sqrt(K);
+    k.phi = (float)phi;
+    k.inv_phi = (float)(1.0 / phi);
+    k.c_darcy = (float)c_darcy;
+    k.c_forch = (float)c_forch;
+    k.l0 = (float)(0.5 * (1.0 + 0.5 * c_darcy));
+    k.l1 = (float)(0.5 * c_forch);
+    // heterogeneous medium
+    k.phi_field = L.has_phi_field ? c->phi_dev : nullptr;
+    double pr = L.phi_ref;
+    double kc_ref = pr * pr * pr / ((1.0 - pr) * (1.0 - pr));
+    k.kinf = std::isinf(K) ? 1 : 0;
+    k.cK = k.kinf ? 1.0f : (float)(K / kc_ref);
+    k.nu = (float)L.nu;
+    k.F_phi = (float)L.F_phi;
+    k.hetero_alpha = L.alpha_m >= 0.0 ? 1 : 0;
+    k.alpha_f = (float)L.alpha_f;
+    k.alpha_m = (float)(L.alpha_m >= 0.0 ? L.alpha_m : 0.0);
+    k.inv_sig_csT2 = (float)(1.0 / (L.sigma * L.varpi / 3.0));
+    if (!L.has_phi_field && L.alpha_m >= 0.0) {
+        double ae = phi * L.alpha_f + (1.0 - phi) * L.alpha_m;
+        k.zeta_alpha = (float)(1.0 / (0.5 + ae / (L.sigma * L.varpi / 3.0)));
+        k.hetero_alpha = 0;
+    }
+}
+
+lbm_status usable(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    if (c->sticky != LBM_OK) return c->sticky;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return LBM_OK;
+}
+
+float* cur_pop(lbm_ctx* c) { return c->pop[c->cur]; }
+float* cur_hist(lbm_ctx* c) { return c->hist[c->cur]; }
+
+lbm_status ensure_stage(lbm_ctx* c) {
+    if (!c->stage) LBM_CUDA(cudaMalloc(&c->stage, sizeof(double) * 4 * (size_t)c->ns));
+    return LBM_OK;
+}
+
+lbm_status ensure_mac(lbm_ctx* c) {
+    if (!c->mac) LBM_CUDA(cudaMalloc(&c->mac, sizeof(float) * 9 * (size_t)c->ns));
+    return LBM_OK;
+}
+
+lbm_status reset_hist(lbm_ctx* c) {
+    if (!c->outflow) return LBM_OK;
+    LBM_CUDA(lbm::launch_hist_reset(c->kp, cur_pop(c), cur_hist(c), c->stream));
+    return LBM_OK;
+}
+
+// Equilibrium state from device FP64 fields (or uniform values).
+lbm_status init_state(lbm_ctx* c, const double* T_dev, const double* u_dev, double T_uniform) {
+    LBM_CUDA(lbm::launch_init_eq(c->kp, cur_pop(c), T_dev, u_dev, T_uniform, c->stream));
+    lbm_status s = reset_hist(c);
+    if (s != LBM_OK) return s;
+    c->steps = 0;
+    c->have_prev = false;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
+    if (!p || !out) return LBM_EINVAL;
+    lbm_lattice L;
+    if (derive(p, &L)) return LBM_EINVAL;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ENOMEM;
+    c->prm = *p;
+    c->lat = L;
+    c->ns = (long long)p->nx * p->ny * p->nz;
+    c->sq = (c->ns + 63) / 64 * 64;  // 256-byte aligned population planes
+    c->nyz = (long long)p->ny * p->nz;
+    c->outflow = p->flow_bc[1] == LBM_FLOW_OUTFLOW;
+    lbm_status st = LBM_OK;
+    // the device of a caller's stream, else the calling thread's current device
+    cudaError_t e = stream ? cudaStreamGetDevice((cudaStream_t)stream, &c->device)
+                           : cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) {
+        st = cuda_fail(c, e, "selecting the device");
+    } else if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamCreate");
+        else c->own_stream = true;
+    }
+    size_t pop_bytes = sizeof(float) * (size_t)(lbm::kQ + lbm::kQT) * (size_t)c->sq;
+    for (int k = 0; k < 2 && st == LBM_OK; ++k) {
+        e = cudaMalloc(&c->pop[k], pop_bytes);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(populations)");
+        if (st == LBM_OK && c->outflow) {
+            e = cudaMalloc(&c->hist[k], sizeof(float) * lbm::kOutSlots * (size_t)c->nyz);
+            if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(outflow history)");
+        }
+    }
+    if (st == LBM_OK) {
+        int nr = lbm::reduction_blocks();
+        size_t prof = (size_t)(p->nx > p->ny ? p->nx : p->ny);
+        if ((e = cudaMalloc(&c->partials, sizeof(double) * 5 * nr)) != cudaSuccess ||
+            (e = cudaMalloc(&c->profile, sizeof(double) * prof)) != cudaSuccess ||
+            (e = cudaMalloc(&c->dres, sizeof(double) * 8)) != cudaSuccess ||
+            (e = cudaMallocHost(&c->hres, sizeof(double) * 8)) != cudaSuccess)
+            st = cuda_fail(c, e, "cudaMalloc(scratch)");
+    }
+    if (st == LBM_OK) {
+        fill_kparams(c);
+        st = init_state(c, nullptr, nullptr, p->T_init);
+    }
+    if (st == LBM_OK) {
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "initialisation");
+    }
+    if (st != LBM_OK) {
+        lbm_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->pop[k]);
+        cudaFree(c->hist[k]);
+    }
+    cudaFree(c->phi_dev);
+    cudaFree(c->partials);
+    cudaFree(c->profile);
+    cudaFree(c->dres);
+    cudaFreeHost(c->hres);
+    cudaFree(c->stage);
+    cudaFree(c->mac);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+lbm_status lbm_set_medium(lbm_ctx* c, const float* phi_field, double phi, double K,
+                          double F_phi, double alpha_m, double phi_ref) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    lbm_lattice L = c->lat;
+    double mean = phi;
+    if (phi_field) {
+        double sum = 0.0;
+        for (long long s = 0; s < c->ns; ++s) {
+            double v = phi_field[s];
+            if (!(v > 0.0 && v < 1.0)) return fail(c, LBM_EINVAL, "phi_field[%lld] = %g outside (0, 1)", s, v);
+            sum += v;
+        }
+        mean = sum / (double)c->ns;
+    } else if (!(phi > 0.0 && phi <= 1.0)) {
+        return fail(c, LBM_EINVAL, "phi = %g outside (0, 1]", phi);
+    }
+    if (K <= 0.0) K = c->prm.Da > 0.0 ? c->prm.Da * L.L * L.L : HUGE_VAL;
+    if (std::isnan(K)) return fail(c, LBM_EINVAL, "K is NaN");
+    if (!std::isfinite(F_phi) && !(F_phi < 0.0)) return fail(c, LBM_EINVAL, "F_phi must be finite");
+    if (phi_ref <= 0.0) phi_ref = mean;
+    if (phi_field && !(phi_ref > 0.0 && phi_ref < 1.0))
+        return fail(c, LBM_EINVAL, "phi_ref = %g outside (0, 1)", phi_ref);
+    L.phi = phi_field ? mean : phi;
+    L.K = K;
+    L.F_phi = F_phi < 0.0 ? -1.0 : F_phi;
+    L.alpha_m = alpha_m < 0.0 ? -1.0 : alpha_m;
+    L.phi_ref = phi_ref;
+    L.has_phi_field = phi_field ? 1 : 0;
+    double csT2 = L.varpi / 3.0;
+    double ae = alpha_m < 0.0 ? L.Gamma * L.alpha_f : L.phi * L.alpha_f + (1.0 - L.phi) * alpha_m;
+    L.zeta_alpha = 1.0 / (0.5 + ae / (L.sigma * csT2));  // Eq. 41
+    if (!rate_ok(L.zeta_alpha)) return fail(c, LBM_EINVAL, "zeta_alpha outside (0, 2)");
+    if (phi_field) {
+        if (!c->phi_dev) LBM_CUDA(cudaMalloc(&c->phi_dev, sizeof(float) * (size_t)c->ns));
+        LBM_CUDA(cudaMemcpyAsync(c->phi_dev, phi_field, sizeof(float) * (size_t)c->ns,
+                                 cudaMemcpyHostToDevice, c->stream));
+    }
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    c->lat = L;
+    fill_kparams(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int nsteps) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
+    for (int t = 0; t < nsteps; ++t) {
+        int nxt = c->cur ^ 1;
+        LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pop[c->cur], c->pop[nxt],
+                                  c->hist[c->cur], c->hist[nxt], c->stream));
+        c->cur = nxt;
+        c->steps++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* T_field, const double* u_field,
+                                double T_uniform) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if (!std::isfinite(T_uniform)) return fail(c, LBM_EINVAL, "T_uniform must be finite");
+    const double* Td = nullptr;
+    const double* ud = nullptr;
+    if (T_field || u_field) {
+        if ((st = ensure_stage(c)) != LBM_OK) return st;
+        if (T_field) {
+            LBM_CUDA(cudaMemcpyAsync(c->stage, T_field, sizeof(double) * c->ns,
+                                     cudaMemcpyHostToDevice, c->stream));
+            Td = c->stage;
+        }
+        if (u_field) {
+            LBM_CUDA(cudaMemcpyAsync(c->stage + c->ns, u_field, sizeof(double) * 3 * c->ns,
+                                     cudaMemcpyHostToDevice, c->stream));
+            ud = c->stage + c->ns;
+        }
+    }
+    if ((st = init_state(c, Td, ud, T_uniform)) != LBM_OK) return st;
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+static double plane_offset(const lbm_ctx* c, int q) {
+    // w_i rho0 for the D3Q19 planes (weights under Eq. 24), omega_i sigma T0 for D3Q7 (Eq. 42)
+    const lbm_lattice& L = c->lat;
+    if (q < lbm::kQ) {
+        double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+        return w * L.rho0;
+    }
+    int i = q - lbm::kQ;
+    double om = i == 0 ? 1.0 - L.varpi : L.varpi / 6.0;
+    return om * L.sigma * L.T0;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if (!f || !g) return fail(c, LBM_EINVAL, "f and g are required");
+    if ((st = ensure_stage(c)) != LBM_OK) return st;
+    float* pop = cur_pop(c);
+    for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
+        const double* src = q < lbm::kQ ? f + (size_t)q * c->ns : g + (size_t)(q - lbm::kQ) * c->ns;
+        double* stg = c->stage + (size_t)(q & 3) * c->ns;  // rotate 4 staging planes
+        LBM_CUDA(cudaMemcpyAsync(stg, src, sizeof(double) * c->ns, cudaMemcpyHostToDevice,
+                                 c->stream));
+        LBM_CUDA(lbm::launch_plane_to_dev(stg, pop + (size_t)q * c->sq, plane_offset(c, q), c->ns,
+                                          c->stream));
+    }
+    if ((st = reset_hist(c)) != LBM_OK) return st;
+    c->have_prev = false;
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if ((st = ensure_stage(c)) != LBM_OK) return st;
+    const float* pop = cur_pop(c);
+    for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
+        double* dst = q < lbm::kQ ? (f ? f + (size_t)q * c->ns : nullptr)
+                                  : (g ? g + (size_t)(q - lbm::kQ) * c->ns : nullptr);
+        if (!dst) continue;
+        double* stg = c->stage + (size_t)(q & 3) * c->ns;
+        LBM_CUDA(lbm::launch_plane_to_host(pop + (size_t)q * c->sq, stg, plane_offset(c, q), c->ns,
+                                           c->stream));
+        LBM_CUDA(cudaMemcpyAsync(dst, stg, sizeof(double) * c->ns, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    }
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_macros_device(lbm_ctx* c, float* rho, float* u, float* T) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, cur_pop(c), cur_hist(c), rho, u, T, c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* T) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if ((st = ensure_mac(c)) != LBM_OK) return st;
+    float* half = c->mac + (size_t)(c->snap ^ 1) * 4 * c->ns;  // the half not holding the snapshot
+    float* du = half;
+    float* dT = half + 3 * c->ns;
+    float* drho = c->mac + 8 * c->ns;
+    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, cur_pop(c), cur_hist(c), rho ? drho : nullptr,
+                                u ? du : nullptr, T ? dT : nullptr, c->stream));
+    if (rho)
+        LBM_CUDA(cudaMemcpyAsync(rho, drho, sizeof(float) * c->ns, cudaMemcpyDeviceToHost, c->stream));
+    if (u)
+        LBM_CUDA(cudaMemcpyAsync(u, du, sizeof(float) * 3 * c->ns, cudaMemcpyDeviceToHost, c->stream));
+    if (T)
+        LBM_CUDA(cudaMemcpyAsync(T, dT, sizeof(float) * c->ns, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile, double* nu_mp) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if (face < 0 || face > 5) return fail(c, LBM_EINVAL, "face must be 0..5");
+    if (c->prm.heat_bc[face] != LBM_HEAT_DIRICHLET)
+        return fail(c, LBM_EINVAL, "face %d is not a Dirichlet (fixed temperature) face", face);
+    int axis = face >> 1;
+    int n[3] = {c->prm.nx, c->prm.ny, c->prm.nz};
+    if (n[axis] < 2) return fail(c, LBM_EINVAL, "Nusselt needs >= 2 sites normal to the face");
+    int n1 = axis == 0 ? c->prm.ny : c->prm.nx;
+    double scale = c->lat.L / c->lat.dT;
+    LBM_CUDA(lbm::launch_nusselt(c->kp, c->outflow, cur_pop(c), cur_hist(c), face,
+                                 c->prm.face_T[face], scale, c->profile, c->dres, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                             c->stream));
+    if (nu_profile)
+        LBM_CUDA(cudaMemcpyAsync(nu_profile, c->profile, sizeof(double) * n1,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (!std::isfinite(c->hres[0])) return fail(c, LBM_EUNSTABLE, "Nusselt number is not finite");
+    if (nu_avg) *nu_avg = c->hres[0];
+    if (nu_mp) *nu_mp = c->hres[1];
+    return LBM_OK;
+}
+
+lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    int nr = lbm::reduction_blocks();
+    LBM_CUDA(lbm::launch_sums(c->kp, cur_pop(c), c->partials, nr, c->dres, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 2, cudaMemcpyDeviceToHost,
+                             c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (mass_dev) *mass_dev = c->hres[0];
+    if (heat_dev) *heat_dev = c->hres[1];
+    if (!std::isfinite(c->hres[0]) || !std::isfinite(c->hres[1]))
+        return fail(c, LBM_EUNSTABLE, "population totals are not finite");
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if ((st = ensure_mac(c)) != LBM_OK) return st;
+    float* cu = c->mac + (size_t)(c->snap ^ 1) * 4 * c->ns;  // new fields
+    float* cT = cu + 3 * c->ns;
+    const float* pu = c->mac + (size_t)c->snap * 4 * c->ns;  // snapshot of the previous call
+    const float* pT = pu + 3 * c->ns;
+    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, cur_pop(c), cur_hist(c), nullptr, cu, cT,
+                                c->stream));
+    bool first = !c->have_prev;
+    if (first) {
+        pu = cu;
+        pT = cT;
+    }
+    int nr = lbm::reduction_blocks();
+    LBM_CUDA(lbm::launch_residual(cu, cT, pu, pT, c->ns, c->partials, nr, c->dres, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 5, cudaMemcpyDeviceToHost,
+                             c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    const double* h = c->hres;
+    c->snap ^= 1;
+    c->have_prev = true;
+    if (h[4] > 0.0) return fail(c, LBM_EUNSTABLE, "velocity or temperature is not finite");
+    double ru = first ? HUGE_VAL : (h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : HUGE_VAL);
+    double rT = first ? HUGE_VAL : (h[3] > 0.0 ? std::sqrt(h[2] / h[3]) : HUGE_VAL);
+    if (r_u) *r_u = ru;
+    if (r_T) *r_T = rT;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_lattice(const lbm_ctx* c, lbm_lattice* out) {
+    if (!c || !out) return LBM_EINVAL;
+    *out = c->lat;
+    return LBM_OK;
+}
+
+}  // extern "C"

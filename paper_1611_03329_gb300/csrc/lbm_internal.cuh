@@ -1,0 +1,73 @@
+// Internal declarations shared by the two translation units of the CUDA library
+// (kernels and host API).  Not part of the public ABI (include/lbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int kQ = 19;   // D3Q19 flow populations (Eq. 19)
+constexpr int kQT = 7;   // D3Q7 temperature populations (Eq. 12, first seven columns)
+constexpr int kOutSlots = 6;  // populations entering across the x-high face: 5 f + 1 g
+constexpr int kBlock = 256;   // threads per block of the site kernels
+
+// Everything a site kernel needs, passed by value (__grid_constant__).
+struct KParams {
+    int nx, ny, nz;
+    long long ns;   // sites
+    long long sq;   // elements between consecutive population planes (>= ns, padded)
+
+    // boundaries (face bits: 1 << face, faces x-low, x-high, y-low, y-high, z-low, z-high)
+    unsigned per_mask;    // periodic faces (flow and heat)
+    unsigned wall_mask;   // no-slip walls
+    unsigned vel_mask;    // velocity faces
+    int heat_kind[6];     // LBM_HEAT_* per face
+    float heat_abb[6];    // 2 (varpi/6) sigma (T_w - T0): anti-bounce-back term, deviation form
+    float face_u[6][3];   // wall velocity of velocity faces
+    float out_a, out_b;   // convective outflow weights 1/(1+U), U/(1+U)
+
+    // fluid and lattice
+    float rho0, inv_rho0, sigma, inv_sigma, T0, varpi;
+    float s_e, s_eps, s_q, s_nu, s_pi, s_m;        // Lambda (Eq. 22), s_rho = s_j = 1
+    float zeta_e, zeta_nu, zeta_alpha;              // Q (Eq. 38), zeta_T = 1
+    float buoy[3], accel[3];                        // G = buoy (T - T0) + accel (Eq. 5)
+
+    // uniform medium, precomputed (Eqs. 4, 28)
+    float phi, inv_phi, l0, l1, c_darcy, c_forch;
+
+    // heterogeneous medium: phi per site, K(phi) = cK phi^3 / (1 - phi)^2 (Eq. 6)
+    const float* phi_field;  // device, or nullptr for the uniform medium
+    float cK, nu, F_phi;     // F_phi < 0: Ergun per site
+    int kinf;                // no Darcy / Forchheimer drag
+    int hetero_alpha;        // zeta_alpha per site from alpha_e(phi)
+    float alpha_f, alpha_m, inv_sig_csT2;
+};
+
+// Launch wrappers (defined in lbm_kernels.cu).  All are asynchronous on `st`.
+cudaError_t launch_step(const KParams& p, bool outflow, const float* pin, float* pout,
+                        const float* hin, float* hout, cudaStream_t st);
+cudaError_t launch_macros(const KParams& p, bool outflow, const float* pin, const float* hin,
+                          float* rho, float* u, float* T, cudaStream_t st);
+cudaError_t launch_init_eq(const KParams& p, float* pop, const double* T_field,
+                           const double* u_field, double T_uniform, cudaStream_t st);
+cudaError_t launch_plane_to_dev(const double* src, float* dst, double offset, long long n,
+                                cudaStream_t st);
+cudaError_t launch_plane_to_host(const float* src, double* dst, double offset, long long n,
+                                 cudaStream_t st);
+cudaError_t launch_hist_reset(const KParams& p, const float* pop, float* hist, cudaStream_t st);
+// FP64 totals of the stored deviations: out[0] = sum f', out[1] = sum g'.
+cudaError_t launch_sums(const KParams& p, const float* pop, double* partials, int nparts,
+                        double* out, cudaStream_t st);
+// Nusselt profile and its mean / centre value: out[0] = Nu_3D, out[1] = Nu_mp.
+cudaError_t launch_nusselt(const KParams& p, bool outflow, const float* pin, const float* hin,
+                           int face, double Tw, double scale, double* profile, double* out,
+                           cudaStream_t st);
+// Residual sums: out = (sum |du|^2, sum |u|^2, sum dT^2, sum T^2, nonfinite count).
+cudaError_t launch_residual(const float* u, const float* T, const float* up, const float* Tp,
+                            long long ns, double* partials, int nparts, double* out,
+                            cudaStream_t st);
+
+int reduction_blocks();  // number of partial sums the reductions write (<= partials size)
+
+}  // namespace lbm

@@ -1,0 +1,735 @@
+// Device kernels of the GB300 library for the 3D DDF-MRT porous-convection model
+// (Liu & He, arXiv:1611.03329).
+//
+// Storage: FP32 deviations f'_i = f_i - w_i rho0 and g'_i = g_i - omega_i sigma T0, planes of
+// sq floats per population, f planes 0..18 then g planes 19..25, x-fastest sites.  The
+// moment-space equilibria are affine in rho and in sigma T, so the collision runs on the
+// deviations directly (rho is replaced by rho' = rho - rho0, sigma T by sigma (T - T0)).
+//
+// One thread updates one site: pull 26 populations (Eqs. 10, 35 with the wall rules),
+// collide in moment space with the sparse integer M of Eq. A2 and N of Eq. 36 unrolled in
+// registers, push the back-transform through M^-1 = M^T diag(1/|M_k|^2) (the rows of Eq. A2
+// are orthogonal) and N^-1 of Eq. 43, and store 26 populations.
+#include <cuda_runtime.h>
+
+#include <utility>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+// ---- lattice constants -------------------------------------------------------------------
+// D3Q19 velocity components, Eq. 19.
+__host__ __device__ constexpr int ex19(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)    ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                                  : 0;
+}
+__host__ __device__ constexpr int ey19(int i) {
+    return (i == 3 || i == 7 || i == 8 || i == 15 || i == 17)    ? 1
+           : (i == 4 || i == 9 || i == 10 || i == 16 || i == 18) ? -1
+                                                                  : 0;
+}
+__host__ __device__ constexpr int ez19(int i) {
+    return (i == 5 || i == 11 || i == 12 || i == 15 || i == 16)  ? 1
+           : (i == 6 || i == 13 || i == 14 || i == 17 || i == 18) ? -1
+                                                                  : 0;
+}
+__host__ __device__ constexpr int opp19(int i) {
+    return i == 0 ? 0 : (i <= 6 ? ((i & 1) ? i + 1 : i - 1) : 7 + 4 * ((i - 7) / 4) + 3 - (i - 7) % 4);
+}
+// Weights stated under Eq. 24.
+__host__ __device__ constexpr float w19(int i) {
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+// Slot of the outflow history for the five D3Q19 velocities with e_x = -1.
+__host__ __device__ constexpr int slot19(int i) {
+    return i == 2 ? 0 : i == 8 ? 1 : i == 10 ? 2 : i == 12 ? 3 : i == 14 ? 4 : -1;
+}
+// D3Q7 velocity components (first seven columns of Eq. 12).
+__host__ __device__ constexpr int ex7(int i) { return i == 1 ? 1 : i == 2 ? -1 : 0; }
+__host__ __device__ constexpr int ey7(int i) { return i == 3 ? 1 : i == 4 ? -1 : 0; }
+__host__ __device__ constexpr int ez7(int i) { return i == 5 ? 1 : i == 6 ? -1 : 0; }
+__host__ __device__ constexpr int opp7(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+static_assert(opp19(7) == 10 && opp19(8) == 9 && opp19(12) == 13 && opp19(16) == 17, "opp19");
+static_assert(ex19(opp19(13)) == -ex19(13) && ez19(opp19(13)) == -ez19(13), "opp19 sign");
+
+// ---- site coordinates and medium -----------------------------------------------------------
+struct Site {
+    int x, y, z;
+    long long s;
+};
+
+__device__ __forceinline__ Site site_of(const KParams& p, long long s) {
+    Site c;
+    c.s = s;
+    long long yz = s / p.nx;
+    c.x = (int)(s - yz * p.nx);
+    c.z = (int)(yz / p.ny);
+    c.y = (int)(yz - (long long)c.z * p.ny);
+    return c;
+}
+
+struct Medium {
+    float phi, inv_phi, l0, l1, c_darcy, c_forch, zeta_alpha;
+};
+
+// Eq. 4 / Eq. 28 coefficients at a site; Eq. 6 (Kozeny-Carman K, Ergun F_phi) for a field.
+template <bool HET>
+__device__ __forceinline__ Medium medium_at(const KParams& p, long long s) {
+    Medium m;
+    if (!HET) {
+        m.phi = p.phi;
+        m.inv_phi = p.inv_phi;
+        m.l0 = p.l0;
+        m.l1 = p.l1;
+        m.c_darcy = p.c_darcy;
+        m.c_forch = p.c_forch;
+        m.zeta_alpha = p.zeta_alpha;
+    } else {
+        float ph = __ldg(p.phi_field + s);
+        float ph3 = ph * ph * ph;
+        float omp = 1.0f - ph;
+        float Fp = p.F_phi < 0.0f ? 1.75f * rsqrtf(150.0f * ph3) : p.F_phi;
+        float inv_sqrtK = p.kinf ? 0.0f : omp * rsqrtf(p.cK * ph3);  // 1/sqrt(K(phi))
+        m.phi = ph;
+        m.inv_phi = 1.0f / ph;
+        m.c_darcy = ph * p.nu * inv_sqrtK * inv_sqrtK;  // phi nu / K
+        m.c_forch = ph * Fp * inv_sqrtK;                // phi F_phi / sqrt(K)
+        m.l0 = 0.5f * (1.0f + 0.5f * m.c_darcy);
+        m.l1 = 0.5f * m.c_forch;
+        m.zeta_alpha = p.hetero_alpha
+                           ? 1.0f / (0.5f + (ph * p.alpha_f + omp * p.alpha_m) * p.inv_sig_csT2)
+                           : p.zeta_alpha;
+    }
+    return m;
+}
+
+// ---- streaming with boundary rules ------------------------------------------------------------
+// Pull of f_I at c: the post-collision population at c - e_I, or the wall rule when that source
+// lies outside the lattice (periodic faces wrap; a no-slip wall wins over a velocity face, which
+// wins over the outflow).  OUTF enables the convective outflow on the x-high face.
+template <int I, bool OUTF>
+__device__ __forceinline__ float pull_f(const float* __restrict__ fin, const KParams& p,
+                                        int x, int y, int z, long long s,
+                                        const float* __restrict__ hist, bool* via) {
+    constexpr int ex = ex19(I), ey = ey19(I), ez = ez19(I);
+    int sx = x - ex, sy = y - ey, sz = z - ez;
+    unsigned crossed = 0u;
+    if (ex == 1 && sx < 0) { if (p.per_mask & 1u) sx += p.nx; else crossed |= 1u; }
+    if (ex == -1 && sx >= p.nx) { if (p.per_mask & 2u) sx -= p.nx; else crossed |= 2u; }
+    if (ey == 1 && sy < 0) { if (p.per_mask & 4u) sy += p.ny; else crossed |= 4u; }
+    if (ey == -1 && sy >= p.ny) { if (p.per_mask & 8u) sy -= p.ny; else crossed |= 8u; }
+    if (ez == 1 && sz < 0) { if (p.per_mask & 16u) sz += p.nz; else crossed |= 16u; }
+    if (ez == -1 && sz >= p.nz) { if (p.per_mask & 32u) sz -= p.nz; else crossed |= 32u; }
+    if (crossed == 0u)
+        return __ldg(fin + (long long)I * p.sq + sx + (long long)p.nx * (sy + (long long)p.ny * sz));
+    float bb = __ldg(fin + (long long)opp19(I) * p.sq + s);
+    if (crossed & p.wall_mask) return bb;
+    unsigned vm = crossed & p.vel_mask;
+    if (vm) {
+        int face = __ffs(vm) - 1;
+        float eu = (float)ex * p.face_u[face][0] + (float)ey * p.face_u[face][1] +
+                   (float)ez * p.face_u[face][2];
+        return bb + 6.0f * w19(I) * p.rho0 * eu;  // 2 w_i rho0 (e_i . u_w) / c_s^2
+    }
+    if constexpr (OUTF && ex == -1) {
+        // convective outflow: p(N-1, t+1) = (p(N-1, t) + U p(N-2, t+1)) / (1 + U)
+        *via = true;
+        float inner = pull_f<I, false>(fin, p, x - 1, y, z, s - 1, nullptr, nullptr);
+        float old = __ldg(hist + (long long)slot19(I) * p.ny * p.nz + y + (long long)p.ny * z);
+        return p.out_a * old + p.out_b * inner;
+    }
+    return bb;  // not reached for validated boundary sets
+}
+
+template <int I, bool OUTF>
+__device__ __forceinline__ float pull_g(const float* __restrict__ gin, const KParams& p,
+                                        int x, int y, int z, long long s,
+                                        const float* __restrict__ hist) {
+    constexpr int ex = ex7(I), ey = ey7(I), ez = ez7(I);
+    int sx = x - ex, sy = y - ey, sz = z - ez;
+    int face = -1;
+    if (ex == 1 && sx < 0) { if (p.per_mask & 1u) sx += p.nx; else face = 0; }
+    if (ex == -1 && sx >= p.nx) { if (p.per_mask & 2u) sx -= p.nx; else face = 1; }
+    if (ey == 1 && sy < 0) { if (p.per_mask & 4u) sy += p.ny; else face = 2; }
+    if (ey == -1 && sy >= p.ny) { if (p.per_mask & 8u) sy -= p.ny; else face = 3; }
+    if (ez == 1 && sz < 0) { if (p.per_mask & 16u) sz += p.nz; else face = 4; }
+    if (ez == -1 && sz >= p.nz) { if (p.per_mask & 32u) sz -= p.nz; else face = 5; }
+    if (face < 0)
+        return __ldg(gin + (long long)I * p.sq + sx + (long long)p.nx * (sy + (long long)p.ny * sz));
+    float bb = __ldg(gin + (long long)opp7(I) * p.sq + s);
+    int kind = p.heat_kind[face];
+    if (kind == 2) return -bb + p.heat_abb[face];  // Dirichlet: anti-bounce-back
+    if constexpr (OUTF && ex == -1) {
+        if (kind == 3) {
+            float inner = __ldg(gin + (long long)I * p.sq + s);  // g_I(N-2, t+1) = g*_I(N-1, t)
+            float old = __ldg(hist + 5LL * p.ny * p.nz + y + (long long)p.ny * z);
+            return p.out_a * old + p.out_b * inner;
+        }
+    }
+    return bb;  // adiabatic: bounce-back
+}
+
+template <bool OUTF, int... I>
+__device__ __forceinline__ void gather_f_bc(float* f, bool* via, const float* fin, const KParams& p,
+                                            const Site& c, const float* hist,
+                                            std::integer_sequence<int, I...>) {
+    ((f[I] = pull_f<I, OUTF>(fin, p, c.x, c.y, c.z, c.s, hist, &via[I])), ...);
+}
+
+template <bool OUTF, int... I>
+__device__ __forceinline__ void gather_g_bc(float* g, const float* gin, const KParams& p,
+                                            const Site& c, const float* hist,
+                                            std::integer_sequence<int, I...>) {
+    ((g[I] = pull_g<I, OUTF>(gin, p, c.x, c.y, c.z, c.s, hist)), ...);
+}
+
+// Pre-collision populations of one site.  Interior sites take unconditional loads.
+template <bool OUTF>
+__device__ __forceinline__ void gather(const float* __restrict__ pin, const KParams& p,
+                                       const Site& c, const float* __restrict__ hist, float* f,
+                                       float* g) {
+    const float* fin = pin;
+    const float* gin = pin + (long long)kQ * p.sq;
+    bool interior = c.x > 0 && c.x < p.nx - 1 && c.y > 0 && c.y < p.ny - 1 && c.z > 0 &&
+                    c.z < p.nz - 1;
+    if (interior) {
+        const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i)
+            f[i] = __ldg(fin + (long long)i * p.sq + c.s - (ex19(i) + ey19(i) * nx + ez19(i) * nxy));
+#pragma unroll
+        for (int i = 0; i < kQT; ++i)
+            g[i] = __ldg(gin + (long long)i * p.sq + c.s - (ex7(i) + ey7(i) * nx + ez7(i) * nxy));
+        return;
+    }
+    bool via[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) via[i] = false;
+    gather_f_bc<OUTF>(f, via, fin, p, c, hist, std::make_integer_sequence<int, kQ>{});
+    gather_g_bc<OUTF>(g, gin, p, c, hist, std::make_integer_sequence<int, kQT>{});
+    if (OUTF && c.x == p.nx - 1) {
+        // pressure anchor: shift the populations set by the outflow rule by
+        // w_i (rho0 - rho) / sum(w_i) so that the outlet density is rho0
+        float rho = 0.0f, wsum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            rho += f[i];
+            if (via[i]) wsum += w19(i);
+        }
+        if (wsum > 0.0f) {
+            float corr = -rho / wsum;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i)
+                if (via[i]) f[i] += w19(i) * corr;
+        }
+    }
+}
+
+// ---- collision -------------------------------------------------------------------------------
+struct Macro {
+    float rho, ux, uy, uz, T;
+};
+
+// Eqs. 39, 5, 25, 27-28, 4, then (FULL) Eq. 9 with Eqs. 21-23 in moment space and Eq. 34 with
+// Eqs. 37-38, back-transformed in place.  f, g are deviations on entry and exit.
+template <bool FULL>
+__device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g) {
+    // temperature (Eq. 39) and body force (Eq. 5)
+    const float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
+    const float dT = n0 * p.inv_sigma;
+    const float T = p.T0 + dT;
+    const float Gx = p.buoy[0] * dT + p.accel[0];
+    const float Gy = p.buoy[1] * dT + p.accel[1];
+    const float Gz = p.buoy[2] * dT + p.accel[2];
+
+    // symmetric / antisymmetric sums over opposite pairs
+    const float s1 = f[1] + f[2], d1 = f[1] - f[2];
+    const float s2 = f[3] + f[4], d2 = f[3] - f[4];
+    const float s3 = f[5] + f[6], d3 = f[5] - f[6];
+    const float s4 = f[7] + f[10], d4 = f[7] - f[10];   // ( 1, 1, 0)
+    const float s5 = f[8] + f[9], d5 = f[8] - f[9];     // (-1, 1, 0)
+    const float s6 = f[11] + f[14], d6 = f[11] - f[14]; // ( 1, 0, 1)
+    const float s7 = f[12] + f[13], d7 = f[12] - f[13]; // (-1, 0, 1)
+    const float s8 = f[15] + f[18], d8 = f[15] - f[18]; // ( 0, 1, 1)
+    const float s9 = f[16] + f[17], d9 = f[16] - f[17]; // ( 0,-1, 1)
+    const float A = s1 + s2 + s3;
+    const float Dxy = s4 + s5, Dxz = s6 + s7, Dyz = s8 + s9;
+    const float D = Dxy + Dxz + Dyz;
+    const float rho = f[0] + A + D;  // rho - rho0 (Eq. 25)
+    const float jx = d1 + (d4 - d5) + (d6 - d7);
+    const float jy = d2 + (d4 + d5) + (d8 - d9);
+    const float jz = d3 + (d6 + d7) + (d8 + d9);
+
+    // velocity (Eqs. 27-28) and total force (Eq. 4)
+    const float vx = jx * p.inv_rho0 + 0.5f * md.phi * Gx;
+    const float vy = jy * p.inv_rho0 + 0.5f * md.phi * Gy;
+    const float vz = jz * p.inv_rho0 + 0.5f * md.phi * Gz;
+    const float vmag = sqrtf(vx * vx + vy * vy + vz * vz);
+    const float inv_den = 1.0f / (md.l0 + sqrtf(md.l0 * md.l0 + md.l1 * vmag));
+    const float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
+
+    Macro mac;
+    mac.rho = p.rho0 + rho;
+    mac.ux = ux;
+    mac.uy = uy;
+    mac.uz = uz;
+    mac.T = T;
+    if (!FULL) return mac;
+
+    const float umag = sqrtf(ux * ux + uy * uy + uz * uz);
+    const float drag = md.c_darcy + md.c_forch * umag;
+    const float Fx = md.phi * Gx - drag * ux;
+    const float Fy = md.phi * Gy - drag * uy;
+    const float Fz = md.phi * Gz - drag * uz;
+
+    // moments of Eq. 20 (rows of Eq. A2) that relax
+    const float m_e = -30.0f * f[0] - 11.0f * A + 8.0f * D;
+    const float m_eps = 12.0f * f[0] - 4.0f * A + D;
+    const float qx = jx - 5.0f * d1, qy = jy - 5.0f * d2, qz = jz - 5.0f * d3;
+    const float m_pxx = 2.0f * s1 - s2 - s3 + Dxy + Dxz - 2.0f * Dyz;
+    const float m_pixx = -4.0f * s1 + 2.0f * (s2 + s3) + Dxy + Dxz - 2.0f * Dyz;
+    const float m_pww = s2 - s3 + Dxy - Dxz;
+    const float m_piww = 2.0f * (s3 - s2) + Dxy - Dxz;
+    const float m_pxy = s4 - s5, m_pyz = s8 - s9, m_pzx = s6 - s7;
+    const float m_mx = (d4 - d5) - (d6 - d7);
+    const float m_my = (d8 - d9) - (d4 + d5);
+    const float m_mz = (d6 + d7) - (d8 + d9);
+
+    // equilibria (Eq. 21, beta1 = 3, beta2 = -11/2, beta3 = -1/2) and forcing (Eq. 23)
+    const float r0p = p.rho0 * md.inv_phi;
+    const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+    const float usq = uxx + uyy + uzz;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+    const float Fxx = ux * Fx, Fyy = uy * Fy, Fzz = uz * Fz;
+    const float eq_e = -11.0f * rho + 19.0f * r0p * usq;
+    const float eq_eps = 3.0f * rho - 5.5f * r0p * usq;
+    const float eq_pxx = r0p * (2.0f * uxx - uyy - uzz);
+    const float eq_pww = r0p * (uyy - uzz);
+    const float S_pxx = 2.0f * r0p * (2.0f * Fxx - Fyy - Fzz);
+    const float S_pww = 2.0f * r0p * (Fyy - Fzz);
+    const float c23 = 2.0f / 3.0f * p.rho0;
+
+    // dm_k = -s_k (m_k - m_k^eq) + (1 - s_k/2) S_k, scaled by 1/|M_k|^2; the conserved
+    // momentum gains rho0 F whatever s_j is (Eqs. 9, 14, 26)
+    const float he = 1.0f - 0.5f * p.s_e, heps = 1.0f - 0.5f * p.s_eps, hq = 1.0f - 0.5f * p.s_q;
+    const float hnu = 1.0f - 0.5f * p.s_nu, hpi = 1.0f - 0.5f * p.s_pi;
+    const float de = (-p.s_e * (m_e - eq_e) + he * 38.0f * r0p * uF) * (1.0f / 2394.0f);
+    const float deps = (-p.s_eps * (m_eps - eq_eps) - heps * 11.0f * r0p * uF) * (1.0f / 252.0f);
+    const float djx = p.rho0 * Fx * 0.1f, djy = p.rho0 * Fy * 0.1f, djz = p.rho0 * Fz * 0.1f;
+    const float dqx = (-p.s_q * (qx + c23 * ux) - hq * c23 * Fx) * (1.0f / 40.0f);
+    const float dqy = (-p.s_q * (qy + c23 * uy) - hq * c23 * Fy) * (1.0f / 40.0f);
+    const float dqz = (-p.s_q * (qz + c23 * uz) - hq * c23 * Fz) * (1.0f / 40.0f);
+    const float dpxx = (-p.s_nu * (m_pxx - eq_pxx) + hnu * S_pxx) * (1.0f / 36.0f);
+    const float dpixx = (-p.s_pi * (m_pixx + 0.5f * eq_pxx) - hpi * 0.5f * S_pxx) * (1.0f / 72.0f);
+    const float dpww = (-p.s_nu * (m_pww - eq_pww) + hnu * S_pww) * (1.0f / 12.0f);
+    const float dpiww = (-p.s_pi * (m_piww + 0.5f * eq_pww) - hpi * 0.5f * S_pww) * (1.0f / 24.0f);
+    const float dpxy = (-p.s_nu * (m_pxy - r0p * ux * uy) + hnu * r0p * (ux * Fy + uy * Fx)) * 0.25f;
+    const float dpyz = (-p.s_nu * (m_pyz - r0p * uy * uz) + hnu * r0p * (uy * Fz + uz * Fy)) * 0.25f;
+    const float dpzx = (-p.s_nu * (m_pzx - r0p * uz * ux) + hnu * r0p * (uz * Fx + ux * Fz)) * 0.25f;
+    const float dmx = -p.s_m * m_mx * 0.125f;
+    const float dmy = -p.s_m * m_my * 0.125f;
+    const float dmz = -p.s_m * m_mz * 0.125f;
+
+    // f* = f + M^T diag(1/|M_k|^2) dm
+    f[0] += -30.0f * de + 12.0f * deps;
+    const float Eax = -11.0f * de - 4.0f * deps;
+    const float Ex = Eax + 2.0f * dpxx - 4.0f * dpixx;
+    const float Ey = Eax - dpxx + 2.0f * dpixx + dpww - 2.0f * dpiww;
+    const float Ez = Eax - dpxx + 2.0f * dpixx - dpww + 2.0f * dpiww;
+    const float Ox = djx - 4.0f * dqx, Oy = djy - 4.0f * dqy, Oz = djz - 4.0f * dqz;
+    f[1] += Ex + Ox;
+    f[2] += Ex - Ox;
+    f[3] += Ey + Oy;
+    f[4] += Ey - Oy;
+    f[5] += Ez + Oz;
+    f[6] += Ez - Oz;
+    const float Cd = 8.0f * de + deps;
+    const float Exy = Cd + dpxx + dpixx + dpww + dpiww;
+    const float Exz = Cd + dpxx + dpixx - dpww - dpiww;
+    const float Eyz = Cd - 2.0f * (dpxx + dpixx);
+    const float Jx = djx + dqx, Jy = djy + dqy, Jz = djz + dqz;
+    const float O7 = Jx + Jy + dmx - dmy;
+    const float O8 = -Jx + Jy - dmx - dmy;
+    const float O11 = Jx + Jz - dmx + dmz;
+    const float O12 = -Jx + Jz + dmx + dmz;
+    const float O15 = Jy + Jz + dmy - dmz;
+    const float O16 = -Jy + Jz - dmy - dmz;
+    f[7] += Exy + dpxy + O7;
+    f[10] += Exy + dpxy - O7;
+    f[8] += Exy - dpxy + O8;
+    f[9] += Exy - dpxy - O8;
+    f[11] += Exz + dpzx + O11;
+    f[14] += Exz + dpzx - O11;
+    f[12] += Exz - dpzx + O12;
+    f[13] += Exz - dpzx - O12;
+    f[15] += Eyz + dpyz + O15;
+    f[18] += Eyz + dpyz - O15;
+    f[16] += Eyz - dpyz + O16;
+    f[17] += Eyz - dpyz - O16;
+
+    // D3Q7: n = N g (Eq. 36), n_eq = T (sigma, u, varpi sigma, 0, 0) (Eq. 37), Eq. 34, Eq. 43
+    const float nxm = g[1] - g[2], nym = g[3] - g[4], nzm = g[5] - g[6];
+    const float n4 = ((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]);  // minus varpi sigma T0
+    const float n5 = (g[1] + g[2]) - (g[3] + g[4]);
+    const float n6 = (g[1] + g[2]) - (g[5] + g[6]);
+    const float dn1 = -md.zeta_alpha * (nxm - T * ux);
+    const float dn2 = -md.zeta_alpha * (nym - T * uy);
+    const float dn3 = -md.zeta_alpha * (nzm - T * uz);
+    const float dn4 = -p.zeta_e * (n4 - p.varpi * n0);
+    const float dn5 = -p.zeta_nu * n5;
+    const float dn6 = -p.zeta_nu * n6;
+    const float c4 = dn4 * (1.0f / 6.0f);
+    const float c5 = dn5 * (1.0f / 6.0f), c6 = dn6 * (1.0f / 6.0f);
+    g[0] -= dn4;
+    const float gx = c4 + c5 + c6, gy = c4 - 2.0f * c5 + c6, gz = c4 + c5 - 2.0f * c6;
+    g[1] += gx + 0.5f * dn1;
+    g[2] += gx - 0.5f * dn1;
+    g[3] += gy + 0.5f * dn2;
+    g[4] += gy - 0.5f * dn2;
+    g[5] += gz + 0.5f * dn3;
+    g[6] += gz - 0.5f * dn3;
+    return mac;
+}
+
+// ---- kernels ---------------------------------------------------------------------------------
+template <bool HET, bool OUTF>
+__global__ void __launch_bounds__(kBlock, 2)
+    step_kernel(const __grid_constant__ KParams p, const float* __restrict__ pin,
+                float* __restrict__ pout, const float* __restrict__ hin,
+                float* __restrict__ hout) {
+    long long s = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (s >= p.ns) return;
+    const Site c = site_of(p, s);
+    float f[kQ], g[kQT];
+    gather<OUTF>(pin, p, c, hin, f, g);
+    if (OUTF && c.x == p.nx - 1) {
+        const long long nyz = (long long)p.ny * p.nz, yz = c.y + (long long)p.ny * c.z;
+        hout[0 * nyz + yz] = f[2];
+        hout[1 * nyz + yz] = f[8];
+        hout[2 * nyz + yz] = f[10];
+        hout[3 * nyz + yz] = f[12];
+        hout[4 * nyz + yz] = f[14];
+        hout[5 * nyz + yz] = g[2];
+    }
+    const Medium md = medium_at<HET>(p, s);
+    collide<true>(p, md, f, g);
+    float* fo = pout;
+    float* go = pout + (long long)kQ * p.sq;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) fo[(long long)i * p.sq + s] = f[i];
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) go[(long long)i * p.sq + s] = g[i];
+}
+
+template <bool HET, bool OUTF>
+__global__ void __launch_bounds__(kBlock)
+    macros_kernel(const __grid_constant__ KParams p, const float* __restrict__ pin,
+                  const float* __restrict__ hin, float* __restrict__ rho, float* __restrict__ u,
+                  float* __restrict__ T) {
+    long long s = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (s >= p.ns) return;
+    const Site c = site_of(p, s);
+    float f[kQ], g[kQT];
+    gather<OUTF>(pin, p, c, hin, f, g);
+    const Medium md = medium_at<HET>(p, s);
+    Macro m = collide<false>(p, md, f, g);
+    if (rho) rho[s] = m.rho;
+    if (u) {
+        u[s] = m.ux;
+        u[p.ns + s] = m.uy;
+        u[2 * p.ns + s] = m.uz;
+    }
+    if (T) T[s] = m.T;
+}
+
+// Equilibrium state (Eqs. 24 and 42) with rho = rho0, in FP64, stored as FP32 deviations.
+__global__ void init_eq_kernel(const __grid_constant__ KParams p, float* __restrict__ pop,
+                               const double* __restrict__ T_field,
+                               const double* __restrict__ u_field, double T_uniform) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.ns) return;
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    if (u_field) {
+        ux = u_field[s];
+        uy = u_field[p.ns + s];
+        uz = u_field[2 * p.ns + s];
+    }
+    double T = T_field ? T_field[s] : T_uniform;
+    double phi = p.phi_field ? (double)p.phi_field[s] : (double)p.phi;
+    double rho0 = p.rho0, usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        double eu = ex19(i) * ux + ey19(i) * uy + ez19(i) * uz;
+        double w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+        double dev = w * rho0 * (3.0 * eu + 4.5 * eu * eu / phi - 1.5 * usq / phi);
+        pop[(long long)i * p.sq + s] = (float)dev;
+    }
+    double varpi = p.varpi, sigma = p.sigma, T0 = p.T0, csT2 = varpi / 3.0;
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) {
+        double om = i == 0 ? 1.0 - varpi : varpi / 6.0;
+        double eu = ex7(i) * ux + ey7(i) * uy + ez7(i) * uz;
+        double dev = om * (sigma * (T - T0) + T * eu / csT2);
+        pop[(long long)(kQ + i) * p.sq + s] = (float)dev;
+    }
+}
+
+__global__ void plane_to_dev_kernel(const double* __restrict__ src, float* __restrict__ dst,
+                                    double offset, long long n) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        dst[k] = (float)(src[k] - offset);
+}
+
+__global__ void plane_to_host_kernel(const float* __restrict__ src, double* __restrict__ dst,
+                                     double offset, long long n) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        dst[k] = (double)src[k] + offset;
+}
+
+__global__ void hist_reset_kernel(const __grid_constant__ KParams p, const float* __restrict__ pop,
+                                  float* __restrict__ hist) {
+    long long nyz = (long long)p.ny * p.nz;
+    long long yz = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (yz >= nyz) return;
+    long long s = (long long)(p.nx - 1) + (long long)p.nx * yz;
+    hist[0 * nyz + yz] = pop[2LL * p.sq + s];
+    hist[1 * nyz + yz] = pop[8LL * p.sq + s];
+    hist[2 * nyz + yz] = pop[10LL * p.sq + s];
+    hist[3 * nyz + yz] = pop[12LL * p.sq + s];
+    hist[4 * nyz + yz] = pop[14LL * p.sq + s];
+    hist[5 * nyz + yz] = pop[(long long)(kQ + 2) * p.sq + s];
+}
+
+// ---- FP64 reductions ---------------------------------------------------------------------------
+constexpr int kRedBlocks = 608;  // 4 per SM of a 152-SM GB300
+constexpr int kRedThreads = 256;
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out) {
+    __shared__ double sh[NV][kRedThreads / 32];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = threadIdx.x < kRedThreads / 32 ? sh[k][threadIdx.x] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (threadIdx.x == 0) out[k] = x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    sums_kernel(const __grid_constant__ KParams p, const float* __restrict__ pop,
+                double* __restrict__ partials) {
+    double v[2] = {0.0, 0.0};
+    for (long long s = (long long)blockIdx.x * kRedThreads + threadIdx.x; s < p.ns;
+         s += (long long)gridDim.x * kRedThreads) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) v[0] += (double)pop[(long long)i * p.sq + s];
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) v[1] += (double)pop[(long long)(kQ + i) * p.sq + s];
+    }
+    block_reduce_store<2>(v, partials + 2 * blockIdx.x);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads)
+    finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += kRedThreads)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += partials[NV * b + k];
+    block_reduce_store<NV>(v, out);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    residual_kernel(const float* __restrict__ u, const float* __restrict__ T,
+                    const float* __restrict__ up, const float* __restrict__ Tp, long long ns,
+                    double* __restrict__ partials) {
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long s = (long long)blockIdx.x * kRedThreads + threadIdx.x; s < ns;
+         s += (long long)gridDim.x * kRedThreads) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double x = u[a * ns + s], d = x - (double)up[a * ns + s];
+            v[0] += d * d;
+            v[1] += x * x;
+            if (!isfinite(x)) v[4] += 1.0;
+        }
+        double t = T[s], dt = t - (double)Tp[s];
+        v[2] += dt * dt;
+        v[3] += t * t;
+        if (!isfinite(t)) v[4] += 1.0;
+    }
+    block_reduce_store<5>(v, partials + 5 * blockIdx.x);
+}
+
+// Temperature at a site from the streamed D3Q7 populations (Eq. 39).
+template <bool OUTF>
+__device__ __forceinline__ double temperature_at(const float* pin, const KParams& p, int x, int y,
+                                                 int z, const float* hist) {
+    Site c;
+    c.x = x;
+    c.y = y;
+    c.z = z;
+    c.s = x + (long long)p.nx * (y + (long long)p.ny * z);
+    float g[kQT];
+    gather_g_bc<OUTF>(g, pin + (long long)kQ * p.sq, p, c, hist,
+                      std::make_integer_sequence<int, kQT>{});
+    float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+    return (double)p.T0 + (double)n0 * (double)p.inv_sigma;
+}
+
+// One block per entry of the Nusselt profile (first tangential axis); threads average the
+// local Nusselt number of Eq. 53 over the second tangential axis (Eq. 54).
+template <bool OUTF>
+__global__ void __launch_bounds__(kRedThreads)
+    nusselt_kernel(const __grid_constant__ KParams p, const float* __restrict__ pin,
+                   const float* __restrict__ hist, int face, double Tw, double scale,
+                   double* __restrict__ profile) {
+    const int axis = face >> 1, hi = face & 1;
+    const int n[3] = {p.nx, p.ny, p.nz};
+    const int t1 = axis == 0 ? 1 : 0;            // profile axis
+    const int t2 = axis == 2 ? 1 : 2;            // averaged axis
+    const int j = blockIdx.x;
+    double v[1] = {0.0};
+    for (int k = threadIdx.x; k < n[t2]; k += kRedThreads) {
+        int c0[3], c1[3];
+        c0[t1] = c1[t1] = j;
+        c0[t2] = c1[t2] = k;
+        c0[axis] = hi ? n[axis] - 1 : 0;
+        c1[axis] = hi ? n[axis] - 2 : 1;
+        double T0 = temperature_at<OUTF>(pin, p, c0[0], c0[1], c0[2], hist);
+        double T1 = temperature_at<OUTF>(pin, p, c1[0], c1[1], c1[2], hist);
+        v[0] += (8.0 * Tw - 9.0 * T0 + T1) / 3.0 * scale;
+    }
+    double out[1];
+    __shared__ double res;
+    block_reduce_store<1>(v, out);
+    if (threadIdx.x == 0) res = out[0];
+    __syncthreads();
+    if (threadIdx.x == 0) profile[j] = res / n[t2];
+}
+
+// Nu_3D = mean of the profile (Eq. 55); Nu_mp = centre value (mean of the two middle entries
+// for an even length).
+__global__ void nusselt_finalize_kernel(const double* __restrict__ profile, int n,
+                                        double* __restrict__ out) {
+    double v[1] = {0.0};
+    for (int j = threadIdx.x; j < n; j += kRedThreads) v[0] += profile[j];
+    double r[1];
+    block_reduce_store<1>(v, r);
+    if (threadIdx.x == 0) {
+        out[0] = r[0] / n;
+        out[1] = (n % 2 == 0) ? 0.5 * (profile[n / 2 - 1] + profile[n / 2]) : profile[n / 2];
+    }
+}
+
+inline unsigned blocks_for(long long n, int threads) {
+    return (unsigned)((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+// ---- launch wrappers ---------------------------------------------------------------------------
+int reduction_blocks() { return kRedBlocks; }
+
+cudaError_t launch_step(const KParams& p, bool outflow, const float* pin, float* pout,
+                        const float* hin, float* hout, cudaStream_t st) {
+    unsigned nb = blocks_for(p.ns, kBlock);
+    bool het = p.phi_field != nullptr;
+    if (het && outflow)
+        step_kernel<true, true><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+    else if (het)
+        step_kernel<true, false><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+    else if (outflow)
+        step_kernel<false, true><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+    else
+        step_kernel<false, false><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macros(const KParams& p, bool outflow, const float* pin, const float* hin,
+                          float* rho, float* u, float* T, cudaStream_t st) {
+    unsigned nb = blocks_for(p.ns, kBlock);
+    bool het = p.phi_field != nullptr;
+    if (het && outflow)
+        macros_kernel<true, true><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+    else if (het)
+        macros_kernel<true, false><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+    else if (outflow)
+        macros_kernel<false, true><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+    else
+        macros_kernel<false, false><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_eq(const KParams& p, float* pop, const double* T_field,
+                           const double* u_field, double T_uniform, cudaStream_t st) {
+    init_eq_kernel<<<blocks_for(p.ns, 128), 128, 0, st>>>(p, pop, T_field, u_field, T_uniform);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_to_dev(const double* src, float* dst, double offset, long long n,
+                                cudaStream_t st) {
+    plane_to_dev_kernel<<<1216, 256, 0, st>>>(src, dst, offset, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_to_host(const float* src, double* dst, double offset, long long n,
+                                 cudaStream_t st) {
+    plane_to_host_kernel<<<1216, 256, 0, st>>>(src, dst, offset, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_reset(const KParams& p, const float* pop, float* hist, cudaStream_t st) {
+    long long nyz = (long long)p.ny * p.nz;
+    hist_reset_kernel<<<blocks_for(nyz, 128), 128, 0, st>>>(p, pop, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sums(const KParams& p, const float* pop, double* partials, int nparts,
+                        double* out, cudaStream_t st) {
+    sums_kernel<<<nparts, kRedThreads, 0, st>>>(p, pop, partials);
+    finalize_kernel<2><<<1, kRedThreads, 0, st>>>(partials, nparts, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nusselt(const KParams& p, bool outflow, const float* pin, const float* hin,
+                           int face, double Tw, double scale, double* profile, double* out,
+                           cudaStream_t st) {
+    const int axis = face >> 1;
+    const int n1 = axis == 0 ? p.ny : p.nx;
+    if (outflow)
+        nusselt_kernel<true><<<n1, kRedThreads, 0, st>>>(p, pin, hin, face, Tw, scale, profile);
+    else
+        nusselt_kernel<false><<<n1, kRedThreads, 0, st>>>(p, pin, hin, face, Tw, scale, profile);
+    nusselt_finalize_kernel<<<1, kRedThreads, 0, st>>>(profile, n1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const float* u, const float* T, const float* up, const float* Tp,
+                            long long ns, double* partials, int nparts, double* out,
+                            cudaStream_t st) {
+    residual_kernel<<<nparts, kRedThreads, 0, st>>>(u, T, up, Tp, ns, partials);
+    finalize_kernel<5><<<1, kRedThreads, 0, st>>>(partials, nparts, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

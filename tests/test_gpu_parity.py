@@ -1,0 +1,261 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances follow from FP32 storage and arithmetic of the population deviations:
+ - one step from the same state: every population within 1e-5 of the largest population
+   deviation |f - w rho0| (|g - omega sigma T0| for g), element by element;
+ - many steps: the field-normalised error max|a - a_ref| / max|a_ref| of u and T within
+   1e-5 (the FP32 target), Nusselt numbers within 1e-5 relative.
+"""
+import math
+import zlib
+
+import numpy as np
+import pytest
+
+from lbm_inputs import (cavity_problem, channel_problem, porosity_field, random_macros,
+                        uniform)
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-5
+TOL_FIELD = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import paper_1611_03329_gb300 as gb
+
+    gb.build.build()
+    gb.lib()
+    return gb
+
+
+def _w(orc, lp):
+    t = orc.tables()
+    wf = t["w19"] * lp.rho0
+    om = np.array([1 - lp.varpi] + [lp.varpi / 6] * 6) * lp.sigma * lp.T0
+    return wf.reshape(19, 1, 1, 1), om.reshape(7, 1, 1, 1)
+
+
+def _random_state(orc, pb, seed, u_amp=0.03, noise=3e-4):
+    """Near-equilibrium populations: the oracle's equilibrium of seeded random (rho, u, T)
+    fields plus seeded uniform noise."""
+    lp = orc.map_problem(pb)
+    o = orc.Oracle(lp)
+    rho, u, T = random_macros(lp.nx, lp.ny, lp.nz, seed, u_amp=u_amp)
+    o.init_equilibrium(0.5, T, u)
+    f, g = o.populations()
+    f = f + noise * uniform(f.shape, seed + 1)
+    g = g + noise * uniform(g.shape, seed + 2)
+    return lp, o, f, g
+
+
+def _pop_error(orc, lp, fa, ga, fb, gb_):
+    wf, om = _w(orc, lp)
+    ef = np.abs(fa - fb).max() / np.abs(fb - wf).max()
+    eg = np.abs(ga - gb_).max() / np.abs(gb_ - om).max()
+    return ef, eg
+
+
+def _single_step(gb, orc, pb, seed, steps=1):
+    lp, o, f, g = _random_state(orc, pb, seed)
+    lat = gb.Lattice(pb)
+    lat.set_populations(f, g)
+    o.set_populations(f, g)
+    # macroscopic fields of the state itself (lbm_macros)
+    r_g, u_g, T_g = lat.macros()
+    r_o, u_o, T_o = o.macros()
+    mac_err = (orc.field_error(u_g, u_o), orc.field_error(T_g, T_o),
+               np.abs(r_g - r_o).max())
+    lat.step(steps)
+    o.step(steps)
+    fa, ga = lat.populations()
+    fb, gb_ = o.populations()
+    return _pop_error(orc, lp, fa, ga, fb, gb_), mac_err, lat, o
+
+
+def _hetero_cavity(n=12):
+    phi = porosity_field(n, n - 2, n - 4, seed=11).astype(np.float32).astype(np.float64)
+    pb = cavity_problem(n, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71, phi_field=phi, alpha_m=0.02)
+    pb.update(ny=n - 2, nz=n - 4)
+    return pb
+
+
+CASES = {
+    "cavity_ragged": dict(cavity_problem(13, Ra=1e4, Da=1e-2, phi=0.6, Pr=0.71), ny=11, nz=9),
+    "cavity_bd_model": dict(cavity_problem(10, Ra=5e3, Da=1e-1, phi=0.8, Pr=0.71, F_phi=0.0)),
+    "channel_ragged": channel_problem(19, 10, 7, Da=1e-2),
+    "channel_T_out": dict(channel_problem(21, 8, 5, Da=1e-2), heat_bc=[2, 3, 2, 2, 0, 0]),
+    "channel_adiabatic_out": dict(channel_problem(21, 8, 5, Da=1e-2), heat_bc=[2, 1, 2, 2, 0, 0]),
+    "periodic_forced": dict(nx=37, ny=5, nz=3, mapping="lattice", nu_e=0.05, alpha_f=0.03,
+                            gbeta=2e-3, phi=0.5, K=2.0, F_phi=0.4, accel=[2e-4, -1e-4, 5e-5]),
+    "moving_lid": dict(cavity_problem(9, Ra=1e4, Da=None, phi=1.0, Pr=0.71), nz=7,
+                       flow_bc=[1, 1, 1, 1, 1, 2],
+                       face_u=[(0, 0, 0)] * 5 + [(0.02, -0.01, 0.0)]),
+    "hetero_phi": _hetero_cavity(),
+    "sigma_gamma": dict(cavity_problem(8, Ra=2e4, Da=1e-2, phi=0.7, Pr=0.71, J=1.4,
+                                       sigma=1.6, Gamma=1.3), ny=6),
+    "tiny_3": cavity_problem(3, Ra=1e4, Da=1e-2, phi=0.6),
+    "line_1xNx1": dict(nx=1, ny=17, nz=1, mapping="lattice", nu_e=0.1, phi=0.6, K=5.0,
+                       F_phi=0.3, accel=[1e-4, 0, 0], flow_bc=[0, 0, 1, 1, 0, 0],
+                       heat_bc=[0, 0, 2, 2, 0, 0], face_T=[0, 0, 1, 0, 0, 0]),
+    "vertical_gravity_y": dict(cavity_problem(11, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71),
+                               gravity_axis=1, gravity_sign=1, ny=9, nz=10),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_single_step_populations(gb, orc, name):
+    (ef, eg), (eu, eT, er), _, _ = _single_step(gb, orc, CASES[name], seed=zlib.crc32(name.encode()) % 1000)
+    assert ef < TOL_STEP and eg < TOL_STEP, (ef, eg)
+    assert eu < TOL_FIELD and eT < TOL_FIELD and er < 1e-6, (eu, eT, er)
+
+
+@pytest.mark.parametrize("name", ["cavity_ragged", "channel_ragged", "hetero_phi",
+                                  "periodic_forced", "moving_lid"])
+def test_twenty_steps_populations(gb, orc, name):
+    (ef, eg), _, _, _ = _single_step(gb, orc, CASES[name], seed=7, steps=20)
+    assert ef < 4 * TOL_STEP and eg < 4 * TOL_STEP, (ef, eg)
+
+
+def test_cavity_32_5000_steps(gb, orc):
+    """The 32^3 porous cavity (phi = 0.6, Da = 1e-2, Ra = 1e3, Pr = 1, Ergun F_phi) run for
+    the full 5000 steps from u = 0, T = 0.5: u and T within 1e-5 of the FP64 oracle."""
+    pb = cavity_problem(32, Ra=1e3, Da=1e-2, phi=0.6, Pr=1.0)
+    lat = gb.Lattice(pb)
+    lat.step(5000)
+    o = orc.Oracle(orc.map_problem(pb))
+    o.step(5000)
+    _, u_g, T_g = lat.macros()
+    _, u_o, T_o = o.macros()
+    assert orc.field_error(u_g, u_o) < TOL_FIELD
+    assert orc.field_error(T_g, T_o) < TOL_FIELD
+    nu_g, prof_g, mp_g = lat.nusselt(0)
+    nu_o, prof_o, mp_o = orc.nusselt(T_o, 0, 1.0, 32)
+    assert nu_g == pytest.approx(nu_o, rel=1e-5)
+    assert mp_g == pytest.approx(mp_o, rel=1e-5)
+    assert np.allclose(prof_g, prof_o, rtol=1e-5)
+    assert 1.0 < nu_o < 1.2  # Darcy Ra* = 10 lies below Table 3's Ra* = 50 values
+
+
+def test_channel_64x16x16(gb, orc):
+    """Reduced porous channel (velocity inlet, anchored convective outflow, heated walls)
+    for 2000 steps: u and T within 1e-5 of the oracle."""
+    pb = channel_problem(64, 16, 16)
+    lat = gb.Lattice(pb)
+    lat.step(2000)
+    o = orc.Oracle(orc.map_problem(pb))
+    o.step(2000)
+    r_g, u_g, T_g = lat.macros()
+    r_o, u_o, T_o = o.macros()
+    assert orc.field_error(u_g, u_o) < TOL_FIELD
+    assert orc.field_error(T_g, T_o) < TOL_FIELD
+    assert np.abs(r_g - r_o).max() < 1e-5
+
+
+def test_channel_full_size_ten_steps(gb, orc):
+    """The 256 x 64 x 64 channel in the launch configuration of the benchmark: every
+    population after 10 steps from a seeded random state matches the oracle."""
+    (ef, eg), (eu, eT, _), _, _ = _single_step(gb, orc, channel_problem(256, 64, 64), seed=3,
+                                               steps=10)
+    assert ef < 4 * TOL_STEP and eg < 4 * TOL_STEP, (ef, eg)
+    assert eu < TOL_FIELD and eT < TOL_FIELD
+
+
+def test_heterogeneous_cavity_500_steps(gb, orc):
+    n = 24
+    phi = porosity_field(n, n, n, seed=5).astype(np.float32).astype(np.float64)
+    pb = cavity_problem(n, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71, phi_field=phi)
+    lat = gb.Lattice(pb)
+    lat.step(500)
+    o = orc.Oracle(orc.map_problem(pb))
+    o.step(500)
+    _, u_g, T_g = lat.macros()
+    _, u_o, T_o = o.macros()
+    assert orc.field_error(u_g, u_o) < TOL_FIELD
+    assert orc.field_error(T_g, T_o) < TOL_FIELD
+
+
+def test_diagnostics_match_oracle(gb, orc):
+    """lbm_sums, lbm_residual and lbm_nusselt against their plain definitions on the
+    oracle's fields."""
+    pb = cavity_problem(16, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71)
+    lp = orc.map_problem(pb)
+    lat = gb.Lattice(pb)
+    o = orc.Oracle(lp)
+    lat.step(300)
+    o.step(300)
+    lat.residual()
+    _, u1, T1 = o.macros()
+    lat.step(100)
+    o.step(100)
+    ru, rT = lat.residual()
+    _, u2, T2 = o.macros()
+    assert ru == pytest.approx(orc.residual(u2, u1), rel=1e-3)
+    assert rT == pytest.approx(orc.residual(T2, T1), rel=1e-3)
+    f, g = o.populations()
+    m, h = lat.sums()
+    assert m == pytest.approx(f.sum() - f[0].size * lp.rho0, abs=1e-4)
+    assert h == pytest.approx(g.sum() - g[0].size * lp.sigma * lp.T0, abs=1e-4)
+    for face, Tw in ((0, 1.0), (1, 0.0)):
+        nu_g, prof_g, mp_g = lat.nusselt(face)
+        nu_o, prof_o, mp_o = orc.nusselt(o.macros()[2], face, Tw, lp.L)
+        assert nu_g == pytest.approx(nu_o, rel=1e-5, abs=1e-6)
+        assert np.allclose(prof_g, prof_o, rtol=1e-5, atol=1e-6)
+
+
+def test_closed_cavity_mass_on_gpu(gb):
+    pb = cavity_problem(16, Ra=1e5, Da=1e-2, phi=0.8, Pr=0.71)
+    lat = gb.Lattice(pb)
+    m0, _ = lat.sums()
+    lat.step(2000)
+    m1, _ = lat.sums()
+    assert abs(m1 - m0) < 1e-3  # FP32 round-off over 4096 sites x 2000 steps
+
+
+def test_zero_steps_and_fixed_point(gb, orc):
+    """nsteps = 0 leaves the state untouched; a force-free equilibrium stays put."""
+    pb = dict(nx=8, ny=6, nz=5, mapping="lattice", nu_e=0.1, alpha_f=0.05)
+    lat = gb.Lattice(pb)
+    u = np.zeros((3, 5, 6, 8))
+    u[0] = 0.02
+    u[2] = -0.01
+    lat.init_equilibrium(0.7, None, u)
+    f0, g0 = lat.populations()
+    lat.step(0)
+    f1, g1 = lat.populations()
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    lat.step(50)
+    _, ug, Tg = lat.macros()
+    assert np.abs(ug - u).max() < 1e-6 and np.abs(Tg - 0.7).max() < 1e-6
+
+
+def test_nonfinite_state_is_reported(gb, orc):
+    """A NaN planted in the host-side state is reported as LBM_EUNSTABLE by the
+    reductions (the kernels keep running on finite memory)."""
+    pb = cavity_problem(6, Ra=1e4, Da=1e-2, phi=0.6)
+    lp, o, f, g = _random_state(orc, pb, 1)
+    f[3, 2, 2, 2] = float("nan")
+    lat = gb.Lattice(pb)
+    lat.set_populations(f, g)
+    with pytest.raises(gb.LbmError) as ei:
+        lat.sums()
+    assert ei.value.status == gb.LBM_EUNSTABLE
+    lat.step(3)
+    with pytest.raises(gb.LbmError) as ei:
+        lat.residual()
+    assert ei.value.status == gb.LBM_EUNSTABLE
+
+
+def test_invalid_medium_rejected(gb):
+    pb = cavity_problem(6, Ra=1e4, Da=1e-2, phi=0.6)
+    lat = gb.Lattice(pb)
+    with pytest.raises(gb.LbmError) as ei:
+        lat.set_medium(None, phi=1.5)
+    assert ei.value.status == gb.LBM_EINVAL
+    bad = np.full((6, 6, 6), 0.5, np.float32)
+    bad[1, 1, 1] = 1.0
+    with pytest.raises(gb.LbmError):
+        lat.set_medium(bad)
+    lat.step(1)  # the context stays usable
+    assert lat.steps == 1
