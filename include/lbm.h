@@ -204,6 +204,30 @@ lbm_status lbm_sums(lbm_ctx* ctx, double* mass_dev, double* heat_dev);
  * init returns +inf.  Synchronises.  LBM_EUNSTABLE if a field holds NaN or Inf. */
 lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
 
+/* Largest field, in sites, that lbm_residual_noalloc accepts (2^25, e.g. 256 x 256 x 512). */
+#define LBM_NOALLOC_MAX_SITES 33554432LL
+
+/* Allocation-free steady-state residual.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- an application that gives the
+ * library a fixed arena and forbids cudaMalloc after start-up, a loop in which an
+ * allocation (which may synchronise the device) would stall, or work recorded into a CUDA
+ * stream capture, where allocation calls are not permitted.
+ * It computes what lbm_residual computes, r_u = ||u - u_prev||_2 / ||u||_2 and the same for
+ * T (FP64 accumulation), from fields the caller holds, e.g. two results of
+ * lbm_macros_device:
+ *  u, u_prev : device, 3 x ns floats ([3][ns]);  T, T_prev : device, ns floats;
+ *  ns        : 1 .. LBM_NOALLOC_MAX_SITES, else LBM_EINVAL and nothing is launched;
+ *  out       : device, 3 doubles, written asynchronously: r_u, r_T (+inf where the norm of
+ *              the new field is 0) and the number of non-finite values met;
+ *  stream    : cudaStream_t to queue on (NULL: the current device's default stream).
+ * It allocates nothing: its partial sums live in a static 320 KiB device array that every
+ * GPU loading the library holds until exit.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls whose kernels overlap on the GPU race and must
+ * be serialised.  Errors: LBM_EINVAL (NULL pointer or ns out of range), LBM_ECUDA. */
+lbm_status lbm_residual_noalloc(const float* u, const float* T, const float* u_prev,
+                                const float* T_prev, long long ns, double* out, void* stream);
+
 /* Derived lattice parameters of the context, including the current medium. */
 lbm_status lbm_get_lattice(const lbm_ctx* ctx, lbm_lattice* out);
 

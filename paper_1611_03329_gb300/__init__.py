@@ -31,7 +31,10 @@ ABI_SYMBOLS = (
     "lbm_step", "lbm_init_equilibrium", "lbm_set_populations", "lbm_get_populations",
     "lbm_macros", "lbm_macros_device", "lbm_nusselt", "lbm_sums", "lbm_residual",
     "lbm_get_lattice", "lbm_steps_done", "lbm_sync", "lbm_last_error", "lbm_status_string",
+    "lbm_residual_noalloc",
 )
+
+NOALLOC_MAX_SITES = 33554432  # LBM_NOALLOC_MAX_SITES
 
 
 class LbmParams(C.Structure):
@@ -130,6 +133,7 @@ def lib():
         L.lbm_last_error.restype = C.c_char_p
         L.lbm_status_string.argtypes = [C.c_int]
         L.lbm_status_string.restype = C.c_char_p
+        L.lbm_residual_noalloc.argtypes = [vp, vp, vp, vp, C.c_longlong, vp, vp]
         _lib = L
     return _lib
 
@@ -308,6 +312,18 @@ class Lattice:
         out = LbmLattice()
         self._check(lib().lbm_get_lattice(self._h, C.byref(out)), "lbm_get_lattice")
         return out.as_dict()
+
+
+def residual_noalloc(u_ptr: int, T_ptr: int, u_prev_ptr: int, T_prev_ptr: int, ns: int,
+                     out_ptr: int, stream: Optional[int] = None) -> None:
+    """Allocation-free residual of caller-held device fields (``lbm_residual_noalloc``):
+    writes r_u, r_T and the non-finite count to the 3 device doubles at ``out_ptr``,
+    asynchronously on ``stream``.  For callers that cannot allocate device memory."""
+    st = lib().lbm_residual_noalloc(C.c_void_p(u_ptr), C.c_void_p(T_ptr), C.c_void_p(u_prev_ptr),
+                                    C.c_void_p(T_prev_ptr), C.c_longlong(ns),
+                                    C.c_void_p(out_ptr), C.c_void_p(stream or 0))
+    if st != LBM_OK:
+        raise LbmError(st, f"lbm_residual_noalloc: {lib().lbm_status_string(st).decode()}")
 
 
 def medium_args(pb: dict) -> dict:

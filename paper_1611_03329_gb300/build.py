@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "liblbm_gb300.so"
 LIB = os.path.join(OUT_DIR, LIB_NAME)
-SOURCES = ["lbm_kernels.cu", "lbm_api.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
