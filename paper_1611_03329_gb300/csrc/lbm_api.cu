@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -23,7 +24,9 @@ struct lbm_ctx {
     float* pop[2] = {nullptr, nullptr};   // ping-pong population copies, 26 planes each
     float* hist[2] = {nullptr, nullptr};  // outflow history, 6 x ny*nz
     int cur = 0;
+    lbm::Planes pl[2];  // launch planes reading copy 0 / copy 1
     bool outflow = false;
+    int block_threads = 128;     // site-kernel block size (LBM_BLOCK_THREADS overrides)
     float* phi_dev = nullptr;
     KParams kp{};
     double* partials = nullptr;  // reduction scratch
@@ -79,6 +82,7 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
     double ns = (double)p->nx * p->ny * p->nz;
     if (ns >= 2147483647.0) return "lattice too large (sites must fit in 31 bits)";
+    if (p->nz > 65535) return "nz must be <= 65535 (one grid slice per z-plane)";
     if (p->storage != LBM_STORE_FP32) return "unsupported storage";
     if (!finite_pos(p->rho0)) return "rho0 must be > 0";
     if (!(p->varpi > 0.0 && p->varpi < 1.0)) return "varpi must lie in (0, 1)";
@@ -264,6 +268,8 @@ void fill_kparams(lbm_ctx* c) {
     k.nx = p.nx;
     k.ny = p.ny;
     k.nz = p.nz;
+    k.nyz = p.ny * p.nz;
+    k.block_threads = c->block_threads;
     k.ns = c->ns;
     k.sq = c->sq;
     for (int f = 0; f < 6; ++f) {
@@ -339,6 +345,19 @@ lbm_status usable(lbm_ctx* c) {
 float* cur_pop(lbm_ctx* c) { return c->pop[c->cur]; }
 float* cur_hist(lbm_ctx* c) { return c->hist[c->cur]; }
 
+// Planes of a step that reads copy `from` and writes the other copy.
+lbm::Planes planes(const lbm_ctx* c, int from) {
+    lbm::Planes pl;
+    const int to = from ^ 1;
+    for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
+        pl.in[q] = c->pop[from] + (size_t)q * c->sq;
+        pl.out[q] = c->pop[to] + (size_t)q * c->sq;
+    }
+    pl.hin = c->hist[from];
+    pl.hout = c->hist[to];
+    return pl;
+}
+
 lbm_status ensure_stage(lbm_ctx* c) {
     if (!c->stage) LBM_CUDA(cudaMalloc(&c->stage, sizeof(double) * 4 * (size_t)c->ns));
     return LBM_OK;
@@ -381,6 +400,10 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     c->sq = (c->ns + 63) / 64 * 64;  // 256-byte aligned population planes
     c->nyz = (long long)p->ny * p->nz;
     c->outflow = p->flow_bc[1] == LBM_FLOW_OUTFLOW;
+    if (const char* bt = std::getenv("LBM_BLOCK_THREADS")) {
+        int v = std::atoi(bt);
+        if (v == 32 || v == 64 || v == 128 || v == 256) c->block_threads = v;
+    }
     lbm_status st = LBM_OK;
     // the device of a caller's stream, else the calling thread's current device
     cudaError_t e = stream ? cudaStreamGetDevice((cudaStream_t)stream, &c->device)
@@ -415,6 +438,8 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     }
     if (st == LBM_OK) {
         fill_kparams(c);
+        c->pl[0] = planes(c, 0);
+        c->pl[1] = planes(c, 1);
         st = init_state(c, nullptr, nullptr, p->T_init);
     }
     if (st == LBM_OK) {
@@ -498,8 +523,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
     for (int t = 0; t < nsteps; ++t) {
         int nxt = c->cur ^ 1;
-        LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pop[c->cur], c->pop[nxt],
-                                  c->hist[c->cur], c->hist[nxt], c->stream));
+        LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pl[c->cur], c->stream));
         c->cur = nxt;
         c->steps++;
     }
@@ -592,7 +616,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
 lbm_status lbm_macros_device(lbm_ctx* c, float* rho, float* u, float* T) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
-    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, cur_pop(c), cur_hist(c), rho, u, T, c->stream));
+    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, c->pl[c->cur], rho, u, T, c->stream));
     return LBM_OK;
 }
 
@@ -604,7 +628,7 @@ lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* T) {
     float* du = half;
     float* dT = half + 3 * c->ns;
     float* drho = c->mac + 8 * c->ns;
-    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, cur_pop(c), cur_hist(c), rho ? drho : nullptr,
+    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, c->pl[c->cur], rho ? drho : nullptr,
                                 u ? du : nullptr, T ? dT : nullptr, c->stream));
     if (rho)
         LBM_CUDA(cudaMemcpyAsync(rho, drho, sizeof(float) * c->ns, cudaMemcpyDeviceToHost, c->stream));
@@ -627,8 +651,8 @@ lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile,
     if (n[axis] < 2) return fail(c, LBM_EINVAL, "Nusselt needs >= 2 sites normal to the face");
     int n1 = axis == 0 ? c->prm.ny : c->prm.nx;
     double scale = c->lat.L / c->lat.dT;
-    LBM_CUDA(lbm::launch_nusselt(c->kp, c->outflow, cur_pop(c), cur_hist(c), face,
-                                 c->prm.face_T[face], scale, c->profile, c->dres, c->stream));
+    LBM_CUDA(lbm::launch_nusselt(c->kp, c->outflow, c->pl[c->cur], face, c->prm.face_T[face],
+                                 scale, c->profile, c->dres, c->stream));
     LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 2, cudaMemcpyDeviceToHost,
                              c->stream));
     if (nu_profile)
@@ -664,7 +688,7 @@ lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
     float* cT = cu + 3 * c->ns;
     const float* pu = c->mac + (size_t)c->snap * 4 * c->ns;  // snapshot of the previous call
     const float* pT = pu + 3 * c->ns;
-    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, cur_pop(c), cur_hist(c), nullptr, cu, cT,
+    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, c->pl[c->cur], nullptr, cu, cT,
                                 c->stream));
     bool first = !c->have_prev;
     if (first) {

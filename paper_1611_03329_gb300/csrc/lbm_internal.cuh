@@ -11,10 +11,13 @@ constexpr int kQ = 19;   // D3Q19 flow populations (Eq. 19)
 constexpr int kQT = 7;   // D3Q7 temperature populations (Eq. 12, first seven columns)
 constexpr int kOutSlots = 6;  // populations entering across the x-high face: 5 f + 1 g
 constexpr int kBlock = 256;   // threads per block of the site kernels
+constexpr int kStepMinBlocks = 4;  // resident blocks per SM the step kernel is compiled for
 
 // Everything a site kernel needs, passed by value (__grid_constant__).
 struct KParams {
     int nx, ny, nz;
+    int nyz;        // ny * nz (outflow history plane)
+    int block_threads;  // threads per block of the site kernels (host launch setting)
     long long ns;   // sites
     long long sq;   // elements between consecutive population planes (>= ns, padded)
 
@@ -44,11 +47,19 @@ struct KParams {
     float alpha_f, alpha_m, inv_sig_csT2;
 };
 
+// Population planes of one launch: the 26 planes read (in) and written (out) and the outflow
+// history read (hin) and written (hout).
+struct Planes {
+    const float* in[kQ + kQT];
+    float* out[kQ + kQT];
+    const float* hin;
+    float* hout;
+};
+
 // Launch wrappers (defined in lbm_kernels.cu).  All are asynchronous on `st`.
-cudaError_t launch_step(const KParams& p, bool outflow, const float* pin, float* pout,
-                        const float* hin, float* hout, cudaStream_t st);
-cudaError_t launch_macros(const KParams& p, bool outflow, const float* pin, const float* hin,
-                          float* rho, float* u, float* T, cudaStream_t st);
+cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st);
+cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,
+                          float* T, cudaStream_t st);
 cudaError_t launch_init_eq(const KParams& p, float* pop, const double* T_field,
                            const double* u_field, double T_uniform, cudaStream_t st);
 cudaError_t launch_plane_to_dev(const double* src, float* dst, double offset, long long n,
@@ -60,9 +71,8 @@ cudaError_t launch_hist_reset(const KParams& p, const float* pop, float* hist, c
 cudaError_t launch_sums(const KParams& p, const float* pop, double* partials, int nparts,
                         double* out, cudaStream_t st);
 // Nusselt profile and its mean / centre value: out[0] = Nu_3D, out[1] = Nu_mp.
-cudaError_t launch_nusselt(const KParams& p, bool outflow, const float* pin, const float* hin,
-                           int face, double Tw, double scale, double* profile, double* out,
-                           cudaStream_t st);
+cudaError_t launch_nusselt(const KParams& p, bool outflow, const Planes& pl, int face, double Tw,
+                           double scale, double* profile, double* out, cudaStream_t st);
 // Residual sums: out = (sum |du|^2, sum |u|^2, sum dT^2, sum T^2, nonfinite count).
 cudaError_t launch_residual(const float* u, const float* T, const float* up, const float* Tp,
                             long long ns, double* partials, int nparts, double* out,

@@ -9,7 +9,10 @@
 // One thread updates one site: pull 26 populations (Eqs. 10, 35 with the wall rules),
 // collide in moment space with the sparse integer M of Eq. A2 and N of Eq. 36 unrolled in
 // registers, push the back-transform through M^-1 = M^T diag(1/|M_k|^2) (the rows of Eq. A2
-// are orthogonal) and N^-1 of Eq. 43, and store 26 populations.
+// are orthogonal) and N^-1 of Eq. 43, and store 26 populations.  Threads are laid out as a
+// 3D grid (x fastest, one z-plane per grid slice) so that no index division is needed; a
+// warp whose 32 sites are all interior takes unconditional loads, any other warp takes the
+// predicated boundary path.
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -56,20 +59,44 @@ __host__ __device__ constexpr int opp7(int i) { return i == 0 ? 0 : ((i & 1) ? i
 static_assert(opp19(7) == 10 && opp19(8) == 9 && opp19(12) == 13 && opp19(16) == 17, "opp19");
 static_assert(ex19(opp19(13)) == -ex19(13) && ez19(opp19(13)) == -ez19(13), "opp19 sign");
 
-// ---- site coordinates and medium -----------------------------------------------------------
-struct Site {
-    int x, y, z;
-    long long s;
+// ---- site and neighbourhood ----------------------------------------------------------------
+// A site with the offsets (in sites) of its six axis neighbours' sources and the faces that
+// a pull would cross.  For a velocity with component +1 along an axis the source lies at -1
+// (offset *m); with -1 at +1 (offset *p).  Periodic faces wrap the offset; a non-periodic
+// face sets its bit in `cross` (bits: x-low, x-high, y-low, y-high, z-low, z-high).
+struct Nbr {
+    int x, y, z, s;
+    int xm, xp, ym, yp, zm, zp;
+    unsigned cross;
 };
 
-__device__ __forceinline__ Site site_of(const KParams& p, long long s) {
-    Site c;
-    c.s = s;
-    long long yz = s / p.nx;
-    c.x = (int)(s - yz * p.nx);
-    c.z = (int)(yz / p.ny);
-    c.y = (int)(yz - (long long)c.z * p.ny);
-    return c;
+__device__ __forceinline__ Nbr neighbourhood(const KParams& p, int x, int y, int z) {
+    Nbr n;
+    n.x = x;
+    n.y = y;
+    n.z = z;
+    const int nxy = p.nx * p.ny;
+    n.s = x + p.nx * (y + p.ny * z);
+    n.cross = 0u;
+    n.xm = -1;
+    n.xp = 1;
+    n.ym = -p.nx;
+    n.yp = p.nx;
+    n.zm = -nxy;
+    n.zp = nxy;
+    if (x == 0) { if (p.per_mask & 1u) n.xm = p.nx - 1; else { n.xm = 0; n.cross |= 1u; } }
+    if (x == p.nx - 1) { if (p.per_mask & 2u) n.xp = 1 - p.nx; else { n.xp = 0; n.cross |= 2u; } }
+    if (y == 0) { if (p.per_mask & 4u) n.ym = p.nx * (p.ny - 1); else { n.ym = 0; n.cross |= 4u; } }
+    if (y == p.ny - 1) { if (p.per_mask & 8u) n.yp = -p.nx * (p.ny - 1); else { n.yp = 0; n.cross |= 8u; } }
+    if (z == 0) { if (p.per_mask & 16u) n.zm = nxy * (p.nz - 1); else { n.zm = 0; n.cross |= 16u; } }
+    if (z == p.nz - 1) { if (p.per_mask & 32u) n.zp = -nxy * (p.nz - 1); else { n.zp = 0; n.cross |= 32u; } }
+    return n;
+}
+
+// Source offset along one axis for velocity component e: +1 pulls from -1 and vice versa.
+__device__ __forceinline__ int axis_off(int e, int m, int p_) { return e == 1 ? m : (e == -1 ? p_ : 0); }
+__device__ __forceinline__ unsigned axis_cross(int e, unsigned cr, unsigned lo, unsigned hi) {
+    return e == 1 ? (cr & lo) : (e == -1 ? (cr & hi) : 0u);
 }
 
 struct Medium {
@@ -78,7 +105,7 @@ struct Medium {
 
 // Eq. 4 / Eq. 28 coefficients at a site; Eq. 6 (Kozeny-Carman K, Ergun F_phi) for a field.
 template <bool HET>
-__device__ __forceinline__ Medium medium_at(const KParams& p, long long s) {
+__device__ __forceinline__ Medium medium_at(const KParams& p, int s) {
     Medium m;
     if (!HET) {
         m.phi = p.phi;
@@ -108,27 +135,19 @@ __device__ __forceinline__ Medium medium_at(const KParams& p, long long s) {
 }
 
 // ---- streaming with boundary rules ------------------------------------------------------------
-// Pull of f_I at c: the post-collision population at c - e_I, or the wall rule when that source
-// lies outside the lattice (periodic faces wrap; a no-slip wall wins over a velocity face, which
-// wins over the outflow).  OUTF enables the convective outflow on the x-high face.
+// Pull of f_I at site n: the post-collision population at x - e_I, or the wall rule when that
+// source lies outside (a no-slip wall wins over a velocity face, which wins over the outflow).
 template <int I, bool OUTF>
-__device__ __forceinline__ float pull_f(const float* __restrict__ fin, const KParams& p,
-                                        int x, int y, int z, long long s,
-                                        const float* __restrict__ hist, bool* via) {
+__device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, const Nbr& n,
+                                        bool* via) {
     constexpr int ex = ex19(I), ey = ey19(I), ez = ez19(I);
-    int sx = x - ex, sy = y - ey, sz = z - ez;
-    unsigned crossed = 0u;
-    if (ex == 1 && sx < 0) { if (p.per_mask & 1u) sx += p.nx; else crossed |= 1u; }
-    if (ex == -1 && sx >= p.nx) { if (p.per_mask & 2u) sx -= p.nx; else crossed |= 2u; }
-    if (ey == 1 && sy < 0) { if (p.per_mask & 4u) sy += p.ny; else crossed |= 4u; }
-    if (ey == -1 && sy >= p.ny) { if (p.per_mask & 8u) sy -= p.ny; else crossed |= 8u; }
-    if (ez == 1 && sz < 0) { if (p.per_mask & 16u) sz += p.nz; else crossed |= 16u; }
-    if (ez == -1 && sz >= p.nz) { if (p.per_mask & 32u) sz -= p.nz; else crossed |= 32u; }
-    if (crossed == 0u)
-        return __ldg(fin + (long long)I * p.sq + sx + (long long)p.nx * (sy + (long long)p.ny * sz));
-    float bb = __ldg(fin + (long long)opp19(I) * p.sq + s);
-    if (crossed & p.wall_mask) return bb;
-    unsigned vm = crossed & p.vel_mask;
+    const int oyz = axis_off(ey, n.ym, n.yp) + axis_off(ez, n.zm, n.zp);
+    const unsigned cyz = axis_cross(ey, n.cross, 4u, 8u) | axis_cross(ez, n.cross, 16u, 32u);
+    const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | cyz;
+    if (cr == 0u) return __ldg(pl.in[I] + n.s + axis_off(ex, n.xm, n.xp) + oyz);
+    const float bb = __ldg(pl.in[opp19(I)] + n.s);
+    if (cr & p.wall_mask) return bb;
+    unsigned vm = cr & p.vel_mask;
     if (vm) {
         int face = __ffs(vm) - 1;
         float eu = (float)ex * p.face_u[face][0] + (float)ey * p.face_u[face][1] +
@@ -136,37 +155,44 @@ __device__ __forceinline__ float pull_f(const float* __restrict__ fin, const KPa
         return bb + 6.0f * w19(I) * p.rho0 * eu;  // 2 w_i rho0 (e_i . u_w) / c_s^2
     }
     if constexpr (OUTF && ex == -1) {
-        // convective outflow: p(N-1, t+1) = (p(N-1, t) + U p(N-2, t+1)) / (1 + U)
+        // convective outflow: p(N-1, t+1) = (p(N-1, t) + U p(N-2, t+1)) / (1 + U), with
+        // p(N-2, t+1) pulled at the inner neighbour (same y, z, so the same y/z crossings)
         *via = true;
-        float inner = pull_f<I, false>(fin, p, x - 1, y, z, s - 1, nullptr, nullptr);
-        float old = __ldg(hist + (long long)slot19(I) * p.ny * p.nz + y + (long long)p.ny * z);
+        float inner;
+        if (cyz == 0u) {
+            inner = __ldg(pl.in[I] + n.s + oyz);  // source of x-1 along -x is x itself
+        } else {
+            inner = __ldg(pl.in[opp19(I)] + n.s - 1);
+            unsigned vmi = cyz & p.vel_mask;
+            if (!(cyz & p.wall_mask) && vmi) {
+                int face = __ffs(vmi) - 1;
+                float eu = (float)ex * p.face_u[face][0] + (float)ey * p.face_u[face][1] +
+                           (float)ez * p.face_u[face][2];
+                inner += 6.0f * w19(I) * p.rho0 * eu;
+            }
+        }
+        float old = __ldg(pl.hin + slot19(I) * p.nyz + n.y + p.ny * n.z);
         return p.out_a * old + p.out_b * inner;
     }
     return bb;  // not reached for validated boundary sets
 }
 
 template <int I, bool OUTF>
-__device__ __forceinline__ float pull_g(const float* __restrict__ gin, const KParams& p,
-                                        int x, int y, int z, long long s,
-                                        const float* __restrict__ hist) {
+__device__ __forceinline__ float pull_g(const Planes& pl, const KParams& p, const Nbr& n) {
     constexpr int ex = ex7(I), ey = ey7(I), ez = ez7(I);
-    int sx = x - ex, sy = y - ey, sz = z - ez;
-    int face = -1;
-    if (ex == 1 && sx < 0) { if (p.per_mask & 1u) sx += p.nx; else face = 0; }
-    if (ex == -1 && sx >= p.nx) { if (p.per_mask & 2u) sx -= p.nx; else face = 1; }
-    if (ey == 1 && sy < 0) { if (p.per_mask & 4u) sy += p.ny; else face = 2; }
-    if (ey == -1 && sy >= p.ny) { if (p.per_mask & 8u) sy -= p.ny; else face = 3; }
-    if (ez == 1 && sz < 0) { if (p.per_mask & 16u) sz += p.nz; else face = 4; }
-    if (ez == -1 && sz >= p.nz) { if (p.per_mask & 32u) sz -= p.nz; else face = 5; }
-    if (face < 0)
-        return __ldg(gin + (long long)I * p.sq + sx + (long long)p.nx * (sy + (long long)p.ny * sz));
-    float bb = __ldg(gin + (long long)opp7(I) * p.sq + s);
-    int kind = p.heat_kind[face];
+    const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
+                        axis_cross(ez, n.cross, 16u, 32u);
+    if (cr == 0u)
+        return __ldg(pl.in[kQ + I] + n.s + axis_off(ex, n.xm, n.xp) + axis_off(ey, n.ym, n.yp) +
+                     axis_off(ez, n.zm, n.zp));
+    const float bb = __ldg(pl.in[kQ + opp7(I)] + n.s);
+    const int face = __ffs(cr) - 1;  // a D3Q7 velocity crosses one face at most
+    const int kind = p.heat_kind[face];
     if (kind == 2) return -bb + p.heat_abb[face];  // Dirichlet: anti-bounce-back
     if constexpr (OUTF && ex == -1) {
         if (kind == 3) {
-            float inner = __ldg(gin + (long long)I * p.sq + s);  // g_I(N-2, t+1) = g*_I(N-1, t)
-            float old = __ldg(hist + 5LL * p.ny * p.nz + y + (long long)p.ny * z);
+            float inner = __ldg(pl.in[kQ + I] + n.s);  // g_I(N-2, t+1) = g*_I(N-1, t)
+            float old = __ldg(pl.hin + 5 * p.nyz + n.y + p.ny * n.z);
             return p.out_a * old + p.out_b * inner;
         }
     }
@@ -174,44 +200,28 @@ __device__ __forceinline__ float pull_g(const float* __restrict__ gin, const KPa
 }
 
 template <bool OUTF, int... I>
-__device__ __forceinline__ void gather_f_bc(float* f, bool* via, const float* fin, const KParams& p,
-                                            const Site& c, const float* hist,
+__device__ __forceinline__ void gather_f_bc(float* f, bool* via, const Planes& pl,
+                                            const KParams& p, const Nbr& n,
                                             std::integer_sequence<int, I...>) {
-    ((f[I] = pull_f<I, OUTF>(fin, p, c.x, c.y, c.z, c.s, hist, &via[I])), ...);
+    ((f[I] = pull_f<I, OUTF>(pl, p, n, &via[I])), ...);
 }
 
 template <bool OUTF, int... I>
-__device__ __forceinline__ void gather_g_bc(float* g, const float* gin, const KParams& p,
-                                            const Site& c, const float* hist,
-                                            std::integer_sequence<int, I...>) {
-    ((g[I] = pull_g<I, OUTF>(gin, p, c.x, c.y, c.z, c.s, hist)), ...);
+__device__ __forceinline__ void gather_g_bc(float* g, const Planes& pl, const KParams& p,
+                                            const Nbr& n, std::integer_sequence<int, I...>) {
+    ((g[I] = pull_g<I, OUTF>(pl, p, n)), ...);
 }
 
-// Pre-collision populations of one site.  Interior sites take unconditional loads.
+// Predicated pull of all 26 populations (any site), with the outflow's pressure anchor.
 template <bool OUTF>
-__device__ __forceinline__ void gather(const float* __restrict__ pin, const KParams& p,
-                                       const Site& c, const float* __restrict__ hist, float* f,
-                                       float* g) {
-    const float* fin = pin;
-    const float* gin = pin + (long long)kQ * p.sq;
-    bool interior = c.x > 0 && c.x < p.nx - 1 && c.y > 0 && c.y < p.ny - 1 && c.z > 0 &&
-                    c.z < p.nz - 1;
-    if (interior) {
-        const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
-#pragma unroll
-        for (int i = 0; i < kQ; ++i)
-            f[i] = __ldg(fin + (long long)i * p.sq + c.s - (ex19(i) + ey19(i) * nx + ez19(i) * nxy));
-#pragma unroll
-        for (int i = 0; i < kQT; ++i)
-            g[i] = __ldg(gin + (long long)i * p.sq + c.s - (ex7(i) + ey7(i) * nx + ez7(i) * nxy));
-        return;
-    }
+__device__ __forceinline__ void gather_general(const Planes& pl, const KParams& p, const Nbr& n,
+                                               float* f, float* g) {
     bool via[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) via[i] = false;
-    gather_f_bc<OUTF>(f, via, fin, p, c, hist, std::make_integer_sequence<int, kQ>{});
-    gather_g_bc<OUTF>(g, gin, p, c, hist, std::make_integer_sequence<int, kQT>{});
-    if (OUTF && c.x == p.nx - 1) {
+    gather_f_bc<OUTF>(f, via, pl, p, n, std::make_integer_sequence<int, kQ>{});
+    gather_g_bc<OUTF>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
+    if (OUTF && n.x == p.nx - 1) {
         // pressure anchor: shift the populations set by the outflow rule by
         // w_i (rho0 - rho) / sum(w_i) so that the outlet density is rho0
         float rho = 0.0f, wsum = 0.0f;
@@ -225,6 +235,86 @@ __device__ __forceinline__ void gather(const float* __restrict__ pin, const KPar
 #pragma unroll
             for (int i = 0; i < kQ; ++i)
                 if (via[i]) f[i] += w19(i) * corr;
+        }
+    }
+}
+
+// Pull for a warp whose sites all lie inside the y and z ranges (y, z neighbours need no
+// rule): unconditional loads with per-lane x offsets, then, only in a warp that holds an
+// x-face site, the x-face rule for the velocities that cross it.  With no x-face lane this is
+// the interior path.
+template <bool OUTF>
+__device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
+                                                   int z, int s, float* f, float* g) {
+    const int nx = p.nx, nxy = p.nx * p.ny;
+    int xm = -1, xp = 1;  // source offsets of +x and -x velocities
+    bool cxm = false, cxp = false;
+    if (x == 0) { if (p.per_mask & 1u) xm = nx - 1; else { xm = 0; cxm = true; } }
+    if (x == nx - 1) { if (p.per_mask & 2u) xp = 1 - nx; else { xp = 0; cxp = true; } }
+#pragma unroll
+    for (int i = 0; i < kQ; ++i)
+        f[i] = __ldg(pl.in[i] + s + axis_off(ex19(i), xm, xp) - (ey19(i) * nx + ez19(i) * nxy));
+#pragma unroll
+    for (int i = 0; i < kQT; ++i)
+        g[i] = __ldg(pl.in[kQ + i] + s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
+    if (!__any_sync(0xffffffffu, cxm || cxp)) return;  // interior warp
+    if (cxm) {
+        // x-low face: wall or velocity face (an outflow is only allowed on x-high)
+        const bool vel = (p.vel_mask & 1u) && !(p.wall_mask & 1u);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            if (ex19(i) != 1) continue;
+            float v = __ldg(pl.in[opp19(i)] + s);
+            if (vel)
+                v += 6.0f * w19(i) * p.rho0 *
+                     (p.face_u[0][0] + (float)ey19(i) * p.face_u[0][1] + (float)ez19(i) * p.face_u[0][2]);
+            f[i] = v;
+        }
+        const float bb = __ldg(pl.in[kQ + 2] + s);
+        g[1] = p.heat_kind[0] == 2 ? -bb + p.heat_abb[0] : bb;
+    }
+    if (cxp) {
+        const bool wall = p.wall_mask & 2u, vel = p.vel_mask & 2u;
+        if (!OUTF || wall || vel) {
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                if (ex19(i) != -1) continue;
+                float v = __ldg(pl.in[opp19(i)] + s);
+                if (vel && !wall)
+                    v += 6.0f * w19(i) * p.rho0 *
+                         (-p.face_u[1][0] + (float)ey19(i) * p.face_u[1][1] +
+                          (float)ez19(i) * p.face_u[1][2]);
+                f[i] = v;
+            }
+        } else {
+            // convective outflow of every -x velocity (their y/z sources are inside), then the
+            // pressure anchor: shift them by w_i (rho0 - rho) / sum(w_i), sum(w_i) = 1/6
+            const int yz = y + p.ny * z;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                if (ex19(i) != -1) continue;
+                float inner = __ldg(pl.in[i] + s - (ey19(i) * nx + ez19(i) * nxy));
+                float old = __ldg(pl.hin + slot19(i) * p.nyz + yz);
+                f[i] = p.out_a * old + p.out_b * inner;
+            }
+            float rho = 0.0f;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) rho += f[i];
+            const float corr = -6.0f * rho;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i)
+                if (ex19(i) == -1) f[i] += w19(i) * corr;
+        }
+        const float bb = __ldg(pl.in[kQ + 1] + s);
+        const int kind = p.heat_kind[1];
+        if (kind == 2) {
+            g[2] = -bb + p.heat_abb[1];
+        } else if (OUTF && kind == 3) {
+            float inner = __ldg(pl.in[kQ + 2] + s);
+            float old = __ldg(pl.hin + 5 * p.nyz + y + p.ny * z);
+            g[2] = p.out_a * old + p.out_b * inner;
+        } else {
+            g[2] = bb;
         }
     }
 }
@@ -396,47 +486,55 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
+// 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
+// blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
 template <bool HET, bool OUTF>
-__global__ void __launch_bounds__(kBlock, 2)
-    step_kernel(const __grid_constant__ KParams p, const float* __restrict__ pin,
-                float* __restrict__ pout, const float* __restrict__ hin,
-                float* __restrict__ hout) {
-    long long s = (long long)blockIdx.x * kBlock + threadIdx.x;
-    if (s >= p.ns) return;
-    const Site c = site_of(p, s);
+__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
+    step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x < p.nx && y < p.ny;
+    const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
+    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+    if (!valid) return;
     float f[kQ], g[kQT];
-    gather<OUTF>(pin, p, c, hin, f, g);
-    if (OUTF && c.x == p.nx - 1) {
-        const long long nyz = (long long)p.ny * p.nz, yz = c.y + (long long)p.ny * c.z;
-        hout[0 * nyz + yz] = f[2];
-        hout[1 * nyz + yz] = f[8];
-        hout[2 * nyz + yz] = f[10];
-        hout[3 * nyz + yz] = f[12];
-        hout[4 * nyz + yz] = f[14];
-        hout[5 * nyz + yz] = g[2];
+    const int s = x + p.nx * (y + p.ny * z);
+    if (warp_yz_in) {
+        gather_yz_interior<OUTF>(pl, p, x, y, z, s, f, g);
+    } else {
+        const Nbr n = neighbourhood(p, x, y, z);
+        gather_general<OUTF>(pl, p, n, f, g);
+    }
+    if (OUTF && x == p.nx - 1) {
+        const int yz = y + p.ny * z;
+        pl.hout[0 * p.nyz + yz] = f[2];
+        pl.hout[1 * p.nyz + yz] = f[8];
+        pl.hout[2 * p.nyz + yz] = f[10];
+        pl.hout[3 * p.nyz + yz] = f[12];
+        pl.hout[4 * p.nyz + yz] = f[14];
+        pl.hout[5 * p.nyz + yz] = g[2];
     }
     const Medium md = medium_at<HET>(p, s);
     collide<true>(p, md, f, g);
-    float* fo = pout;
-    float* go = pout + (long long)kQ * p.sq;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) fo[(long long)i * p.sq + s] = f[i];
-#pragma unroll
-    for (int i = 0; i < kQT; ++i) go[(long long)i * p.sq + s] = g[i];
+    for (int i = 0; i < kQ + kQT; ++i) pl.out[i][s] = i < kQ ? f[i] : g[i - kQ];
 }
 
 template <bool HET, bool OUTF>
 __global__ void __launch_bounds__(kBlock)
-    macros_kernel(const __grid_constant__ KParams p, const float* __restrict__ pin,
-                  const float* __restrict__ hin, float* __restrict__ rho, float* __restrict__ u,
-                  float* __restrict__ T) {
-    long long s = (long long)blockIdx.x * kBlock + threadIdx.x;
-    if (s >= p.ns) return;
-    const Site c = site_of(p, s);
+    macros_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
+                  float* __restrict__ rho, float* __restrict__ u, float* __restrict__ T) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const Nbr n = neighbourhood(p, x, y, z);
     float f[kQ], g[kQT];
-    gather<OUTF>(pin, p, c, hin, f, g);
-    const Medium md = medium_at<HET>(p, s);
+    gather_general<OUTF>(pl, p, n, f, g);
+    const Medium md = medium_at<HET>(p, n.s);
     Macro m = collide<false>(p, md, f, g);
+    const long long s = n.s;
     if (rho) rho[s] = m.rho;
     if (u) {
         u[s] = m.ux;
@@ -582,16 +680,11 @@ __global__ void __launch_bounds__(kRedThreads)
 
 // Temperature at a site from the streamed D3Q7 populations (Eq. 39).
 template <bool OUTF>
-__device__ __forceinline__ double temperature_at(const float* pin, const KParams& p, int x, int y,
-                                                 int z, const float* hist) {
-    Site c;
-    c.x = x;
-    c.y = y;
-    c.z = z;
-    c.s = x + (long long)p.nx * (y + (long long)p.ny * z);
+__device__ __forceinline__ double temperature_at(const Planes& pl, const KParams& p, int x, int y,
+                                                 int z) {
+    const Nbr n = neighbourhood(p, x, y, z);
     float g[kQT];
-    gather_g_bc<OUTF>(g, pin + (long long)kQ * p.sq, p, c, hist,
-                      std::make_integer_sequence<int, kQT>{});
+    gather_g_bc<OUTF>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
     float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
     return (double)p.T0 + (double)n0 * (double)p.inv_sigma;
 }
@@ -600,9 +693,8 @@ __device__ __forceinline__ double temperature_at(const float* pin, const KParams
 // local Nusselt number of Eq. 53 over the second tangential axis (Eq. 54).
 template <bool OUTF>
 __global__ void __launch_bounds__(kRedThreads)
-    nusselt_kernel(const __grid_constant__ KParams p, const float* __restrict__ pin,
-                   const float* __restrict__ hist, int face, double Tw, double scale,
-                   double* __restrict__ profile) {
+    nusselt_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
+                   int face, double Tw, double scale, double* __restrict__ profile) {
     const int axis = face >> 1, hi = face & 1;
     const int n[3] = {p.nx, p.ny, p.nz};
     const int t1 = axis == 0 ? 1 : 0;            // profile axis
@@ -615,8 +707,8 @@ __global__ void __launch_bounds__(kRedThreads)
         c0[t2] = c1[t2] = k;
         c0[axis] = hi ? n[axis] - 1 : 0;
         c1[axis] = hi ? n[axis] - 2 : 1;
-        double T0 = temperature_at<OUTF>(pin, p, c0[0], c0[1], c0[2], hist);
-        double T1 = temperature_at<OUTF>(pin, p, c1[0], c1[1], c1[2], hist);
+        double T0 = temperature_at<OUTF>(pl, p, c0[0], c0[1], c0[2]);
+        double T1 = temperature_at<OUTF>(pl, p, c1[0], c1[1], c1[2]);
         v[0] += (8.0 * Tw - 9.0 * T0 + T1) / 3.0 * scale;
     }
     double out[1];
@@ -650,33 +742,45 @@ inline unsigned blocks_for(long long n, int threads) {
 // ---- launch wrappers ---------------------------------------------------------------------------
 int reduction_blocks() { return kRedBlocks; }
 
-cudaError_t launch_step(const KParams& p, bool outflow, const float* pin, float* pout,
-                        const float* hin, float* hout, cudaStream_t st) {
-    unsigned nb = blocks_for(p.ns, kBlock);
+// Block of p.block_threads (32..kBlock) threads: blockDim.x = the smallest power of two >= nx
+// within that size, the rest along y.
+void site_grid(const KParams& p, dim3* grid, dim3* block) {
+    int nt = p.block_threads >= 32 && p.block_threads <= kBlock ? p.block_threads : kBlock;
+    int bx = 32;
+    while (bx < p.nx && bx < nt) bx *= 2;
+    int by = nt / bx > 0 ? nt / bx : 1;
+    *block = dim3(bx, by, 1);
+    *grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
+}
+
+cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st) {
+    dim3 grid, block;
+    site_grid(p, &grid, &block);
     bool het = p.phi_field != nullptr;
     if (het && outflow)
-        step_kernel<true, true><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+        step_kernel<true, true><<<grid, block, 0, st>>>(p, pl);
     else if (het)
-        step_kernel<true, false><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+        step_kernel<true, false><<<grid, block, 0, st>>>(p, pl);
     else if (outflow)
-        step_kernel<false, true><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+        step_kernel<false, true><<<grid, block, 0, st>>>(p, pl);
     else
-        step_kernel<false, false><<<nb, kBlock, 0, st>>>(p, pin, pout, hin, hout);
+        step_kernel<false, false><<<grid, block, 0, st>>>(p, pl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_macros(const KParams& p, bool outflow, const float* pin, const float* hin,
-                          float* rho, float* u, float* T, cudaStream_t st) {
-    unsigned nb = blocks_for(p.ns, kBlock);
+cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,
+                          float* T, cudaStream_t st) {
+    dim3 grid, block;
+    site_grid(p, &grid, &block);
     bool het = p.phi_field != nullptr;
     if (het && outflow)
-        macros_kernel<true, true><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+        macros_kernel<true, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
     else if (het)
-        macros_kernel<true, false><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+        macros_kernel<true, false><<<grid, block, 0, st>>>(p, pl, rho, u, T);
     else if (outflow)
-        macros_kernel<false, true><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+        macros_kernel<false, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
     else
-        macros_kernel<false, false><<<nb, kBlock, 0, st>>>(p, pin, hin, rho, u, T);
+        macros_kernel<false, false><<<grid, block, 0, st>>>(p, pl, rho, u, T);
     return cudaGetLastError();
 }
 
@@ -711,15 +815,14 @@ cudaError_t launch_sums(const KParams& p, const float* pop, double* partials, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_nusselt(const KParams& p, bool outflow, const float* pin, const float* hin,
-                           int face, double Tw, double scale, double* profile, double* out,
-                           cudaStream_t st) {
+cudaError_t launch_nusselt(const KParams& p, bool outflow, const Planes& pl, int face, double Tw,
+                           double scale, double* profile, double* out, cudaStream_t st) {
     const int axis = face >> 1;
     const int n1 = axis == 0 ? p.ny : p.nx;
     if (outflow)
-        nusselt_kernel<true><<<n1, kRedThreads, 0, st>>>(p, pin, hin, face, Tw, scale, profile);
+        nusselt_kernel<true><<<n1, kRedThreads, 0, st>>>(p, pl, face, Tw, scale, profile);
     else
-        nusselt_kernel<false><<<n1, kRedThreads, 0, st>>>(p, pin, hin, face, Tw, scale, profile);
+        nusselt_kernel<false><<<n1, kRedThreads, 0, st>>>(p, pl, face, Tw, scale, profile);
     nusselt_finalize_kernel<<<1, kRedThreads, 0, st>>>(profile, n1, out);
     return cudaGetLastError();
 }
