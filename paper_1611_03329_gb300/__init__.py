@@ -95,14 +95,15 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The shared library the binding loads: ``LBM_LIBRARY`` if set, else the in-tree build."""
+    return os.environ.get("LBM_LIBRARY") or _build.LIB
 
 
 def lib():
     """Load the CUDA library; raises if it has not been built."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = library_path()
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library not built ({path}); run "
                                "`python -c 'import __graft_entry__ as g; g.build()'`")

@@ -299,6 +299,34 @@ void fill_kparams(lbm_ctx* c) {
     k.s_m = (float)L.s[16];
     k.zeta_e = (float)L.zeta_e;
     k.zeta_nu = (float)L.zeta_nu;
+    {
+        // per-moment collision factors: s_k / |M_k|^2 and (1 - s_k / 2) / |M_k|^2 (Eq. 9)
+        auto a = [](double sk, double n2) { return (float)(sk / n2); };
+        auto b = [](double sk, double n2) { return (float)((1.0 - 0.5 * sk) / n2); };
+        double se = L.s[1], seps = L.s[2], sq = L.s[4], snu = L.s[9], spi = L.s[10], sm = L.s[16];
+        double c23 = 2.0 / 3.0 * L.rho0;
+        k.ae = a(se, 2394.0);
+        k.be = b(se, 2394.0);
+        k.aeps = a(seps, 252.0);
+        k.beps = b(seps, 252.0);
+        k.aq = a(sq, 40.0);
+        k.aqc = (float)(sq / 40.0 * c23);
+        k.bqc = (float)((1.0 - 0.5 * sq) / 40.0 * c23);
+        k.anu36 = a(snu, 36.0);
+        k.bnu36 = b(snu, 36.0);
+        k.api72 = a(spi, 72.0);
+        k.hbpi72 = (float)(0.5 * (1.0 - 0.5 * spi) / 72.0);
+        k.anu12 = a(snu, 12.0);
+        k.bnu12 = b(snu, 12.0);
+        k.api24 = a(spi, 24.0);
+        k.hbpi24 = (float)(0.5 * (1.0 - 0.5 * spi) / 24.0);
+        k.anu4 = a(snu, 4.0);
+        k.bnu4 = b(snu, 4.0);
+        k.am8 = a(sm, 8.0);
+        k.rho0_10 = (float)(L.rho0 / 10.0);
+        k.ze6 = (float)(L.zeta_e / 6.0);
+        k.zn6 = (float)(L.zeta_nu / 6.0);
+    }
     k.zeta_alpha = (float)L.zeta_alpha;
     for (int a = 0; a < 3; ++a) {
         k.buoy[a] = (float)L.buoy[a];

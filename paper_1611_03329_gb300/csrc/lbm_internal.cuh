@@ -34,6 +34,11 @@ struct KParams {
     float rho0, inv_rho0, sigma, inv_sigma, T0, varpi;
     float s_e, s_eps, s_q, s_nu, s_pi, s_m;        // Lambda (Eq. 22), s_rho = s_j = 1
     float zeta_e, zeta_nu, zeta_alpha;              // Q (Eq. 38), zeta_T = 1
+    // collision factors: a = s_k / |M_k|^2, b = (1 - s_k/2) / |M_k|^2 for the rows of Eq. A2
+    // (|M_k|^2 = 2394, 252, 40, 36, 72, 12, 24, 4, 8), with 2/3 rho0 folded into the q rows
+    float ae, be, aeps, beps, aq, aqc, bqc, anu36, bnu36, api72, hbpi72, anu12, bnu12;
+    float api24, hbpi24, anu4, bnu4, am8, rho0_10;
+    float ze6, zn6;  // zeta_e / 6, zeta_nu / 6 (Eq. 43 columns)
     float buoy[3], accel[3];                        // G = buoy (T - T0) + accel (Eq. 5)
 
     // uniform medium, precomputed (Eqs. 4, 28)

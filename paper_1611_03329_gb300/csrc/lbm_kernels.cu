@@ -122,7 +122,7 @@ __device__ __forceinline__ Medium medium_at(const KParams& p, int s) {
         float Fp = p.F_phi < 0.0f ? 1.75f * rsqrtf(150.0f * ph3) : p.F_phi;
         float inv_sqrtK = p.kinf ? 0.0f : omp * rsqrtf(p.cK * ph3);  // 1/sqrt(K(phi))
         m.phi = ph;
-        m.inv_phi = 1.0f / ph;
+        m.inv_phi = __fdividef(1.0f, ph);
         m.c_darcy = ph * p.nu * inv_sqrtK * inv_sqrtK;  // phi nu / K
         m.c_forch = ph * Fp * inv_sqrtK;                // phi F_phi / sqrt(K)
         m.l0 = 0.5f * (1.0f + 0.5f * m.c_darcy);
@@ -324,8 +324,12 @@ struct Macro {
     float rho, ux, uy, uz, T;
 };
 
+// sqrt of a non-negative value through the hardware reciprocal square root (exact zero kept).
+__device__ __forceinline__ float sqrt_nonneg(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
+
 // Eqs. 39, 5, 25, 27-28, 4, then (FULL) Eq. 9 with Eqs. 21-23 in moment space and Eq. 34 with
-// Eqs. 37-38, back-transformed in place.  f, g are deviations on entry and exit.
+// Eqs. 37-38, back-transformed in place.  f, g are deviations on entry and exit.  The
+// per-moment factors s_k / |M_k|^2 and (1 - s_k/2) / |M_k|^2 come precomputed in KParams.
 template <bool FULL>
 __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g) {
     // temperature (Eq. 39) and body force (Eq. 5)
@@ -355,11 +359,12 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     const float jz = d3 + (d6 + d7) + (d8 + d9);
 
     // velocity (Eqs. 27-28) and total force (Eq. 4)
-    const float vx = jx * p.inv_rho0 + 0.5f * md.phi * Gx;
-    const float vy = jy * p.inv_rho0 + 0.5f * md.phi * Gy;
-    const float vz = jz * p.inv_rho0 + 0.5f * md.phi * Gz;
-    const float vmag = sqrtf(vx * vx + vy * vy + vz * vz);
-    const float inv_den = 1.0f / (md.l0 + sqrtf(md.l0 * md.l0 + md.l1 * vmag));
+    const float hphi = 0.5f * md.phi;
+    const float vx = jx * p.inv_rho0 + hphi * Gx;
+    const float vy = jy * p.inv_rho0 + hphi * Gy;
+    const float vz = jz * p.inv_rho0 + hphi * Gz;
+    const float vmag = sqrt_nonneg(vx * vx + vy * vy + vz * vz);
+    const float inv_den = __fdividef(1.0f, md.l0 + sqrt_nonneg(md.l0 * md.l0 + md.l1 * vmag));
     const float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
 
     Macro mac;
@@ -370,7 +375,7 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     mac.T = T;
     if (!FULL) return mac;
 
-    const float umag = sqrtf(ux * ux + uy * uy + uz * uz);
+    const float umag = vmag * inv_den;  // |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|))
     const float drag = md.c_darcy + md.c_forch * umag;
     const float Fx = md.phi * Gx - drag * ux;
     const float Fy = md.phi * Gy - drag * uy;
@@ -389,47 +394,46 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     const float m_my = (d8 - d9) - (d4 + d5);
     const float m_mz = (d6 + d7) - (d8 + d9);
 
-    // equilibria (Eq. 21, beta1 = 3, beta2 = -11/2, beta3 = -1/2) and forcing (Eq. 23)
+    // equilibria (Eq. 21, beta1 = 3, beta2 = -11/2, beta3 = -1/2) and forcing (Eq. 23), with
+    // the velocity scaled by rho0 / phi once: w = rho0 u / phi
     const float r0p = p.rho0 * md.inv_phi;
-    const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
-    const float usq = uxx + uyy + uzz;
-    const float uF = ux * Fx + uy * Fy + uz * Fz;
-    const float Fxx = ux * Fx, Fyy = uy * Fy, Fzz = uz * Fz;
-    const float eq_e = -11.0f * rho + 19.0f * r0p * usq;
-    const float eq_eps = 3.0f * rho - 5.5f * r0p * usq;
-    const float eq_pxx = r0p * (2.0f * uxx - uyy - uzz);
-    const float eq_pww = r0p * (uyy - uzz);
-    const float S_pxx = 2.0f * r0p * (2.0f * Fxx - Fyy - Fzz);
-    const float S_pww = 2.0f * r0p * (Fyy - Fzz);
-    const float c23 = 2.0f / 3.0f * p.rho0;
+    const float wx = r0p * ux, wy = r0p * uy, wz = r0p * uz;
+    const float pxx = wx * ux, pyy = wy * uy, pzz = wz * uz;  // rho0 u_a^2 / phi
+    const float fxx = wx * Fx, fyy = wy * Fy, fzz = wz * Fz;  // rho0 u_a F_a / phi
+    const float usq = pxx + pyy + pzz;
+    const float uF = fxx + fyy + fzz;
+    const float eq_pxx = 2.0f * pxx - pyy - pzz;
+    const float eq_pww = pyy - pzz;
+    const float S_pxx = 2.0f * (2.0f * fxx - fyy - fzz);
+    const float S_pww = 2.0f * (fyy - fzz);
 
-    // dm_k = -s_k (m_k - m_k^eq) + (1 - s_k/2) S_k, scaled by 1/|M_k|^2; the conserved
+    // dm_k / |M_k|^2 = -s_k (m_k - m_k^eq) / |M_k|^2 + (1 - s_k/2) S_k / |M_k|^2; the conserved
     // momentum gains rho0 F whatever s_j is (Eqs. 9, 14, 26)
-    const float he = 1.0f - 0.5f * p.s_e, heps = 1.0f - 0.5f * p.s_eps, hq = 1.0f - 0.5f * p.s_q;
-    const float hnu = 1.0f - 0.5f * p.s_nu, hpi = 1.0f - 0.5f * p.s_pi;
-    const float de = (-p.s_e * (m_e - eq_e) + he * 38.0f * r0p * uF) * (1.0f / 2394.0f);
-    const float deps = (-p.s_eps * (m_eps - eq_eps) - heps * 11.0f * r0p * uF) * (1.0f / 252.0f);
-    const float djx = p.rho0 * Fx * 0.1f, djy = p.rho0 * Fy * 0.1f, djz = p.rho0 * Fz * 0.1f;
-    const float dqx = (-p.s_q * (qx + c23 * ux) - hq * c23 * Fx) * (1.0f / 40.0f);
-    const float dqy = (-p.s_q * (qy + c23 * uy) - hq * c23 * Fy) * (1.0f / 40.0f);
-    const float dqz = (-p.s_q * (qz + c23 * uz) - hq * c23 * Fz) * (1.0f / 40.0f);
-    const float dpxx = (-p.s_nu * (m_pxx - eq_pxx) + hnu * S_pxx) * (1.0f / 36.0f);
-    const float dpixx = (-p.s_pi * (m_pixx + 0.5f * eq_pxx) - hpi * 0.5f * S_pxx) * (1.0f / 72.0f);
-    const float dpww = (-p.s_nu * (m_pww - eq_pww) + hnu * S_pww) * (1.0f / 12.0f);
-    const float dpiww = (-p.s_pi * (m_piww + 0.5f * eq_pww) - hpi * 0.5f * S_pww) * (1.0f / 24.0f);
-    const float dpxy = (-p.s_nu * (m_pxy - r0p * ux * uy) + hnu * r0p * (ux * Fy + uy * Fx)) * 0.25f;
-    const float dpyz = (-p.s_nu * (m_pyz - r0p * uy * uz) + hnu * r0p * (uy * Fz + uz * Fy)) * 0.25f;
-    const float dpzx = (-p.s_nu * (m_pzx - r0p * uz * ux) + hnu * r0p * (uz * Fx + ux * Fz)) * 0.25f;
-    const float dmx = -p.s_m * m_mx * 0.125f;
-    const float dmy = -p.s_m * m_my * 0.125f;
-    const float dmz = -p.s_m * m_mz * 0.125f;
+    const float de = p.ae * (-11.0f * rho + 19.0f * usq - m_e) + p.be * 38.0f * uF;
+    const float deps = p.aeps * (3.0f * rho - 5.5f * usq - m_eps) - p.beps * 11.0f * uF;
+    const float djx = p.rho0_10 * Fx, djy = p.rho0_10 * Fy, djz = p.rho0_10 * Fz;
+    const float dqx = -p.aq * qx - (p.aqc * ux + p.bqc * Fx);
+    const float dqy = -p.aq * qy - (p.aqc * uy + p.bqc * Fy);
+    const float dqz = -p.aq * qz - (p.aqc * uz + p.bqc * Fz);
+    const float dpxx = p.anu36 * (eq_pxx - m_pxx) + p.bnu36 * S_pxx;
+    const float dpixx = -p.api72 * (0.5f * eq_pxx + m_pixx) - p.hbpi72 * S_pxx;
+    const float dpww = p.anu12 * (eq_pww - m_pww) + p.bnu12 * S_pww;
+    const float dpiww = -p.api24 * (0.5f * eq_pww + m_piww) - p.hbpi24 * S_pww;
+    const float dpxy = p.anu4 * (wx * uy - m_pxy) + p.bnu4 * (wx * Fy + wy * Fx);
+    const float dpyz = p.anu4 * (wy * uz - m_pyz) + p.bnu4 * (wy * Fz + wz * Fy);
+    const float dpzx = p.anu4 * (wz * ux - m_pzx) + p.bnu4 * (wz * Fx + wx * Fz);
+    const float dmx = -p.am8 * m_mx;
+    const float dmy = -p.am8 * m_my;
+    const float dmz = -p.am8 * m_mz;
 
     // f* = f + M^T diag(1/|M_k|^2) dm
     f[0] += -30.0f * de + 12.0f * deps;
     const float Eax = -11.0f * de - 4.0f * deps;
     const float Ex = Eax + 2.0f * dpxx - 4.0f * dpixx;
-    const float Ey = Eax - dpxx + 2.0f * dpixx + dpww - 2.0f * dpiww;
-    const float Ez = Eax - dpxx + 2.0f * dpixx - dpww + 2.0f * dpiww;
+    const float Eyz2 = Eax - dpxx + 2.0f * dpixx;
+    const float Pw = dpww - 2.0f * dpiww;
+    const float Ey = Eyz2 + Pw;
+    const float Ez = Eyz2 - Pw;
     const float Ox = djx - 4.0f * dqx, Oy = djy - 4.0f * dqy, Oz = djz - 4.0f * dqz;
     f[1] += Ex + Ox;
     f[2] += Ex - Ox;
@@ -438,8 +442,10 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     f[5] += Ez + Oz;
     f[6] += Ez - Oz;
     const float Cd = 8.0f * de + deps;
-    const float Exy = Cd + dpxx + dpixx + dpww + dpiww;
-    const float Exz = Cd + dpxx + dpixx - dpww - dpiww;
+    const float Cp = Cd + dpxx + dpixx;
+    const float Pww = dpww + dpiww;
+    const float Exy = Cp + Pww;
+    const float Exz = Cp - Pww;
     const float Eyz = Cd - 2.0f * (dpxx + dpixx);
     const float Jx = djx + dqx, Jy = djy + dqy, Jz = djz + dqz;
     const float O7 = Jx + Jy + dmx - dmy;
@@ -448,33 +454,32 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     const float O12 = -Jx + Jz + dmx + dmz;
     const float O15 = Jy + Jz + dmy - dmz;
     const float O16 = -Jy + Jz - dmy - dmz;
-    f[7] += Exy + dpxy + O7;
-    f[10] += Exy + dpxy - O7;
-    f[8] += Exy - dpxy + O8;
-    f[9] += Exy - dpxy - O8;
-    f[11] += Exz + dpzx + O11;
-    f[14] += Exz + dpzx - O11;
-    f[12] += Exz - dpzx + O12;
-    f[13] += Exz - dpzx - O12;
-    f[15] += Eyz + dpyz + O15;
-    f[18] += Eyz + dpyz - O15;
-    f[16] += Eyz - dpyz + O16;
-    f[17] += Eyz - dpyz - O16;
+    const float Ea = Exy + dpxy, Eb = Exy - dpxy;
+    const float Ec = Exz + dpzx, Ed = Exz - dpzx;
+    const float Ee = Eyz + dpyz, Ef = Eyz - dpyz;
+    f[7] += Ea + O7;
+    f[10] += Ea - O7;
+    f[8] += Eb + O8;
+    f[9] += Eb - O8;
+    f[11] += Ec + O11;
+    f[14] += Ec - O11;
+    f[12] += Ed + O12;
+    f[13] += Ed - O12;
+    f[15] += Ee + O15;
+    f[18] += Ee - O15;
+    f[16] += Ef + O16;
+    f[17] += Ef - O16;
 
     // D3Q7: n = N g (Eq. 36), n_eq = T (sigma, u, varpi sigma, 0, 0) (Eq. 37), Eq. 34, Eq. 43
-    const float nxm = g[1] - g[2], nym = g[3] - g[4], nzm = g[5] - g[6];
-    const float n4 = ((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]);  // minus varpi sigma T0
-    const float n5 = (g[1] + g[2]) - (g[3] + g[4]);
-    const float n6 = (g[1] + g[2]) - (g[5] + g[6]);
-    const float dn1 = -md.zeta_alpha * (nxm - T * ux);
-    const float dn2 = -md.zeta_alpha * (nym - T * uy);
-    const float dn3 = -md.zeta_alpha * (nzm - T * uz);
-    const float dn4 = -p.zeta_e * (n4 - p.varpi * n0);
-    const float dn5 = -p.zeta_nu * n5;
-    const float dn6 = -p.zeta_nu * n6;
-    const float c4 = dn4 * (1.0f / 6.0f);
-    const float c5 = dn5 * (1.0f / 6.0f), c6 = dn6 * (1.0f / 6.0f);
-    g[0] -= dn4;
+    const float g12 = g[1] + g[2], g34 = g[3] + g[4], g56 = g[5] + g[6];
+    const float n4 = g12 + g34 + g56;  // minus varpi sigma T0
+    const float dn1 = md.zeta_alpha * (T * ux - (g[1] - g[2]));
+    const float dn2 = md.zeta_alpha * (T * uy - (g[3] - g[4]));
+    const float dn3 = md.zeta_alpha * (T * uz - (g[5] - g[6]));
+    const float c4 = p.ze6 * (p.varpi * n0 - n4);  // dn4 / 6
+    const float c5 = -p.zn6 * (g12 - g34);         // dn5 / 6
+    const float c6 = -p.zn6 * (g12 - g56);         // dn6 / 6
+    g[0] -= 6.0f * c4;
     const float gx = c4 + c5 + c6, gy = c4 - 2.0f * c5 + c6, gz = c4 + c5 - 2.0f * c6;
     g[1] += gx + 0.5f * dn1;
     g[2] += gx - 0.5f * dn1;
