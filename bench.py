@@ -48,6 +48,44 @@ def _config(extra=None):
     return cfg
 
 
+KERNEL_SOURCES = ("paper_1611_03329_gb300/csrc/lbm_kernels.cu",
+                  "paper_1611_03329_gb300/csrc/lbm_internal.cuh")
+TRAFFIC_PROFILE = "profiles/step_kernel_channel_256x64x64.md"
+
+
+def kernel_source_hash() -> str:
+    """SHA-256 over the step kernel's sources (ties a profile to the code it measured)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when
+    the kernel has changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        if ":" in line and line.split(":", 1)[0] in ("kernel_source_sha256", "dram_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return int(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -263,7 +301,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": _config({"parallelism": f"replicas{ws}" if ws > 1 else "single"}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
                      "kernel": "step_kernel<false,true> (fused stream-collide, outflow)"},
