@@ -29,20 +29,47 @@ if ROOT not in sys.path:
 METRIC = "MLUPS (D3Q19+D3Q7)"
 UNIT = "MLUPS"
 NX, NY, NZ = 256, 64, 64
-WORKLOAD = "porous mixed-convection channel 256x64x64, D3Q19+D3Q7 MRT, FP32"
+# Workloads: the headline channel, and the heterogeneous-porosity cavities of the precision
+# sweep (edge 128 or 256, Ra = 1e5, Da = 1e-2, mean porosity 0.6, Pr = 0.71).
+WORKLOADS = {
+    "channel": (256, 64, 64),
+    "cavity128": (128, 128, 128),
+    "cavity256": (256, 256, 256),
+}
 
 
-def _problem(nz=NZ):
-    from lbm_inputs import channel_problem
+def _problem(nz=None, storage="fp32", workload="channel"):
+    from lbm_inputs import cavity_problem, channel_problem, porosity_field
 
-    return channel_problem(NX, NY, nz)
+    nx, ny, nz0 = WORKLOADS[workload]
+    if workload == "channel":
+        return channel_problem(nx, ny, nz or nz0, storage=storage)
+    phi = porosity_field(nx, ny, nz0, seed=20161110).astype("float32")
+    return cavity_problem(nx, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71, phi_field=phi, phi_ref=0.6,
+                          storage=storage)
 
 
-def _config(extra=None):
-    cfg = {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "phi": 0.7, "Da": 1e-3,
-           "Re": 10, "Pr": 0.71, "Ri": 1.0, "u0": 0.01, "storage": "fp32-deviation",
-           "scheme": "ping-pong pull",
-           "l2": "inputs larger than L2: two population copies of 218 MB vs 126 MB L2, no flush"}
+def _workload_text(workload, storage):
+    nx, ny, nz = WORKLOADS[workload]
+    if workload == "channel":
+        return f"porous mixed-convection channel {nx}x{ny}x{nz}, D3Q19+D3Q7 MRT, {storage.upper()} storage"
+    return (f"porous natural-convection cavity {nx}^3 with seeded porosity field, D3Q19+D3Q7 MRT, "
+            f"{storage.upper()} storage")
+
+
+def _config(workload="channel", storage="fp32", extra=None):
+    nx, ny, nz = WORKLOADS[workload]
+    elem = 4 if storage == "fp32" else 2
+    state = 2 * 26 * elem * nx * ny * nz / 1e6
+    l2 = (f"inputs larger than L2: two population copies of {state:.0f} MB vs 126 MB L2, no flush"
+          if state > 2 * 126 else
+          f"two population copies of {state:.0f} MB, partly L2-resident (126 MB L2)")
+    cfg = {"workload": _workload_text(workload, storage), "nx": nx, "ny": ny, "nz": nz,
+           "storage": f"{storage}-deviation", "scheme": "ping-pong pull", "l2": l2}
+    if workload == "channel":
+        cfg.update({"phi": 0.7, "Da": 1e-3, "Re": 10, "Pr": 0.71, "Ri": 1.0, "u0": 0.01})
+    else:
+        cfg.update({"phi_mean": 0.6, "phi_std": 0.05, "Da": 1e-2, "Ra": 1e5, "Pr": 0.71})
     if extra:
         cfg.update(extra)
     return cfg
@@ -171,7 +198,7 @@ class ClockSampler:
 def _oracle_run(nz: int, steps: int, warmup: int):
     import oracle
 
-    lp = oracle.map_problem(_problem(nz))
+    lp = oracle.map_problem(_problem(nz))  # the channel, periodic in z
     o = oracle.Oracle(lp)
     if warmup:
         o.step(warmup)
@@ -211,7 +238,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config({"sample_nz": nz}),
+            "config": _config(extra={"sample_nz": nz}),
             "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -234,8 +261,9 @@ def run_ours(args):
     gb.build.build()
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    pb = _problem()
-    ns = NX * NY * NZ
+    pb = _problem(storage=args.storage, workload=args.workload)
+    wnx, wny, wnz = WORKLOADS[args.workload]
+    ns = wnx * wny * wnz
     with torch.cuda.stream(stream):
         lat = gb.Lattice(pb, stream=stream.cuda_stream)
         lat.step(args.warmup)
@@ -260,13 +288,13 @@ def run_ours(args):
         m_dev, h_dev = lat.sums()
 
         # ---- end to end through the host-buffer C ABI ----
-        n_e2e = max(1, min(args.steps, 50))
+        n_e2e = max(1, min(args.steps, 50 if args.workload == "channel" else 5))
         f, g = lat.populations()
         fp = torch.from_numpy(f).pin_memory().numpy()
         gp = torch.from_numpy(g).pin_memory().numpy()
-        rho_h = torch.empty((NZ, NY, NX), dtype=torch.float32).pin_memory().numpy()
-        u_h = torch.empty((3, NZ, NY, NX), dtype=torch.float32).pin_memory().numpy()
-        T_h = torch.empty((NZ, NY, NX), dtype=torch.float32).pin_memory().numpy()
+        rho_h = torch.empty((wnz, wny, wnx), dtype=torch.float32).pin_memory().numpy()
+        u_h = torch.empty((3, wnz, wny, wnx), dtype=torch.float32).pin_memory().numpy()
+        T_h = torch.empty((wnz, wny, wnx), dtype=torch.float32).pin_memory().numpy()
         for _ in range(3):
             lat.set_populations(fp, gp)
             lat.step(1)
@@ -294,17 +322,24 @@ def run_ours(args):
     bytes_site = gb.algorithmic_bytes_per_site(pb)
     kernel_ms = ms / args.steps  # one fused step kernel per time step
     achieved = bytes_site * ns / (kernel_ms * 1e-3) / 1e9
-    cpu = cpu_baseline() if (ws == 1 and not args.no_cpu_baseline) else None
+    cpu = (cpu_baseline() if (ws == 1 and not args.no_cpu_baseline and args.workload == "channel")
+           else None)
     line = {
         "metric": METRIC, "value": round(mlups, 2), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 6),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": _config({"parallelism": f"replicas{ws}" if ws > 1 else "single"}),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
+        "data": "synthetic",
+        "config": _config(args.workload, args.storage,
+                          {"parallelism": f"replicas{ws}" if ws > 1 else "single"}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                     "frac": round(achieved / peak, 4),
+                     "traffic": profiled_traffic() if (args.workload, args.storage) == ("channel", "fp32") else None,
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
-                     "kernel": "step_kernel<false,true> (fused stream-collide, outflow)"},
+                     "kernel": ("step_kernel<false,true> (fused stream-collide, outflow)"
+                                if args.workload == "channel" else
+                                "step_kernel<true,false> (fused stream-collide, porosity field)")},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_mlups, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(fp.nbytes + gp.nbytes),
@@ -329,6 +364,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", choices=("fp32", "fp16", "bf16"), default="fp32",
+                    help="population storage (the headline workload is fp32)")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="channel",
+                    help="the headline workload is the 256x64x64 channel")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -65,7 +65,12 @@ enum {
     LBM_MAP_LATTICE = 2  /* lattice units given directly (nu_e, alpha_f, gbeta) */
 };
 
-enum { LBM_STORE_FP32 = 0 }; /* populations stored as FP32 deviations from w_i rho0, w_i sigma T0 */
+/* Storage of the populations (arithmetic is FP32 in every case):
+ *  LBM_STORE_FP32     : FP32 deviations f_i - w_i rho0 and g_i - omega_i sigma T0 (208 B/site);
+ *  LBM_STORE_FP16_DEV : FP16 scaled deviations (f_i - w_i rho0) / w_i and
+ *                       (g_i - omega_i sigma T0) / omega_i, rounded to nearest (104 B/site);
+ *  LBM_STORE_BF16_DEV : the same in BF16 (104 B/site). */
+enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16_DEV = 1, LBM_STORE_BF16_DEV = 2 };
 
 /*
  * Problem statement (Sec. 2, Eqs. 1-7, and the problem setups of Sec. 4).  Fill it with
@@ -73,7 +78,7 @@ enum { LBM_STORE_FP32 = 0 }; /* populations stored as FP32 deviations from w_i r
  */
 typedef struct lbm_params {
     int nx, ny, nz;  /* lattice sites per axis, each >= 1 (>= 3 along x with an outflow) */
-    int storage;     /* LBM_STORE_FP32 */
+    int storage;     /* LBM_STORE_* */
     int mapping;     /* LBM_MAP_* */
     double L;        /* characteristic length in lattice units; <= 0: nx (cavity,
                         lattice) or ny (channel) -- the halfway walls make L = N */

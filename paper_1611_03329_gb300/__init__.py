@@ -24,6 +24,9 @@ FLOW_PERIODIC, FLOW_WALL, FLOW_VELOCITY, FLOW_OUTFLOW = range(4)
 HEAT_PERIODIC, HEAT_ADIABATIC, HEAT_DIRICHLET, HEAT_OUTFLOW = range(4)
 MAP_CAVITY, MAP_CHANNEL, MAP_LATTICE = range(3)
 _MAPPINGS = {"cavity": MAP_CAVITY, "channel": MAP_CHANNEL, "lattice": MAP_LATTICE}
+STORE_FP32, STORE_FP16_DEV, STORE_BF16_DEV = range(3)
+_STORAGE = {"fp32": STORE_FP32, "fp16": STORE_FP16_DEV, "bf16": STORE_BF16_DEV}
+STORAGE_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2}
 
 # Every symbol that include/lbm.h declares.
 ABI_SYMBOLS = (
@@ -153,6 +156,7 @@ def params_from_problem(pb: dict) -> LbmParams:
     lib().lbm_params_default(C.byref(p))
     p.nx, p.ny, p.nz = int(pb["nx"]), int(pb["ny"]), int(pb["nz"])
     p.mapping = _MAPPINGS[pb.get("mapping", "cavity")]
+    p.storage = _STORAGE[pb.get("storage", "fp32")]
     scalars = ("L", "Ra", "Pr", "J", "sigma", "Gamma", "Ma", "Re", "Ri", "u0", "dT", "T0",
                "rho0", "varpi", "s_e", "s_eps", "s_q", "s_pi", "s_m", "zeta_T", "zeta_e",
                "zeta_nu", "nu_e", "alpha_f", "gbeta", "T_init", "U_out")
@@ -335,9 +339,9 @@ def medium_args(pb: dict) -> dict:
 
 
 def algorithmic_bytes_per_site(pb: dict) -> int:
-    """Bytes one time step must move per site: 26 FP32 populations read and written, plus
-    the FP32 porosity of a heterogeneous medium."""
-    return 26 * 4 * 2 + (4 if pb.get("phi_field") is not None else 0)
+    """Bytes one time step must move per site: 26 populations read and written in the
+    storage format (4 or 2 bytes each), plus the FP32 porosity of a heterogeneous medium."""
+    return 26 * 2 * STORAGE_BYTES[pb.get("storage", "fp32")] + (4 if pb.get("phi_field") is not None else 0)
 
 
 def nan_safe(x: float) -> float:

@@ -21,8 +21,10 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     long long ns = 0, sq = 0, nyz = 0;
-    float* pop[2] = {nullptr, nullptr};   // ping-pong population copies, 26 planes each
+    void* pop[2] = {nullptr, nullptr};    // ping-pong population copies, 26 planes each
+    size_t elem = sizeof(float);          // bytes per stored population value
     float* hist[2] = {nullptr, nullptr};  // outflow history, 6 x ny*nz
+    float* tplane[2] = {nullptr, nullptr};  // T - T0 per site (16-bit formats only)
     int cur = 0;
     lbm::Planes pl[2];  // launch planes reading copy 0 / copy 1
     bool outflow = false;
@@ -33,7 +35,7 @@ struct lbm_ctx {
     double* profile = nullptr;   // Nusselt profile scratch
     double* dres = nullptr;      // small device results
     double* hres = nullptr;      // pinned host mirror of dres
-    double* stage = nullptr;     // FP64 staging, 4 x ns doubles (lazy)
+    double* stage = nullptr;     // FP64 staging, 7 x ns doubles (lazy)
     float* mac = nullptr;        // macro scratch, 9 x ns floats (lazy): two halves of (u, T)
                                  // and one rho plane; half `snap` holds the residual snapshot
     int snap = 0;
@@ -83,7 +85,9 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
     double ns = (double)p->nx * p->ny * p->nz;
     if (ns >= 2147483647.0) return "lattice too large (sites must fit in 31 bits)";
     if (p->nz > 65535) return "nz must be <= 65535 (one grid slice per z-plane)";
-    if (p->storage != LBM_STORE_FP32) return "unsupported storage";
+    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16_DEV &&
+        p->storage != LBM_STORE_BF16_DEV)
+        return "unknown storage format";
     if (!finite_pos(p->rho0)) return "rho0 must be > 0";
     if (!(p->varpi > 0.0 && p->varpi < 1.0)) return "varpi must lie in (0, 1)";
     if (!finite_pos(p->sigma)) return "sigma must be > 0";
@@ -270,6 +274,11 @@ void fill_kparams(lbm_ctx* c) {
     k.nz = p.nz;
     k.nyz = p.ny * p.nz;
     k.block_threads = c->block_threads;
+    k.storage = p.storage;
+    k.om0 = (float)(1.0 - L.varpi);
+    k.om1 = (float)(L.varpi / 6.0);
+    k.iom0 = (float)(1.0 / (1.0 - L.varpi));
+    k.iom1 = (float)(6.0 / L.varpi);
     k.ns = c->ns;
     k.sq = c->sq;
     for (int f = 0; f < 6; ++f) {
@@ -370,24 +379,30 @@ lbm_status usable(lbm_ctx* c) {
     return LBM_OK;
 }
 
-float* cur_pop(lbm_ctx* c) { return c->pop[c->cur]; }
 float* cur_hist(lbm_ctx* c) { return c->hist[c->cur]; }
+
+// Start of population plane q of copy k.
+void* plane_ptr(const lbm_ctx* c, int k, int q) {
+    return static_cast<char*>(c->pop[k]) + (size_t)q * (size_t)c->sq * c->elem;
+}
 
 // Planes of a step that reads copy `from` and writes the other copy.
 lbm::Planes planes(const lbm_ctx* c, int from) {
     lbm::Planes pl;
     const int to = from ^ 1;
     for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
-        pl.in[q] = c->pop[from] + (size_t)q * c->sq;
-        pl.out[q] = c->pop[to] + (size_t)q * c->sq;
+        pl.in[q] = plane_ptr(c, from, q);
+        pl.out[q] = plane_ptr(c, to, q);
     }
     pl.hin = c->hist[from];
     pl.hout = c->hist[to];
+    pl.tin = c->tplane[from];
+    pl.tout = c->tplane[to];
     return pl;
 }
 
 lbm_status ensure_stage(lbm_ctx* c) {
-    if (!c->stage) LBM_CUDA(cudaMalloc(&c->stage, sizeof(double) * 4 * (size_t)c->ns));
+    if (!c->stage) LBM_CUDA(cudaMalloc(&c->stage, sizeof(double) * 7 * (size_t)c->ns));
     return LBM_OK;
 }
 
@@ -398,13 +413,14 @@ lbm_status ensure_mac(lbm_ctx* c) {
 
 lbm_status reset_hist(lbm_ctx* c) {
     if (!c->outflow) return LBM_OK;
-    LBM_CUDA(lbm::launch_hist_reset(c->kp, cur_pop(c), cur_hist(c), c->stream));
+    LBM_CUDA(lbm::launch_hist_reset(c->kp, c->pl[c->cur], cur_hist(c), c->stream));
     return LBM_OK;
 }
 
 // Equilibrium state from device FP64 fields (or uniform values).
 lbm_status init_state(lbm_ctx* c, const double* T_dev, const double* u_dev, double T_uniform) {
-    LBM_CUDA(lbm::launch_init_eq(c->kp, cur_pop(c), T_dev, u_dev, T_uniform, c->stream));
+    // the equilibrium goes into the current copy: the planes that read copy `cur ^ 1` write it
+    LBM_CUDA(lbm::launch_init_eq(c->kp, c->pl[c->cur ^ 1], T_dev, u_dev, T_uniform, c->stream));
     lbm_status s = reset_hist(c);
     if (s != LBM_OK) return s;
     c->steps = 0;
@@ -428,6 +444,7 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     c->sq = (c->ns + 63) / 64 * 64;  // 256-byte aligned population planes
     c->nyz = (long long)p->ny * p->nz;
     c->outflow = p->flow_bc[1] == LBM_FLOW_OUTFLOW;
+    c->elem = p->storage == LBM_STORE_FP32 ? sizeof(float) : 2;
     if (const char* bt = std::getenv("LBM_BLOCK_THREADS")) {
         int v = std::atoi(bt);
         if (v == 32 || v == 64 || v == 128 || v == 256) c->block_threads = v;
@@ -446,13 +463,17 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamCreate");
         else c->own_stream = true;
     }
-    size_t pop_bytes = sizeof(float) * (size_t)(lbm::kQ + lbm::kQT) * (size_t)c->sq;
+    size_t pop_bytes = c->elem * (size_t)(lbm::kQ + lbm::kQT) * (size_t)c->sq;
     for (int k = 0; k < 2 && st == LBM_OK; ++k) {
         e = cudaMalloc(&c->pop[k], pop_bytes);
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(populations)");
         if (st == LBM_OK && c->outflow) {
             e = cudaMalloc(&c->hist[k], sizeof(float) * lbm::kOutSlots * (size_t)c->nyz);
             if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(outflow history)");
+        }
+        if (st == LBM_OK && p->storage != LBM_STORE_FP32) {
+            e = cudaMalloc(&c->tplane[k], sizeof(float) * (size_t)c->ns);
+            if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(temperature plane)");
         }
     }
     if (st == LBM_OK) {
@@ -489,6 +510,7 @@ void lbm_destroy(lbm_ctx* c) {
     for (int k = 0; k < 2; ++k) {
         cudaFree(c->pop[k]);
         cudaFree(c->hist[k]);
+        cudaFree(c->tplane[k]);
     }
     cudaFree(c->phi_dev);
     cudaFree(c->partials);
@@ -590,6 +612,14 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* T_field, const double*
     return LBM_OK;
 }
 
+// Weight that multiplies a stored value of plane q: 1 for FP32, w_i or omega_i for 16 bits.
+static double plane_scale(const lbm_ctx* c, int q) {
+    if (c->prm.storage == LBM_STORE_FP32) return 1.0;
+    const lbm_lattice& L = c->lat;
+    if (q < lbm::kQ) return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    return q == lbm::kQ ? 1.0 - L.varpi : L.varpi / 6.0;
+}
+
 static double plane_offset(const lbm_ctx* c, int q) {
     // w_i rho0 for the D3Q19 planes (weights under Eq. 24), omega_i sigma T0 for D3Q7 (Eq. 42)
     const lbm_lattice& L = c->lat;
@@ -607,14 +637,20 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
     if (st != LBM_OK) return st;
     if (!f || !g) return fail(c, LBM_EINVAL, "f and g are required");
     if ((st = ensure_stage(c)) != LBM_OK) return st;
-    float* pop = cur_pop(c);
-    for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
+    const bool tshift = c->prm.storage != LBM_STORE_FP32;  // D3Q7 stored against local T
+    const int nq = tshift ? lbm::kQ : lbm::kQ + lbm::kQT;
+    for (int q = 0; q < nq; ++q) {
         const double* src = q < lbm::kQ ? f + (size_t)q * c->ns : g + (size_t)(q - lbm::kQ) * c->ns;
         double* stg = c->stage + (size_t)(q & 3) * c->ns;  // rotate 4 staging planes
         LBM_CUDA(cudaMemcpyAsync(stg, src, sizeof(double) * c->ns, cudaMemcpyHostToDevice,
                                  c->stream));
-        LBM_CUDA(lbm::launch_plane_to_dev(stg, pop + (size_t)q * c->sq, plane_offset(c, q), c->ns,
-                                          c->stream));
+        LBM_CUDA(lbm::launch_plane_to_dev(c->prm.storage, stg, plane_ptr(c, c->cur, q),
+                                          plane_offset(c, q), plane_scale(c, q), c->ns, c->stream));
+    }
+    if (tshift) {
+        LBM_CUDA(cudaMemcpyAsync(c->stage, g, sizeof(double) * lbm::kQT * c->ns,
+                                 cudaMemcpyHostToDevice, c->stream));
+        LBM_CUDA(lbm::launch_g_to_dev(c->kp, c->pl[c->cur ^ 1], c->stage, c->stream));
     }
     if ((st = reset_hist(c)) != LBM_OK) return st;
     c->have_prev = false;
@@ -626,16 +662,24 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if ((st = ensure_stage(c)) != LBM_OK) return st;
-    const float* pop = cur_pop(c);
-    for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
+    const bool tshift = c->prm.storage != LBM_STORE_FP32;
+    const int nq = tshift ? lbm::kQ : lbm::kQ + lbm::kQT;
+    for (int q = 0; q < nq; ++q) {
         double* dst = q < lbm::kQ ? (f ? f + (size_t)q * c->ns : nullptr)
                                   : (g ? g + (size_t)(q - lbm::kQ) * c->ns : nullptr);
         if (!dst) continue;
         double* stg = c->stage + (size_t)(q & 3) * c->ns;
-        LBM_CUDA(lbm::launch_plane_to_host(pop + (size_t)q * c->sq, stg, plane_offset(c, q), c->ns,
-                                           c->stream));
+        LBM_CUDA(lbm::launch_plane_to_host(c->prm.storage, plane_ptr(c, c->cur, q), stg,
+                                           plane_offset(c, q), plane_scale(c, q), c->ns, c->stream));
         LBM_CUDA(cudaMemcpyAsync(dst, stg, sizeof(double) * c->ns, cudaMemcpyDeviceToHost,
                                  c->stream));
+    }
+    if (tshift && g) {
+        // the FP64 planes must not be overwritten while an f copy above is in flight: the
+        // stream orders the kernel after those copies
+        LBM_CUDA(lbm::launch_g_to_host(c->kp, c->pl[c->cur], c->stage, c->stream));
+        LBM_CUDA(cudaMemcpyAsync(g, c->stage, sizeof(double) * lbm::kQT * c->ns,
+                                 cudaMemcpyDeviceToHost, c->stream));
     }
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     return LBM_OK;
@@ -697,7 +741,7 @@ lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     int nr = lbm::reduction_blocks();
-    LBM_CUDA(lbm::launch_sums(c->kp, cur_pop(c), c->partials, nr, c->dres, c->stream));
+    LBM_CUDA(lbm::launch_sums(c->kp, c->pl[c->cur], c->partials, nr, c->dres, c->stream));
     LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 2, cudaMemcpyDeviceToHost,
                              c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));

@@ -17,6 +17,8 @@ constexpr int kStepMinBlocks = 4;  // resident blocks per SM the step kernel is 
 struct KParams {
     int nx, ny, nz;
     int nyz;        // ny * nz (outflow history plane)
+    int storage;    // 0 FP32, 1 FP16, 2 BF16 (LBM_STORE_*)
+    float om0, om1, iom0, iom1;  // D3Q7 weights omega_0, omega_1..6 and their inverses
     int block_threads;  // threads per block of the site kernels (host launch setting)
     long long ns;   // sites
     long long sq;   // elements between consecutive population planes (>= ns, padded)
@@ -55,25 +57,34 @@ struct KParams {
 // Population planes of one launch: the 26 planes read (in) and written (out) and the outflow
 // history read (hin) and written (hout).
 struct Planes {
-    const float* in[kQ + kQT];
-    float* out[kQ + kQT];
+    const void* in[kQ + kQT];  // element type given by KParams::storage
+    void* out[kQ + kQT];
     const float* hin;
     float* hout;
+    const float* tin;  // T - T0 per site (16-bit formats only): planes in / out
+    float* tout;
 };
 
 // Launch wrappers (defined in lbm_kernels.cu).  All are asynchronous on `st`.
 cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st);
 cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,
                           float* T, cudaStream_t st);
-cudaError_t launch_init_eq(const KParams& p, float* pop, const double* T_field,
+// Equilibrium state written into pl.out.
+cudaError_t launch_init_eq(const KParams& p, const Planes& pl, const double* T_field,
                            const double* u_field, double T_uniform, cudaStream_t st);
-cudaError_t launch_plane_to_dev(const double* src, float* dst, double offset, long long n,
-                                cudaStream_t st);
-cudaError_t launch_plane_to_host(const float* src, double* dst, double offset, long long n,
-                                 cudaStream_t st);
-cudaError_t launch_hist_reset(const KParams& p, const float* pop, float* hist, cudaStream_t st);
-// FP64 totals of the stored deviations: out[0] = sum f', out[1] = sum g'.
-cudaError_t launch_sums(const KParams& p, const float* pop, double* partials, int nparts,
+// One plane between FP64 full values and the storage format: stored = (v - offset) / scale.
+cudaError_t launch_plane_to_dev(int storage, const double* src, void* dst, double offset,
+                                double scale, long long n, cudaStream_t st);
+cudaError_t launch_plane_to_host(int storage, const void* src, double* dst, double offset,
+                                 double scale, long long n, cudaStream_t st);
+// D3Q7 planes of a 16-bit format (with its temperature plane) from / to 7 x ns FP64 full
+// values in device memory.
+cudaError_t launch_g_to_dev(const KParams& p, const Planes& pl, const double* src, cudaStream_t st);
+cudaError_t launch_g_to_host(const KParams& p, const Planes& pl, double* dst, cudaStream_t st);
+// Outflow history from the planes pl.in.
+cudaError_t launch_hist_reset(const KParams& p, const Planes& pl, float* hist, cudaStream_t st);
+// FP64 totals of the deviations in pl.in: out[0] = sum f', out[1] = sum g'.
+cudaError_t launch_sums(const KParams& p, const Planes& pl, double* partials, int nparts,
                         double* out, cudaStream_t st);
 // Nusselt profile and its mean / centre value: out[0] = Nu_3D, out[1] = Nu_mp.
 cudaError_t launch_nusselt(const KParams& p, bool outflow, const Planes& pl, int face, double Tw,

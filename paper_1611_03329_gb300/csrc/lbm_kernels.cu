@@ -13,6 +13,8 @@
 // 3D grid (x fastest, one z-plane per grid slice) so that no index division is needed; a
 // warp whose 32 sites are all interior takes unconditional loads, any other warp takes the
 // predicated boundary path.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -58,6 +60,77 @@ __host__ __device__ constexpr int opp7(int i) { return i == 0 ? 0 : ((i & 1) ? i
 
 static_assert(opp19(7) == 10 && opp19(8) == 9 && opp19(12) == 13 && opp19(16) == 17, "opp19");
 static_assert(ex19(opp19(13)) == -ex19(13) && ez19(opp19(13)) == -ez19(13), "opp19 sign");
+
+// ---- population storage ------------------------------------------------------------------
+// FP32 planes hold the deviation f - w_i rho0 (g - omega_i sigma T0) itself; the 16-bit
+// formats hold it divided by the weight, (f - w_i rho0) / w_i and (g - omega_i sigma T0) /
+// omega_i, so that every plane carries values of the order of the Mach number.  Arithmetic is
+// FP32 in every case; 16-bit values are rounded to nearest on store.
+struct StoreF32 {
+    using T = float;
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float ld(const T* q) { return __ldg(q); }
+    static __device__ __forceinline__ void st(T* q, float v) { *q = v; }
+};
+struct StoreF16 {
+    using T = __half;
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float ld(const T* q) { return __half2float(__ldg(q)); }
+    static __device__ __forceinline__ void st(T* q, float v) { *q = __float2half_rn(v); }
+};
+struct StoreBF16 {
+    using T = __nv_bfloat16;
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float ld(const T* q) { return __bfloat162float(__ldg(q)); }
+    static __device__ __forceinline__ void st(T* q, float v) { *q = __float2bfloat16_rn(v); }
+};
+
+// Weight that multiplies the stored value of plane q (q < 19: f, else g).
+template <class S>
+__device__ __forceinline__ float plane_scale(const KParams& p, int q) {
+    if constexpr (!S::kScaled) return 1.0f;
+    else return q < kQ ? w19(q) : (q == kQ ? p.om0 : p.om1);
+}
+template <class S>
+__device__ __forceinline__ float plane_inv_scale(const KParams& p, int q) {
+    if constexpr (!S::kScaled) return 1.0f;
+    else return q < kQ ? 1.0f / w19(q) : (q == kQ ? p.iom0 : p.iom1);
+}
+// Deviation of plane q at site index idx of the planes being read / written.
+template <class S>
+__device__ __forceinline__ float ldp(const Planes& pl, const KParams& p, int q, int idx) {
+    return S::ld(static_cast<const typename S::T*>(pl.in[q]) + idx) * plane_scale<S>(p, q);
+}
+template <class S>
+__device__ __forceinline__ void stp(const Planes& pl, const KParams& p, int q, int idx, float v) {
+    S::st(static_cast<typename S::T*>(pl.out[q]) + idx, v * plane_inv_scale<S>(p, q));
+}
+// D3Q7 population i at site idx as the deviation g_i - omega_i sigma T0.  The 16-bit formats
+// store (g_i - omega_i sigma T_x) / omega_i against the site's own temperature T_x, whose
+// deviation T_x - T0 sits in an FP32 plane (tin / tout): thermal populations are then of the
+// order of T u / c_sT^2 instead of T - T0, and keep their precision.
+template <class S>
+__device__ __forceinline__ float ldg_dev(const Planes& pl, const KParams& p, int i, int idx) {
+    if constexpr (!S::kScaled) {
+        return ldp<S>(pl, p, kQ + i, idx);
+    } else {
+        const float sc = i == 0 ? p.om0 : p.om1;
+        return sc * (S::ld(static_cast<const typename S::T*>(pl.in[kQ + i]) + idx) +
+                     p.sigma * __ldg(pl.tin + idx));
+    }
+}
+// Stores post-collision g' (deviation from omega_i sigma T0) of a site whose temperature
+// deviation is dT.
+template <class S>
+__device__ __forceinline__ void stg_dev(const Planes& pl, const KParams& p, int i, int idx, float v,
+                                        float dT) {
+    if constexpr (!S::kScaled) {
+        stp<S>(pl, p, kQ + i, idx, v);
+    } else {
+        const float isc = i == 0 ? p.iom0 : p.iom1;
+        S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + idx, v * isc - p.sigma * dT);
+    }
+}
 
 // ---- site and neighbourhood ----------------------------------------------------------------
 // A site with the offsets (in sites) of its six axis neighbours' sources and the faces that
@@ -137,15 +210,15 @@ __device__ __forceinline__ Medium medium_at(const KParams& p, int s) {
 // ---- streaming with boundary rules ------------------------------------------------------------
 // Pull of f_I at site n: the post-collision population at x - e_I, or the wall rule when that
 // source lies outside (a no-slip wall wins over a velocity face, which wins over the outflow).
-template <int I, bool OUTF>
+template <int I, bool OUTF, class S>
 __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, const Nbr& n,
                                         bool* via) {
     constexpr int ex = ex19(I), ey = ey19(I), ez = ez19(I);
     const int oyz = axis_off(ey, n.ym, n.yp) + axis_off(ez, n.zm, n.zp);
     const unsigned cyz = axis_cross(ey, n.cross, 4u, 8u) | axis_cross(ez, n.cross, 16u, 32u);
     const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | cyz;
-    if (cr == 0u) return __ldg(pl.in[I] + n.s + axis_off(ex, n.xm, n.xp) + oyz);
-    const float bb = __ldg(pl.in[opp19(I)] + n.s);
+    if (cr == 0u) return ldp<S>(pl, p, I, n.s + axis_off(ex, n.xm, n.xp) + oyz);
+    const float bb = ldp<S>(pl, p, opp19(I), n.s);
     if (cr & p.wall_mask) return bb;
     unsigned vm = cr & p.vel_mask;
     if (vm) {
@@ -160,9 +233,9 @@ __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, cons
         *via = true;
         float inner;
         if (cyz == 0u) {
-            inner = __ldg(pl.in[I] + n.s + oyz);  // source of x-1 along -x is x itself
+            inner = ldp<S>(pl, p, I, n.s + oyz);  // source of x-1 along -x is x itself
         } else {
-            inner = __ldg(pl.in[opp19(I)] + n.s - 1);
+            inner = ldp<S>(pl, p, opp19(I), n.s - 1);
             unsigned vmi = cyz & p.vel_mask;
             if (!(cyz & p.wall_mask) && vmi) {
                 int face = __ffs(vmi) - 1;
@@ -177,21 +250,21 @@ __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, cons
     return bb;  // not reached for validated boundary sets
 }
 
-template <int I, bool OUTF>
+template <int I, bool OUTF, class S>
 __device__ __forceinline__ float pull_g(const Planes& pl, const KParams& p, const Nbr& n) {
     constexpr int ex = ex7(I), ey = ey7(I), ez = ez7(I);
     const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
                         axis_cross(ez, n.cross, 16u, 32u);
     if (cr == 0u)
-        return __ldg(pl.in[kQ + I] + n.s + axis_off(ex, n.xm, n.xp) + axis_off(ey, n.ym, n.yp) +
+        return ldg_dev<S>(pl, p, I, n.s + axis_off(ex, n.xm, n.xp) + axis_off(ey, n.ym, n.yp) +
                      axis_off(ez, n.zm, n.zp));
-    const float bb = __ldg(pl.in[kQ + opp7(I)] + n.s);
+    const float bb = ldg_dev<S>(pl, p, opp7(I), n.s);
     const int face = __ffs(cr) - 1;  // a D3Q7 velocity crosses one face at most
     const int kind = p.heat_kind[face];
     if (kind == 2) return -bb + p.heat_abb[face];  // Dirichlet: anti-bounce-back
     if constexpr (OUTF && ex == -1) {
         if (kind == 3) {
-            float inner = __ldg(pl.in[kQ + I] + n.s);  // g_I(N-2, t+1) = g*_I(N-1, t)
+            float inner = ldg_dev<S>(pl, p, I, n.s);  // g_I(N-2, t+1) = g*_I(N-1, t)
             float old = __ldg(pl.hin + 5 * p.nyz + n.y + p.ny * n.z);
             return p.out_a * old + p.out_b * inner;
         }
@@ -199,28 +272,28 @@ __device__ __forceinline__ float pull_g(const Planes& pl, const KParams& p, cons
     return bb;  // adiabatic: bounce-back
 }
 
-template <bool OUTF, int... I>
+template <bool OUTF, class S, int... I>
 __device__ __forceinline__ void gather_f_bc(float* f, bool* via, const Planes& pl,
                                             const KParams& p, const Nbr& n,
                                             std::integer_sequence<int, I...>) {
-    ((f[I] = pull_f<I, OUTF>(pl, p, n, &via[I])), ...);
+    ((f[I] = pull_f<I, OUTF, S>(pl, p, n, &via[I])), ...);
 }
 
-template <bool OUTF, int... I>
+template <bool OUTF, class S, int... I>
 __device__ __forceinline__ void gather_g_bc(float* g, const Planes& pl, const KParams& p,
                                             const Nbr& n, std::integer_sequence<int, I...>) {
-    ((g[I] = pull_g<I, OUTF>(pl, p, n)), ...);
+    ((g[I] = pull_g<I, OUTF, S>(pl, p, n)), ...);
 }
 
 // Predicated pull of all 26 populations (any site), with the outflow's pressure anchor.
-template <bool OUTF>
+template <bool OUTF, class S>
 __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& p, const Nbr& n,
                                                float* f, float* g) {
     bool via[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) via[i] = false;
-    gather_f_bc<OUTF>(f, via, pl, p, n, std::make_integer_sequence<int, kQ>{});
-    gather_g_bc<OUTF>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
+    gather_f_bc<OUTF, S>(f, via, pl, p, n, std::make_integer_sequence<int, kQ>{});
+    gather_g_bc<OUTF, S>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
     if (OUTF && n.x == p.nx - 1) {
         // pressure anchor: shift the populations set by the outflow rule by
         // w_i (rho0 - rho) / sum(w_i) so that the outlet density is rho0
@@ -243,7 +316,7 @@ __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& 
 // rule): unconditional loads with per-lane x offsets, then, only in a warp that holds an
 // x-face site, the x-face rule for the velocities that cross it.  With no x-face lane this is
 // the interior path.
-template <bool OUTF>
+template <bool OUTF, class S>
 __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
                                                    int z, int s, float* f, float* g) {
     const int nx = p.nx, nxy = p.nx * p.ny;
@@ -253,10 +326,10 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
     if (x == nx - 1) { if (p.per_mask & 2u) xp = 1 - nx; else { xp = 0; cxp = true; } }
 #pragma unroll
     for (int i = 0; i < kQ; ++i)
-        f[i] = __ldg(pl.in[i] + s + axis_off(ex19(i), xm, xp) - (ey19(i) * nx + ez19(i) * nxy));
+        f[i] = ldp<S>(pl, p, i, s + axis_off(ex19(i), xm, xp) - (ey19(i) * nx + ez19(i) * nxy));
 #pragma unroll
     for (int i = 0; i < kQT; ++i)
-        g[i] = __ldg(pl.in[kQ + i] + s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
+        g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
     if (!__any_sync(0xffffffffu, cxm || cxp)) return;  // interior warp
     if (cxm) {
         // x-low face: wall or velocity face (an outflow is only allowed on x-high)
@@ -264,13 +337,13 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             if (ex19(i) != 1) continue;
-            float v = __ldg(pl.in[opp19(i)] + s);
+            float v = ldp<S>(pl, p, opp19(i), s);
             if (vel)
                 v += 6.0f * w19(i) * p.rho0 *
                      (p.face_u[0][0] + (float)ey19(i) * p.face_u[0][1] + (float)ez19(i) * p.face_u[0][2]);
             f[i] = v;
         }
-        const float bb = __ldg(pl.in[kQ + 2] + s);
+        const float bb = ldg_dev<S>(pl, p, 2, s);
         g[1] = p.heat_kind[0] == 2 ? -bb + p.heat_abb[0] : bb;
     }
     if (cxp) {
@@ -279,7 +352,7 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
                 if (ex19(i) != -1) continue;
-                float v = __ldg(pl.in[opp19(i)] + s);
+                float v = ldp<S>(pl, p, opp19(i), s);
                 if (vel && !wall)
                     v += 6.0f * w19(i) * p.rho0 *
                          (-p.face_u[1][0] + (float)ey19(i) * p.face_u[1][1] +
@@ -293,7 +366,7 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
                 if (ex19(i) != -1) continue;
-                float inner = __ldg(pl.in[i] + s - (ey19(i) * nx + ez19(i) * nxy));
+                float inner = ldp<S>(pl, p, i, s - (ey19(i) * nx + ez19(i) * nxy));
                 float old = __ldg(pl.hin + slot19(i) * p.nyz + yz);
                 f[i] = p.out_a * old + p.out_b * inner;
             }
@@ -305,12 +378,12 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
             for (int i = 0; i < kQ; ++i)
                 if (ex19(i) == -1) f[i] += w19(i) * corr;
         }
-        const float bb = __ldg(pl.in[kQ + 1] + s);
+        const float bb = ldg_dev<S>(pl, p, 1, s);
         const int kind = p.heat_kind[1];
         if (kind == 2) {
             g[2] = -bb + p.heat_abb[1];
         } else if (OUTF && kind == 3) {
-            float inner = __ldg(pl.in[kQ + 2] + s);
+            float inner = ldg_dev<S>(pl, p, 2, s);
             float old = __ldg(pl.hin + 5 * p.nyz + y + p.ny * z);
             g[2] = p.out_a * old + p.out_b * inner;
         } else {
@@ -321,7 +394,7 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
 
 // ---- collision -------------------------------------------------------------------------------
 struct Macro {
-    float rho, ux, uy, uz, T;
+    float rho, ux, uy, uz, T, dT;  // dT = T - T0
 };
 
 // sqrt of a non-negative value through the hardware reciprocal square root (exact zero kept).
@@ -373,6 +446,7 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     mac.uy = uy;
     mac.uz = uz;
     mac.T = T;
+    mac.dT = dT;
     if (!FULL) return mac;
 
     const float umag = vmag * inv_den;  // |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|))
@@ -493,7 +567,7 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 // ---- kernels ---------------------------------------------------------------------------------
 // 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
 // blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
-template <bool HET, bool OUTF>
+template <bool HET, bool OUTF, class S>
 __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -506,10 +580,10 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
     if (warp_yz_in) {
-        gather_yz_interior<OUTF>(pl, p, x, y, z, s, f, g);
+        gather_yz_interior<OUTF, S>(pl, p, x, y, z, s, f, g);
     } else {
         const Nbr n = neighbourhood(p, x, y, z);
-        gather_general<OUTF>(pl, p, n, f, g);
+        gather_general<OUTF, S>(pl, p, n, f, g);
     }
     if (OUTF && x == p.nx - 1) {
         const int yz = y + p.ny * z;
@@ -521,12 +595,15 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
         pl.hout[5 * p.nyz + yz] = g[2];
     }
     const Medium md = medium_at<HET>(p, s);
-    collide<true>(p, md, f, g);
+    const Macro m = collide<true>(p, md, f, g);
 #pragma unroll
-    for (int i = 0; i < kQ + kQT; ++i) pl.out[i][s] = i < kQ ? f[i] : g[i - kQ];
+    for (int i = 0; i < kQ; ++i) stp<S>(pl, p, i, s, f[i]);
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, g[i], m.dT);
+    if constexpr (S::kScaled) pl.tout[s] = m.dT;
 }
 
-template <bool HET, bool OUTF>
+template <bool HET, bool OUTF, class S>
 __global__ void __launch_bounds__(kBlock)
     macros_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                   float* __restrict__ rho, float* __restrict__ u, float* __restrict__ T) {
@@ -536,7 +613,7 @@ __global__ void __launch_bounds__(kBlock)
     if (x >= p.nx || y >= p.ny) return;
     const Nbr n = neighbourhood(p, x, y, z);
     float f[kQ], g[kQT];
-    gather_general<OUTF>(pl, p, n, f, g);
+    gather_general<OUTF, S>(pl, p, n, f, g);
     const Medium md = medium_at<HET>(p, n.s);
     Macro m = collide<false>(p, md, f, g);
     const long long s = n.s;
@@ -549,8 +626,10 @@ __global__ void __launch_bounds__(kBlock)
     if (T) T[s] = m.T;
 }
 
-// Equilibrium state (Eqs. 24 and 42) with rho = rho0, in FP64, stored as FP32 deviations.
-__global__ void init_eq_kernel(const __grid_constant__ KParams p, float* __restrict__ pop,
+// Equilibrium state (Eqs. 24 and 42) with rho = rho0, computed in FP64 and stored once
+// rounded in the storage format (deviations, see the storage section above).
+template <class S>
+__global__ void init_eq_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                                const double* __restrict__ T_field,
                                const double* __restrict__ u_field, double T_uniform) {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,45 +647,93 @@ __global__ void init_eq_kernel(const __grid_constant__ KParams p, float* __restr
     for (int i = 0; i < kQ; ++i) {
         double eu = ex19(i) * ux + ey19(i) * uy + ez19(i) * uz;
         double w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-        double dev = w * rho0 * (3.0 * eu + 4.5 * eu * eu / phi - 1.5 * usq / phi);
-        pop[(long long)i * p.sq + s] = (float)dev;
+        double rel = rho0 * (3.0 * eu + 4.5 * eu * eu / phi - 1.5 * usq / phi);  // dev / w
+        S::st(static_cast<typename S::T*>(pl.out[i]) + s, (float)(S::kScaled ? rel : w * rel));
     }
     double varpi = p.varpi, sigma = p.sigma, T0 = p.T0, csT2 = varpi / 3.0;
 #pragma unroll
     for (int i = 0; i < kQT; ++i) {
         double om = i == 0 ? 1.0 - varpi : varpi / 6.0;
         double eu = ex7(i) * ux + ey7(i) * uy + ez7(i) * uz;
-        double dev = om * (sigma * (T - T0) + T * eu / csT2);
-        pop[(long long)(kQ + i) * p.sq + s] = (float)dev;
+        if (S::kScaled)  // (g_eq - omega sigma T) / omega
+            S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + s, (float)(T * eu / csT2));
+        else  // g_eq - omega sigma T0
+            S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + s,
+                  (float)(om * (sigma * (T - T0) + T * eu / csT2)));
+    }
+    if (S::kScaled) pl.tout[s] = (float)(T - T0);
+}
+
+// Host FP64 D3Q7 planes (full values, 7 x n) -> stored planes of a format with a temperature
+// plane: T_x - T0 = sum_i g_i / sigma - T0, stored_i = g_i / omega_i - sigma T_x.
+template <class S>
+__global__ void g_to_dev_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
+                                const double* __restrict__ src, long long n) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        double sum = 0.0;
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) sum += src[i * n + k];
+        const double T = sum / p.sigma;
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) {
+            const double om = i == 0 ? (double)p.om0 : (double)p.om1;
+            S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + k,
+                  (float)(src[i * n + k] / om - p.sigma * T));
+        }
+        pl.tout[k] = (float)(T - p.T0);
     }
 }
 
-__global__ void plane_to_dev_kernel(const double* __restrict__ src, float* __restrict__ dst,
-                                    double offset, long long n) {
+// Stored D3Q7 planes of a format with a temperature plane -> host FP64 full values.
+template <class S>
+__global__ void g_to_host_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
+                                 double* __restrict__ dst, long long n) {
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x)
-        dst[k] = (float)(src[k] - offset);
+         k += (long long)gridDim.x * blockDim.x) {
+        const double T = (double)pl.tin[k] + p.T0;
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) {
+            const double om = i == 0 ? (double)p.om0 : (double)p.om1;
+            const double v = S::ld(static_cast<const typename S::T*>(pl.in[kQ + i]) + k);
+            dst[i * n + k] = om * (v + p.sigma * T);
+        }
+    }
 }
 
-__global__ void plane_to_host_kernel(const float* __restrict__ src, double* __restrict__ dst,
-                                     double offset, long long n) {
+// Host FP64 population plane (full values) -> stored plane: (v - offset) / scale.
+template <class S>
+__global__ void plane_to_dev_kernel(const double* __restrict__ src, void* __restrict__ dst,
+                                    double offset, double inv_scale, long long n) {
+    typename S::T* d = static_cast<typename S::T*>(dst);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x)
-        dst[k] = (double)src[k] + offset;
+        S::st(d + k, (float)((src[k] - offset) * inv_scale));
 }
 
-__global__ void hist_reset_kernel(const __grid_constant__ KParams p, const float* __restrict__ pop,
+// Stored plane -> FP64 full values: v * scale + offset.
+template <class S>
+__global__ void plane_to_host_kernel(const void* __restrict__ src, double* __restrict__ dst,
+                                     double offset, double scale, long long n) {
+    const typename S::T* q = static_cast<const typename S::T*>(src);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        dst[k] = (double)S::ld(q + k) * scale + offset;
+}
+
+template <class S>
+__global__ void hist_reset_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                                   float* __restrict__ hist) {
-    long long nyz = (long long)p.ny * p.nz;
-    long long yz = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nyz = p.ny * p.nz;
+    const int yz = blockIdx.x * blockDim.x + threadIdx.x;
     if (yz >= nyz) return;
-    long long s = (long long)(p.nx - 1) + (long long)p.nx * yz;
-    hist[0 * nyz + yz] = pop[2LL * p.sq + s];
-    hist[1 * nyz + yz] = pop[8LL * p.sq + s];
-    hist[2 * nyz + yz] = pop[10LL * p.sq + s];
-    hist[3 * nyz + yz] = pop[12LL * p.sq + s];
-    hist[4 * nyz + yz] = pop[14LL * p.sq + s];
-    hist[5 * nyz + yz] = pop[(long long)(kQ + 2) * p.sq + s];
+    const int s = (p.nx - 1) + p.nx * yz;
+    hist[0 * nyz + yz] = ldp<S>(pl, p, 2, s);
+    hist[1 * nyz + yz] = ldp<S>(pl, p, 8, s);
+    hist[2 * nyz + yz] = ldp<S>(pl, p, 10, s);
+    hist[3 * nyz + yz] = ldp<S>(pl, p, 12, s);
+    hist[4 * nyz + yz] = ldp<S>(pl, p, 14, s);
+    hist[5 * nyz + yz] = ldg_dev<S>(pl, p, 2, s);
 }
 
 // ---- FP64 reductions ---------------------------------------------------------------------------
@@ -635,16 +762,16 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
     }
 }
 
+template <class S>
 __global__ void __launch_bounds__(kRedThreads)
-    sums_kernel(const __grid_constant__ KParams p, const float* __restrict__ pop,
+    sums_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                 double* __restrict__ partials) {
     double v[2] = {0.0, 0.0};
-    for (long long s = (long long)blockIdx.x * kRedThreads + threadIdx.x; s < p.ns;
-         s += (long long)gridDim.x * kRedThreads) {
+    for (int s = blockIdx.x * kRedThreads + threadIdx.x; s < p.ns; s += gridDim.x * kRedThreads) {
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) v[0] += (double)pop[(long long)i * p.sq + s];
+        for (int i = 0; i < kQ; ++i) v[0] += (double)ldp<S>(pl, p, i, s);
 #pragma unroll
-        for (int i = 0; i < kQT; ++i) v[1] += (double)pop[(long long)(kQ + i) * p.sq + s];
+        for (int i = 0; i < kQT; ++i) v[1] += (double)ldg_dev<S>(pl, p, i, s);
     }
     block_reduce_store<2>(v, partials + 2 * blockIdx.x);
 }
@@ -684,19 +811,19 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 // Temperature at a site from the streamed D3Q7 populations (Eq. 39).
-template <bool OUTF>
+template <bool OUTF, class S>
 __device__ __forceinline__ double temperature_at(const Planes& pl, const KParams& p, int x, int y,
                                                  int z) {
     const Nbr n = neighbourhood(p, x, y, z);
     float g[kQT];
-    gather_g_bc<OUTF>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
+    gather_g_bc<OUTF, S>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
     float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
     return (double)p.T0 + (double)n0 * (double)p.inv_sigma;
 }
 
 // One block per entry of the Nusselt profile (first tangential axis); threads average the
 // local Nusselt number of Eq. 53 over the second tangential axis (Eq. 54).
-template <bool OUTF>
+template <bool OUTF, class S>
 __global__ void __launch_bounds__(kRedThreads)
     nusselt_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                    int face, double Tw, double scale, double* __restrict__ profile) {
@@ -712,8 +839,8 @@ __global__ void __launch_bounds__(kRedThreads)
         c0[t2] = c1[t2] = k;
         c0[axis] = hi ? n[axis] - 1 : 0;
         c1[axis] = hi ? n[axis] - 2 : 1;
-        double T0 = temperature_at<OUTF>(pl, p, c0[0], c0[1], c0[2]);
-        double T1 = temperature_at<OUTF>(pl, p, c1[0], c1[1], c1[2]);
+        double T0 = temperature_at<OUTF, S>(pl, p, c0[0], c0[1], c0[2]);
+        double T1 = temperature_at<OUTF, S>(pl, p, c1[0], c1[1], c1[2]);
         v[0] += (8.0 * Tw - 9.0 * T0 + T1) / 3.0 * scale;
     }
     double out[1];
@@ -742,11 +869,6 @@ inline unsigned blocks_for(long long n, int threads) {
     return (unsigned)((n + threads - 1) / threads);
 }
 
-}  // namespace
-
-// ---- launch wrappers ---------------------------------------------------------------------------
-int reduction_blocks() { return kRedBlocks; }
-
 // Block of p.block_threads (32..kBlock) threads: blockDim.x = the smallest power of two >= nx
 // within that size, the rest along y.
 void site_grid(const KParams& p, dim3* grid, dim3* block) {
@@ -758,78 +880,131 @@ void site_grid(const KParams& p, dim3* grid, dim3* block) {
     *grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
 }
 
+// Calls fn.template operator()<S>() with the storage traits of p.storage.
+template <class Fn>
+cudaError_t with_storage(int storage, Fn&& fn) {
+    if (storage == 1) return fn(StoreF16{});
+    if (storage == 2) return fn(StoreBF16{});
+    return fn(StoreF32{});
+}
+
+}  // namespace
+
+// ---- launch wrappers ---------------------------------------------------------------------------
+int reduction_blocks() { return kRedBlocks; }
+
 cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st) {
     dim3 grid, block;
     site_grid(p, &grid, &block);
-    bool het = p.phi_field != nullptr;
-    if (het && outflow)
-        step_kernel<true, true><<<grid, block, 0, st>>>(p, pl);
-    else if (het)
-        step_kernel<true, false><<<grid, block, 0, st>>>(p, pl);
-    else if (outflow)
-        step_kernel<false, true><<<grid, block, 0, st>>>(p, pl);
-    else
-        step_kernel<false, false><<<grid, block, 0, st>>>(p, pl);
-    return cudaGetLastError();
+    const bool het = p.phi_field != nullptr;
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        if (het && outflow)
+            step_kernel<true, true, S><<<grid, block, 0, st>>>(p, pl);
+        else if (het)
+            step_kernel<true, false, S><<<grid, block, 0, st>>>(p, pl);
+        else if (outflow)
+            step_kernel<false, true, S><<<grid, block, 0, st>>>(p, pl);
+        else
+            step_kernel<false, false, S><<<grid, block, 0, st>>>(p, pl);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,
                           float* T, cudaStream_t st) {
     dim3 grid, block;
     site_grid(p, &grid, &block);
-    bool het = p.phi_field != nullptr;
-    if (het && outflow)
-        macros_kernel<true, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
-    else if (het)
-        macros_kernel<true, false><<<grid, block, 0, st>>>(p, pl, rho, u, T);
-    else if (outflow)
-        macros_kernel<false, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
-    else
-        macros_kernel<false, false><<<grid, block, 0, st>>>(p, pl, rho, u, T);
-    return cudaGetLastError();
+    const bool het = p.phi_field != nullptr;
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        if (het && outflow)
+            macros_kernel<true, true, S><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        else if (het)
+            macros_kernel<true, false, S><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        else if (outflow)
+            macros_kernel<false, true, S><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        else
+            macros_kernel<false, false, S><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_init_eq(const KParams& p, float* pop, const double* T_field,
+cudaError_t launch_init_eq(const KParams& p, const Planes& pl, const double* T_field,
                            const double* u_field, double T_uniform, cudaStream_t st) {
-    init_eq_kernel<<<blocks_for(p.ns, 128), 128, 0, st>>>(p, pop, T_field, u_field, T_uniform);
-    return cudaGetLastError();
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        init_eq_kernel<S><<<blocks_for(p.ns, 128), 128, 0, st>>>(p, pl, T_field, u_field, T_uniform);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_plane_to_dev(const double* src, float* dst, double offset, long long n,
-                                cudaStream_t st) {
-    plane_to_dev_kernel<<<1216, 256, 0, st>>>(src, dst, offset, n);
-    return cudaGetLastError();
+cudaError_t launch_plane_to_dev(int storage, const double* src, void* dst, double offset,
+                                double scale, long long n, cudaStream_t st) {
+    return with_storage(storage, [&](auto tag) {
+        using S = decltype(tag);
+        plane_to_dev_kernel<S><<<1216, 256, 0, st>>>(src, dst, offset, 1.0 / scale, n);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_plane_to_host(const float* src, double* dst, double offset, long long n,
-                                 cudaStream_t st) {
-    plane_to_host_kernel<<<1216, 256, 0, st>>>(src, dst, offset, n);
-    return cudaGetLastError();
+cudaError_t launch_plane_to_host(int storage, const void* src, double* dst, double offset,
+                                 double scale, long long n, cudaStream_t st) {
+    return with_storage(storage, [&](auto tag) {
+        using S = decltype(tag);
+        plane_to_host_kernel<S><<<1216, 256, 0, st>>>(src, dst, offset, scale, n);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_hist_reset(const KParams& p, const float* pop, float* hist, cudaStream_t st) {
-    long long nyz = (long long)p.ny * p.nz;
-    hist_reset_kernel<<<blocks_for(nyz, 128), 128, 0, st>>>(p, pop, hist);
-    return cudaGetLastError();
+cudaError_t launch_g_to_dev(const KParams& p, const Planes& pl, const double* src, cudaStream_t st) {
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        g_to_dev_kernel<S><<<1216, 256, 0, st>>>(p, pl, src, p.ns);
+        return cudaGetLastError();
+    });
 }
 
-cudaError_t launch_sums(const KParams& p, const float* pop, double* partials, int nparts,
+cudaError_t launch_g_to_host(const KParams& p, const Planes& pl, double* dst, cudaStream_t st) {
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        g_to_host_kernel<S><<<1216, 256, 0, st>>>(p, pl, dst, p.ns);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_hist_reset(const KParams& p, const Planes& pl, float* hist, cudaStream_t st) {
+    const long long nyz = (long long)p.ny * p.nz;
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        hist_reset_kernel<S><<<blocks_for(nyz, 128), 128, 0, st>>>(p, pl, hist);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_sums(const KParams& p, const Planes& pl, double* partials, int nparts,
                         double* out, cudaStream_t st) {
-    sums_kernel<<<nparts, kRedThreads, 0, st>>>(p, pop, partials);
-    finalize_kernel<2><<<1, kRedThreads, 0, st>>>(partials, nparts, out);
-    return cudaGetLastError();
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        sums_kernel<S><<<nparts, kRedThreads, 0, st>>>(p, pl, partials);
+        finalize_kernel<2><<<1, kRedThreads, 0, st>>>(partials, nparts, out);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_nusselt(const KParams& p, bool outflow, const Planes& pl, int face, double Tw,
                            double scale, double* profile, double* out, cudaStream_t st) {
     const int axis = face >> 1;
     const int n1 = axis == 0 ? p.ny : p.nx;
-    if (outflow)
-        nusselt_kernel<true><<<n1, kRedThreads, 0, st>>>(p, pl, face, Tw, scale, profile);
-    else
-        nusselt_kernel<false><<<n1, kRedThreads, 0, st>>>(p, pl, face, Tw, scale, profile);
-    nusselt_finalize_kernel<<<1, kRedThreads, 0, st>>>(profile, n1, out);
-    return cudaGetLastError();
+    return with_storage(p.storage, [&](auto tag) {
+        using S = decltype(tag);
+        if (outflow)
+            nusselt_kernel<true, S><<<n1, kRedThreads, 0, st>>>(p, pl, face, Tw, scale, profile);
+        else
+            nusselt_kernel<false, S><<<n1, kRedThreads, 0, st>>>(p, pl, face, Tw, scale, profile);
+        nusselt_finalize_kernel<<<1, kRedThreads, 0, st>>>(profile, n1, out);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_residual(const float* u, const float* T, const float* up, const float* Tp,
