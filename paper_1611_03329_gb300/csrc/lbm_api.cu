@@ -28,7 +28,7 @@ struct lbm_ctx {
     int cur = 0;
     lbm::Planes pl[2];  // launch planes reading copy 0 / copy 1
     bool outflow = false;
-    int block_threads = 128;     // site-kernel block size (LBM_BLOCK_THREADS overrides)
+    int block_threads = 64;      // site-kernel block size (LBM_BLOCK_THREADS overrides)
     float* phi_dev = nullptr;
     KParams kp{};
     double* partials = nullptr;  // reduction scratch

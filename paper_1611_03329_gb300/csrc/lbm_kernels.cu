@@ -565,26 +565,22 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
-// 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
-// blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
-template <bool HET, bool OUTF, class S>
-__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
-    step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    const bool valid = x < p.nx && y < p.ny;
-    const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
-    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
-    if (!valid) return;
-    float f[kQ], g[kQT];
-    const int s = x + p.nx * (y + p.ny * z);
+// Pull of one site (interior or general path; the warp-uniform choice is made by the caller).
+template <bool OUTF, class S>
+__device__ __forceinline__ void gather_site(const Planes& pl, const KParams& p, int x, int y, int z,
+                                            int s, bool warp_yz_in, float* f, float* g) {
     if (warp_yz_in) {
         gather_yz_interior<OUTF, S>(pl, p, x, y, z, s, f, g);
     } else {
         const Nbr n = neighbourhood(p, x, y, z);
         gather_general<OUTF, S>(pl, p, n, f, g);
     }
+}
+
+// Outflow history, collision and store of one gathered site.
+template <bool HET, bool OUTF, class S>
+__device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, int x, int y, int z,
+                                            int s, float* f, float* g) {
     if (OUTF && x == p.nx - 1) {
         const int yz = y + p.ny * z;
         pl.hout[0 * p.nyz + yz] = f[2];
@@ -601,6 +597,24 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
 #pragma unroll
     for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, g[i], m.dT);
     if constexpr (S::kScaled) pl.tout[s] = m.dT;
+}
+
+// 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
+// blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
+template <bool HET, bool OUTF, class S>
+__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
+    step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x < p.nx && y < p.ny;
+    const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
+    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+    if (!valid) return;
+    float f[kQ], g[kQT];
+    const int s = x + p.nx * (y + p.ny * z);
+    gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, f, g);
+    finish_site<HET, OUTF, S>(pl, p, x, y, z, s, f, g);
 }
 
 template <bool HET, bool OUTF, class S>
