@@ -35,6 +35,7 @@ WORKLOADS = {
     "channel": (256, 64, 64),
     "cavity128": (128, 128, 128),
     "cavity256": (256, 256, 256),
+    "batch64": (0, 0, 0),  # 64 cavities of edge 32..128 in one batched launch per step
 }
 
 
@@ -50,6 +51,9 @@ def _problem(nz=None, storage="fp32", workload="channel"):
 
 
 def _workload_text(workload, storage):
+    if workload == "batch64":
+        return (f"64 porous cavities, edges from {{32,48,64,96,128}}, own (phi, Da, Ra), one "
+                f"batched launch per step under a CUDA graph, {storage.upper()} storage")
     nx, ny, nz = WORKLOADS[workload]
     if workload == "channel":
         return f"porous mixed-convection channel {nx}x{ny}x{nz}, D3Q19+D3Q7 MRT, {storage.upper()} storage"
@@ -58,6 +62,12 @@ def _workload_text(workload, storage):
 
 
 def _config(workload="channel", storage="fp32", extra=None):
+    if workload == "batch64":
+        cfg = {"workload": _workload_text(workload, storage), "lattices": 64,
+               "storage": f"{storage}-deviation", "scheme": "ping-pong pull, batched",
+               "seed": 2016, "l2": "inputs larger than L2 (GBs of populations), no flush"}
+        cfg.update(extra or {})
+        return cfg
     nx, ny, nz = WORKLOADS[workload]
     elem = 4 if storage == "fp32" else 2
     state = 2 * 26 * elem * nx * ny * nz / 1e6
@@ -111,6 +121,16 @@ def profiled_traffic():
         return int(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def _peak():
+    """Measured HBM copy bandwidth (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+        return float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 def _dist():
@@ -247,6 +267,56 @@ def run_reference(args):
     return 0
 
 
+# ---- batched workload ------------------------------------------------------------------------
+def run_batch(args, gb, torch):
+    """64 cavities advanced by one batched launch per step (CUDA graph replays of up to 500
+    steps), against the same lattices solved one at a time (each lattice's own launches)."""
+    from lbm_inputs import batch_cavities
+
+    pbs = [dict(pb, storage=args.storage) for pb in batch_cavities(64)]
+    stream = torch.cuda.Stream()
+    lats = [gb.Lattice(pb, stream=stream.cuda_stream) for pb in pbs]
+    sites = sum(l.ns for l in lats)
+    batch = gb.Batch(lats, stream=stream.cuda_stream)
+    block = batch.tune()  # (threads per block, z-planes per block)
+    chunk = max(1, min(args.steps, 500))
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        start.record(stream)
+        left = args.steps
+        while left > 0:
+            batch.step(min(chunk, left))
+            left -= min(chunk, left)
+        stop.record(stream)
+        stop.synchronize()
+    ms = start.elapsed_time(stop)
+    mlups = sites * args.steps / (ms * 1e-3) / 1e6
+    # one at a time: each lattice with its own launches, for the same number of steps
+    n1 = max(1, min(args.steps, 200))
+    torch.cuda.synchronize()
+    start.record(stream)
+    for l in lats:
+        l.step(n1)
+    stop.record(stream)
+    stop.synchronize()
+    ms1 = start.elapsed_time(stop)
+    mlups1 = sites * n1 / (ms1 * 1e-3) / 1e6
+    unstable = 0
+    for l in lats:
+        try:
+            l.sums()
+        except gb.LbmError:
+            unstable += 1
+    batch.close()
+    bytes_site = 26 * 2 * gb.STORAGE_BYTES[args.storage]
+    achieved = bytes_site * sites / (ms / args.steps * 1e-3) / 1e9
+    return mlups, ms, sites, achieved, clk.summary(), {
+        "value": round(mlups1, 2), "unit": UNIT, "steps": n1,
+        "path": "lbm_step per lattice, lattices one after another"}, block, unstable
+
+
 # ---- our arm ---------------------------------------------------------------------------------
 def run_ours(args):
     ws, rank = _dist()
@@ -260,6 +330,30 @@ def run_ours(args):
     dist = _init_dist(ws)
     gb.build.build()
     torch.cuda.set_device(0)
+    if args.workload == "batch64":
+        mlups, ms, sites, achieved, clocks, one, block, unstable = run_batch(args, gb, torch)
+        mlups_all = _max_over_ranks(dist, 0.0)  # keep ranks in step
+        if rank != 0:
+            return 0
+        peak = _peak()
+        line = {"metric": METRIC, "value": round(mlups * ws, 2), "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 6), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math",
+                          "bf16": "bf16-storage/f32-math"}[args.storage],
+                "data": "synthetic",
+                "config": _config("batch64", args.storage, {"sites": sites, "block_threads": block[0],
+                                                            "planes_per_block": block[1],
+                                                            "unstable_lattices": unstable}),
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak[0],
+                             "unit": "GB/s", "frac": round(achieved / peak[0], 4),
+                             "traffic": None, "peak_source": peak[1]},
+                "one_at_a_time": one,
+                "batched_speedup": round(mlups / one["value"], 3),
+                "gpu_launches": args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+        return 0
     stream = torch.cuda.Stream()
     pb = _problem(storage=args.storage, workload=args.workload)
     wnx, wny, wnz = WORKLOADS[args.workload]
@@ -311,14 +405,7 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except OSError:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak, peak_src = _peak()
     bytes_site = gb.algorithmic_bytes_per_site(pb)
     kernel_ms = ms / args.steps  # one fused step kernel per time step
     achieved = bytes_site * ns / (kernel_ms * 1e-3) / 1e9

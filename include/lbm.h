@@ -233,6 +233,41 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
 lbm_status lbm_residual_noalloc(const float* u, const float* T, const float* u_prev,
                                 const float* T_prev, long long ns, double* out, void* stream);
 
+/* ---- batched launches -----------------------------------------------------------------
+ * A batch advances many independent lattices (contexts) with one fused launch per time step
+ * and kernel variant (storage format, uniform or field medium, outflow or not): the step of
+ * Sec. 3 at every site of every lattice, exactly as lbm_step computes it, so a lattice's
+ * results are identical alone and in a batch.  Multi-step sequences are recorded once per
+ * step count as a CUDA graph and replayed.  The contexts keep owning their state; after
+ * lbm_batch_step every per-context call (macros, Nusselt, sums, ...) sees the new state. */
+typedef struct lbm_batch lbm_batch;
+
+/* Group n contexts (same device, each at most once) into a batch queued on `stream`
+ * (NULL: a private stream).  The batch reads each context's parameters, medium and state
+ * at every lbm_batch_step, so changes made through the contexts are picked up.
+ * Errors: LBM_EINVAL (bad list, mixed devices, a failed context), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch** out);
+
+/* Advance every lattice of the batch by nsteps >= 0 time steps (asynchronous; ordered after
+ * and before the contexts' own streams). */
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
+
+/* Time the batched step at 32, 64, 128 and 256 threads per block and 1, 2 and 4 z-planes
+ * per block and keep the fastest shape (written to *block_threads and *rows when non-NULL).
+ * The timed launches write only the buffers that the next step overwrites, so the lattices'
+ * state is unchanged.  Synchronises. */
+lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows);
+
+/* Set the block shape of the batched step: threads (32, 64, 128 or 256) and z-planes per
+ * block (1..64). */
+lbm_status lbm_batch_set_block(lbm_batch* b, int block_threads, int rows);
+
+/* Text of the batch's last error (never NULL). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Release the batch (not its contexts).  NULL is a no-op. */
+void lbm_batch_destroy(lbm_batch* b);
+
 /* Derived lattice parameters of the context, including the current medium. */
 lbm_status lbm_get_lattice(const lbm_ctx* ctx, lbm_lattice* out);
 

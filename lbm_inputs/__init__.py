@@ -90,3 +90,19 @@ def channel_problem(nx: int, ny: int, nz: int, Re: float = 10.0, u0: float = 0.0
               T_init=0.0, T0=0.5, gravity_axis=1, gravity_sign=-1)
     pb.update(kw)
     return pb
+
+
+def batch_cavities(n: int = 64, seed: int = 2016, sizes=(32, 48, 64, 96, 128),
+                   phi_range=(0.4, 0.9), log_da=(-5.0, -1.0), log_ra=(3.0, 6.0),
+                   Pr: float = 0.71) -> list:
+    """n independent porous cavities: edge drawn uniformly from `sizes`, porosity uniform in
+    phi_range, log10 Da and log10 Ra uniform in their ranges (PCG64(seed)); Ergun F_phi."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        edge = int(rng.choice(sizes))
+        phi = float(rng.uniform(*phi_range))
+        Da = float(10.0 ** rng.uniform(*log_da))
+        Ra = float(10.0 ** rng.uniform(*log_ra))
+        out.append(cavity_problem(edge, Ra=Ra, Da=Da, phi=phi, Pr=Pr))
+    return out

@@ -34,7 +34,8 @@ ABI_SYMBOLS = (
     "lbm_step", "lbm_init_equilibrium", "lbm_set_populations", "lbm_get_populations",
     "lbm_macros", "lbm_macros_device", "lbm_nusselt", "lbm_sums", "lbm_residual",
     "lbm_get_lattice", "lbm_steps_done", "lbm_sync", "lbm_last_error", "lbm_status_string",
-    "lbm_residual_noalloc",
+    "lbm_residual_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
+    "lbm_batch_set_block", "lbm_batch_last_error", "lbm_batch_destroy",
 )
 
 NOALLOC_MAX_SITES = 33554432  # LBM_NOALLOC_MAX_SITES
@@ -138,6 +139,14 @@ def lib():
         L.lbm_status_string.argtypes = [C.c_int]
         L.lbm_status_string.restype = C.c_char_p
         L.lbm_residual_noalloc.argtypes = [vp, vp, vp, vp, C.c_longlong, vp, vp]
+        L.lbm_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
+        L.lbm_batch_step.argtypes = [vp, C.c_int]
+        L.lbm_batch_tune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.lbm_batch_set_block.argtypes = [vp, C.c_int, C.c_int]
+        L.lbm_batch_last_error.argtypes = [vp]
+        L.lbm_batch_last_error.restype = C.c_char_p
+        L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -329,6 +338,52 @@ def residual_noalloc(u_ptr: int, T_ptr: int, u_prev_ptr: int, T_prev_ptr: int, n
                                     C.c_void_p(out_ptr), C.c_void_p(stream or 0))
     if st != LBM_OK:
         raise LbmError(st, f"lbm_residual_noalloc: {lib().lbm_status_string(st).decode()}")
+
+
+class Batch:
+    """Many lattices advanced by one fused launch per time step (``lbm_batch_*``)."""
+
+    def __init__(self, lattices, stream: Optional[int] = None):
+        self.lattices = list(lattices)
+        arr = (C.c_void_p * len(self.lattices))(*[l.handle for l in self.lattices])
+        self._h = C.c_void_p()
+        st = lib().lbm_batch_create(arr, len(self.lattices), C.c_void_p(stream or 0),
+                                    C.byref(self._h))
+        if st != LBM_OK:
+            raise LbmError(st, f"lbm_batch_create: {lib().lbm_status_string(st).decode()}")
+
+    def _check(self, st: int, what: str):
+        if st != LBM_OK:
+            raise LbmError(st, f"{what}: {lib().lbm_status_string(st).decode()}: "
+                               f"{lib().lbm_batch_last_error(self._h).decode()}")
+
+    def step(self, n: int = 1):
+        self._check(lib().lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def tune(self):
+        """Autotune the block shape; returns (threads per block, z-planes per block)."""
+        bt, rows = C.c_int(), C.c_int()
+        self._check(lib().lbm_batch_tune(self._h, C.byref(bt), C.byref(rows)), "lbm_batch_tune")
+        return bt.value, rows.value
+
+    def set_block(self, threads: int, rows: int = 1):
+        self._check(lib().lbm_batch_set_block(self._h, int(threads), int(rows)),
+                    "lbm_batch_set_block")
+
+    def sync(self):
+        for l in self.lattices:
+            l.sync()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().lbm_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def medium_args(pb: dict) -> dict:

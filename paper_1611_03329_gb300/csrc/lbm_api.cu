@@ -790,3 +790,305 @@ lbm_status lbm_get_lattice(const lbm_ctx* c, lbm_lattice* out) {
 }
 
 }  // extern "C"
+
+// ---- batched launches --------------------------------------------------------------------------
+#include <map>
+#include <vector>
+
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctx;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int block_threads = 64;
+    int rows = 1;  // z-planes per block of the batched step
+    struct Group {
+        int storage = 0;
+        bool het = false, outflow = false;
+        std::vector<int> members;           // indices into ctx
+        lbm::BatchLattice* dtab = nullptr;  // device table
+        // host mirror in pageable memory: an asynchronous copy from it stages the data before
+        // returning, so the next call may refill it at once
+        std::vector<lbm::BatchLattice> htab;
+        int nblocks = 0;
+        unsigned short* dblk = nullptr;     // block -> lattice map (device)
+        size_t dblk_cap = 0;
+        int dblk_threads = 0, dblk_rows = 0;  // layout the map was built for
+        std::vector<unsigned short> hblk;
+    };
+    std::vector<Group> groups;
+    std::map<int, cudaGraphExec_t> graphs;  // captured n-step sequences
+    cudaEvent_t ev = nullptr;
+    bool tuned = false;
+    char err[256] = {0};
+};
+
+namespace {
+
+lbm_status batch_fail(lbm_batch* b, lbm_status s, const char* what, cudaError_t e = cudaSuccess) {
+    if (b) snprintf(b->err, sizeof(b->err), "%s%s%s", what, e != cudaSuccess ? ": " : "",
+                    e != cudaSuccess ? cudaGetErrorString(e) : "");
+    return s;
+}
+
+#define LBM_BCUDA(call)                                                     \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return batch_fail(b, LBM_ECUDA, #call, e_);  \
+    } while (0)
+
+void batch_clear_graphs(lbm_batch* b) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Host tables of every group from the contexts' current state and the block size.
+void batch_fill_tables(lbm_batch* b) {
+    for (auto& g : b->groups) {
+        int off = 0;
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            lbm_ctx* c = b->ctx[g.members[k]];
+            lbm::BatchLattice& L = g.htab[k];
+            L.p = c->kp;
+            L.pl[0] = c->pl[0];
+            L.pl[1] = c->pl[1];
+            L.cur = c->cur;
+            L.bx = lbm::block_x(c->prm.nx, b->block_threads);
+            const int by = b->block_threads / L.bx;
+            L.gx = (c->prm.nx + L.bx - 1) / L.bx;
+            L.gy = (c->prm.ny + by - 1) / by;
+            L.block_begin = off;
+            off += L.gx * L.gy * ((c->prm.nz + b->rows - 1) / b->rows);
+        }
+        g.nblocks = off;
+    }
+}
+
+// Order the batch stream after every context's pending work (and the reverse at the end).
+lbm_status batch_join(lbm_batch* b, bool into_batch) {
+    for (lbm_ctx* c : b->ctx) {
+        if (c->stream == b->stream) continue;
+        cudaStream_t from = into_batch ? c->stream : b->stream;
+        cudaStream_t to = into_batch ? b->stream : c->stream;
+        LBM_BCUDA(cudaEventRecord(b->ev, from));
+        LBM_BCUDA(cudaStreamWaitEvent(to, b->ev, 0));
+    }
+    return LBM_OK;
+}
+
+lbm_status batch_launch_steps(lbm_batch* b, int nsteps, bool tuning) {
+    for (int t = 0; t < nsteps; ++t)
+        for (auto& g : b->groups)
+            LBM_BCUDA(lbm::launch_batch_step(g.dtab, g.dblk, g.nblocks, b->block_threads, b->rows,
+                                             g.storage, g.het, g.outflow, tuning ? 0 : (t & 1),
+                                             b->stream));
+    return LBM_OK;
+}
+
+// Upload the lattice tables, and the block -> lattice map when the layout changed.
+lbm_status batch_upload(lbm_batch* b) {
+    batch_fill_tables(b);
+    for (auto& g : b->groups) {
+        LBM_BCUDA(cudaMemcpyAsync(g.dtab, g.htab.data(),
+                                  sizeof(lbm::BatchLattice) * g.members.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+        if (g.dblk_threads == b->block_threads && g.dblk_rows == b->rows && g.dblk) continue;
+        g.hblk.assign((size_t)g.nblocks, 0);
+        for (size_t k = 0; k < g.htab.size(); ++k) {
+            const int end = k + 1 < g.htab.size() ? g.htab[k + 1].block_begin : g.nblocks;
+            for (int blk = g.htab[k].block_begin; blk < end; ++blk) g.hblk[blk] = (unsigned short)k;
+        }
+        if ((size_t)g.nblocks > g.dblk_cap) {
+            // the map is sized once per layout; kernels of earlier launches may still read
+            // the old one, so wait for them before freeing it
+            LBM_BCUDA(cudaStreamSynchronize(b->stream));
+            cudaFree(g.dblk);
+            g.dblk = nullptr;
+            LBM_BCUDA(cudaMalloc(&g.dblk, sizeof(unsigned short) * (size_t)g.nblocks));
+            g.dblk_cap = (size_t)g.nblocks;
+        }
+        LBM_BCUDA(cudaMemcpyAsync(g.dblk, g.hblk.data(), sizeof(unsigned short) * g.hblk.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+        g.dblk_threads = b->block_threads;
+        g.dblk_rows = b->rows;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch** out) {
+    if (!ctxs || n < 1 || !out) return LBM_EINVAL;
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ENOMEM;
+    if (n > 65535) {  // the block -> lattice map holds 16-bit indices
+        delete b;
+        return LBM_EINVAL;
+    }
+    for (int k = 0; k < n; ++k) {
+        lbm_ctx* c = ctxs[k];
+        if (!c || c->sticky != LBM_OK) {
+            delete b;
+            return LBM_EINVAL;
+        }
+        for (lbm_ctx* o : b->ctx)
+            if (o == c) {  // a lattice may appear once
+                delete b;
+                return LBM_EINVAL;
+            }
+        if (!b->ctx.empty() && c->device != b->ctx[0]->device) {
+            delete b;
+            return LBM_EINVAL;
+        }
+        b->ctx.push_back(c);
+    }
+    b->device = b->ctx[0]->device;
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            b->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) st = LBM_ECUDA;
+    // group the lattices by kernel variant
+    for (int k = 0; k < n && st == LBM_OK; ++k) {
+        lbm_ctx* c = b->ctx[k];
+        const int stg = c->prm.storage;
+        const bool het = c->lat.has_phi_field != 0, outf = c->outflow;
+        lbm_batch::Group* grp = nullptr;
+        for (auto& gr : b->groups)
+            if (gr.storage == stg && gr.het == het && gr.outflow == outf) grp = &gr;
+        if (!grp) {
+            b->groups.emplace_back();
+            grp = &b->groups.back();
+            grp->storage = stg;
+            grp->het = het;
+            grp->outflow = outf;
+        }
+        grp->members.push_back(k);
+    }
+    for (auto& g : b->groups) {
+        if (st != LBM_OK) break;
+        size_t bytes = sizeof(lbm::BatchLattice) * g.members.size();
+        g.htab.resize(g.members.size());
+        if (cudaMalloc(&g.dtab, bytes) != cudaSuccess) st = LBM_ENOMEM;
+    }
+    if (st != LBM_OK) {
+        lbm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_clear_graphs(b);
+    for (auto& g : b->groups) {
+        cudaFree(g.dtab);
+        cudaFree(g.dblk);
+    }
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
+    if (!b || nsteps < 0) return LBM_EINVAL;
+    for (lbm_ctx* c : b->ctx)
+        if (c->sticky != LBM_OK) return c->sticky;
+    if (nsteps == 0) return LBM_OK;
+    LBM_BCUDA(cudaSetDevice(b->device));
+    lbm_status st = batch_join(b, true);
+    if (st != LBM_OK) return st;
+    if ((st = batch_upload(b)) != LBM_OK) return st;
+    auto it = b->graphs.find(nsteps);
+    if (it == b->graphs.end()) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        LBM_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        lbm_status ls = batch_launch_steps(b, nsteps, false);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (ls != LBM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return ls;
+        }
+        if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "cudaStreamEndCapture", e);
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "cudaGraphInstantiate", e);
+        it = b->graphs.emplace(nsteps, exec).first;
+    }
+    LBM_BCUDA(cudaGraphLaunch(it->second, b->stream));
+    for (lbm_ctx* c : b->ctx) {
+        c->cur ^= (nsteps & 1);
+        c->steps += nsteps;
+    }
+    return batch_join(b, false);
+}
+
+lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows) {
+    if (!b) return LBM_EINVAL;
+    LBM_BCUDA(cudaSetDevice(b->device));
+    lbm_status st = batch_join(b, true);
+    if (st != LBM_OK) return st;
+    cudaEvent_t t0, t1;
+    LBM_BCUDA(cudaEventCreate(&t0));
+    LBM_BCUDA(cudaEventCreate(&t1));
+    const int cand_t[4] = {32, 64, 128, 256};
+    const int cand_r[3] = {1, 2, 4};
+    int best = b->block_threads, best_rows = b->rows;
+    float best_ms = 1e30f;
+    for (int k = 0; k < 12 && st == LBM_OK; ++k) {
+        b->block_threads = cand_t[k / 3];
+        b->rows = cand_r[k % 3];
+        // launches with flip 0 write only the non-current copy: the state is not changed
+        if ((st = batch_upload(b)) != LBM_OK) break;
+        if ((st = batch_launch_steps(b, 2, true)) != LBM_OK) break;  // warm-up
+        cudaEventRecord(t0, b->stream);
+        if ((st = batch_launch_steps(b, 5, true)) != LBM_OK) break;
+        cudaEventRecord(t1, b->stream);
+        cudaError_t e = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) st = batch_fail(b, LBM_ECUDA, "tuning", e);
+        else if (ms < best_ms) {
+            best_ms = ms;
+            best = b->block_threads;
+            best_rows = b->rows;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    b->block_threads = best;
+    b->rows = best_rows;
+    b->tuned = true;
+    batch_clear_graphs(b);
+    if (block_threads) *block_threads = best;
+    if (rows) *rows = best_rows;
+    if (st != LBM_OK) return st;
+    return batch_join(b, false);
+}
+
+lbm_status lbm_batch_set_block(lbm_batch* b, int block_threads, int rows) {
+    if (!b || !(block_threads == 32 || block_threads == 64 || block_threads == 128 ||
+                block_threads == 256) || rows < 1 || rows > 64)
+        return LBM_EINVAL;
+    if (b->block_threads != block_threads || b->rows != rows) batch_clear_graphs(b);
+    b->block_threads = block_threads;
+    b->rows = rows;
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "null batch"; }
+
+}  // extern "C"

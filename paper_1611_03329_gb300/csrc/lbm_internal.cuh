@@ -65,6 +65,20 @@ struct Planes {
     float* tout;
 };
 
+// One lattice of a batched launch: its parameters, its launch planes for either parity, the
+// copy that holds its state when the launch sequence starts, and its part of the flat block
+// list (blocks [block_begin, block_begin + gx * gy * ceil(nz / rows)), bx threads along x
+// per block, `rows` z-planes per block).
+struct BatchLattice {
+    KParams p;
+    Planes pl[2];
+    int cur;
+    int block_begin;
+    int gx, gy;
+    int bx;
+    int pad_;
+};
+
 // Launch wrappers (defined in lbm_kernels.cu).  All are asynchronous on `st`.
 cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st);
 cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,
@@ -94,6 +108,14 @@ cudaError_t launch_residual(const float* u, const float* T, const float* up, con
                             long long ns, double* partials, int nparts, double* out,
                             cudaStream_t st);
 
-int reduction_blocks();  // number of partial sums the reductions write (<= partials size)
+int reduction_blocks();
+// One time step of every lattice of a batch group (same storage, medium kind and outflow):
+// lattice l reads its planes pl[cur ^ flip]; blk_lat maps each of the nblocks blocks to its
+// lattice.
+cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
+                              int block_threads, int rows, int storage, bool het, bool outflow,
+                              int flip, cudaStream_t st);
+// x-extent of a site-kernel block for a lattice of width nx within block_threads threads.
+int block_x(int nx, int block_threads);  // number of partial sums the reductions write (<= partials size)
 
 }  // namespace lbm

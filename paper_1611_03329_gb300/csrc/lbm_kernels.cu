@@ -318,7 +318,8 @@ __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& 
 // the interior path.
 template <bool OUTF, class S>
 __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
-                                                   int z, int s, float* f, float* g) {
+                                                   int z, int s, unsigned lanes, float* f,
+                                                   float* g) {
     const int nx = p.nx, nxy = p.nx * p.ny;
     int xm = -1, xp = 1;  // source offsets of +x and -x velocities
     bool cxm = false, cxp = false;
@@ -330,7 +331,7 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
 #pragma unroll
     for (int i = 0; i < kQT; ++i)
         g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
-    if (!__any_sync(0xffffffffu, cxm || cxp)) return;  // interior warp
+    if (!__any_sync(lanes, cxm || cxp)) return;  // interior warp
     if (cxm) {
         // x-low face: wall or velocity face (an outflow is only allowed on x-high)
         const bool vel = (p.vel_mask & 1u) && !(p.wall_mask & 1u);
@@ -566,11 +567,13 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 
 // ---- kernels ---------------------------------------------------------------------------------
 // Pull of one site (interior or general path; the warp-uniform choice is made by the caller).
+// `lanes` is the mask of the warp's lanes that call it together (the valid sites).
 template <bool OUTF, class S>
 __device__ __forceinline__ void gather_site(const Planes& pl, const KParams& p, int x, int y, int z,
-                                            int s, bool warp_yz_in, float* f, float* g) {
+                                            int s, bool warp_yz_in, unsigned lanes, float* f,
+                                            float* g) {
     if (warp_yz_in) {
-        gather_yz_interior<OUTF, S>(pl, p, x, y, z, s, f, g);
+        gather_yz_interior<OUTF, S>(pl, p, x, y, z, s, lanes, f, g);
     } else {
         const Nbr n = neighbourhood(p, x, y, z);
         gather_general<OUTF, S>(pl, p, n, f, g);
@@ -610,11 +613,50 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     const bool valid = x < p.nx && y < p.ny;
     const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
     const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+    const unsigned lanes = __ballot_sync(0xffffffffu, valid);
     if (!valid) return;
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
-    gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, f, g);
+    gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
     finish_site<HET, OUTF, S>(pl, p, x, y, z, s, f, g);
+}
+
+// Batched step: one flat grid over the blocks of many lattices.  blk_lat[b] names the lattice
+// of block b; the lattice's parameters and planes are read in place through the read-only
+// cache (uniform over the block).  A block covers `rows` consecutive z-planes of one
+// (x-segment, y-band) column, so the lookup is paid once per `rows` site updates.
+template <bool HET, bool OUTF, class S>
+__global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
+    batch_step_kernel(const BatchLattice* __restrict__ tab,
+                      const unsigned short* __restrict__ blk_lat, int flip, int rows) {
+    const BatchLattice* L = tab + __ldg(blk_lat + blockIdx.x);
+    const KParams& p = L->p;
+    const Planes& pl = L->pl[L->cur ^ flip];
+    const int bx = L->bx, gx = L->gx, gy = L->gy;
+    const int local = (int)blockIdx.x - L->block_begin;
+    const int by = blockDim.x / bx;
+    const int tx = threadIdx.x & (bx - 1), ty = threadIdx.x / bx;
+    const int bxi = local % gx, rest = local / gx;
+    const int x = bxi * bx + tx;
+    const int y = (rest % gy) * by + ty;
+    const int z0 = (rest / gy) * rows;
+    const bool valid = x < p.nx && y < p.ny;
+    const bool y_in = y > 0 && y < p.ny - 1;
+    for (int r = 0; r < rows; ++r) {
+        const int z = z0 + r;
+        if (z >= p.nz) break;  // uniform over the block
+        const bool yz_in = y_in && z > 0 && z < p.nz - 1;
+        const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+        // every lane of the warp reaches the two votes above; only the valid lanes go on, so
+        // the votes inside the site update name exactly those lanes
+        const unsigned lanes = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            float f[kQ], g[kQT];
+            const int s = x + p.nx * (y + p.ny * z);
+            gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
+            finish_site<HET, OUTF, S>(pl, p, x, y, z, s, f, g);
+        }
+    }
 }
 
 template <bool HET, bool OUTF, class S>
@@ -885,10 +927,15 @@ inline unsigned blocks_for(long long n, int threads) {
 
 // Block of p.block_threads (32..kBlock) threads: blockDim.x = the smallest power of two >= nx
 // within that size, the rest along y.
+int block_x_of(int nx, int nt) {
+    int bx = 32;
+    while (bx < nx && bx < nt) bx *= 2;
+    return bx;
+}
+
 void site_grid(const KParams& p, dim3* grid, dim3* block) {
     int nt = p.block_threads >= 32 && p.block_threads <= kBlock ? p.block_threads : kBlock;
-    int bx = 32;
-    while (bx < p.nx && bx < nt) bx *= 2;
+    int bx = block_x_of(p.nx, nt);
     int by = nt / bx > 0 ? nt / bx : 1;
     *block = dim3(bx, by, 1);
     *grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
@@ -906,6 +953,26 @@ cudaError_t with_storage(int storage, Fn&& fn) {
 
 // ---- launch wrappers ---------------------------------------------------------------------------
 int reduction_blocks() { return kRedBlocks; }
+
+int block_x(int nx, int block_threads) { return block_x_of(nx, block_threads); }
+
+cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
+                              int block_threads, int rows, int storage, bool het, bool outflow,
+                              int flip, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    return with_storage(storage, [&](auto tag) {
+        using S = decltype(tag);
+        if (het && outflow)
+            batch_step_kernel<true, true, S><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+        else if (het)
+            batch_step_kernel<true, false, S><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+        else if (outflow)
+            batch_step_kernel<false, true, S><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+        else
+            batch_step_kernel<false, false, S><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+        return cudaGetLastError();
+    });
+}
 
 cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st) {
     dim3 grid, block;
