@@ -36,6 +36,7 @@ WORKLOADS = {
     "cavity128": (128, 128, 128),
     "cavity256": (256, 256, 256),
     "batch64": (0, 0, 0),  # 64 cavities of edge 32..128 in one batched launch per step
+    "serve": (0, 0, 0),    # Poisson stream of cavity and channel solves, continuous batching
 }
 
 
@@ -317,6 +318,80 @@ def run_batch(args, gb, torch):
         "path": "lbm_step per lattice, lattices one after another"}, block, unstable
 
 
+# ---- serving workload ------------------------------------------------------------------------
+def _serve_stream(gb, reqs, budget, chunk, tol, max_steps, alone, fill=0):
+    """Submit each request at its arrival time and run the serving loop; with alone=True each
+    request gets a server of its own once the previous one is done (one solve at a time)."""
+    t0 = time.perf_counter()
+    results = []
+    if alone:
+        for arrival, pb in reqs:
+            while time.perf_counter() - t0 < arrival:
+                time.sleep(0.0005)
+            srv = gb.Server(budget_bytes=budget, chunk=chunk)
+            sub = time.perf_counter() - t0
+            srv.submit(pb, tol=tol, max_steps=max_steps)
+            while True:
+                na, nq = srv.advance()
+                got = srv.poll()
+                if got:
+                    r = got[0]
+                    r["arrival"] = arrival
+                    r["finished"] = sub + (r["t_done"] - r["t_submit"])
+                    results.append(r)
+                if na == 0 and nq == 0:
+                    break
+            srv.close()
+        return results, time.perf_counter() - t0
+    srv = gb.Server(budget_bytes=budget, chunk=chunk, max_active_sites=fill)
+    offset = None
+    pending = list(reqs)
+    arrivals = {}
+    while pending or len(results) < len(reqs):
+        now = time.perf_counter() - t0
+        while pending and pending[0][0] <= now:
+            arrival, pb = pending.pop(0)
+            rid = srv.submit(pb, tol=tol, max_steps=max_steps)
+            arrivals[rid] = arrival
+            if offset is None:
+                offset = now - srv.clock()  # server clock -> bench clock
+        na, nq = srv.advance()
+        for r in srv.poll():
+            r["arrival"] = arrivals[r["id"]]
+            r["finished"] = r["t_done"] + offset
+            results.append(r)
+        if na == 0 and nq == 0 and pending:
+            time.sleep(max(0.0, min(0.001, pending[0][0] - (time.perf_counter() - t0))))
+    srv.close()
+    return results, time.perf_counter() - t0
+
+
+def _latency_summary(results):
+    lat = sorted(r["finished"] - r["arrival"] for r in results)
+    lups = sum(r["sites"] * r["steps"] for r in results)
+    span = max(r["finished"] for r in results) - min(r["arrival"] for r in results)
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    return {"p50_s": round(pct(0.5), 4), "p99_s": round(pct(0.99), 4),
+            "mlups": round(lups / span / 1e6, 2), "makespan_s": round(span, 3),
+            "statuses": {s: sum(1 for r in results if r["status"] == s)
+                         for s in sorted({r["status"] for r in results})}}
+
+
+def run_serve(args, gb):
+    from lbm_inputs import serving_mix
+
+    reqs = serving_mix(args.requests, seed=5)
+    tol, max_steps, chunk = 1e-6, args.max_steps, 100
+    mixed, _ = _serve_stream(gb, reqs, 0, chunk, tol, max_steps, alone=False, fill=args.fill)
+    uncapped = None
+    if args.fill:
+        uncapped = _latency_summary(_serve_stream(gb, reqs, 0, chunk, tol, max_steps,
+                                                  alone=False, fill=0)[0])
+    solo, _ = _serve_stream(gb, reqs, 0, chunk, tol, max_steps, alone=True)
+    return (_latency_summary(mixed), _latency_summary(solo), len(reqs), tol, max_steps,
+            uncapped)
+
+
 # ---- our arm ---------------------------------------------------------------------------------
 def run_ours(args):
     ws, rank = _dist()
@@ -330,6 +405,25 @@ def run_ours(args):
     dist = _init_dist(ws)
     gb.build.build()
     torch.cuda.set_device(0)
+    if args.workload == "serve":
+        mixed, solo, n, tol, max_steps, uncapped = run_serve(args, gb)
+        if rank != 0:
+            return 0
+        line = {"metric": "time-to-steady-state p50/p99 and aggregate MLUPS (serving)",
+                "value": mixed["mlups"], "unit": UNIT, "n_gpus": ws, "steps": None,
+                "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32-math, fp32 or fp16 storage per request", "data": "synthetic",
+                "config": {"workload": f"{n} requests, Poisson 20/s (seed 5): porous cavities "
+                                       "32^3-192^3 and 4WxWxW channels (W 32, 64)",
+                           "tol": tol, "max_steps": max_steps, "chunk": 100,
+                           "admission": "FIFO by device footprint (80% of free memory)"
+                                        + (f", at most {args.fill} sites admitted" if args.fill else "")},
+                "latency": {"p50_s": mixed["p50_s"], "p99_s": mixed["p99_s"]},
+                "serving": mixed, "serving_uncapped": uncapped, "one_at_a_time": solo,
+                "speedup_mlups": round(mixed["mlups"] / solo["mlups"], 3),
+                "speedup_p50": round(solo["p50_s"] / mixed["p50_s"], 3)}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "batch64":
         mlups, ms, sites, achieved, clocks, one, block, unstable = run_batch(args, gb, torch)
         mlups_all = _max_over_ranks(dist, 0.0)  # keep ranks in step
@@ -455,6 +549,10 @@ def main(argv=None):
                     help="population storage (the headline workload is fp32)")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="channel",
                     help="the headline workload is the 256x64x64 channel")
+    ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")
+    ap.add_argument("--max-steps", type=int, default=20000, help="serve: step limit")
+    ap.add_argument("--fill", type=int, default=8_000_000,
+                    help="serve: cap on the lattice sites admitted at once (0: none)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

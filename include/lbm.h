@@ -205,8 +205,9 @@ lbm_status lbm_nusselt(lbm_ctx* ctx, int face, double* nu_avg, double* nu_profil
 lbm_status lbm_sums(lbm_ctx* ctx, double* mass_dev, double* heat_dev);
 
 /* Steady-state residual: r_u = ||u - u_prev||_2 / ||u||_2 and the same for T, against the
- * fields saved by the previous call (FP64 accumulation); the first call after create or
- * init returns +inf.  Synchronises.  LBM_EUNSTABLE if a field holds NaN or Inf. */
+ * fields saved by the previous call (FP64 accumulation); 0 for a field that is zero and
+ * unchanged; the first call after create or init returns +inf.  Synchronises.
+ * LBM_EUNSTABLE if a field holds NaN or Inf. */
 lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
 
 /* Largest field, in sites, that lbm_residual_noalloc accepts (2^25, e.g. 256 x 256 x 512). */
@@ -222,8 +223,9 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
  * lbm_macros_device:
  *  u, u_prev : device, 3 x ns floats ([3][ns]);  T, T_prev : device, ns floats;
  *  ns        : 1 .. LBM_NOALLOC_MAX_SITES, else LBM_EINVAL and nothing is launched;
- *  out       : device, 3 doubles, written asynchronously: r_u, r_T (+inf where the norm of
- *              the new field is 0) and the number of non-finite values met;
+ *  out       : device, 3 doubles, written asynchronously: r_u, r_T (0 for a field that is
+ *              zero and unchanged, +inf for one that is zero after changing) and the number
+ *              of non-finite values met;
  *  stream    : cudaStream_t to queue on (NULL: the current device's default stream).
  * It allocates nothing: its partial sums live in a static 320 KiB device array that every
  * GPU loading the library holds until exit.  The first call on a device looks up that
@@ -267,6 +269,74 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* Release the batch (not its contexts).  NULL is a no-op. */
 void lbm_batch_destroy(lbm_batch* b);
+
+/* Device bytes a context for p will hold, including the residual buffers a solve to steady
+ * state allocates (host only, no GPU).  LBM_EINVAL for invalid params. */
+lbm_status lbm_footprint(const lbm_params* p, int has_phi_field, unsigned long long* bytes);
+
+/* ---- serving loop ------------------------------------------------------------------------
+ * A server takes solve requests as they arrive, admits them in arrival order while their
+ * device footprint fits its memory budget, keeps their populations resident and advances all
+ * admitted lattices together with batched launches (lbm_batch_*) in chunks of `chunk` steps.
+ * After every chunk each lattice's steady-state residual (lbm_residual) is checked; a request
+ * finishes when both residuals fall below its tolerance, when it reaches its step limit, or
+ * when its state stops being finite, and its memory is released for the next request.  A
+ * request's result depends only on its own problem: it is the same alone and in the mix. */
+typedef struct lbm_server lbm_server;
+
+/* Medium of a request (the arguments of lbm_set_medium); phi_field is copied at submit. */
+typedef struct lbm_medium {
+    const float* phi_field; /* host, ns floats, or NULL */
+    double phi, K, F_phi, alpha_m, phi_ref;
+} lbm_medium;
+
+enum { LBM_REQ_CONVERGED = 0, LBM_REQ_MAX_STEPS = 1, LBM_REQ_UNSTABLE = 2, LBM_REQ_FAILED = 3 };
+
+/* Result of a finished request.  Times are seconds on the server's host clock since
+ * lbm_server_create: submitted, admitted (state allocated), finished. */
+typedef struct lbm_result {
+    long long id;
+    int status;                 /* LBM_REQ_* */
+    long long steps;            /* time steps taken */
+    double r_u, r_T;            /* last residuals */
+    double nu_avg, nu_mp;       /* Nusselt numbers of face 0 (NaN unless it is Dirichlet) */
+    double mass_dev, heat_dev;  /* lbm_sums of the final state */
+    double t_submit, t_admit, t_done;
+    unsigned long long bytes;   /* device footprint */
+    long long sites;
+} lbm_result;
+
+/* Create a server on the current device with a device-memory budget in bytes (0: 80 % of
+ * the free memory) and a residual interval of `chunk` >= 1 steps, queued on `stream`
+ * (NULL: a private stream).  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_server_create(unsigned long long budget_bytes, int chunk, void* stream,
+                             lbm_server** out);
+
+/* Queue a request: problem p, medium m (NULL: lbm_set_medium defaults), residual tolerance
+ * tol > 0 and step limit max_steps >= 1.  Returns its id.  LBM_EINVAL for an invalid
+ * problem or one larger than the whole budget. */
+lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_medium* m,
+                             double tol, long long max_steps, long long* id);
+
+/* One scheduling round: admit what fits, advance every admitted lattice by one chunk, check
+ * the residuals, retire finished requests.  Reports the numbers of admitted and queued
+ * requests after the round (either pointer may be NULL).  Synchronises. */
+lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued);
+
+/* Move up to `max` finished results into out; *n receives how many. */
+lbm_status lbm_server_poll(lbm_server* s, lbm_result* out, int max, int* n);
+
+/* Cap the lattice sites admitted at once (0, the default: no cap).  Beyond the sites that
+ * fill the GPU, admitting more requests adds no throughput and only delays the earlier
+ * ones; with a cap the head of the queue waits until the admitted lattices hold fewer than
+ * max_active_sites sites together (a request is always admitted when nothing else is). */
+lbm_status lbm_server_set_fill(lbm_server* s, long long max_active_sites);
+
+/* Seconds since lbm_server_create on the server's host clock. */
+double lbm_server_clock(const lbm_server* s);
+
+/* Release the server and every request it still holds.  NULL is a no-op. */
+void lbm_server_destroy(lbm_server* s);
 
 /* Derived lattice parameters of the context, including the current medium. */
 lbm_status lbm_get_lattice(const lbm_ctx* ctx, lbm_lattice* out);

@@ -106,3 +106,30 @@ def batch_cavities(n: int = 64, seed: int = 2016, sizes=(32, 48, 64, 96, 128),
         Ra = float(10.0 ** rng.uniform(*log_ra))
         out.append(cavity_problem(edge, Ra=Ra, Da=Da, phi=phi, Pr=Pr))
     return out
+
+
+def serving_mix(n: int = 24, seed: int = 5, rate: float = 20.0,
+                edges=(32, 48, 64, 96, 128, 160, 192), widths=(32, 64),
+                p_channel: float = 0.4, p_fp16: float = 0.5) -> list:
+    """Seeded stream of solve requests: (arrival time in s, problem).  Poisson arrivals of
+    mean `rate` per second; a request is a porous cavity (edge from `edges`, porosity in
+    [0.4, 0.9], log10 Da in [-5, -1], log10 Ra in [3, 6]) or, with probability p_channel, a
+    porous channel of length 4W and section W x W (W from `widths`, porosity 0.7, log10 Da in
+    [-3, -2]); storage FP16 with probability p_fp16, else FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        storage = "fp16" if rng.uniform() < p_fp16 else "fp32"
+        if rng.uniform() < p_channel:
+            w = int(rng.choice(widths))
+            pb = channel_problem(4 * w, w, w, Da=float(10.0 ** rng.uniform(-3.0, -2.0)))
+        else:
+            edge = int(rng.choice(edges))
+            pb = cavity_problem(edge, Ra=float(10.0 ** rng.uniform(3.0, 6.0)),
+                                Da=float(10.0 ** rng.uniform(-5.0, -1.0)),
+                                phi=float(rng.uniform(0.4, 0.9)), Pr=0.71)
+        pb["storage"] = storage
+        out.append((t, pb))
+    return out

@@ -431,11 +431,15 @@ def nusselt(T: np.ndarray, face: int, T_wall: float, L: float, dT: float = 1.0):
 
 
 def residual(new: np.ndarray, old: np.ndarray) -> float:
-    """Relative change ||new - old||_2 / ||new||_2 (steady-state test)."""
+    """Relative change ||new - old||_2 / ||new||_2 (steady-state test); 0 for a field that
+    is zero and unchanged."""
     new = np.asarray(new, dtype=np.float64)
     old = np.asarray(old, dtype=np.float64)
     den = math.sqrt(float(np.sum(new * new)))
-    return math.sqrt(float(np.sum((new - old) ** 2))) / den if den > 0 else math.inf
+    num = math.sqrt(float(np.sum((new - old) ** 2)))
+    if den > 0:
+        return num / den
+    return math.inf if num > 0 else 0.0
 
 
 def field_error(a: np.ndarray, ref: np.ndarray) -> float:

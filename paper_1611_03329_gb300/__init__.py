@@ -35,8 +35,13 @@ ABI_SYMBOLS = (
     "lbm_macros", "lbm_macros_device", "lbm_nusselt", "lbm_sums", "lbm_residual",
     "lbm_get_lattice", "lbm_steps_done", "lbm_sync", "lbm_last_error", "lbm_status_string",
     "lbm_residual_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
-    "lbm_batch_set_block", "lbm_batch_last_error", "lbm_batch_destroy",
+    "lbm_batch_set_block", "lbm_batch_last_error", "lbm_batch_destroy", "lbm_footprint",
+    "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_poll",
+    "lbm_server_clock", "lbm_server_destroy", "lbm_server_set_fill",
 )
+
+REQ_CONVERGED, REQ_MAX_STEPS, REQ_UNSTABLE, REQ_FAILED = range(4)
+REQ_STATUS = {0: "converged", 1: "max_steps", 2: "unstable", 3: "failed"}
 
 NOALLOC_MAX_SITES = 33554432  # LBM_NOALLOC_MAX_SITES
 
@@ -87,6 +92,26 @@ class LbmLattice(C.Structure):
             v = getattr(self, name)
             out[name] = list(v) if hasattr(v, "__len__") else v
         return out
+
+
+class LbmMedium(C.Structure):
+    """Mirror of ``lbm_medium`` (include/lbm.h)."""
+    _fields_ = [("phi_field", C.POINTER(C.c_float)), ("phi", C.c_double), ("K", C.c_double),
+                ("F_phi", C.c_double), ("alpha_m", C.c_double), ("phi_ref", C.c_double)]
+
+
+class LbmResult(C.Structure):
+    """Mirror of ``lbm_result`` (include/lbm.h)."""
+    _fields_ = [("id", C.c_longlong), ("status", C.c_int), ("steps", C.c_longlong),
+                ("r_u", C.c_double), ("r_T", C.c_double), ("nu_avg", C.c_double),
+                ("nu_mp", C.c_double), ("mass_dev", C.c_double), ("heat_dev", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("bytes", C.c_ulonglong), ("sites", C.c_longlong)]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["status"] = REQ_STATUS.get(self.status, str(self.status))
+        return d
 
 
 class LbmError(RuntimeError):
@@ -147,6 +172,17 @@ def lib():
         L.lbm_batch_last_error.restype = C.c_char_p
         L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_batch_destroy.restype = None
+        L.lbm_footprint.argtypes = [pp, C.c_int, C.POINTER(C.c_ulonglong)]
+        L.lbm_server_create.argtypes = [C.c_ulonglong, C.c_int, vp, C.POINTER(vp)]
+        L.lbm_server_submit.argtypes = [vp, pp, C.POINTER(LbmMedium), C.c_double, C.c_longlong,
+                                        C.POINTER(C.c_longlong)]
+        L.lbm_server_advance.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.lbm_server_poll.argtypes = [vp, C.POINTER(LbmResult), C.c_int, C.POINTER(C.c_int)]
+        L.lbm_server_set_fill.argtypes = [vp, C.c_longlong]
+        L.lbm_server_clock.argtypes = [vp]
+        L.lbm_server_clock.restype = C.c_double
+        L.lbm_server_destroy.argtypes = [vp]
+        L.lbm_server_destroy.restype = None
         _lib = L
     return _lib
 
@@ -377,6 +413,82 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().lbm_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint(pb: dict) -> int:
+    """Device bytes a lattice for problem pb holds while it is solved (host only)."""
+    out = C.c_ulonglong()
+    st = lib().lbm_footprint(C.byref(params_from_problem(pb)),
+                             int(pb.get("phi_field") is not None), C.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_footprint: invalid problem")
+    return out.value
+
+
+class Server:
+    """Continuous-batching serving loop (``lbm_server_*``): submit problems as they arrive,
+    call advance() repeatedly, poll() finished results."""
+
+    def __init__(self, budget_bytes: int = 0, chunk: int = 100, stream: Optional[int] = None,
+                 max_active_sites: int = 0):
+        self._h = C.c_void_p()
+        st = lib().lbm_server_create(C.c_ulonglong(budget_bytes), int(chunk),
+                                     C.c_void_p(stream or 0), C.byref(self._h))
+        if st != LBM_OK:
+            raise LbmError(st, f"lbm_server_create: {lib().lbm_status_string(st).decode()}")
+        if max_active_sites:
+            st = lib().lbm_server_set_fill(self._h, C.c_longlong(max_active_sites))
+            if st != LBM_OK:
+                raise LbmError(st, "lbm_server_set_fill")
+
+    def submit(self, pb: dict, tol: float = 1e-6, max_steps: int = 50000) -> int:
+        m = LbmMedium()
+        m.phi = float(pb.get("phi", 1.0))
+        m.K = float(pb.get("K", 0.0) or 0.0)
+        m.F_phi = float(pb.get("F_phi", 0.0))
+        m.alpha_m = float(pb.get("alpha_m", -1.0))
+        m.phi_ref = float(pb.get("phi_ref", 0.0))
+        keep = None
+        if pb.get("phi_field") is not None:
+            keep = np.ascontiguousarray(np.asarray(pb["phi_field"], dtype=np.float32).reshape(-1))
+            m.phi_field = keep.ctypes.data_as(C.POINTER(C.c_float))
+        rid = C.c_longlong()
+        st = lib().lbm_server_submit(self._h, C.byref(params_from_problem(pb)), C.byref(m),
+                                     float(tol), int(max_steps), C.byref(rid))
+        del keep
+        if st != LBM_OK:
+            raise LbmError(st, f"lbm_server_submit: {lib().lbm_status_string(st).decode()}")
+        return rid.value
+
+    def advance(self):
+        """One scheduling round; returns (admitted, queued)."""
+        na, nq = C.c_int(), C.c_int()
+        st = lib().lbm_server_advance(self._h, C.byref(na), C.byref(nq))
+        if st != LBM_OK:
+            raise LbmError(st, f"lbm_server_advance: {lib().lbm_status_string(st).decode()}")
+        return na.value, nq.value
+
+    def poll(self, max_results: int = 1024) -> list:
+        buf = (LbmResult * max_results)()
+        n = C.c_int()
+        st = lib().lbm_server_poll(self._h, buf, max_results, C.byref(n))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_server_poll")
+        return [buf[k].as_dict() for k in range(n.value)]
+
+    def clock(self) -> float:
+        return lib().lbm_server_clock(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().lbm_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

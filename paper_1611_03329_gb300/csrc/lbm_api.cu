@@ -776,8 +776,12 @@ lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
     c->snap ^= 1;
     c->have_prev = true;
     if (h[4] > 0.0) return fail(c, LBM_EUNSTABLE, "velocity or temperature is not finite");
-    double ru = first ? HUGE_VAL : (h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : HUGE_VAL);
-    double rT = first ? HUGE_VAL : (h[3] > 0.0 ? std::sqrt(h[2] / h[3]) : HUGE_VAL);
+    // relative change; a field that is zero and unchanged has residual 0
+    auto rel = [](double num, double den) {
+        return den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? HUGE_VAL : 0.0);
+    };
+    double ru = first ? HUGE_VAL : rel(h[0], h[1]);
+    double rT = first ? HUGE_VAL : rel(h[2], h[3]);
     if (r_u) *r_u = ru;
     if (r_T) *r_T = rT;
     return LBM_OK;
@@ -1090,5 +1094,257 @@ lbm_status lbm_batch_set_block(lbm_batch* b, int block_threads, int rows) {
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "null batch"; }
+
+}  // extern "C"
+
+// ---- footprint and serving loop ---------------------------------------------------------------
+#include <chrono>
+#include <deque>
+
+namespace {
+
+unsigned long long footprint_of(const lbm_params* p, const lbm_lattice& L, int has_phi_field) {
+    const unsigned long long ns = (unsigned long long)p->nx * p->ny * p->nz;
+    const unsigned long long sq = (ns + 63) / 64 * 64;
+    const unsigned long long elem = p->storage == LBM_STORE_FP32 ? 4 : 2;
+    unsigned long long b = 2ull * (lbm::kQ + lbm::kQT) * elem * sq;  // two population copies
+    if (p->flow_bc[1] == LBM_FLOW_OUTFLOW) b += 2ull * lbm::kOutSlots * 4 * p->ny * p->nz;
+    if (p->storage != LBM_STORE_FP32) b += 2ull * 4 * ns;  // temperature planes
+    if (has_phi_field) b += 4 * ns;
+    b += 9ull * 4 * ns;  // macro fields of the residual
+    b += 5ull * 8 * lbm::reduction_blocks() + 8ull * (p->nx > p->ny ? p->nx : p->ny) + 64;
+    (void)L;
+    return b;
+}
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct lbm_server {
+    struct Req {
+        long long id = 0;
+        lbm_params p{};
+        double phi = 1.0, K = 0.0, F_phi = 0.0, alpha_m = -1.0, phi_ref = 0.0;
+        std::vector<float> phi_field;
+        double tol = 1e-6;
+        long long max_steps = 1;
+        unsigned long long bytes = 0;
+        double t_submit = 0.0, t_admit = 0.0;
+        lbm_ctx* ctx = nullptr;
+        double r_u = HUGE_VAL, r_T = HUGE_VAL;
+    };
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    unsigned long long budget = 0, used = 0;
+    long long max_active_sites = 0;  // 0: no cap
+    long long active_sites = 0;
+    int chunk = 100;
+    std::deque<Req*> queue;
+    std::vector<Req*> active;
+    std::vector<lbm_result> done;
+    lbm_batch* batch = nullptr;
+    bool dirty = true;
+    long long next_id = 1;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+};
+
+namespace {
+
+void server_finish(lbm_server* s, size_t k, int status) {
+    lbm_server::Req* r = s->active[k];
+    lbm_result res{};
+    res.id = r->id;
+    res.status = status;
+    res.steps = r->ctx ? r->ctx->steps : 0;
+    res.r_u = r->r_u;
+    res.r_T = r->r_T;
+    res.nu_avg = res.nu_mp = NAN;
+    res.mass_dev = res.heat_dev = NAN;
+    if (r->ctx && status != LBM_REQ_FAILED) {
+        if (r->p.heat_bc[0] == LBM_HEAT_DIRICHLET && r->p.nx >= 2)
+            lbm_nusselt(r->ctx, 0, &res.nu_avg, nullptr, &res.nu_mp);
+        lbm_sums(r->ctx, &res.mass_dev, &res.heat_dev);
+    }
+    res.t_submit = r->t_submit;
+    res.t_admit = r->t_admit;
+    res.t_done = now_s(s->t0);
+    res.bytes = r->bytes;
+    res.sites = (long long)r->p.nx * r->p.ny * r->p.nz;
+    s->done.push_back(res);
+    lbm_destroy(r->ctx);
+    s->used -= r->bytes;
+    s->active_sites -= res.sites;
+    delete r;
+    s->active.erase(s->active.begin() + (long)k);
+    s->dirty = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_footprint(const lbm_params* p, int has_phi_field, unsigned long long* bytes) {
+    if (!p || !bytes) return LBM_EINVAL;
+    lbm_lattice L;
+    if (derive(p, &L)) return LBM_EINVAL;
+    *bytes = footprint_of(p, L, has_phi_field);
+    return LBM_OK;
+}
+
+lbm_status lbm_server_create(unsigned long long budget_bytes, int chunk, void* stream,
+                             lbm_server** out) {
+    if (!out || chunk < 1) return LBM_EINVAL;
+    lbm_server* s = new (std::nothrow) lbm_server();
+    if (!s) return LBM_ENOMEM;
+    s->chunk = chunk;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess && !budget_bytes) {
+        size_t fr = 0, tot = 0;
+        e = cudaMemGetInfo(&fr, &tot);
+        budget_bytes = (unsigned long long)(0.8 * (double)fr);
+    }
+    if (e == cudaSuccess) {
+        if (stream) {
+            s->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+            s->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e != cudaSuccess) {
+        delete s;
+        return LBM_ECUDA;
+    }
+    s->budget = budget_bytes;
+    *out = s;
+    return LBM_OK;
+}
+
+lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_medium* m, double tol,
+                             long long max_steps, long long* id) {
+    if (!s || !p || !(tol > 0.0) || max_steps < 1) return LBM_EINVAL;
+    lbm_lattice L;
+    if (derive(p, &L)) return LBM_EINVAL;
+    auto* r = new (std::nothrow) lbm_server::Req();
+    if (!r) return LBM_ENOMEM;
+    r->p = *p;
+    if (m) {
+        r->phi = m->phi;
+        r->K = m->K;
+        r->F_phi = m->F_phi;
+        r->alpha_m = m->alpha_m;
+        r->phi_ref = m->phi_ref;
+        if (m->phi_field)
+            r->phi_field.assign(m->phi_field, m->phi_field + (size_t)p->nx * p->ny * p->nz);
+    }
+    r->tol = tol;
+    r->max_steps = max_steps;
+    r->bytes = footprint_of(p, L, m && m->phi_field ? 1 : 0);
+    if (r->bytes > s->budget) {
+        delete r;
+        return LBM_EINVAL;
+    }
+    r->id = s->next_id++;
+    r->t_submit = now_s(s->t0);
+    s->queue.push_back(r);
+    if (id) *id = r->id;
+    return LBM_OK;
+}
+
+lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
+    if (!s) return LBM_EINVAL;
+    if (cudaSetDevice(s->device) != cudaSuccess) return LBM_ECUDA;
+    // admission in arrival order while the head of the queue fits the memory budget and, with
+    // a cap, while the admitted lattices hold fewer sites than the cap (a lone request is
+    // always admitted)
+    while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
+        lbm_server::Req* r = s->queue.front();
+        const long long sites = (long long)r->p.nx * r->p.ny * r->p.nz;
+        if (s->max_active_sites > 0 && s->active_sites > 0 &&
+            s->active_sites + sites > s->max_active_sites)
+            break;
+        s->queue.pop_front();
+        s->active_sites += sites;
+        r->t_admit = now_s(s->t0);
+        lbm_status st = lbm_create(&r->p, s->stream, &r->ctx);
+        if (st == LBM_OK)
+            st = lbm_set_medium(r->ctx, r->phi_field.empty() ? nullptr : r->phi_field.data(),
+                                r->phi, r->K, r->F_phi, r->alpha_m, r->phi_ref);
+        s->active.push_back(r);
+        s->used += r->bytes;
+        s->dirty = true;
+        if (st != LBM_OK) server_finish(s, s->active.size() - 1, LBM_REQ_FAILED);
+    }
+    if (!s->active.empty()) {
+        if (s->dirty) {
+            lbm_batch_destroy(s->batch);
+            s->batch = nullptr;
+            std::vector<lbm_ctx*> ctxs;
+            for (auto* r : s->active) ctxs.push_back(r->ctx);
+            lbm_status st = lbm_batch_create(ctxs.data(), (int)ctxs.size(), s->stream, &s->batch);
+            if (st != LBM_OK) return st;
+            s->dirty = false;
+        }
+        lbm_status st = lbm_batch_step(s->batch, s->chunk);
+        if (st != LBM_OK) return st;
+        for (size_t k = 0; k < s->active.size();) {
+            lbm_server::Req* r = s->active[k];
+            st = lbm_residual(r->ctx, &r->r_u, &r->r_T);
+            int status = -1;
+            if (st == LBM_EUNSTABLE) status = LBM_REQ_UNSTABLE;
+            else if (st != LBM_OK) status = LBM_REQ_FAILED;
+            else if (r->r_u < r->tol && r->r_T < r->tol) status = LBM_REQ_CONVERGED;
+            else if (r->ctx->steps >= r->max_steps) status = LBM_REQ_MAX_STEPS;
+            if (status >= 0) server_finish(s, k, status);
+            else ++k;
+        }
+    }
+    if (s->active.empty() && s->batch) {
+        lbm_batch_destroy(s->batch);
+        s->batch = nullptr;
+    }
+    if (n_active) *n_active = (int)s->active.size();
+    if (n_queued) *n_queued = (int)s->queue.size();
+    return LBM_OK;
+}
+
+lbm_status lbm_server_poll(lbm_server* s, lbm_result* out, int max, int* n) {
+    if (!s || (max > 0 && !out)) return LBM_EINVAL;
+    int k = 0;
+    while (k < max && !s->done.empty()) {
+        out[k++] = s->done.front();
+        s->done.erase(s->done.begin());
+    }
+    if (n) *n = k;
+    return LBM_OK;
+}
+
+double lbm_server_clock(const lbm_server* s) { return s ? now_s(s->t0) : 0.0; }
+
+lbm_status lbm_server_set_fill(lbm_server* s, long long max_active_sites) {
+    if (!s || max_active_sites < 0) return LBM_EINVAL;
+    s->max_active_sites = max_active_sites;
+    return LBM_OK;
+}
+
+void lbm_server_destroy(lbm_server* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    lbm_batch_destroy(s->batch);
+    for (auto* r : s->active) {
+        lbm_destroy(r->ctx);
+        delete r;
+    }
+    for (auto* r : s->queue) delete r;
+    if (s->own_stream && s->stream) {
+        cudaStreamSynchronize(s->stream);
+        cudaStreamDestroy(s->stream);
+    }
+    delete s;
+}
 
 }  // extern "C"

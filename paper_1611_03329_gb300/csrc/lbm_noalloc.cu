@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(kThreads)
         for (int k = 0; k < kVals; ++k)
             t[k] = warp_sum(threadIdx.x < kThreads / 32 ? sh[k][threadIdx.x] : 0.0);
         if (threadIdx.x == 0) {
-            out[0] = t[1] > 0.0 ? sqrt(t[0] / t[1]) : HUGE_VAL;
-            out[1] = t[3] > 0.0 ? sqrt(t[2] / t[3]) : HUGE_VAL;
+            out[0] = t[1] > 0.0 ? sqrt(t[0] / t[1]) : (t[0] > 0.0 ? HUGE_VAL : 0.0);
+            out[1] = t[3] > 0.0 ? sqrt(t[2] / t[3]) : (t[2] > 0.0 ? HUGE_VAL : 0.0);
             out[2] = t[4];
         }
     }
