@@ -49,6 +49,11 @@ class _Lattice(C.Structure):
         ("flow_bc", C.c_int * 6), ("heat_bc", C.c_int * 6),
         ("face_T", C.c_double * 6), ("face_u", (C.c_double * 3) * 6),
         ("U_out", C.c_double),
+        ("enthalpy", C.c_int), ("flow_off", C.c_int),
+        ("c_pl", C.c_double), ("c_ref", C.c_double),
+        ("sigma_s", C.c_double), ("sigma_l", C.c_double),
+        ("T_s", C.c_double), ("T_l", C.c_double), ("L_a", C.c_double),
+        ("alpha_s", C.c_double), ("alpha_l", C.c_double),
     ]
 
 
@@ -86,6 +91,10 @@ def lib():
                                    C.c_double, dp]
         L.orc_collide_site.argtypes = [C.POINTER(_Lattice), dp, dp, C.c_double, C.c_double,
                                        C.c_double, C.c_double, dp, dp, dp]
+        L.orc_enthalpy_state.argtypes = [C.POINTER(_Lattice), C.c_double, C.c_double, dp, dp]
+        L.orc_enthalpy_of.argtypes = [C.POINTER(_Lattice), C.c_double, C.c_double]
+        L.orc_enthalpy_of.restype = C.c_double
+        L.orc_geq7_enthalpy.argtypes = [C.POINTER(_Lattice), C.c_double, C.c_double, dp, dp]
         if L.orc_sizeof_lattice() != C.sizeof(_Lattice):
             raise RuntimeError("oracle struct layout mismatch")
         _lib = L
@@ -202,6 +211,17 @@ class LatticeParams:
     L: float = 1.0
     dT: float = 1.0
     T_init: float = 0.5
+    enthalpy: bool = False
+    flow_off: bool = False
+    c_pl: float = 1.0
+    c_ref: float = 1.0
+    sigma_s: float = 1.0
+    sigma_l: float = 1.0
+    T_s: float = 0.0
+    T_l: float = 0.0
+    L_a: float = 1.0
+    alpha_s: float = 0.0
+    alpha_l: float = 0.0
     phi_field: Optional[np.ndarray] = field(default=None, repr=False)
 
     def to_c(self) -> _Lattice:
@@ -224,6 +244,12 @@ class LatticeParams:
             for a in range(3):
                 c.face_u[k][a] = self.face_u[k][a]
         c.U_out = self.U_out
+        c.enthalpy = int(self.enthalpy)
+        c.flow_off = int(self.flow_off)
+        c.c_pl, c.c_ref = self.c_pl, self.c_ref
+        c.sigma_s, c.sigma_l = self.sigma_s, self.sigma_l
+        c.T_s, c.T_l, c.L_a = self.T_s, self.T_l, self.L_a
+        c.alpha_s, c.alpha_l = self.alpha_s, self.alpha_l
         return c
 
 
@@ -301,7 +327,23 @@ def map_problem(pb: dict) -> LatticeParams:
     if U_out <= 0:
         U_out = u0
     face_u = [tuple(float(v) for v in fu) for fu in pb.get("face_u", [(0.0, 0.0, 0.0)] * 6)]
+    # enthalpy model (App. B): melting point T_m (T_s = T_l unless given), Stefan number
+    # St = c_pl dT / L_a, c_ref the harmonic mean of c_pl and c_ps (Eq. B13), liquid
+    # diffusivity = alpha_f, solid diffusivity alpha_f / alpha_ratio (alpha_l / alpha_s).
+    ent = {}
+    if pb.get("enthalpy", False):
+        c_pl = float(pb.get("c_pl", 1.0)); c_ps = float(pb.get("c_ps", 1.0))
+        T_m = float(pb.get("T_m", 0.5))
+        ent = dict(enthalpy=True, flow_off=bool(pb.get("flow_off", False)), c_pl=c_pl,
+                   c_ref=2.0 / (1.0 / c_pl + 1.0 / c_ps),
+                   sigma_s=float(pb.get("sigma_s", sigma)), sigma_l=float(pb.get("sigma_l", sigma)),
+                   T_s=float(pb.get("T_s", T_m)), T_l=float(pb.get("T_l", T_m)),
+                   L_a=c_pl * dT / float(pb.get("St", 1.0)),
+                   alpha_l=float(pb.get("alpha_l", alpha_f)),
+                   alpha_s=float(pb.get("alpha_s", float(pb.get("alpha_l", alpha_f))
+                                        / float(pb.get("alpha_ratio", 1.0)))))
     return LatticeParams(
+        **ent,
         nx=nx, ny=ny, nz=nz, rho0=float(pb.get("rho0", 1.0)), T0=float(pb.get("T0", 0.5)),
         sigma=sigma, varpi=varpi,
         s=relaxation_vector(s_nu, rates["s_e"], rates["s_eps"], rates["s_q"], rates["s_pi"],
@@ -383,6 +425,27 @@ class Oracle:
         T = np.zeros(self.shape)
         lib().orc_macros(self._h, _p(rho), _p(u), _p(T))
         return rho, u, T
+
+
+def enthalpy_state(lp: LatticeParams, En: float, phi: float = 1.0):
+    """(T, f_l) from the effective enthalpy (Eqs. B8, B9)."""
+    T, fl = C.c_double(), C.c_double()
+    c = lp.to_c()
+    lib().orc_enthalpy_state(C.byref(c), float(phi), float(En), C.byref(T), C.byref(fl))
+    return T.value, fl.value
+
+
+def enthalpy_of(lp: LatticeParams, T: float, phi: float = 1.0) -> float:
+    c = lp.to_c()
+    return lib().orc_enthalpy_of(C.byref(c), float(phi), float(T))
+
+
+def geq7_enthalpy(lp: LatticeParams, En: float, T: float, u) -> np.ndarray:
+    """Eq. B12."""
+    out = np.zeros(Q7)
+    c = lp.to_c()
+    lib().orc_geq7_enthalpy(C.byref(c), float(En), float(T), _p(_vec(u)), _p(out))
+    return out
 
 
 def collide_site(lp: LatticeParams, f, g, phi=None, K=None, Fphi=None, zeta_alpha=None):

@@ -22,6 +22,9 @@
  *  11. n = N g (Eq. 36); n_eq (Eq. 37); n* = n - Q (n - n_eq) (Eq. 34);
  *      g* = N^-1 n* with N^-1 typed from Eq. 43;
  *  12. store f*, g* in the other array.
+ * With the enthalpy model (App. B) step 2 becomes En_e = sum g (Eq. B7) with T and f_l from
+ * Eqs. B8-B9, the flow is collided only where f_l >= 0.5 (elsewhere f rests at f_eq(rho, 0)
+ * and u = 0), and step 11 uses n_eq of Eq. B6 with zeta_alpha from Eq. B11.
  *
  * Boundary rules (the paper uses non-equilibrium extrapolation; this oracle follows the
  * halfway rules that the GPU library implements, Eqs. 10 and 35 in pull form):
@@ -311,6 +314,14 @@ typedef struct {
     double face_T[6];
     double face_u[6][3];
     double U_out;          /* advection speed of the convective outflow */
+    /* enthalpy-based D3Q7 model for solid-liquid phase change (App. B) */
+    int enthalpy;          /* 1: g carries the effective enthalpy En_e (Eq. B7) */
+    int flow_off;          /* 1: u = 0 everywhere (conduction melting) */
+    double c_pl, c_ref;    /* liquid and reference specific heats (Eq. B13) */
+    double sigma_s, sigma_l; /* heat-capacity ratios of the solid and liquid regions (Eq. B4) */
+    double T_s, T_l;       /* solidus and liquidus temperatures */
+    double L_a;            /* latent heat */
+    double alpha_s, alpha_l; /* diffusivities of the solid and liquid phases */
 } orc_lattice;
 
 typedef struct {
@@ -438,14 +449,53 @@ static double pull_g(const orc_state* S, const double* gp, int i, int x, int y, 
     int io = opposite7(i);
     if (L->heat_bc[face] == HT_ADIABATIC) return gp[(long)io * S->ns + here];
     if (L->heat_bc[face] == HT_DIRICHLET) {
+        /* twice the even part of the wall equilibrium: omega sigma T_w (Eq. 42) or
+         * varpi c_ref T_w / 6 (Eq. B12) */
         double om = L->varpi / 6.0;
-        return -gp[(long)io * S->ns + here] + 2.0 * om * L->sigma * L->face_T[face];
+        double c = L->enthalpy ? L->c_ref : L->sigma;
+        return -gp[(long)io * S->ns + here] + 2.0 * om * c * L->face_T[face];
     }
     /* convective outflow on the x-high face */
     if (!use_outflow) return 0.0;
     double inner = pull_g(S, gp, i, x - 1, y, z, 0, hist);
     double old = hist[y + (long)L->ny * z];
     return (old + L->U_out * inner) / (1.0 + L->U_out);
+}
+
+/* ---- enthalpy model (App. B) ---------------------------------------------------------- */
+
+/* Eqs. B8 and B9: temperature and liquid fraction from the effective enthalpy, with
+ * En_{e,s} = sigma_s c_pl T_s and En_{e,l} = sigma_l c_pl T_l + phi L_a. */
+void orc_enthalpy_state(const orc_lattice* L, double phi, double En, double* T, double* fl) {
+    double Es = L->sigma_s * L->c_pl * L->T_s;
+    double El = L->sigma_l * L->c_pl * L->T_l + phi * L->L_a;
+    if (En <= Es) {
+        *T = En / (L->sigma_s * L->c_pl);
+        *fl = 0.0;
+    } else if (En >= El) {
+        *T = L->T_l + (En - El) / (L->sigma_l * L->c_pl);
+        *fl = 1.0;
+    } else {
+        double frac = (En - Es) / (El - Es);
+        *T = L->T_s + frac * (L->T_l - L->T_s);
+        *fl = frac;
+    }
+}
+
+/* Effective enthalpy of a phase-pure state at temperature T: solid at or below T_s, else
+ * liquid (the inverse of Eq. B8 outside the mushy range). */
+double orc_enthalpy_of(const orc_lattice* L, double phi, double T) {
+    if (T <= L->T_s) return L->sigma_s * L->c_pl * T;
+    return L->sigma_l * L->c_pl * T + phi * L->L_a;
+}
+
+/* Eq. B12: g_0 = En - varpi c_ref T, g_i = varpi c_ref T / 6 + (e_i . u) c_pl T / 2. */
+void orc_geq7_enthalpy(const orc_lattice* L, double En, double T, const double* u, double* geq) {
+    geq[0] = En - L->varpi * L->c_ref * T;
+    for (int i = 1; i < Q7; ++i) {
+        double eu = E7[0][i] * u[0] + E7[1][i] * u[1] + E7[2][i] * u[2];
+        geq[i] = L->varpi * L->c_ref * T / 6.0 + 0.5 * eu * L->c_pl * T;
+    }
 }
 
 /* ---- one site ------------------------------------------------------------------------ */
@@ -457,7 +507,11 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
     ensure_minv();
     double sumg = 0.0;
     for (int i = 0; i < Q7; ++i) sumg += g[i];
-    double T = sumg / L->sigma; /* Eq. 39 */
+    double T, fl = 1.0;
+    if (L->enthalpy)
+        orc_enthalpy_state(L, phi, sumg, &T, &fl); /* Eqs. B7-B9 */
+    else
+        T = sumg / L->sigma; /* Eq. 39 */
     double G[3];
     for (int a = 0; a < 3; ++a) G[a] = L->buoy[a] * (T - L->T0) + L->accel[a]; /* Eq. 5 */
     double rho = 0.0;
@@ -468,6 +522,13 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
     orc_force(u, G, phi, L->nu, K, Fphi, F); /* Eq. 4 */
 
     double m[Q19], feq[Q19], meq[Q19], S[Q19], ms[Q19];
+    if (L->enthalpy && (L->flow_off || fl < 0.5)) {
+        /* solid (or no flow): the flow is not collided; the populations rest at f_eq(rho, 0) */
+        u[0] = u[1] = u[2] = 0.0;
+        double zero[3] = {0.0, 0.0, 0.0};
+        orc_feq19(rho, zero, phi, L->rho0, fout);
+        goto thermal;
+    }
     for (int k = 0; k < Q19; ++k) {
         m[k] = 0.0;
         for (int i = 0; i < Q19; ++i) m[k] += M19[k][i] * f[i];
@@ -485,8 +546,11 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
         for (int k = 0; k < Q19; ++k) fout[i] += MINV19[i][k] * ms[k];
     }
 
+thermal:;
     double n[Q7], neq[Q7], ns[Q7], zeta[Q7];
     zeta[0] = L->zeta_T;
+    if (L->enthalpy) /* Eq. B11 with alpha_e = f_l alpha_l + (1 - f_l) alpha_s */
+        zeta_alpha = 1.0 / (0.5 + (fl * L->alpha_l + (1.0 - fl) * L->alpha_s) / (L->varpi / 3.0));
     zeta[1] = zeta[2] = zeta[3] = zeta_alpha;
     zeta[4] = L->zeta_e;
     zeta[5] = zeta[6] = L->zeta_nu;
@@ -494,7 +558,16 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
         n[k] = 0.0;
         for (int i = 0; i < Q7; ++i) n[k] += N7[k][i] * g[i];
     }
-    orc_neq7(T, u, L->sigma, L->varpi, neq);
+    if (L->enthalpy) { /* Eq. B6 */
+        neq[0] = sumg;
+        neq[1] = L->c_pl * T * u[0];
+        neq[2] = L->c_pl * T * u[1];
+        neq[3] = L->c_pl * T * u[2];
+        neq[4] = L->varpi * L->c_ref * T;
+        neq[5] = neq[6] = 0.0;
+    } else {
+        orc_neq7(T, u, L->sigma, L->varpi, neq);
+    }
     for (int k = 0; k < Q7; ++k) ns[k] = n[k] - zeta[k] * (n[k] - neq[k]); /* Eq. 34 */
     for (int i = 0; i < Q7; ++i) {
         gout[i] = 0.0;
@@ -581,7 +654,10 @@ void orc_init_equilibrium(void* h, double T_uniform, const double* T_field, cons
         double T = T_field ? T_field[s] : T_uniform;
         double feq[Q19], geq[Q7];
         orc_feq19(L->rho0, u, phi, L->rho0, feq);
-        orc_geq7(T, u, L->sigma, L->varpi, geq);
+        if (L->enthalpy)
+            orc_geq7_enthalpy(L, orc_enthalpy_of(L, phi, T), T, u, geq);
+        else
+            orc_geq7(T, u, L->sigma, L->varpi, geq);
         for (int i = 0; i < Q19; ++i) S->f[(long)i * S->ns + s] = feq[i];
         for (int i = 0; i < Q7; ++i) S->g[(long)i * S->ns + s] = geq[i];
     }
