@@ -100,6 +100,18 @@ typedef struct lbm_params {
     double face_u[6][3];             /* velocity of LBM_FLOW_VELOCITY faces */
     double T_init;                   /* initial uniform temperature */
     double U_out;                    /* convective outflow speed; <= 0: u0 */
+    /* enthalpy-based D3Q7 model for solid-liquid phase change (App. B); FP32 storage,
+     * uniform medium and no outflow only.  The D3Q7 populations then carry the effective
+     * enthalpy En_e (Eq. B7); T and the liquid fraction follow Eqs. B8-B9; the flow is
+     * collided only where f_l >= 0.5 (elsewhere it rests at f_eq(rho, 0), u = 0). */
+    int enthalpy;                    /* 1 enables the model */
+    int flow_off;                    /* 1: u = 0 everywhere (conduction melting) */
+    double T_m;                      /* melting point; T_s = T_l = T_m unless T_l > T_s */
+    double T_s, T_l;                 /* solidus and liquidus temperatures */
+    double St;                       /* Stefan number c_pl dT / L_a (1) */
+    double c_pl, c_ps;               /* specific heats (1, 1); c_ref = harmonic mean (Eq. B13) */
+    double sigma_s, sigma_l;         /* heat-capacity ratios (Eq. B4); <= 0: sigma */
+    double alpha_ratio;              /* alpha_l / alpha_s (1); alpha_l = the fluid diffusivity */
 } lbm_params;
 
 /*
@@ -117,6 +129,8 @@ typedef struct lbm_lattice {
     double phi, K, F_phi, phi_ref;     /* F_phi < 0: Ergun per site; K may be +inf */
     int has_phi_field;
     double U_out;
+    int enthalpy, flow_off;
+    double c_pl, c_ref, sigma_s, sigma_l, T_s, T_l, L_a, alpha_s, alpha_l;
 } lbm_lattice;
 
 /* Fill p with the paper's defaults (Sec. 4: rho0 = 1, J = sigma = Gamma = 1, varpi = 1/2,
@@ -200,7 +214,8 @@ lbm_status lbm_nusselt(lbm_ctx* ctx, int face, double* nu_avg, double* nu_profil
                        double* nu_mp);
 
 /* Totals of the stored populations, FP64 accumulation: mass_dev = sum_s sum_i f_i - ns rho0
- * (mass, Eq. 25) and heat_dev = sum_s sum_i g_i - ns sigma T0 (heat, Eq. 39).
+ * (mass, Eq. 25) and heat_dev = sum_s sum_i g_i - ns sigma T0 (heat, Eq. 39); with the
+ * enthalpy model heat_dev is the total effective enthalpy sum_s sum_i g_i (Eq. B7).
  * Either pointer may be NULL.  Synchronises.  LBM_EUNSTABLE if a total is not finite. */
 lbm_status lbm_sums(lbm_ctx* ctx, double* mass_dev, double* heat_dev);
 

@@ -522,7 +522,9 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
     orc_force(u, G, phi, L->nu, K, Fphi, F); /* Eq. 4 */
 
     double m[Q19], feq[Q19], meq[Q19], S[Q19], ms[Q19];
-    if (L->enthalpy && (L->flow_off || fl < 0.5)) {
+    /* the liquid-fraction gate is a discrete decision: taken on the FP32 value of f_l, the
+     * precision the GPU kernel decides in */
+    if (L->enthalpy && (L->flow_off || (float)fl < 0.5f)) {
         /* solid (or no flow): the flow is not collided; the populations rest at f_eq(rho, 0) */
         u[0] = u[1] = u[2] = 0.0;
         double zero[3] = {0.0, 0.0, 0.0};

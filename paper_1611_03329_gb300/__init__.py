@@ -66,6 +66,10 @@ class LbmParams(C.Structure):
         ("flow_bc", C.c_int * 6), ("heat_bc", C.c_int * 6),
         ("face_T", C.c_double * 6), ("face_u", (C.c_double * 3) * 6),
         ("T_init", C.c_double), ("U_out", C.c_double),
+        ("enthalpy", C.c_int), ("flow_off", C.c_int),
+        ("T_m", C.c_double), ("T_s", C.c_double), ("T_l", C.c_double), ("St", C.c_double),
+        ("c_pl", C.c_double), ("c_ps", C.c_double), ("sigma_s", C.c_double),
+        ("sigma_l", C.c_double), ("alpha_ratio", C.c_double),
     ]
 
 
@@ -84,6 +88,10 @@ class LbmLattice(C.Structure):
         ("phi", C.c_double), ("K", C.c_double), ("F_phi", C.c_double), ("phi_ref", C.c_double),
         ("has_phi_field", C.c_int),
         ("U_out", C.c_double),
+        ("enthalpy", C.c_int), ("flow_off", C.c_int),
+        ("c_pl", C.c_double), ("c_ref", C.c_double), ("sigma_s", C.c_double),
+        ("sigma_l", C.c_double), ("T_s", C.c_double), ("T_l", C.c_double), ("L_a", C.c_double),
+        ("alpha_s", C.c_double), ("alpha_l", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -212,6 +220,11 @@ def params_from_problem(pb: dict) -> LbmParams:
         p.Da = float(pb["Da"])
     if "T_init" not in pb:
         p.T_init = p.T0
+    p.enthalpy = int(bool(pb.get("enthalpy", False)))
+    p.flow_off = int(bool(pb.get("flow_off", False)))
+    for k in ("T_m", "T_s", "T_l", "St", "c_pl", "c_ps", "sigma_s", "sigma_l", "alpha_ratio"):
+        if k in pb and pb[k] is not None:
+            setattr(p, k, float(pb[k]))
     p.gravity_axis = int(pb.get("gravity_axis", 2))
     p.gravity_sign = int(pb.get("gravity_sign", -1))
     for a, v in enumerate(pb.get("accel", (0.0, 0.0, 0.0))):

@@ -202,6 +202,26 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
         if (!finite_pos(L->U_out)) return "outflow speed must be > 0";
     }
     if (!std::isfinite(p->T_init)) return "T_init must be finite";
+    L->enthalpy = p->enthalpy ? 1 : 0;
+    L->flow_off = p->flow_off ? 1 : 0;
+    if (p->enthalpy) {
+        if (p->storage != LBM_STORE_FP32) return "the enthalpy model stores FP32 populations";
+        if (p->flow_bc[1] == LBM_FLOW_OUTFLOW) return "the enthalpy model has no outflow";
+        if (!finite_pos(p->St) || !finite_pos(p->c_pl) || !finite_pos(p->c_ps) ||
+            !finite_pos(p->alpha_ratio))
+            return "St, c_pl, c_ps and alpha_ratio must be > 0";
+        if (!std::isfinite(p->T_m) || !std::isfinite(p->T_s) || !std::isfinite(p->T_l))
+            return "phase-change temperatures must be finite";
+        L->c_pl = p->c_pl;
+        L->c_ref = 2.0 / (1.0 / p->c_pl + 1.0 / p->c_ps);  // Eq. B13
+        L->sigma_s = p->sigma_s > 0.0 ? p->sigma_s : p->sigma;
+        L->sigma_l = p->sigma_l > 0.0 ? p->sigma_l : p->sigma;
+        L->T_s = p->T_l > p->T_s ? p->T_s : p->T_m;
+        L->T_l = p->T_l > p->T_s ? p->T_l : p->T_m;
+        L->L_a = p->c_pl * dT / p->St;  // St = c_pl dT / L_a
+        L->alpha_l = L->alpha_f;
+        L->alpha_s = L->alpha_f / p->alpha_ratio;
+    }
     return nullptr;
 }
 
@@ -232,6 +252,11 @@ lbm_status lbm_params_default(lbm_params* p) {
     p->gravity_axis = 2;
     p->gravity_sign = -1;
     p->T_init = 0.5;
+    p->T_m = 0.5;
+    p->St = 1.0;
+    p->c_pl = p->c_ps = 1.0;
+    p->sigma_s = p->sigma_l = -1.0;
+    p->alpha_ratio = 1.0;
     return LBM_OK;
 }
 
@@ -274,6 +299,24 @@ void fill_kparams(lbm_ctx* c) {
     k.nz = p.nz;
     k.nyz = p.ny * p.nz;
     k.block_threads = c->block_threads;
+    k.enthalpy = L.enthalpy;
+    k.flow_off = L.flow_off;
+    if (L.enthalpy) {
+        const double Es = L.sigma_s * L.c_pl * L.T_s;
+        const double El = L.sigma_l * L.c_pl * L.T_l + L.phi * L.L_a;
+        k.ent_Es = (float)Es;
+        k.ent_El = (float)El;
+        k.ent_is = (float)(1.0 / (L.sigma_s * L.c_pl));
+        k.ent_il = (float)(1.0 / (L.sigma_l * L.c_pl));
+        k.ent_Ts = (float)L.T_s;
+        k.ent_Tl = (float)L.T_l;
+        k.ent_idE = El > Es ? (float)(1.0 / (El - Es)) : 0.0f;
+        k.c_pl = (float)L.c_pl;
+        k.c_ref = (float)L.c_ref;
+        k.alpha_s = (float)L.alpha_s;
+        k.alpha_l = (float)L.alpha_l;
+        k.inv_csT2 = (float)(3.0 / L.varpi);
+    }
     k.storage = p.storage;
     k.om0 = (float)(1.0 - L.varpi);
     k.om1 = (float)(L.varpi / 6.0);
@@ -288,7 +331,9 @@ void fill_kparams(lbm_ctx* c) {
         if (p.flow_bc[f] == LBM_FLOW_VELOCITY) k.vel_mask |= bit;
         k.heat_kind[f] = p.heat_bc[f];
         // anti-bounce-back term 2 omega_i sigma (T_w - T0) in deviation form, omega_i = varpi/6
-        k.heat_abb[f] = (float)(2.0 * (L.varpi / 6.0) * L.sigma * (p.face_T[f] - L.T0));
+        // enthalpy model: full values, weight varpi c_ref / 6 (Eq. B12)
+        k.heat_abb[f] = L.enthalpy ? (float)(2.0 * (L.varpi / 6.0) * L.c_ref * p.face_T[f])
+                                   : (float)(2.0 * (L.varpi / 6.0) * L.sigma * (p.face_T[f] - L.T0));
         for (int a = 0; a < 3; ++a) k.face_u[f][a] = (float)p.face_u[f][a];
     }
     double U = L.U_out > 0.0 ? L.U_out : 0.0;
@@ -529,6 +574,8 @@ lbm_status lbm_set_medium(lbm_ctx* c, const float* phi_field, double phi, double
     if (st != LBM_OK) return st;
     lbm_lattice L = c->lat;
     double mean = phi;
+    if (phi_field && L.enthalpy)
+        return fail(c, LBM_EINVAL, "the enthalpy model takes a uniform medium");
     if (phi_field) {
         double sum = 0.0;
         for (long long s = 0; s < c->ns; ++s) {
@@ -627,6 +674,7 @@ static double plane_offset(const lbm_ctx* c, int q) {
         double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
         return w * L.rho0;
     }
+    if (L.enthalpy) return 0.0;  // D3Q7 planes hold the full enthalpy populations
     int i = q - lbm::kQ;
     double om = i == 0 ? 1.0 - L.varpi : L.varpi / 6.0;
     return om * L.sigma * L.T0;
@@ -808,7 +856,7 @@ struct lbm_batch {
     int rows = 1;  // z-planes per block of the batched step
     struct Group {
         int storage = 0;
-        bool het = false, outflow = false;
+        bool het = false, outflow = false, enthalpy = false;
         std::vector<int> members;           // indices into ctx
         lbm::BatchLattice* dtab = nullptr;  // device table
         // host mirror in pageable memory: an asynchronous copy from it stages the data before
@@ -884,8 +932,8 @@ lbm_status batch_launch_steps(lbm_batch* b, int nsteps, bool tuning) {
     for (int t = 0; t < nsteps; ++t)
         for (auto& g : b->groups)
             LBM_BCUDA(lbm::launch_batch_step(g.dtab, g.dblk, g.nblocks, b->block_threads, b->rows,
-                                             g.storage, g.het, g.outflow, tuning ? 0 : (t & 1),
-                                             b->stream));
+                                             g.storage, g.het, g.outflow, g.enthalpy,
+                                             tuning ? 0 : (t & 1), b->stream));
     return LBM_OK;
 }
 
@@ -966,15 +1014,18 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
         lbm_ctx* c = b->ctx[k];
         const int stg = c->prm.storage;
         const bool het = c->lat.has_phi_field != 0, outf = c->outflow;
+        const bool ent = c->lat.enthalpy != 0;
         lbm_batch::Group* grp = nullptr;
         for (auto& gr : b->groups)
-            if (gr.storage == stg && gr.het == het && gr.outflow == outf) grp = &gr;
+            if (gr.storage == stg && gr.het == het && gr.outflow == outf && gr.enthalpy == ent)
+                grp = &gr;
         if (!grp) {
             b->groups.emplace_back();
             grp = &b->groups.back();
             grp->storage = stg;
             grp->het = het;
             grp->outflow = outf;
+            grp->enthalpy = ent;
         }
         grp->members.push_back(k);
     }

@@ -41,6 +41,11 @@ struct KParams {
     float ae, be, aeps, beps, aq, aqc, bqc, anu36, bnu36, api72, hbpi72, anu12, bnu12;
     float api24, hbpi24, anu4, bnu4, am8, rho0_10;
     float ze6, zn6;  // zeta_e / 6, zeta_nu / 6 (Eq. 43 columns)
+    // enthalpy model (App. B): En_{e,s}, En_{e,l}, 1/(sigma_s c_pl), 1/(sigma_l c_pl),
+    // 1/(En_{e,l} - En_{e,s}) (0 when isothermal), phase diffusivities, 3/varpi
+    int enthalpy, flow_off;
+    float ent_Es, ent_El, ent_is, ent_il, ent_Ts, ent_Tl, ent_idE;
+    float c_pl, c_ref, alpha_s, alpha_l, inv_csT2;
     float buoy[3], accel[3];                        // G = buoy (T - T0) + accel (Eq. 5)
 
     // uniform medium, precomputed (Eqs. 4, 28)
@@ -114,7 +119,7 @@ int reduction_blocks();
 // lattice.
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
-                              int flip, cudaStream_t st);
+                              bool enthalpy, int flip, cudaStream_t st);
 // x-extent of a site-kernel block for a lattice of width nx within block_threads threads.
 int block_x(int nx, int block_threads);  // number of partial sums the reductions write (<= partials size)
 

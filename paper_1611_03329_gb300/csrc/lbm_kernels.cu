@@ -394,6 +394,20 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
 }
 
 // ---- collision -------------------------------------------------------------------------------
+// Eqs. B8-B9: temperature and liquid fraction from the effective enthalpy.
+__device__ __forceinline__ void enthalpy_state(const KParams& p, float En, float& T, float& fl) {
+    if (En <= p.ent_Es) {
+        T = En * p.ent_is;
+        fl = 0.0f;
+    } else if (En >= p.ent_El) {
+        T = p.ent_Tl + (En - p.ent_El) * p.ent_il;
+        fl = 1.0f;
+    } else {
+        fl = (En - p.ent_Es) * p.ent_idE;
+        T = p.ent_Ts + fl * (p.ent_Tl - p.ent_Ts);
+    }
+}
+
 struct Macro {
     float rho, ux, uy, uz, T, dT;  // dT = T - T0
 };
@@ -404,12 +418,18 @@ __device__ __forceinline__ float sqrt_nonneg(float v) { return v > 0.0f ? v * rs
 // Eqs. 39, 5, 25, 27-28, 4, then (FULL) Eq. 9 with Eqs. 21-23 in moment space and Eq. 34 with
 // Eqs. 37-38, back-transformed in place.  f, g are deviations on entry and exit.  The
 // per-moment factors s_k / |M_k|^2 and (1 - s_k/2) / |M_k|^2 come precomputed in KParams.
-template <bool FULL>
+template <bool FULL, bool ENTH = false>
 __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g) {
-    // temperature (Eq. 39) and body force (Eq. 5)
+    // temperature (Eq. 39, or Eqs. B7-B9 with the enthalpy model) and body force (Eq. 5)
     const float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
-    const float dT = n0 * p.inv_sigma;
-    const float T = p.T0 + dT;
+    float T, dT, fl = 1.0f;                                                     // or En_e
+    if constexpr (ENTH) {
+        enthalpy_state(p, n0, T, fl);
+        dT = T - p.T0;
+    } else {
+        dT = n0 * p.inv_sigma;
+        T = p.T0 + dT;
+    }
     const float Gx = p.buoy[0] * dT + p.accel[0];
     const float Gy = p.buoy[1] * dT + p.accel[1];
     const float Gz = p.buoy[2] * dT + p.accel[2];
@@ -439,7 +459,13 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     const float vz = jz * p.inv_rho0 + hphi * Gz;
     const float vmag = sqrt_nonneg(vx * vx + vy * vy + vz * vz);
     const float inv_den = __fdividef(1.0f, md.l0 + sqrt_nonneg(md.l0 * md.l0 + md.l1 * vmag));
-    const float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
+    float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
+    // enthalpy model: the flow is collided only where f_l >= 0.5; elsewhere u = 0
+    bool rest = false;
+    if constexpr (ENTH) {
+        rest = p.flow_off || fl < 0.5f;
+        if (rest) ux = uy = uz = 0.0f;
+    }
 
     Macro mac;
     mac.rho = p.rho0 + rho;
@@ -450,6 +476,10 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     mac.dT = dT;
     if (!FULL) return mac;
 
+    if (rest) {  // f_eq(rho, 0) in deviation form: w_i (rho - rho0)
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) f[i] = w19(i) * rho;
+    } else {
     const float umag = vmag * inv_den;  // |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|))
     const float drag = md.c_darcy + md.c_forch * umag;
     const float Fx = md.phi * Gx - drag * ux;
@@ -545,13 +575,23 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     f[16] += Ef + O16;
     f[17] += Ef - O16;
 
-    // D3Q7: n = N g (Eq. 36), n_eq = T (sigma, u, varpi sigma, 0, 0) (Eq. 37), Eq. 34, Eq. 43
+    }  // flow collision
+
+    // D3Q7: n = N g (Eq. 36), n_eq = T (sigma, u, varpi sigma, 0, 0) (Eq. 37), Eq. 34, Eq. 43;
+    // enthalpy model: n_eq = (En_e, c_pl T u, varpi c_ref T, 0, 0) (Eq. B6) on full values,
+    // zeta_alpha from Eq. B11 with alpha_e = f_l alpha_l + (1 - f_l) alpha_s
     const float g12 = g[1] + g[2], g34 = g[3] + g[4], g56 = g[5] + g[6];
-    const float n4 = g12 + g34 + g56;  // minus varpi sigma T0
-    const float dn1 = md.zeta_alpha * (T * ux - (g[1] - g[2]));
-    const float dn2 = md.zeta_alpha * (T * uy - (g[3] - g[4]));
-    const float dn3 = md.zeta_alpha * (T * uz - (g[5] - g[6]));
-    const float c4 = p.ze6 * (p.varpi * n0 - n4);  // dn4 / 6
+    const float n4 = g12 + g34 + g56;  // minus varpi sigma T0 (standard model)
+    float tu = T, n4eq = p.varpi * n0, za = md.zeta_alpha;
+    if constexpr (ENTH) {
+        tu = p.c_pl * T;
+        n4eq = p.varpi * p.c_ref * T;
+        za = __fdividef(1.0f, 0.5f + (fl * p.alpha_l + (1.0f - fl) * p.alpha_s) * p.inv_csT2);
+    }
+    const float dn1 = za * (tu * ux - (g[1] - g[2]));
+    const float dn2 = za * (tu * uy - (g[3] - g[4]));
+    const float dn3 = za * (tu * uz - (g[5] - g[6]));
+    const float c4 = p.ze6 * (n4eq - n4);  // dn4 / 6
     const float c5 = -p.zn6 * (g12 - g34);         // dn5 / 6
     const float c6 = -p.zn6 * (g12 - g56);         // dn6 / 6
     g[0] -= 6.0f * c4;
@@ -581,7 +621,7 @@ __device__ __forceinline__ void gather_site(const Planes& pl, const KParams& p, 
 }
 
 // Outflow history, collision and store of one gathered site.
-template <bool HET, bool OUTF, class S>
+template <bool HET, bool OUTF, class S, bool ENTH = false>
 __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, int x, int y, int z,
                                             int s, float* f, float* g) {
     if (OUTF && x == p.nx - 1) {
@@ -594,7 +634,7 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
         pl.hout[5 * p.nyz + yz] = g[2];
     }
     const Medium md = medium_at<HET>(p, s);
-    const Macro m = collide<true>(p, md, f, g);
+    const Macro m = collide<true, ENTH>(p, md, f, g);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) stp<S>(pl, p, i, s, f[i]);
 #pragma unroll
@@ -604,7 +644,7 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
 
 // 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
 // blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
-template <bool HET, bool OUTF, class S>
+template <bool HET, bool OUTF, class S, bool ENTH = false>
 __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -618,14 +658,14 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
     gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
-    finish_site<HET, OUTF, S>(pl, p, x, y, z, s, f, g);
+    finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
 }
 
 // Batched step: one flat grid over the blocks of many lattices.  blk_lat[b] names the lattice
 // of block b; the lattice's parameters and planes are read in place through the read-only
 // cache (uniform over the block).  A block covers `rows` consecutive z-planes of one
 // (x-segment, y-band) column, so the lookup is paid once per `rows` site updates.
-template <bool HET, bool OUTF, class S>
+template <bool HET, bool OUTF, class S, bool ENTH = false>
 __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     batch_step_kernel(const BatchLattice* __restrict__ tab,
                       const unsigned short* __restrict__ blk_lat, int flip, int rows) {
@@ -654,12 +694,12 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
             float f[kQ], g[kQT];
             const int s = x + p.nx * (y + p.ny * z);
             gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
-            finish_site<HET, OUTF, S>(pl, p, x, y, z, s, f, g);
+            finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
         }
     }
 }
 
-template <bool HET, bool OUTF, class S>
+template <bool HET, bool OUTF, class S, bool ENTH = false>
 __global__ void __launch_bounds__(kBlock)
     macros_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                   float* __restrict__ rho, float* __restrict__ u, float* __restrict__ T) {
@@ -671,7 +711,7 @@ __global__ void __launch_bounds__(kBlock)
     float f[kQ], g[kQT];
     gather_general<OUTF, S>(pl, p, n, f, g);
     const Medium md = medium_at<HET>(p, n.s);
-    Macro m = collide<false>(p, md, f, g);
+    Macro m = collide<false, ENTH>(p, md, f, g);
     const long long s = n.s;
     if (rho) rho[s] = m.rho;
     if (u) {
@@ -707,6 +747,19 @@ __global__ void init_eq_kernel(const __grid_constant__ KParams p, const __grid_c
         S::st(static_cast<typename S::T*>(pl.out[i]) + s, (float)(S::kScaled ? rel : w * rel));
     }
     double varpi = p.varpi, sigma = p.sigma, T0 = p.T0, csT2 = varpi / 3.0;
+    if (p.enthalpy) {
+        // Eq. B12 with the phase-pure enthalpy of T (solid at or below T_s), full values
+        const double En = T <= (double)p.ent_Ts ? T / (double)p.ent_is
+                                                : (double)p.ent_El + (T - (double)p.ent_Tl) / (double)p.ent_il;
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) {
+            const double eu = ex7(i) * ux + ey7(i) * uy + ez7(i) * uz;
+            const double v = i == 0 ? En - varpi * p.c_ref * T
+                                    : varpi * p.c_ref * T / 6.0 + 0.5 * eu * p.c_pl * T;
+            S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + s, (float)v);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < kQT; ++i) {
         double om = i == 0 ? 1.0 - varpi : varpi / 6.0;
@@ -874,6 +927,11 @@ __device__ __forceinline__ double temperature_at(const Planes& pl, const KParams
     float g[kQT];
     gather_g_bc<OUTF, S>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
     float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+    if (p.enthalpy) {  // Eq. B8
+        float T, fl;
+        enthalpy_state(p, n0, T, fl);
+        return (double)T;
+    }
     return (double)p.T0 + (double)n0 * (double)p.inv_sigma;
 }
 
@@ -958,8 +1016,13 @@ int block_x(int nx, int block_threads) { return block_x_of(nx, block_threads); }
 
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
-                              int flip, cudaStream_t st) {
+                              bool enthalpy, int flip, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
+    if (enthalpy) {
+        batch_step_kernel<false, false, StoreF32, true>
+            <<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+        return cudaGetLastError();
+    }
     return with_storage(storage, [&](auto tag) {
         using S = decltype(tag);
         if (het && outflow)
@@ -978,6 +1041,10 @@ cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaSt
     dim3 grid, block;
     site_grid(p, &grid, &block);
     const bool het = p.phi_field != nullptr;
+    if (p.enthalpy) {  // FP32, uniform medium, no outflow (validated on the host)
+        step_kernel<false, false, StoreF32, true><<<grid, block, 0, st>>>(p, pl);
+        return cudaGetLastError();
+    }
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
         if (het && outflow)
@@ -997,6 +1064,10 @@ cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, floa
     dim3 grid, block;
     site_grid(p, &grid, &block);
     const bool het = p.phi_field != nullptr;
+    if (p.enthalpy) {
+        macros_kernel<false, false, StoreF32, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        return cudaGetLastError();
+    }
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
         if (het && outflow)
