@@ -414,7 +414,8 @@ def run_ours(args):
                 "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32-math, fp32 or fp16 storage per request", "data": "synthetic",
                 "config": {"workload": f"{n} requests, Poisson 20/s (seed 5): porous cavities "
-                                       "32^3-192^3 and 4WxWxW channels (W 32, 64)",
+                                       "32^3-192^3, 4WxWxW channels (W 32, 64) and, one "
+                                       "in ten, melting cavities (enthalpy model)",
                            "tol": tol, "max_steps": max_steps, "chunk": 100,
                            "admission": "FIFO by device footprint (80% of free memory)"
                                         + (f", at most {args.fill} sites admitted" if args.fill else "")},

@@ -110,19 +110,28 @@ def batch_cavities(n: int = 64, seed: int = 2016, sizes=(32, 48, 64, 96, 128),
 
 def serving_mix(n: int = 24, seed: int = 5, rate: float = 20.0,
                 edges=(32, 48, 64, 96, 128, 160, 192), widths=(32, 64),
-                p_channel: float = 0.4, p_fp16: float = 0.5) -> list:
+                p_channel: float = 0.4, p_fp16: float = 0.5, p_melt: float = 0.1) -> list:
     """Seeded stream of solve requests: (arrival time in s, problem).  Poisson arrivals of
-    mean `rate` per second; a request is a porous cavity (edge from `edges`, porosity in
-    [0.4, 0.9], log10 Da in [-5, -1], log10 Ra in [3, 6]) or, with probability p_channel, a
-    porous channel of length 4W and section W x W (W from `widths`, porosity 0.7, log10 Da in
-    [-3, -2]); storage FP16 with probability p_fp16, else FP32."""
+    mean `rate` per second; a request is, with probability p_melt, a melting cavity (clear
+    fluid, edge from `edges`, solid at T = 0 below a melting point of 0.5, Stefan number 1,
+    log10 Ra in [4, 6], FP32: the enthalpy model of App. B), else with probability
+    p_channel a porous channel of length 4W and section W x W (W from `widths`, porosity
+    0.7, log10 Da in [-3, -2]), else a porous cavity (edge from `edges`, porosity in
+    [0.4, 0.9], log10 Da in [-5, -1], log10 Ra in [3, 6]); storage of the last two FP16
+    with probability p_fp16, else FP32."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     out = []
     for _ in range(n):
         t += float(rng.exponential(1.0 / rate))
         storage = "fp16" if rng.uniform() < p_fp16 else "fp32"
-        if rng.uniform() < p_channel:
+        kind = rng.uniform()
+        if kind < p_melt:
+            edge = int(rng.choice(edges))
+            pb = cavity_problem(edge, Ra=float(10.0 ** rng.uniform(4.0, 6.0)), Da=None,
+                                phi=1.0, Pr=0.71, enthalpy=True, T_m=0.5, St=1.0, T_init=0.0)
+            storage = "fp32"
+        elif kind < p_melt + (1.0 - p_melt) * p_channel:
             w = int(rng.choice(widths))
             pb = channel_problem(4 * w, w, w, Da=float(10.0 ** rng.uniform(-3.0, -2.0)))
         else:
