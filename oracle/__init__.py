@@ -23,7 +23,7 @@ import numpy as np
 
 from . import build as _build
 
-Q19, Q7 = 19, 7
+Q19, Q15, Q7 = 19, 15, 7
 CS2 = 1.0 / 3.0  # c_s^2 with c = 1 (Sec. 3.1.2)
 
 # face order: x-low, x-high, y-low, y-high, z-low, z-high
@@ -54,6 +54,7 @@ class _Lattice(C.Structure):
         ("sigma_s", C.c_double), ("sigma_l", C.c_double),
         ("T_s", C.c_double), ("T_l", C.c_double), ("L_a", C.c_double),
         ("alpha_s", C.c_double), ("alpha_l", C.c_double),
+        ("q", C.c_int),
     ]
 
 
@@ -95,6 +96,12 @@ def lib():
         L.orc_enthalpy_of.argtypes = [C.POINTER(_Lattice), C.c_double, C.c_double]
         L.orc_enthalpy_of.restype = C.c_double
         L.orc_geq7_enthalpy.argtypes = [C.POINTER(_Lattice), C.c_double, C.c_double, dp, dp]
+        L.orc_tables15.argtypes = [dp] * 4
+        L.orc_feq15.argtypes = [C.c_double, dp, C.c_double, C.c_double, dp]
+        L.orc_meq15_eq15.argtypes = [C.c_double, dp, C.c_double, C.c_double, dp]
+        L.orc_stilde15.argtypes = [dp, dp, C.c_double, C.c_double, dp]
+        L.orc_velocity15.argtypes = [dp, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, dp]
         if L.orc_sizeof_lattice() != C.sizeof(_Lattice):
             raise RuntimeError("oracle struct layout mismatch")
         _lib = L
@@ -127,6 +134,39 @@ def tables() -> dict:
     ninv = np.zeros((Q7, Q7))
     lib().orc_tables(_p(e19), _p(w19), _p(m), _p(minv), _p(e7), _p(n7), _p(ninv))
     return dict(e19=e19, w19=w19, M=m, Minv=minv, e7=e7, N=n7, Ninv=ninv)
+
+
+def tables15() -> dict:
+    """e15 (3x15, Eq. 12), w15 (under Eq. 18), M (Eq. A1), M^-1 (Gauss-Jordan)."""
+    e15 = np.zeros((3, Q15)); w15 = np.zeros(Q15); m = np.zeros((Q15, Q15))
+    minv = np.zeros((Q15, Q15))
+    lib().orc_tables15(_p(e15), _p(w15), _p(m), _p(minv))
+    return dict(e15=e15, w15=w15, M=m, Minv=minv)
+
+
+def feq15(rho, u, phi, rho0=1.0) -> np.ndarray:
+    out = np.zeros(Q15)
+    lib().orc_feq15(float(rho), _p(_vec(u)), float(phi), float(rho0), _p(out))
+    return out
+
+
+def meq15_eq15(rho, u, phi, rho0=1.0) -> np.ndarray:
+    out = np.zeros(Q15)
+    lib().orc_meq15_eq15(float(rho), _p(_vec(u)), float(phi), float(rho0), _p(out))
+    return out
+
+
+def stilde15(u, F, phi, rho0=1.0) -> np.ndarray:
+    out = np.zeros(Q15)
+    lib().orc_stilde15(_p(_vec(u)), _p(_vec(F)), float(phi), float(rho0), _p(out))
+    return out
+
+
+def velocity15(f, G, phi, nu, K, Fphi, rho0=1.0) -> np.ndarray:
+    out = np.zeros(3)
+    lib().orc_velocity15(_p(_vec(f)), _p(_vec(G)), float(phi), float(nu), float(K),
+                         float(Fphi), float(rho0), _p(out))
+    return out
 
 
 def feq19(rho, u, phi, rho0=1.0) -> np.ndarray:
@@ -222,13 +262,14 @@ class LatticeParams:
     L_a: float = 1.0
     alpha_s: float = 0.0
     alpha_l: float = 0.0
+    q: int = 19
     phi_field: Optional[np.ndarray] = field(default=None, repr=False)
 
     def to_c(self) -> _Lattice:
         c = _Lattice()
         c.nx, c.ny, c.nz = self.nx, self.ny, self.nz
         c.rho0, c.T0, c.sigma, c.varpi = self.rho0, self.T0, self.sigma, self.varpi
-        for k in range(Q19):
+        for k in range(len(self.s)):
             c.s[k] = self.s[k]
         c.zeta_T, c.zeta_e, c.zeta_nu = self.zeta_T, self.zeta_e, self.zeta_nu
         c.alpha_f, c.alpha_m, c.Gamma = self.alpha_f, self.alpha_m, self.Gamma
@@ -250,6 +291,7 @@ class LatticeParams:
         c.sigma_s, c.sigma_l = self.sigma_s, self.sigma_l
         c.T_s, c.T_l, c.L_a = self.T_s, self.T_l, self.L_a
         c.alpha_s, c.alpha_l = self.alpha_s, self.alpha_l
+        c.q = int(self.q)
         return c
 
 
@@ -258,6 +300,13 @@ def relaxation_vector(s_nu, s_e=1.1, s_eps=1.1, s_q=1.1, s_pi=1.1, s_m=1.2):
     s_rho = s_j = 1.0
     return [s_rho, s_e, s_eps, s_j, s_q, s_j, s_q, s_j, s_q,
             s_nu, s_pi, s_nu, s_pi, s_nu, s_nu, s_nu, s_m, s_m, s_m]
+
+
+def relaxation_vector15(s_nu, s_e=1.1, s_eps=1.1, s_q=1.1, s_m=1.2):
+    """Diagonal of Lambda in the moment order of Eq. 13 (Eq. 16), s_rho = s_j = 1."""
+    s_rho = s_j = 1.0
+    return [s_rho, s_e, s_eps, s_j, s_q, s_j, s_q, s_j, s_q,
+            s_nu, s_nu, s_nu, s_nu, s_nu, s_m]
 
 
 def ergun_F(phi: float) -> float:
@@ -342,12 +391,18 @@ def map_problem(pb: dict) -> LatticeParams:
                    alpha_l=float(pb.get("alpha_l", alpha_f)),
                    alpha_s=float(pb.get("alpha_s", float(pb.get("alpha_l", alpha_f))
                                         / float(pb.get("alpha_ratio", 1.0)))))
+    q = int(pb.get("q", Q19))  # flow lattice: D3Q19 (Sec. 3.1.2) or D3Q15 (Sec. 3.1.1)
+    if q not in (Q15, Q19):
+        raise ValueError(f"flow lattice D3Q{q}")
     return LatticeParams(
         **ent,
         nx=nx, ny=ny, nz=nz, rho0=float(pb.get("rho0", 1.0)), T0=float(pb.get("T0", 0.5)),
         sigma=sigma, varpi=varpi,
-        s=relaxation_vector(s_nu, rates["s_e"], rates["s_eps"], rates["s_q"], rates["s_pi"],
-                            rates["s_m"]),
+        s=(relaxation_vector15(s_nu, rates["s_e"], rates["s_eps"], rates["s_q"], rates["s_m"])
+           if q == Q15 else
+           relaxation_vector(s_nu, rates["s_e"], rates["s_eps"], rates["s_q"], rates["s_pi"],
+                             rates["s_m"])),
+        q=q,
         zeta_T=rates["zeta_T"], zeta_e=rates["zeta_e"], zeta_nu=rates["zeta_nu"],
         alpha_f=alpha_f, alpha_m=alpha_m, Gamma=Gamma, nu=nu, nu_e=nu_e,
         phi=phi, K=K, F_phi=F_phi, phi_ref=phi_ref,
@@ -370,6 +425,7 @@ class Oracle:
         self.lp = lp
         self.shape = (lp.nz, lp.ny, lp.nx)
         self.ns = lp.nx * lp.ny * lp.nz
+        self.q = int(lp.q)
         self._c = lp.to_c()
         phi = None
         if lp.phi_field is not None:
@@ -402,11 +458,11 @@ class Oracle:
     def set_populations(self, f: np.ndarray, g: np.ndarray):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
-        assert f.size == Q19 * self.ns and g.size == Q7 * self.ns
+        assert f.size == self.q * self.ns and g.size == Q7 * self.ns
         lib().orc_set_populations(self._h, _p(f), _p(g))
 
     def populations(self):
-        f = np.zeros((Q19,) + self.shape)
+        f = np.zeros((self.q,) + self.shape)
         g = np.zeros((Q7,) + self.shape)
         lib().orc_get_populations(self._h, _p(f), _p(g))
         return f, g
@@ -456,7 +512,7 @@ def collide_site(lp: LatticeParams, f, g, phi=None, K=None, Fphi=None, zeta_alph
     if Fphi is None:
         Fphi = ergun_F(phi) if lp.F_phi < 0 else lp.F_phi
     za = lp.zeta_alpha if zeta_alpha is None else zeta_alpha
-    fo = np.zeros(Q19); go = np.zeros(Q7); mac = np.zeros(5)
+    fo = np.zeros(lp.q); go = np.zeros(Q7); mac = np.zeros(5)
     lib().orc_collide_site(C.byref(c), _p(_vec(f)), _p(_vec(g)), float(phi), float(K),
                            float(Fphi), float(za), _p(fo), _p(go), _p(mac))
     return fo, go, mac

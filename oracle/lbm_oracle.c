@@ -14,7 +14,9 @@
  *   3. G = buoy*(T - T0) + a (Eq. 5);
  *   4. rho = sum f_i (Eq. 25); v, l0, l1 (Eq. 28, sum over ALL i); u (Eq. 27);
  *   5. F (Eq. 4);
- *   6. m = M f with the dense 19x19 matrix typed from Eq. A2;
+ *   6. m = M f with the dense 19x19 matrix typed from Eq. A2 (D3Q15: the 15x15 matrix of
+ *      Eq. A1, velocities of Eq. 12, f_eq of Eq. 18, m_eq of Eq. 15, S~ of Eq. 17, Lambda of
+ *      Eq. 16);
  *   7. m_eq = M f_eq with f_eq from Eq. 24 (Eq. 11);
  *   8. S~ from Eq. 23;
  *   9. m* = m - Lambda (m - m_eq) + (I - Lambda/2) S~ (Eq. 9, dt = 1);
@@ -49,6 +51,8 @@
 #endif
 
 #define Q19 19
+#define Q15 15
+#define QMAX 19
 #define Q7 7
 
 /* ---- lattice tables ------------------------------------------------------------- */
@@ -87,6 +91,34 @@ static const double M19[Q19][Q19] = {
     {0, 0, 0, 0, 0, 0, 0, -1, -1, 1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
     {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, -1, -1, -1, -1, 1, 1}};
 
+/* D3Q15 velocities, Eq. 12 (columns i = 0..14). */
+static const int E15[3][Q15] = {{0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1},
+                                {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1},
+                                {0, 0, 0, 0, 0, 1, -1, 1, 1, 1, 1, -1, -1, -1, -1}};
+
+/* D3Q15 weights, stated under Eq. 18. */
+static const double W15[Q15] = {2.0 / 9,  1.0 / 9,  1.0 / 9,  1.0 / 9,  1.0 / 9,
+                                1.0 / 9,  1.0 / 9,  1.0 / 72, 1.0 / 72, 1.0 / 72,
+                                1.0 / 72, 1.0 / 72, 1.0 / 72, 1.0 / 72, 1.0 / 72};
+
+/* D3Q15 transformation matrix, Eq. A1 (rows in the moment order of Eq. 13). */
+static const double M15[Q15][Q15] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-2, -1, -1, -1, -1, -1, -1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {16, -4, -4, -4, -4, -4, -4, 1, 1, 1, 1, 1, 1, 1, 1},
+    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1},
+    {0, -4, 4, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1},
+    {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1},
+    {0, 0, 0, -4, 4, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 1, 1, 1, 1, -1, -1, -1, -1},
+    {0, 0, 0, 0, 0, -4, 4, 1, 1, 1, 1, -1, -1, -1, -1},
+    {0, 2, 2, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 1, 1, -1, -1, -1, -1, 1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, -1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, -1, 1, 1, -1}};
+
 /* D3Q7 velocities: the first seven columns of Eq. 12. */
 static const int E7[3][Q7] = {{0, 1, -1, 0, 0, 0, 0},
                               {0, 0, 0, 1, -1, 0, 0},
@@ -112,11 +144,25 @@ static const double CS2 = 1.0 / 3.0; /* c_s^2, c = 1 (Sec. 3.1.2) */
 
 /* M^-1, computed once by Gauss-Jordan elimination with partial pivoting. */
 static double MINV19[Q19][Q19];
+static double MINV15[Q15][Q15];
 static int minv_ready = 0;
 
-static int opposite19(int i) {
-    for (int j = 0; j < Q19; ++j)
-        if (E19[0][j] == -E19[0][i] && E19[1][j] == -E19[1][i] && E19[2][j] == -E19[2][i])
+/* The flow lattice of a run: D3Q19 (Sec. 3.1.2) or D3Q15 (Sec. 3.1.1). */
+typedef struct {
+    int q;
+    const int* e;       /* e[a * q + i] */
+    const double* w;
+    const double* m;    /* m[k * q + i] */
+    const double* minv; /* minv[i * q + k] */
+} flow_lattice;
+static const flow_lattice D19 = {Q19, &E19[0][0], W19, &M19[0][0], &MINV19[0][0]};
+static const flow_lattice D15 = {Q15, &E15[0][0], W15, &M15[0][0], &MINV15[0][0]};
+
+static int opposite_in(const flow_lattice* D, int i) {
+    const int q = D->q;
+    for (int j = 0; j < q; ++j)
+        if (D->e[j] == -D->e[i] && D->e[q + j] == -D->e[q + i] &&
+            D->e[2 * q + j] == -D->e[2 * q + i])
             return j;
     return -1;
 }
@@ -165,6 +211,7 @@ static int invert_matrix(int n, const double* a, double* inv) {
 static void ensure_minv(void) {
     if (!minv_ready) {
         invert_matrix(Q19, &M19[0][0], &MINV19[0][0]);
+        invert_matrix(Q15, &M15[0][0], &MINV15[0][0]);
         minv_ready = 1;
     }
 }
@@ -184,16 +231,81 @@ void orc_tables(double* e19, double* w19, double* m19, double* minv19, double* e
     memcpy(ninv7, NINV7, sizeof(NINV7));
 }
 
+void orc_tables15(double* e15, double* w15, double* m15, double* minv15) {
+    ensure_minv();
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < Q15; ++i) e15[a * Q15 + i] = E15[a][i];
+    for (int i = 0; i < Q15; ++i) w15[i] = W15[i];
+    memcpy(m15, M15, sizeof(M15));
+    memcpy(minv15, MINV15, sizeof(MINV15));
+}
+
 /* ---- pointwise formulas ---------------------------------------------------------- */
 
-/* Eq. 24: f_i^eq = w_i { rho + rho0 [ e.u/cs^2 + (e.u)^2/(2 phi cs^4) - |u|^2/(2 phi cs^2) ] } */
-void orc_feq19(double rho, const double* u, double phi, double rho0, double* feq) {
+/* Eqs. 18 and 24 (the same form on either lattice): f_i^eq = w_i { rho + rho0 [ e.u/cs^2 +
+ * (e.u)^2/(2 phi cs^4) - |u|^2/(2 phi cs^2) ] }. */
+static void feq_on(const flow_lattice* D, double rho, const double* u, double phi, double rho0,
+                   double* feq) {
+    const int q = D->q;
     double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    for (int i = 0; i < Q19; ++i) {
-        double eu = E19[0][i] * u[0] + E19[1][i] * u[1] + E19[2][i] * u[2];
-        feq[i] = W19[i] * (rho + rho0 * (eu / CS2 + eu * eu / (2.0 * phi * CS2 * CS2) -
-                                         usq / (2.0 * phi * CS2)));
+    for (int i = 0; i < q; ++i) {
+        double eu = D->e[i] * u[0] + D->e[q + i] * u[1] + D->e[2 * q + i] * u[2];
+        feq[i] = D->w[i] * (rho + rho0 * (eu / CS2 + eu * eu / (2.0 * phi * CS2 * CS2) -
+                                          usq / (2.0 * phi * CS2)));
     }
+}
+
+void orc_feq15(double rho, const double* u, double phi, double rho0, double* feq) {
+    feq_on(&D15, rho, u, phi, rho0, feq);
+}
+
+/* Eq. 15 with beta1 = 1, beta2 = -5 (stated with Eq. 18); the conserved moments are rho (m0)
+ * and rho0 u (m3, m5, m7), the values of M f_eq. */
+void orc_meq15_eq15(double rho, const double* u, double phi, double rho0, double* meq) {
+    const double b1 = 1.0, b2 = -5.0;
+    double ux = u[0], uy = u[1], uz = u[2];
+    double usq = ux * ux + uy * uy + uz * uz;
+    meq[0] = rho;
+    meq[1] = -rho + rho0 * usq / phi;
+    meq[2] = b1 * rho + b2 * rho0 * usq / phi;
+    meq[3] = rho0 * ux;
+    meq[4] = -7.0 / 3.0 * rho0 * ux;
+    meq[5] = rho0 * uy;
+    meq[6] = -7.0 / 3.0 * rho0 * uy;
+    meq[7] = rho0 * uz;
+    meq[8] = -7.0 / 3.0 * rho0 * uz;
+    meq[9] = rho0 * (2 * ux * ux - uy * uy - uz * uz) / phi;
+    meq[10] = rho0 * (uy * uy - uz * uz) / phi;
+    meq[11] = rho0 * ux * uy / phi;
+    meq[12] = rho0 * uy * uz / phi;
+    meq[13] = rho0 * uz * ux / phi;
+    meq[14] = 0.0;
+}
+
+/* Eq. 17: forcing term in moment space (D3Q15). */
+void orc_stilde15(const double* u, const double* F, double phi, double rho0, double* S) {
+    double ux = u[0], uy = u[1], uz = u[2], Fx = F[0], Fy = F[1], Fz = F[2];
+    double uF = ux * Fx + uy * Fy + uz * Fz;
+    S[0] = 0.0;
+    S[1] = 2.0 * rho0 * uF / phi;
+    S[2] = -10.0 * rho0 * uF / phi;
+    S[3] = rho0 * Fx;
+    S[4] = -7.0 / 3.0 * rho0 * Fx;
+    S[5] = rho0 * Fy;
+    S[6] = -7.0 / 3.0 * rho0 * Fy;
+    S[7] = rho0 * Fz;
+    S[8] = -7.0 / 3.0 * rho0 * Fz;
+    S[9] = 2.0 * rho0 * (2 * ux * Fx - uy * Fy - uz * Fz) / phi;
+    S[10] = 2.0 * rho0 * (uy * Fy - uz * Fz) / phi;
+    S[11] = rho0 * (ux * Fy + uy * Fx) / phi;
+    S[12] = rho0 * (uy * Fz + uz * Fy) / phi;
+    S[13] = rho0 * (ux * Fz + uz * Fx) / phi;
+    S[14] = 0.0;
+}
+
+/* Eq. 24 on the D3Q19 lattice. */
+void orc_feq19(double rho, const double* u, double phi, double rho0, double* feq) {
+    feq_on(&D19, rho, u, phi, rho0, feq);
 }
 
 /* Eq. 21 with beta1 = 3, beta2 = -5.5, beta3 = -0.5 (stated under Eq. 23); the conserved
@@ -275,13 +387,13 @@ void orc_force(const double* u, const double* G, double phi, double nu, double K
 }
 
 /* Eqs. 27-28: explicit solution of the nonlinear Eq. 26 for u (dt = 1).  The sum in v runs
- * over all 19 velocities (the printed upper limit 8 is read as a misprint). */
-void orc_velocity(const double* f, const double* G, double phi, double nu, double K,
-                  double Fphi, double rho0, double* u) {
+ * over all velocities of the lattice (the printed upper limit 8 is read as a misprint). */
+static void velocity_on(const flow_lattice* D, const double* f, const double* G, double phi,
+                        double nu, double K, double Fphi, double rho0, double* u) {
     double v[3];
     for (int a = 0; a < 3; ++a) {
         double s = 0.0;
-        for (int i = 0; i < Q19; ++i) s += E19[a][i] * f[i];
+        for (int i = 0; i < D->q; ++i) s += D->e[a * D->q + i] * f[i];
         v[a] = s / rho0 + 0.5 * phi * G[a];
     }
     double l0 = 0.5 * (1.0 + phi * 0.5 * nu / K);
@@ -289,6 +401,16 @@ void orc_velocity(const double* f, const double* G, double phi, double nu, doubl
     double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     double den = l0 + sqrt(l0 * l0 + l1 * vmag);
     for (int a = 0; a < 3; ++a) u[a] = v[a] / den;
+}
+
+void orc_velocity(const double* f, const double* G, double phi, double nu, double K,
+                  double Fphi, double rho0, double* u) {
+    velocity_on(&D19, f, G, phi, nu, K, Fphi, rho0, u);
+}
+
+void orc_velocity15(const double* f, const double* G, double phi, double nu, double K,
+                    double Fphi, double rho0, double* u) {
+    velocity_on(&D15, f, G, phi, nu, K, Fphi, rho0, u);
 }
 
 /* ---- lattice parameters and state -------------------------------------------------- */
@@ -299,7 +421,7 @@ enum { HT_PERIODIC = 0, HT_ADIABATIC = 1, HT_DIRICHLET = 2, HT_OUTFLOW = 3 };
 typedef struct {
     int nx, ny, nz;
     double rho0, T0, sigma, varpi;
-    double s[Q19];         /* Lambda, Eq. 22 */
+    double s[QMAX];        /* Lambda, Eq. 22 (D3Q15: the first 15, Eq. 16) */
     double zeta_T, zeta_e, zeta_nu; /* Q, Eq. 38 (zeta_alpha from alpha_e, Eq. 41) */
     double alpha_f;        /* fluid thermal diffusivity */
     double alpha_m;        /* matrix diffusivity; < 0 selects alpha_e = Gamma * alpha_f */
@@ -322,7 +444,10 @@ typedef struct {
     double T_s, T_l;       /* solidus and liquidus temperatures */
     double L_a;            /* latent heat */
     double alpha_s, alpha_l; /* diffusivities of the solid and liquid phases */
+    int q;                 /* flow lattice: 19 (D3Q19, Sec. 3.1.2) or 15 (D3Q15, Sec. 3.1.1) */
 } orc_lattice;
+
+static const flow_lattice* lattice_of(const orc_lattice* L) { return L->q == Q15 ? &D15 : &D19; }
 
 typedef struct {
     orc_lattice L;
@@ -340,8 +465,9 @@ typedef struct {
     long steps;
 } orc_state;
 
-/* Directions of the D3Q19 lattice that enter the domain across the x-high face. */
-static int outflow_slot19(int i) {
+/* Directions that enter the domain across the x-high face (e_x = -1): 2, 8, 10, 12 and 14
+ * on both lattices (Eqs. 12 and 19). */
+static int outflow_slot(int i) {
     static const int slot[Q19] = {-1, -1, 0, -1, -1, -1, -1, -1, 1, -1,
                                   2,  -1, 3, -1, 4,  -1, -1, -1, -1};
     return slot[i];
@@ -393,8 +519,10 @@ static double pull_f(const orc_state* S, const double* fp, int i, int x, int y, 
 static double pull_f_core(const orc_state* S, const double* fp, int i, int x, int y, int z,
                           int use_outflow, const double* hist, int* via_outflow) {
     const orc_lattice* L = &S->L;
+    const flow_lattice* D = lattice_of(L);
+    const int q = D->q;
     int n[3] = {L->nx, L->ny, L->nz};
-    int c[3] = {x - E19[0][i], y - E19[1][i], z - E19[2][i]};
+    int c[3] = {x - D->e[i], y - D->e[q + i], z - D->e[2 * q + i]};
     int faces[3] = {-1, -1, -1};
     int any = 0;
     for (int a = 0; a < 3; ++a) {
@@ -408,20 +536,20 @@ static double pull_f_core(const orc_state* S, const double* fp, int i, int x, in
     }
     if (!any) return fp[(long)i * S->ns + site_index(L, c[0], c[1], c[2])];
     long here = site_index(L, x, y, z);
-    int io = opposite19(i);
+    int io = opposite_in(D, i);
     for (int a = 0; a < 3; ++a)
         if (faces[a] >= 0 && L->flow_bc[faces[a]] == BC_WALL) return fp[(long)io * S->ns + here];
     for (int a = 0; a < 3; ++a)
         if (faces[a] >= 0 && L->flow_bc[faces[a]] == BC_VELOCITY) {
             const double* uw = L->face_u[faces[a]];
-            double eu = E19[0][i] * uw[0] + E19[1][i] * uw[1] + E19[2][i] * uw[2];
-            return fp[(long)io * S->ns + here] + 2.0 * W19[i] * L->rho0 * eu / CS2;
+            double eu = D->e[i] * uw[0] + D->e[q + i] * uw[1] + D->e[2 * q + i] * uw[2];
+            return fp[(long)io * S->ns + here] + 2.0 * D->w[i] * L->rho0 * eu / CS2;
         }
     /* remaining case: the x-high convective outflow */
     if (!use_outflow) return 0.0; /* unreachable for valid configurations */
     if (via_outflow) *via_outflow = 1;
     double inner = pull_f(S, fp, i, x - 1, y, z, 0, hist, NULL);
-    double old = hist[(long)outflow_slot19(i) * L->ny * L->nz + y + (long)L->ny * z];
+    double old = hist[(long)outflow_slot(i) * L->ny * L->nz + y + (long)L->ny * z];
     return (old + L->U_out * inner) / (1.0 + L->U_out);
 }
 
@@ -505,6 +633,8 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
                       double K, double Fphi, double zeta_alpha, double* fout, double* gout,
                       double* macro) {
     ensure_minv();
+    const flow_lattice* D = lattice_of(L);
+    const int q = D->q;
     double sumg = 0.0;
     for (int i = 0; i < Q7; ++i) sumg += g[i];
     double T, fl = 1.0;
@@ -515,37 +645,40 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
     double G[3];
     for (int a = 0; a < 3; ++a) G[a] = L->buoy[a] * (T - L->T0) + L->accel[a]; /* Eq. 5 */
     double rho = 0.0;
-    for (int i = 0; i < Q19; ++i) rho += f[i]; /* Eq. 25 */
+    for (int i = 0; i < q; ++i) rho += f[i]; /* Eq. 25 */
     double u[3];
-    orc_velocity(f, G, phi, L->nu, K, Fphi, L->rho0, u); /* Eqs. 27-28 */
+    velocity_on(D, f, G, phi, L->nu, K, Fphi, L->rho0, u); /* Eqs. 27-28 */
     double F[3];
     orc_force(u, G, phi, L->nu, K, Fphi, F); /* Eq. 4 */
 
-    double m[Q19], feq[Q19], meq[Q19], S[Q19], ms[Q19];
+    double m[QMAX], feq[QMAX], meq[QMAX], S[QMAX], ms[QMAX];
     /* the liquid-fraction gate is a discrete decision: taken on the FP32 value of f_l, the
      * precision the GPU kernel decides in */
     if (L->enthalpy && (L->flow_off || (float)fl < 0.5f)) {
         /* solid (or no flow): the flow is not collided; the populations rest at f_eq(rho, 0) */
         u[0] = u[1] = u[2] = 0.0;
         double zero[3] = {0.0, 0.0, 0.0};
-        orc_feq19(rho, zero, phi, L->rho0, fout);
+        feq_on(D, rho, zero, phi, L->rho0, fout);
         goto thermal;
     }
-    for (int k = 0; k < Q19; ++k) {
+    for (int k = 0; k < q; ++k) {
         m[k] = 0.0;
-        for (int i = 0; i < Q19; ++i) m[k] += M19[k][i] * f[i];
+        for (int i = 0; i < q; ++i) m[k] += D->m[k * q + i] * f[i];
     }
-    orc_feq19(rho, u, phi, L->rho0, feq);
-    for (int k = 0; k < Q19; ++k) {
+    feq_on(D, rho, u, phi, L->rho0, feq);
+    for (int k = 0; k < q; ++k) { /* m_eq = M f_eq (Eq. 11) */
         meq[k] = 0.0;
-        for (int i = 0; i < Q19; ++i) meq[k] += M19[k][i] * feq[i];
+        for (int i = 0; i < q; ++i) meq[k] += D->m[k * q + i] * feq[i];
     }
-    orc_stilde19(u, F, phi, L->rho0, S);
-    for (int k = 0; k < Q19; ++k)
+    if (q == Q15)
+        orc_stilde15(u, F, phi, L->rho0, S); /* Eq. 17 */
+    else
+        orc_stilde19(u, F, phi, L->rho0, S); /* Eq. 23 */
+    for (int k = 0; k < q; ++k)
         ms[k] = m[k] - L->s[k] * (m[k] - meq[k]) + (1.0 - 0.5 * L->s[k]) * S[k]; /* Eq. 9 */
-    for (int i = 0; i < Q19; ++i) {
+    for (int i = 0; i < q; ++i) {
         fout[i] = 0.0;
-        for (int k = 0; k < Q19; ++k) fout[i] += MINV19[i][k] * ms[k];
+        for (int k = 0; k < q; ++k) fout[i] += D->minv[i * q + k] * ms[k];
     }
 
 thermal:;
@@ -595,8 +728,8 @@ static void reset_outflow_history(orc_state* S) {
     for (int z = 0; z < L->nz; ++z)
         for (int y = 0; y < L->ny; ++y) {
             long s = site_index(L, L->nx - 1, y, z);
-            for (int i = 0; i < Q19; ++i) {
-                int k = outflow_slot19(i);
+            for (int i = 0; i < L->q; ++i) {
+                int k = outflow_slot(i);
                 if (k >= 0) S->pf[k * nyz + y + (long)L->ny * z] = S->f[(long)i * S->ns + s];
             }
             S->pg[y + (long)L->ny * z] = S->g[2L * S->ns + s];
@@ -609,9 +742,10 @@ void* orc_create(const orc_lattice* L, const double* phi_field) {
     if (!S) return NULL;
     S->L = *L;
     S->ns = (long)L->nx * L->ny * L->nz;
-    S->f = (double*)calloc((size_t)Q19 * S->ns, sizeof(double));
+    if (S->L.q != Q15) S->L.q = Q19;
+    S->f = (double*)calloc((size_t)S->L.q * S->ns, sizeof(double));
     S->g = (double*)calloc((size_t)Q7 * S->ns, sizeof(double));
-    S->fn = (double*)calloc((size_t)Q19 * S->ns, sizeof(double));
+    S->fn = (double*)calloc((size_t)S->L.q * S->ns, sizeof(double));
     S->gn = (double*)calloc((size_t)Q7 * S->ns, sizeof(double));
     if (phi_field) {
         S->phi_site = (double*)malloc(sizeof(double) * S->ns);
@@ -654,13 +788,13 @@ void orc_init_equilibrium(void* h, double T_uniform, const double* T_field, cons
         if (u_field)
             for (int a = 0; a < 3; ++a) u[a] = u_field[a * S->ns + s];
         double T = T_field ? T_field[s] : T_uniform;
-        double feq[Q19], geq[Q7];
-        orc_feq19(L->rho0, u, phi, L->rho0, feq);
+        double feq[QMAX], geq[Q7];
+        feq_on(lattice_of(L), L->rho0, u, phi, L->rho0, feq);
         if (L->enthalpy)
             orc_geq7_enthalpy(L, orc_enthalpy_of(L, phi, T), T, u, geq);
         else
             orc_geq7(T, u, L->sigma, L->varpi, geq);
-        for (int i = 0; i < Q19; ++i) S->f[(long)i * S->ns + s] = feq[i];
+        for (int i = 0; i < L->q; ++i) S->f[(long)i * S->ns + s] = feq[i];
         for (int i = 0; i < Q7; ++i) S->g[(long)i * S->ns + s] = geq[i];
     }
     reset_outflow_history(S);
@@ -669,14 +803,14 @@ void orc_init_equilibrium(void* h, double T_uniform, const double* T_field, cons
 
 void orc_set_populations(void* h, const double* f, const double* g) {
     orc_state* S = (orc_state*)h;
-    memcpy(S->f, f, sizeof(double) * Q19 * S->ns);
+    memcpy(S->f, f, sizeof(double) * S->L.q * S->ns);
     memcpy(S->g, g, sizeof(double) * Q7 * S->ns);
     reset_outflow_history(S);
 }
 
 void orc_get_populations(void* h, double* f, double* g) {
     orc_state* S = (orc_state*)h;
-    if (f) memcpy(f, S->f, sizeof(double) * Q19 * S->ns);
+    if (f) memcpy(f, S->f, sizeof(double) * S->L.q * S->ns);
     if (g) memcpy(g, S->g, sizeof(double) * Q7 * S->ns);
 }
 
@@ -684,9 +818,10 @@ void orc_get_populations(void* h, double* f, double* g) {
  * history for the next step. */
 static void gather_site(orc_state* S, int x, int y, int z, double* f, double* g, int rec) {
     const orc_lattice* L = &S->L;
+    const flow_lattice* D = lattice_of(L);
     int outf = has_outflow(L);
-    int via[Q19];
-    for (int i = 0; i < Q19; ++i) {
+    int via[QMAX];
+    for (int i = 0; i < D->q; ++i) {
         via[i] = 0;
         f[i] = pull_f(S, S->f, i, x, y, z, outf, S->pf, &via[i]);
     }
@@ -694,20 +829,20 @@ static void gather_site(orc_state* S, int x, int y, int z, double* f, double* g,
      * rule by w_i * (rho0 - rho) / sum(w_i) so that the outlet density equals rho0. */
     if (outf && x == L->nx - 1) {
         double rho = 0.0, wsum = 0.0;
-        for (int i = 0; i < Q19; ++i) {
+        for (int i = 0; i < D->q; ++i) {
             rho += f[i];
-            if (via[i]) wsum += W19[i];
+            if (via[i]) wsum += D->w[i];
         }
         if (wsum > 0.0)
-            for (int i = 0; i < Q19; ++i)
-                if (via[i]) f[i] += W19[i] * (L->rho0 - rho) / wsum;
+            for (int i = 0; i < D->q; ++i)
+                if (via[i]) f[i] += D->w[i] * (L->rho0 - rho) / wsum;
     }
     for (int i = 0; i < Q7; ++i) g[i] = pull_g(S, S->g, i, x, y, z, outf, S->pg);
     if (rec && outf && x == L->nx - 1) {
         long nyz = (long)L->ny * L->nz;
         long yz = y + (long)L->ny * z;
-        for (int i = 0; i < Q19; ++i) {
-            int k = outflow_slot19(i);
+        for (int i = 0; i < D->q; ++i) {
+            int k = outflow_slot(i);
             if (k >= 0) S->pfn[k * nyz + yz] = f[i];
         }
         S->pgn[yz] = g[2];
@@ -723,12 +858,12 @@ void orc_step(void* h, int nsteps) {
             for (int y = 0; y < L->ny; ++y)
                 for (int x = 0; x < L->nx; ++x) {
                     long s = site_index(L, x, y, z);
-                    double f[Q19], g[Q7], fo[Q19], go[Q7];
+                    double f[QMAX], g[Q7], fo[QMAX], go[Q7];
                     double phi, K, Fphi;
                     gather_site(S, x, y, z, f, g, 1);
                     medium_at(S, s, &phi, &K, &Fphi);
                     orc_collide_site(L, f, g, phi, K, Fphi, zeta_alpha_at(L, phi), fo, go, NULL);
-                    for (int i = 0; i < Q19; ++i) S->fn[(long)i * S->ns + s] = fo[i];
+                    for (int i = 0; i < L->q; ++i) S->fn[(long)i * S->ns + s] = fo[i];
                     for (int i = 0; i < Q7; ++i) S->gn[(long)i * S->ns + s] = go[i];
                 }
         }
@@ -752,7 +887,7 @@ void orc_macros(void* h, double* rho, double* u, double* T) {
         for (int y = 0; y < L->ny; ++y)
             for (int x = 0; x < L->nx; ++x) {
                 long s = site_index(L, x, y, z);
-                double f[Q19], g[Q7], fo[Q19], go[Q7], mac[5];
+                double f[QMAX], g[Q7], fo[QMAX], go[Q7], mac[5];
                 double phi, K, Fphi;
                 gather_site(S, x, y, z, f, g, 0);
                 medium_at(S, s, &phi, &K, &Fphi);
