@@ -40,29 +40,29 @@ WORKLOADS = {
 }
 
 
-def _problem(nz=None, storage="fp32", workload="channel"):
+def _problem(nz=None, storage="fp32", workload="channel", q=19):
     from lbm_inputs import cavity_problem, channel_problem, porosity_field
 
     nx, ny, nz0 = WORKLOADS[workload]
     if workload == "channel":
-        return channel_problem(nx, ny, nz or nz0, storage=storage)
+        return channel_problem(nx, ny, nz or nz0, storage=storage, q=q)
     phi = porosity_field(nx, ny, nz0, seed=20161110).astype("float32")
     return cavity_problem(nx, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71, phi_field=phi, phi_ref=0.6,
-                          storage=storage)
+                          storage=storage, q=q)
 
 
-def _workload_text(workload, storage):
+def _workload_text(workload, storage, q=19):
     if workload == "batch64":
         return (f"64 porous cavities, edges from {{32,48,64,96,128}}, own (phi, Da, Ra), one "
                 f"batched launch per step under a CUDA graph, {storage.upper()} storage")
     nx, ny, nz = WORKLOADS[workload]
     if workload == "channel":
-        return f"porous mixed-convection channel {nx}x{ny}x{nz}, D3Q19+D3Q7 MRT, {storage.upper()} storage"
-    return (f"porous natural-convection cavity {nx}^3 with seeded porosity field, D3Q19+D3Q7 MRT, "
+        return f"porous mixed-convection channel {nx}x{ny}x{nz}, D3Q{q}+D3Q7 MRT, {storage.upper()} storage"
+    return (f"porous natural-convection cavity {nx}^3 with seeded porosity field, D3Q{q}+D3Q7 MRT, "
             f"{storage.upper()} storage")
 
 
-def _config(workload="channel", storage="fp32", extra=None):
+def _config(workload="channel", storage="fp32", extra=None, q=19):
     if workload == "batch64":
         cfg = {"workload": _workload_text(workload, storage), "lattices": 64,
                "storage": f"{storage}-deviation", "scheme": "ping-pong pull, batched",
@@ -71,11 +71,11 @@ def _config(workload="channel", storage="fp32", extra=None):
         return cfg
     nx, ny, nz = WORKLOADS[workload]
     elem = 4 if storage == "fp32" else 2
-    state = 2 * 26 * elem * nx * ny * nz / 1e6
+    state = 2 * (q + 7) * elem * nx * ny * nz / 1e6
     l2 = (f"inputs larger than L2: two population copies of {state:.0f} MB vs 126 MB L2, no flush"
           if state > 2 * 126 else
           f"two population copies of {state:.0f} MB, partly L2-resident (126 MB L2)")
-    cfg = {"workload": _workload_text(workload, storage), "nx": nx, "ny": ny, "nz": nz,
+    cfg = {"workload": _workload_text(workload, storage, q), "nx": nx, "ny": ny, "nz": nz,
            "storage": f"{storage}-deviation", "scheme": "ping-pong pull", "l2": l2}
     if workload == "channel":
         cfg.update({"phi": 0.7, "Da": 1e-3, "Re": 10, "Pr": 0.71, "Ri": 1.0, "u0": 0.01})
@@ -450,7 +450,8 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
         return 0
     stream = torch.cuda.Stream()
-    pb = _problem(storage=args.storage, workload=args.workload)
+    q = 15 if args.lattice == "d3q15" else 19
+    pb = _problem(storage=args.storage, workload=args.workload, q=q)
     wnx, wny, wnz = WORKLOADS[args.workload]
     ns = wnx * wny * wnz
     with torch.cuda.stream(stream):
@@ -504,24 +505,26 @@ def run_ours(args):
     bytes_site = gb.algorithmic_bytes_per_site(pb)
     kernel_ms = ms / args.steps  # one fused step kernel per time step
     achieved = bytes_site * ns / (kernel_ms * 1e-3) / 1e9
-    cpu = (cpu_baseline() if (ws == 1 and not args.no_cpu_baseline and args.workload == "channel")
+    cpu = (cpu_baseline() if (ws == 1 and not args.no_cpu_baseline and args.workload == "channel" and q == 19)
            else None)
     line = {
-        "metric": METRIC, "value": round(mlups, 2), "unit": UNIT, "n_gpus": ws,
+        "metric": METRIC if q == 19 else "MLUPS (D3Q15+D3Q7)", "value": round(mlups, 2),
+        "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 6),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
         "data": "synthetic",
-        "config": _config(args.workload, args.storage,
+        "config": _config(args.workload, args.storage, q=q, extra=
                           {"parallelism": f"replicas{ws}" if ws > 1 else "single"}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": profiled_traffic() if (args.workload, args.storage) == ("channel", "fp32") else None,
+                     "traffic": (profiled_traffic() if (args.workload, args.storage, q) == ("channel", "fp32", 19)
+                                 else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
-                     "kernel": ("step_kernel<false,true> (fused stream-collide, outflow)"
+                     "kernel": (f"step_kernel<false,true,D3Q{q}> (fused stream-collide, outflow)"
                                 if args.workload == "channel" else
-                                "step_kernel<true,false> (fused stream-collide, porosity field)")},
+                                f"step_kernel<true,false,D3Q{q}> (fused stream-collide, porosity field)")},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_mlups, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(fp.nbytes + gp.nbytes),
@@ -550,6 +553,8 @@ def main(argv=None):
                     help="population storage (the headline workload is fp32)")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="channel",
                     help="the headline workload is the 256x64x64 channel")
+    ap.add_argument("--lattice", choices=("d3q19", "d3q15"), default="d3q19",
+                    help="flow lattice of the channel / cavity workloads (the headline is D3Q19)")
     ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")
     ap.add_argument("--max-steps", type=int, default=20000, help="serve: step limit")
     ap.add_argument("--fill", type=int, default=8_000_000,

@@ -112,6 +112,12 @@ typedef struct lbm_params {
     double c_pl, c_ps;               /* specific heats (1, 1); c_ref = harmonic mean (Eq. B13) */
     double sigma_s, sigma_l;         /* heat-capacity ratios (Eq. B4); <= 0: sigma */
     double alpha_ratio;              /* alpha_l / alpha_s (1); alpha_l = the fluid diffusivity */
+    /* flow lattice: 19 (D3Q19-MRT, Sec. 3.1.2, the default; 0 reads as 19) or 15 (D3Q15-MRT,
+     * Sec. 3.1.1: velocities of Eq. 12, moments of Eq. 13 / Eq. A1, equilibria of Eq. 15,
+     * Lambda of Eq. 16 from s_e, s_eps, s_q, s_nu, s_m, forcing of Eq. 17).  D3Q15 runs with
+     * FP32 storage, without the enthalpy model, and outside lbm_batch / lbm_server; its f
+     * arrays in lbm_set_populations / lbm_get_populations hold 15 planes. */
+    int q_flow;
 } lbm_params;
 
 /*
@@ -131,6 +137,9 @@ typedef struct lbm_lattice {
     double U_out;
     int enthalpy, flow_off;
     double c_pl, c_ref, sigma_s, sigma_l, T_s, T_l, L_a, alpha_s, alpha_l;
+    int q;                     /* flow lattice (19 or 15); with 15, s[] keeps the D3Q19 order
+                                  and the D3Q15 rates s_e, s_eps, s_q, s_nu, s_m of Eq. 16 are
+                                  s[1], s[2], s[4], s[9], s[16] */
 } lbm_lattice;
 
 /* Fill p with the paper's defaults (Sec. 4: rho0 = 1, J = sigma = Gamma = 1, varpi = 1/2,
@@ -185,13 +194,13 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const double* T_field, const double* u_field,
                                 double T_uniform);
 
-/* Replace the stored post-collision populations f*(x, t-1), g*(x, t-1) (host, 19 x ns and
- * 7 x ns doubles, full values, not deviations).  The outflow history is reset to the
+/* Replace the stored post-collision populations f*(x, t-1), g*(x, t-1) (host, Q x ns and
+ * 7 x ns doubles with Q = 19 or 15 the flow lattice, full values, not deviations).  The outflow history is reset to the
  * stored populations of the x-high column.  Synchronises. */
 lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g);
 
-/* Copy the stored post-collision populations to host (19 x ns and 7 x ns doubles, full
- * values); either pointer may be NULL.  Synchronises. */
+/* Copy the stored post-collision populations to host (Q x ns and 7 x ns doubles, Q = 19 or
+ * 15, full values); either pointer may be NULL.  Synchronises. */
 lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* g);
 
 /* Macroscopic fields at the current time, computed from the streamed populations exactly

@@ -70,6 +70,7 @@ class LbmParams(C.Structure):
         ("T_m", C.c_double), ("T_s", C.c_double), ("T_l", C.c_double), ("St", C.c_double),
         ("c_pl", C.c_double), ("c_ps", C.c_double), ("sigma_s", C.c_double),
         ("sigma_l", C.c_double), ("alpha_ratio", C.c_double),
+        ("q_flow", C.c_int),
     ]
 
 
@@ -92,6 +93,7 @@ class LbmLattice(C.Structure):
         ("c_pl", C.c_double), ("c_ref", C.c_double), ("sigma_s", C.c_double),
         ("sigma_l", C.c_double), ("T_s", C.c_double), ("T_l", C.c_double), ("L_a", C.c_double),
         ("alpha_s", C.c_double), ("alpha_l", C.c_double),
+        ("q", C.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -220,6 +222,7 @@ def params_from_problem(pb: dict) -> LbmParams:
         p.Da = float(pb["Da"])
     if "T_init" not in pb:
         p.T_init = p.T0
+    p.q_flow = int(pb.get("q", 19))
     p.enthalpy = int(bool(pb.get("enthalpy", False)))
     p.flow_off = int(bool(pb.get("flow_off", False)))
     for k in ("T_m", "T_s", "T_l", "St", "c_pl", "c_ps", "sigma_s", "sigma_l", "alpha_ratio"):
@@ -260,6 +263,7 @@ class Lattice:
         self.nx, self.ny, self.nz = int(pb["nx"]), int(pb["ny"]), int(pb["nz"])
         self.shape = (self.nz, self.ny, self.nx)
         self.ns = self.nx * self.ny * self.nz
+        self.q = 15 if int(pb.get("q", 19)) == 15 else 19  # flow lattice
         self._h = C.c_void_p()
         self._params = params_from_problem(pb)
         st = lib().lbm_create(C.byref(self._params), C.c_void_p(stream or 0), C.byref(self._h))
@@ -323,11 +327,11 @@ class Lattice:
     def set_populations(self, f: np.ndarray, g: np.ndarray):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
-        assert f.size == Q19 * self.ns and g.size == Q7 * self.ns
+        assert f.size == self.q * self.ns and g.size == Q7 * self.ns
         self._check(lib().lbm_set_populations(self._h, _dp(f), _dp(g)), "lbm_set_populations")
 
     def populations(self):
-        f = np.zeros((Q19,) + self.shape)
+        f = np.zeros((self.q,) + self.shape)
         g = np.zeros((Q7,) + self.shape)
         self._check(lib().lbm_get_populations(self._h, _dp(f), _dp(g)), "lbm_get_populations")
         return f, g
@@ -519,9 +523,12 @@ def medium_args(pb: dict) -> dict:
 
 
 def algorithmic_bytes_per_site(pb: dict) -> int:
-    """Bytes one time step must move per site: 26 populations read and written in the
-    storage format (4 or 2 bytes each), plus the FP32 porosity of a heterogeneous medium."""
-    return 26 * 2 * STORAGE_BYTES[pb.get("storage", "fp32")] + (4 if pb.get("phi_field") is not None else 0)
+    """Bytes one time step must move per site: the Q + 7 populations (26 for D3Q19, 22 for
+    D3Q15) read and written in the storage format (4 or 2 bytes each), plus the FP32
+    porosity of a heterogeneous medium."""
+    npop = (15 if int(pb.get("q", 19)) == 15 else 19) + 7
+    return (npop * 2 * STORAGE_BYTES[pb.get("storage", "fp32")]
+            + (4 if pb.get("phi_field") is not None else 0))
 
 
 def nan_safe(x: float) -> float:

@@ -88,6 +88,9 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
     if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16_DEV &&
         p->storage != LBM_STORE_BF16_DEV)
         return "unknown storage format";
+    L->q = p->q_flow == 0 ? 19 : p->q_flow;
+    if (L->q != 19 && L->q != 15) return "q_flow must be 19 (D3Q19) or 15 (D3Q15)";
+    if (L->q == 15 && p->storage != LBM_STORE_FP32) return "D3Q15 runs with FP32 storage only";
     if (!finite_pos(p->rho0)) return "rho0 must be > 0";
     if (!(p->varpi > 0.0 && p->varpi < 1.0)) return "varpi must lie in (0, 1)";
     if (!finite_pos(p->sigma)) return "sigma must be > 0";
@@ -207,6 +210,7 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
     if (p->enthalpy) {
         if (p->storage != LBM_STORE_FP32) return "the enthalpy model stores FP32 populations";
         if (p->flow_bc[1] == LBM_FLOW_OUTFLOW) return "the enthalpy model has no outflow";
+        if (L->q == 15) return "the enthalpy model runs on the D3Q19 lattice";
         if (!finite_pos(p->St) || !finite_pos(p->c_pl) || !finite_pos(p->c_ps) ||
             !finite_pos(p->alpha_ratio))
             return "St, c_pl, c_ps and alpha_ratio must be > 0";
@@ -257,6 +261,7 @@ lbm_status lbm_params_default(lbm_params* p) {
     p->c_pl = p->c_ps = 1.0;
     p->sigma_s = p->sigma_l = -1.0;
     p->alpha_ratio = 1.0;
+    p->q_flow = 19;
     return LBM_OK;
 }
 
@@ -353,6 +358,7 @@ void fill_kparams(lbm_ctx* c) {
     k.s_m = (float)L.s[16];
     k.zeta_e = (float)L.zeta_e;
     k.zeta_nu = (float)L.zeta_nu;
+    k.qf = L.q == 15 ? 15 : 19;
     {
         // per-moment collision factors: s_k / |M_k|^2 and (1 - s_k / 2) / |M_k|^2 (Eq. 9)
         auto a = [](double sk, double n2) { return (float)(sk / n2); };
@@ -378,6 +384,16 @@ void fill_kparams(lbm_ctx* c) {
         k.bnu4 = b(snu, 4.0);
         k.am8 = a(sm, 8.0);
         k.rho0_10 = (float)(L.rho0 / 10.0);
+        // D3Q15 (Eq. A1 row norms: e 18, eps 360, q 40, 3p_xx 12, p_ww 4, p_xy.. 8, m_xyz 8)
+        const double c73 = 7.0 / 3.0 * L.rho0;  // q_eq = -7/3 rho0 u (Eq. 15)
+        k.ae15 = a(se, 18.0);
+        k.be15 = b(se, 18.0);
+        k.aeps15 = a(seps, 360.0);
+        k.beps15 = b(seps, 360.0);
+        k.aqc15 = (float)(sq / 40.0 * c73);
+        k.bqc15 = (float)((1.0 - 0.5 * sq) / 40.0 * c73);
+        k.anu8 = a(snu, 8.0);
+        k.bnu8 = b(snu, 8.0);
         k.ze6 = (float)(L.zeta_e / 6.0);
         k.zn6 = (float)(L.zeta_nu / 6.0);
     }
@@ -426,9 +442,15 @@ lbm_status usable(lbm_ctx* c) {
 
 float* cur_hist(lbm_ctx* c) { return c->hist[c->cur]; }
 
-// Start of population plane q of copy k.
+// Flow populations of the context's lattice (19 or 15) and whether logical plane q exists:
+// f planes 0 .. Q-1, the D3Q7 planes at 19 .. 25 whatever the flow lattice.
+int flow_q(const lbm_ctx* c) { return c->lat.q == 15 ? 15 : 19; }
+bool has_plane(const lbm_ctx* c, int q) { return q < flow_q(c) || q >= lbm::kQ; }
+
+// Start of logical population plane q of copy k (copies hold Q + 7 planes).
 void* plane_ptr(const lbm_ctx* c, int k, int q) {
-    return static_cast<char*>(c->pop[k]) + (size_t)q * (size_t)c->sq * c->elem;
+    const int phys = q < lbm::kQ ? q : flow_q(c) + (q - lbm::kQ);
+    return static_cast<char*>(c->pop[k]) + (size_t)phys * (size_t)c->sq * c->elem;
 }
 
 // Planes of a step that reads copy `from` and writes the other copy.
@@ -436,8 +458,8 @@ lbm::Planes planes(const lbm_ctx* c, int from) {
     lbm::Planes pl;
     const int to = from ^ 1;
     for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
-        pl.in[q] = plane_ptr(c, from, q);
-        pl.out[q] = plane_ptr(c, to, q);
+        pl.in[q] = has_plane(c, q) ? plane_ptr(c, from, q) : nullptr;
+        pl.out[q] = has_plane(c, q) ? plane_ptr(c, to, q) : nullptr;
     }
     pl.hin = c->hist[from];
     pl.hout = c->hist[to];
@@ -508,7 +530,7 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamCreate");
         else c->own_stream = true;
     }
-    size_t pop_bytes = c->elem * (size_t)(lbm::kQ + lbm::kQT) * (size_t)c->sq;
+    size_t pop_bytes = c->elem * (size_t)((L.q == 15 ? 15 : lbm::kQ) + lbm::kQT) * (size_t)c->sq;
     for (int k = 0; k < 2 && st == LBM_OK; ++k) {
         e = cudaMalloc(&c->pop[k], pop_bytes);
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(populations)");
@@ -663,15 +685,17 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* T_field, const double*
 static double plane_scale(const lbm_ctx* c, int q) {
     if (c->prm.storage == LBM_STORE_FP32) return 1.0;
     const lbm_lattice& L = c->lat;
-    if (q < lbm::kQ) return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    if (q < lbm::kQ) return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);  // D3Q19 only
     return q == lbm::kQ ? 1.0 - L.varpi : L.varpi / 6.0;
 }
 
 static double plane_offset(const lbm_ctx* c, int q) {
-    // w_i rho0 for the D3Q19 planes (weights under Eq. 24), omega_i sigma T0 for D3Q7 (Eq. 42)
+    // w_i rho0 for the flow planes (D3Q19 weights under Eq. 24, D3Q15 under Eq. 18),
+    // omega_i sigma T0 for D3Q7 (Eq. 42)
     const lbm_lattice& L = c->lat;
     if (q < lbm::kQ) {
-        double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+        double w = L.q == 15 ? (q == 0 ? 2.0 / 9.0 : (q <= 6 ? 1.0 / 9.0 : 1.0 / 72.0))
+                             : (q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0));
         return w * L.rho0;
     }
     if (L.enthalpy) return 0.0;  // D3Q7 planes hold the full enthalpy populations
@@ -688,6 +712,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
     const bool tshift = c->prm.storage != LBM_STORE_FP32;  // D3Q7 stored against local T
     const int nq = tshift ? lbm::kQ : lbm::kQ + lbm::kQT;
     for (int q = 0; q < nq; ++q) {
+        if (!has_plane(c, q)) continue;
         const double* src = q < lbm::kQ ? f + (size_t)q * c->ns : g + (size_t)(q - lbm::kQ) * c->ns;
         double* stg = c->stage + (size_t)(q & 3) * c->ns;  // rotate 4 staging planes
         LBM_CUDA(cudaMemcpyAsync(stg, src, sizeof(double) * c->ns, cudaMemcpyHostToDevice,
@@ -713,6 +738,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
     const bool tshift = c->prm.storage != LBM_STORE_FP32;
     const int nq = tshift ? lbm::kQ : lbm::kQ + lbm::kQT;
     for (int q = 0; q < nq; ++q) {
+        if (!has_plane(c, q)) continue;
         double* dst = q < lbm::kQ ? (f ? f + (size_t)q * c->ns : nullptr)
                                   : (g ? g + (size_t)(q - lbm::kQ) * c->ns : nullptr);
         if (!dst) continue;
@@ -981,7 +1007,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
     }
     for (int k = 0; k < n; ++k) {
         lbm_ctx* c = ctxs[k];
-        if (!c || c->sticky != LBM_OK) {
+        if (!c || c->sticky != LBM_OK || c->lat.q == 15) {  // D3Q15 lattices step alone
             delete b;
             return LBM_EINVAL;
         }
@@ -1158,13 +1184,13 @@ unsigned long long footprint_of(const lbm_params* p, const lbm_lattice& L, int h
     const unsigned long long ns = (unsigned long long)p->nx * p->ny * p->nz;
     const unsigned long long sq = (ns + 63) / 64 * 64;
     const unsigned long long elem = p->storage == LBM_STORE_FP32 ? 4 : 2;
-    unsigned long long b = 2ull * (lbm::kQ + lbm::kQT) * elem * sq;  // two population copies
+    const unsigned long long nq = (L.q == 15 ? 15 : lbm::kQ) + lbm::kQT;
+    unsigned long long b = 2ull * nq * elem * sq;  // two population copies
     if (p->flow_bc[1] == LBM_FLOW_OUTFLOW) b += 2ull * lbm::kOutSlots * 4 * p->ny * p->nz;
     if (p->storage != LBM_STORE_FP32) b += 2ull * 4 * ns;  // temperature planes
     if (has_phi_field) b += 4 * ns;
     b += 9ull * 4 * ns;  // macro fields of the residual
     b += 5ull * 8 * lbm::reduction_blocks() + 8ull * (p->nx > p->ny ? p->nx : p->ny) + 64;
-    (void)L;
     return b;
 }
 
@@ -1280,6 +1306,7 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
     if (!s || !p || !(tol > 0.0) || max_steps < 1) return LBM_EINVAL;
     lbm_lattice L;
     if (derive(p, &L)) return LBM_EINVAL;
+    if (L.q == 15) return LBM_EINVAL;  // the serving loop batches D3Q19 lattices
     auto* r = new (std::nothrow) lbm_server::Req();
     if (!r) return LBM_ENOMEM;
     r->p = *p;

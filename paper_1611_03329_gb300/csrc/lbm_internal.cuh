@@ -40,6 +40,9 @@ struct KParams {
     // (|M_k|^2 = 2394, 252, 40, 36, 72, 12, 24, 4, 8), with 2/3 rho0 folded into the q rows
     float ae, be, aeps, beps, aq, aqc, bqc, anu36, bnu36, api72, hbpi72, anu12, bnu12;
     float api24, hbpi24, anu4, bnu4, am8, rho0_10;
+    // D3Q15 (Eq. A1 norms 18, 360, 40, 8; the 12 and 4 rows share anu12 / anu4 above)
+    int qf;  // flow populations: 19 (D3Q19) or 15 (D3Q15)
+    float ae15, be15, aeps15, beps15, aqc15, bqc15, anu8, bnu8;
     float ze6, zn6;  // zeta_e / 6, zeta_nu / 6 (Eq. 43 columns)
     // enthalpy model (App. B): En_{e,s}, En_{e,l}, 1/(sigma_s c_pl), 1/(sigma_l c_pl),
     // 1/(En_{e,l} - En_{e,s}) (0 when isothermal), phase diffusivities, 3/varpi

@@ -58,6 +58,62 @@ __host__ __device__ constexpr int ey7(int i) { return i == 3 ? 1 : i == 4 ? -1 :
 __host__ __device__ constexpr int ez7(int i) { return i == 5 ? 1 : i == 6 ? -1 : 0; }
 __host__ __device__ constexpr int opp7(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// Flow lattices as traits of the site kernels: D3Q19 (Eq. 19, the default) and D3Q15
+// (Eq. 12).  Both put the velocities with e_x = -1 at 2, 8, 10, 12, 14 (the outflow slots).
+struct D3Q19 {
+    static constexpr int kQ = 19;
+    __host__ __device__ static constexpr int ex(int i) { return ex19(i); }
+    __host__ __device__ static constexpr int ey(int i) { return ey19(i); }
+    __host__ __device__ static constexpr int ez(int i) { return ez19(i); }
+    __host__ __device__ static constexpr int opp(int i) { return opp19(i); }
+    __host__ __device__ static constexpr float w(int i) { return w19(i); }
+    __host__ __device__ static constexpr double wd(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int slot(int i) { return slot19(i); }
+};
+struct D3Q15 {
+    static constexpr int kQ = 15;
+    __host__ __device__ static constexpr int ex(int i) {
+        return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)    ? 1
+               : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                                      : 0;
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return (i == 3 || i == 7 || i == 8 || i == 11 || i == 12)    ? 1
+               : (i == 4 || i == 9 || i == 10 || i == 13 || i == 14) ? -1
+                                                                      : 0;
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        return (i == 5 || i == 7 || i == 8 || i == 9 || i == 10)     ? 1
+               : (i == 6 || i == 11 || i == 12 || i == 13 || i == 14) ? -1
+                                                                       : 0;
+    }
+    __host__ __device__ static constexpr int opp(int i) {
+        return i == 0 ? 0 : (i <= 6 ? ((i & 1) ? i + 1 : i - 1) : 21 - i);
+    }
+    // weights stated under Eq. 18
+    __host__ __device__ static constexpr float w(int i) {
+        return i == 0 ? 2.0f / 9.0f : (i <= 6 ? 1.0f / 9.0f : 1.0f / 72.0f);
+    }
+    __host__ __device__ static constexpr double wd(int i) {
+        return i == 0 ? 2.0 / 9.0 : (i <= 6 ? 1.0 / 9.0 : 1.0 / 72.0);
+    }
+    __host__ __device__ static constexpr int slot(int i) { return slot19(i); }
+};
+template <class L>
+constexpr bool lattice_consistent() {
+    for (int i = 0; i < L::kQ; ++i) {
+        const int o = L::opp(i);
+        if (L::opp(o) != i || L::ex(o) != -L::ex(i) || L::ey(o) != -L::ey(i) ||
+            L::ez(o) != -L::ez(i))
+            return false;
+        if ((L::ex(i) == -1) != (L::slot(i) >= 0)) return false;
+    }
+    return true;
+}
+static_assert(lattice_consistent<D3Q19>() && lattice_consistent<D3Q15>(), "lattice tables");
+
 static_assert(opp19(7) == 10 && opp19(8) == 9 && opp19(12) == 13 && opp19(16) == 17, "opp19");
 static_assert(ex19(opp19(13)) == -ex19(13) && ez19(opp19(13)) == -ez19(13), "opp19 sign");
 
@@ -210,22 +266,22 @@ __device__ __forceinline__ Medium medium_at(const KParams& p, int s) {
 // ---- streaming with boundary rules ------------------------------------------------------------
 // Pull of f_I at site n: the post-collision population at x - e_I, or the wall rule when that
 // source lies outside (a no-slip wall wins over a velocity face, which wins over the outflow).
-template <int I, bool OUTF, class S>
+template <class L, int I, bool OUTF, class S>
 __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, const Nbr& n,
                                         bool* via) {
-    constexpr int ex = ex19(I), ey = ey19(I), ez = ez19(I);
+    constexpr int ex = L::ex(I), ey = L::ey(I), ez = L::ez(I);
     const int oyz = axis_off(ey, n.ym, n.yp) + axis_off(ez, n.zm, n.zp);
     const unsigned cyz = axis_cross(ey, n.cross, 4u, 8u) | axis_cross(ez, n.cross, 16u, 32u);
     const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | cyz;
     if (cr == 0u) return ldp<S>(pl, p, I, n.s + axis_off(ex, n.xm, n.xp) + oyz);
-    const float bb = ldp<S>(pl, p, opp19(I), n.s);
+    const float bb = ldp<S>(pl, p, L::opp(I), n.s);
     if (cr & p.wall_mask) return bb;
     unsigned vm = cr & p.vel_mask;
     if (vm) {
         int face = __ffs(vm) - 1;
         float eu = (float)ex * p.face_u[face][0] + (float)ey * p.face_u[face][1] +
                    (float)ez * p.face_u[face][2];
-        return bb + 6.0f * w19(I) * p.rho0 * eu;  // 2 w_i rho0 (e_i . u_w) / c_s^2
+        return bb + 6.0f * L::w(I) * p.rho0 * eu;  // 2 w_i rho0 (e_i . u_w) / c_s^2
     }
     if constexpr (OUTF && ex == -1) {
         // convective outflow: p(N-1, t+1) = (p(N-1, t) + U p(N-2, t+1)) / (1 + U), with
@@ -235,16 +291,16 @@ __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, cons
         if (cyz == 0u) {
             inner = ldp<S>(pl, p, I, n.s + oyz);  // source of x-1 along -x is x itself
         } else {
-            inner = ldp<S>(pl, p, opp19(I), n.s - 1);
+            inner = ldp<S>(pl, p, L::opp(I), n.s - 1);
             unsigned vmi = cyz & p.vel_mask;
             if (!(cyz & p.wall_mask) && vmi) {
                 int face = __ffs(vmi) - 1;
                 float eu = (float)ex * p.face_u[face][0] + (float)ey * p.face_u[face][1] +
                            (float)ez * p.face_u[face][2];
-                inner += 6.0f * w19(I) * p.rho0 * eu;
+                inner += 6.0f * L::w(I) * p.rho0 * eu;
             }
         }
-        float old = __ldg(pl.hin + slot19(I) * p.nyz + n.y + p.ny * n.z);
+        float old = __ldg(pl.hin + L::slot(I) * p.nyz + n.y + p.ny * n.z);
         return p.out_a * old + p.out_b * inner;
     }
     return bb;  // not reached for validated boundary sets
@@ -272,11 +328,11 @@ __device__ __forceinline__ float pull_g(const Planes& pl, const KParams& p, cons
     return bb;  // adiabatic: bounce-back
 }
 
-template <bool OUTF, class S, int... I>
+template <class L, bool OUTF, class S, int... I>
 __device__ __forceinline__ void gather_f_bc(float* f, bool* via, const Planes& pl,
                                             const KParams& p, const Nbr& n,
                                             std::integer_sequence<int, I...>) {
-    ((f[I] = pull_f<I, OUTF, S>(pl, p, n, &via[I])), ...);
+    ((f[I] = pull_f<L, I, OUTF, S>(pl, p, n, &via[I])), ...);
 }
 
 template <bool OUTF, class S, int... I>
@@ -285,29 +341,29 @@ __device__ __forceinline__ void gather_g_bc(float* g, const Planes& pl, const KP
     ((g[I] = pull_g<I, OUTF, S>(pl, p, n)), ...);
 }
 
-// Predicated pull of all 26 populations (any site), with the outflow's pressure anchor.
-template <bool OUTF, class S>
+// Predicated pull of all populations (any site), with the outflow's pressure anchor.
+template <bool OUTF, class S, class L = D3Q19>
 __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& p, const Nbr& n,
                                                float* f, float* g) {
-    bool via[kQ];
+    bool via[L::kQ];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) via[i] = false;
-    gather_f_bc<OUTF, S>(f, via, pl, p, n, std::make_integer_sequence<int, kQ>{});
+    for (int i = 0; i < L::kQ; ++i) via[i] = false;
+    gather_f_bc<L, OUTF, S>(f, via, pl, p, n, std::make_integer_sequence<int, L::kQ>{});
     gather_g_bc<OUTF, S>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
     if (OUTF && n.x == p.nx - 1) {
         // pressure anchor: shift the populations set by the outflow rule by
         // w_i (rho0 - rho) / sum(w_i) so that the outlet density is rho0
         float rho = 0.0f, wsum = 0.0f;
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) {
+        for (int i = 0; i < L::kQ; ++i) {
             rho += f[i];
-            if (via[i]) wsum += w19(i);
+            if (via[i]) wsum += L::w(i);
         }
         if (wsum > 0.0f) {
             float corr = -rho / wsum;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i)
-                if (via[i]) f[i] += w19(i) * corr;
+            for (int i = 0; i < L::kQ; ++i)
+                if (via[i]) f[i] += L::w(i) * corr;
         }
     }
 }
@@ -316,7 +372,7 @@ __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& 
 // rule): unconditional loads with per-lane x offsets, then, only in a warp that holds an
 // x-face site, the x-face rule for the velocities that cross it.  With no x-face lane this is
 // the interior path.
-template <bool OUTF, class S>
+template <bool OUTF, class S, class L = D3Q19>
 __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
                                                    int z, int s, unsigned lanes, float* f,
                                                    float* g) {
@@ -326,8 +382,8 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
     if (x == 0) { if (p.per_mask & 1u) xm = nx - 1; else { xm = 0; cxm = true; } }
     if (x == nx - 1) { if (p.per_mask & 2u) xp = 1 - nx; else { xp = 0; cxp = true; } }
 #pragma unroll
-    for (int i = 0; i < kQ; ++i)
-        f[i] = ldp<S>(pl, p, i, s + axis_off(ex19(i), xm, xp) - (ey19(i) * nx + ez19(i) * nxy));
+    for (int i = 0; i < L::kQ; ++i)
+        f[i] = ldp<S>(pl, p, i, s + axis_off(L::ex(i), xm, xp) - (L::ey(i) * nx + L::ez(i) * nxy));
 #pragma unroll
     for (int i = 0; i < kQT; ++i)
         g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
@@ -336,12 +392,12 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
         // x-low face: wall or velocity face (an outflow is only allowed on x-high)
         const bool vel = (p.vel_mask & 1u) && !(p.wall_mask & 1u);
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            if (ex19(i) != 1) continue;
-            float v = ldp<S>(pl, p, opp19(i), s);
+        for (int i = 0; i < L::kQ; ++i) {
+            if (L::ex(i) != 1) continue;
+            float v = ldp<S>(pl, p, L::opp(i), s);
             if (vel)
-                v += 6.0f * w19(i) * p.rho0 *
-                     (p.face_u[0][0] + (float)ey19(i) * p.face_u[0][1] + (float)ez19(i) * p.face_u[0][2]);
+                v += 6.0f * L::w(i) * p.rho0 *
+                     (p.face_u[0][0] + (float)L::ey(i) * p.face_u[0][1] + (float)L::ez(i) * p.face_u[0][2]);
             f[i] = v;
         }
         const float bb = ldg_dev<S>(pl, p, 2, s);
@@ -351,13 +407,13 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
         const bool wall = p.wall_mask & 2u, vel = p.vel_mask & 2u;
         if (!OUTF || wall || vel) {
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                if (ex19(i) != -1) continue;
-                float v = ldp<S>(pl, p, opp19(i), s);
+            for (int i = 0; i < L::kQ; ++i) {
+                if (L::ex(i) != -1) continue;
+                float v = ldp<S>(pl, p, L::opp(i), s);
                 if (vel && !wall)
-                    v += 6.0f * w19(i) * p.rho0 *
-                         (-p.face_u[1][0] + (float)ey19(i) * p.face_u[1][1] +
-                          (float)ez19(i) * p.face_u[1][2]);
+                    v += 6.0f * L::w(i) * p.rho0 *
+                         (-p.face_u[1][0] + (float)L::ey(i) * p.face_u[1][1] +
+                          (float)L::ez(i) * p.face_u[1][2]);
                 f[i] = v;
             }
         } else {
@@ -365,19 +421,19 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
             // pressure anchor: shift them by w_i (rho0 - rho) / sum(w_i), sum(w_i) = 1/6
             const int yz = y + p.ny * z;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                if (ex19(i) != -1) continue;
-                float inner = ldp<S>(pl, p, i, s - (ey19(i) * nx + ez19(i) * nxy));
-                float old = __ldg(pl.hin + slot19(i) * p.nyz + yz);
+            for (int i = 0; i < L::kQ; ++i) {
+                if (L::ex(i) != -1) continue;
+                float inner = ldp<S>(pl, p, i, s - (L::ey(i) * nx + L::ez(i) * nxy));
+                float old = __ldg(pl.hin + L::slot(i) * p.nyz + yz);
                 f[i] = p.out_a * old + p.out_b * inner;
             }
             float rho = 0.0f;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) rho += f[i];
+            for (int i = 0; i < L::kQ; ++i) rho += f[i];
             const float corr = -6.0f * rho;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i)
-                if (ex19(i) == -1) f[i] += w19(i) * corr;
+            for (int i = 0; i < L::kQ; ++i)
+                if (L::ex(i) == -1) f[i] += L::w(i) * corr;
         }
         const float bb = ldg_dev<S>(pl, p, 1, s);
         const int kind = p.heat_kind[1];
@@ -414,6 +470,37 @@ struct Macro {
 
 // sqrt of a non-negative value through the hardware reciprocal square root (exact zero kept).
 __device__ __forceinline__ float sqrt_nonneg(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
+
+// D3Q7: n = N g (Eq. 36), n_eq = T (sigma, u, varpi sigma, 0, 0) (Eq. 37), Eq. 34, Eq. 43;
+// enthalpy model: n_eq = (En_e, c_pl T u, varpi c_ref T, 0, 0) (Eq. B6) on full values,
+// zeta_alpha from Eq. B11 with alpha_e = f_l alpha_l + (1 - f_l) alpha_s.  n0 = sum g (the
+// deviation sigma (T - T0), or En_e), u the flow's velocity; g is updated in place.
+template <bool ENTH>
+__device__ __forceinline__ void collide_g(const KParams& p, const Medium& md, float* g, float n0,
+                                          float T, float fl, float ux, float uy, float uz) {
+    const float g12 = g[1] + g[2], g34 = g[3] + g[4], g56 = g[5] + g[6];
+    const float n4 = g12 + g34 + g56;  // minus varpi sigma T0 (standard model)
+    float tu = T, n4eq = p.varpi * n0, za = md.zeta_alpha;
+    if constexpr (ENTH) {
+        tu = p.c_pl * T;
+        n4eq = p.varpi * p.c_ref * T;
+        za = __fdividef(1.0f, 0.5f + (fl * p.alpha_l + (1.0f - fl) * p.alpha_s) * p.inv_csT2);
+    }
+    const float dn1 = za * (tu * ux - (g[1] - g[2]));
+    const float dn2 = za * (tu * uy - (g[3] - g[4]));
+    const float dn3 = za * (tu * uz - (g[5] - g[6]));
+    const float c4 = p.ze6 * (n4eq - n4);  // dn4 / 6
+    const float c5 = -p.zn6 * (g12 - g34);         // dn5 / 6
+    const float c6 = -p.zn6 * (g12 - g56);         // dn6 / 6
+    g[0] -= 6.0f * c4;
+    const float gx = c4 + c5 + c6, gy = c4 - 2.0f * c5 + c6, gz = c4 + c5 - 2.0f * c6;
+    g[1] += gx + 0.5f * dn1;
+    g[2] += gx - 0.5f * dn1;
+    g[3] += gy + 0.5f * dn2;
+    g[4] += gy - 0.5f * dn2;
+    g[5] += gz + 0.5f * dn3;
+    g[6] += gz - 0.5f * dn3;
+}
 
 // Eqs. 39, 5, 25, 27-28, 4, then (FULL) Eq. 9 with Eqs. 21-23 in moment space and Eq. 34 with
 // Eqs. 37-38, back-transformed in place.  f, g are deviations on entry and exit.  The
@@ -577,51 +664,155 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 
     }  // flow collision
 
-    // D3Q7: n = N g (Eq. 36), n_eq = T (sigma, u, varpi sigma, 0, 0) (Eq. 37), Eq. 34, Eq. 43;
-    // enthalpy model: n_eq = (En_e, c_pl T u, varpi c_ref T, 0, 0) (Eq. B6) on full values,
-    // zeta_alpha from Eq. B11 with alpha_e = f_l alpha_l + (1 - f_l) alpha_s
-    const float g12 = g[1] + g[2], g34 = g[3] + g[4], g56 = g[5] + g[6];
-    const float n4 = g12 + g34 + g56;  // minus varpi sigma T0 (standard model)
-    float tu = T, n4eq = p.varpi * n0, za = md.zeta_alpha;
-    if constexpr (ENTH) {
-        tu = p.c_pl * T;
-        n4eq = p.varpi * p.c_ref * T;
-        za = __fdividef(1.0f, 0.5f + (fl * p.alpha_l + (1.0f - fl) * p.alpha_s) * p.inv_csT2);
-    }
-    const float dn1 = za * (tu * ux - (g[1] - g[2]));
-    const float dn2 = za * (tu * uy - (g[3] - g[4]));
-    const float dn3 = za * (tu * uz - (g[5] - g[6]));
-    const float c4 = p.ze6 * (n4eq - n4);  // dn4 / 6
-    const float c5 = -p.zn6 * (g12 - g34);         // dn5 / 6
-    const float c6 = -p.zn6 * (g12 - g56);         // dn6 / 6
-    g[0] -= 6.0f * c4;
-    const float gx = c4 + c5 + c6, gy = c4 - 2.0f * c5 + c6, gz = c4 + c5 - 2.0f * c6;
-    g[1] += gx + 0.5f * dn1;
-    g[2] += gx - 0.5f * dn1;
-    g[3] += gy + 0.5f * dn2;
-    g[4] += gy - 0.5f * dn2;
-    g[5] += gz + 0.5f * dn3;
-    g[6] += gz - 0.5f * dn3;
+    collide_g<ENTH>(p, md, g, n0, T, fl, ux, uy, uz);
     return mac;
+}
+
+// D3Q15 (Sec. 3.1.1): the same steps with the moments of Eq. 13 (rows of Eq. A1), the
+// equilibria of Eq. 15 (beta1 = 1, beta2 = -5), the forcing of Eq. 17 and Lambda of Eq. 16,
+// back-transformed through M^T diag(1/|M_k|^2) (the rows of Eq. A1 are orthogonal, with
+// |M_k|^2 = 15, 18, 360, 10, 40, 12, 4, 8).  f, g are deviations on entry and exit.
+template <bool FULL>
+__device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, float* f, float* g) {
+    const float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
+    const float dT = n0 * p.inv_sigma;
+    const float T = p.T0 + dT;
+    const float Gx = p.buoy[0] * dT + p.accel[0];
+    const float Gy = p.buoy[1] * dT + p.accel[1];
+    const float Gz = p.buoy[2] * dT + p.accel[2];
+
+    // sums / differences over opposite pairs; the four corner pairs along (+-1, +-1, 1)
+    const float s1 = f[1] + f[2], d1 = f[1] - f[2];
+    const float s2 = f[3] + f[4], d2 = f[3] - f[4];
+    const float s3 = f[5] + f[6], d3 = f[5] - f[6];
+    const float sa = f[7] + f[14], da = f[7] - f[14];    // ( 1, 1, 1)
+    const float sb = f[8] + f[13], db = f[8] - f[13];    // (-1, 1, 1)
+    const float sc = f[9] + f[12], dc = f[9] - f[12];    // ( 1,-1, 1)
+    const float sd = f[10] + f[11], dd = f[10] - f[11];  // (-1,-1, 1)
+    const float A = s1 + s2 + s3;
+    const float Cs = (sa + sb) + (sc + sd);
+    const float rho = f[0] + A + Cs;  // rho - rho0 (Eq. 25)
+    const float jx = d1 + (da - db) + (dc - dd);
+    const float jy = d2 + (da + db) - (dc + dd);
+    const float jz = d3 + (da + db) + (dc + dd);
+
+    // velocity (Eqs. 27-28) and total force (Eq. 4)
+    const float hphi = 0.5f * md.phi;
+    const float vx = jx * p.inv_rho0 + hphi * Gx;
+    const float vy = jy * p.inv_rho0 + hphi * Gy;
+    const float vz = jz * p.inv_rho0 + hphi * Gz;
+    const float vmag = sqrt_nonneg(vx * vx + vy * vy + vz * vz);
+    const float inv_den = __fdividef(1.0f, md.l0 + sqrt_nonneg(md.l0 * md.l0 + md.l1 * vmag));
+    const float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
+
+    Macro mac;
+    mac.rho = p.rho0 + rho;
+    mac.ux = ux;
+    mac.uy = uy;
+    mac.uz = uz;
+    mac.T = T;
+    mac.dT = dT;
+    if (!FULL) return mac;
+
+    const float umag = vmag * inv_den;
+    const float drag = md.c_darcy + md.c_forch * umag;
+    const float Fx = md.phi * Gx - drag * ux;
+    const float Fy = md.phi * Gy - drag * uy;
+    const float Fz = md.phi * Gz - drag * uz;
+
+    // moments of Eq. 13 (rows of Eq. A1) that relax
+    const float m_e = -2.0f * f[0] - A + Cs;
+    const float m_eps = 16.0f * f[0] - 4.0f * A + Cs;
+    const float qx = jx - 5.0f * d1, qy = jy - 5.0f * d2, qz = jz - 5.0f * d3;
+    const float m_pxx = 2.0f * s1 - s2 - s3;
+    const float m_pww = s2 - s3;
+    const float m_pxy = (sa + sd) - (sb + sc);
+    const float m_pyz = (sa + sb) - (sc + sd);
+    const float m_pzx = (sa + sc) - (sb + sd);
+    const float m_xyz = (da + dd) - (db + dc);
+
+    // equilibria (Eq. 15) and forcing (Eq. 17) with w = rho0 u / phi
+    const float r0p = p.rho0 * md.inv_phi;
+    const float wx = r0p * ux, wy = r0p * uy, wz = r0p * uz;
+    const float pxx = wx * ux, pyy = wy * uy, pzz = wz * uz;
+    const float fxx = wx * Fx, fyy = wy * Fy, fzz = wz * Fz;
+    const float usq = pxx + pyy + pzz;
+    const float uF = fxx + fyy + fzz;
+    const float eq_pxx = 2.0f * pxx - pyy - pzz;
+    const float eq_pww = pyy - pzz;
+    const float S_pxx = 2.0f * (2.0f * fxx - fyy - fzz);
+    const float S_pww = 2.0f * (fyy - fzz);
+
+    // dm_k / |M_k|^2 (Eq. 9); the conserved momentum gains rho0 F whatever s_j is
+    const float de = p.ae15 * (usq - rho - m_e) + p.be15 * 2.0f * uF;
+    const float deps = p.aeps15 * (rho - 5.0f * usq - m_eps) - p.beps15 * 10.0f * uF;
+    const float djx = p.rho0_10 * Fx, djy = p.rho0_10 * Fy, djz = p.rho0_10 * Fz;
+    const float dqx = -p.aq * qx - (p.aqc15 * ux + p.bqc15 * Fx);
+    const float dqy = -p.aq * qy - (p.aqc15 * uy + p.bqc15 * Fy);
+    const float dqz = -p.aq * qz - (p.aqc15 * uz + p.bqc15 * Fz);
+    const float dpxx = p.anu12 * (eq_pxx - m_pxx) + p.bnu12 * S_pxx;
+    const float dpww = p.anu4 * (eq_pww - m_pww) + p.bnu4 * S_pww;
+    const float dpxy = p.anu8 * (wx * uy - m_pxy) + p.bnu8 * (wx * Fy + wy * Fx);
+    const float dpyz = p.anu8 * (wy * uz - m_pyz) + p.bnu8 * (wy * Fz + wz * Fy);
+    const float dpzx = p.anu8 * (wz * ux - m_pzx) + p.bnu8 * (wz * Fx + wx * Fz);
+    const float dm = -p.am8 * m_xyz;
+
+    // f* = f + M^T diag(1/|M_k|^2) dm (columns of Eq. A1)
+    f[0] += -2.0f * de + 16.0f * deps;
+    const float Ea = -de - 4.0f * deps;
+    const float Ex = Ea + 2.0f * dpxx;
+    const float Ey = Ea - dpxx + dpww;
+    const float Ez = Ea - dpxx - dpww;
+    const float Ox = djx - 4.0f * dqx, Oy = djy - 4.0f * dqy, Oz = djz - 4.0f * dqz;
+    f[1] += Ex + Ox;
+    f[2] += Ex - Ox;
+    f[3] += Ey + Oy;
+    f[4] += Ey - Oy;
+    f[5] += Ez + Oz;
+    f[6] += Ez - Oz;
+    const float Cc = de + deps;
+    const float Jx = djx + dqx, Jy = djy + dqy, Jz = djz + dqz;
+    const float E7 = Cc + dpxy + dpyz + dpzx, O7 = Jx + Jy + Jz + dm;     // ( 1, 1, 1)
+    const float E8 = Cc - dpxy + dpyz - dpzx, O8 = -Jx + Jy + Jz - dm;    // (-1, 1, 1)
+    const float E9 = Cc - dpxy - dpyz + dpzx, O9 = Jx - Jy + Jz - dm;     // ( 1,-1, 1)
+    const float E10 = Cc + dpxy - dpyz - dpzx, O10 = -Jx - Jy + Jz + dm;  // (-1,-1, 1)
+    f[7] += E7 + O7;
+    f[14] += E7 - O7;
+    f[8] += E8 + O8;
+    f[13] += E8 - O8;
+    f[9] += E9 + O9;
+    f[12] += E9 - O9;
+    f[10] += E10 + O10;
+    f[11] += E10 - O10;
+
+    collide_g<false>(p, md, g, n0, T, 1.0f, ux, uy, uz);
+    return mac;
+}
+
+// The collision of the flow lattice L.
+template <bool FULL, bool ENTH, class L>
+__device__ __forceinline__ Macro collide_on(const KParams& p, const Medium& md, float* f, float* g) {
+    if constexpr (L::kQ == 15) return collide15<FULL>(p, md, f, g);
+    else return collide<FULL, ENTH>(p, md, f, g);
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
 // Pull of one site (interior or general path; the warp-uniform choice is made by the caller).
 // `lanes` is the mask of the warp's lanes that call it together (the valid sites).
-template <bool OUTF, class S>
+template <bool OUTF, class S, class L = D3Q19>
 __device__ __forceinline__ void gather_site(const Planes& pl, const KParams& p, int x, int y, int z,
                                             int s, bool warp_yz_in, unsigned lanes, float* f,
                                             float* g) {
     if (warp_yz_in) {
-        gather_yz_interior<OUTF, S>(pl, p, x, y, z, s, lanes, f, g);
+        gather_yz_interior<OUTF, S, L>(pl, p, x, y, z, s, lanes, f, g);
     } else {
         const Nbr n = neighbourhood(p, x, y, z);
-        gather_general<OUTF, S>(pl, p, n, f, g);
+        gather_general<OUTF, S, L>(pl, p, n, f, g);
     }
 }
 
 // Outflow history, collision and store of one gathered site.
-template <bool HET, bool OUTF, class S, bool ENTH = false>
+template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19>
 __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, int x, int y, int z,
                                             int s, float* f, float* g) {
     if (OUTF && x == p.nx - 1) {
@@ -634,9 +825,9 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
         pl.hout[5 * p.nyz + yz] = g[2];
     }
     const Medium md = medium_at<HET>(p, s);
-    const Macro m = collide<true, ENTH>(p, md, f, g);
+    const Macro m = collide_on<true, ENTH, L>(p, md, f, g);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) stp<S>(pl, p, i, s, f[i]);
+    for (int i = 0; i < L::kQ; ++i) stp<S>(pl, p, i, s, f[i]);
 #pragma unroll
     for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, g[i], m.dT);
     if constexpr (S::kScaled) pl.tout[s] = m.dT;
@@ -644,7 +835,7 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
 
 // 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
 // blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
-template <bool HET, bool OUTF, class S, bool ENTH = false>
+template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19>
 __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -655,10 +846,10 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
     const unsigned lanes = __ballot_sync(0xffffffffu, valid);
     if (!valid) return;
-    float f[kQ], g[kQT];
+    float f[L::kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
-    gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
-    finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
+    gather_site<OUTF, S, L>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
+    finish_site<HET, OUTF, S, ENTH, L>(pl, p, x, y, z, s, f, g);
 }
 
 // Batched step: one flat grid over the blocks of many lattices.  blk_lat[b] names the lattice
@@ -699,7 +890,7 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     }
 }
 
-template <bool HET, bool OUTF, class S, bool ENTH = false>
+template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19>
 __global__ void __launch_bounds__(kBlock)
     macros_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                   float* __restrict__ rho, float* __restrict__ u, float* __restrict__ T) {
@@ -708,10 +899,10 @@ __global__ void __launch_bounds__(kBlock)
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const Nbr n = neighbourhood(p, x, y, z);
-    float f[kQ], g[kQT];
-    gather_general<OUTF, S>(pl, p, n, f, g);
+    float f[L::kQ], g[kQT];
+    gather_general<OUTF, S, L>(pl, p, n, f, g);
     const Medium md = medium_at<HET>(p, n.s);
-    Macro m = collide<false, ENTH>(p, md, f, g);
+    Macro m = collide_on<false, ENTH, L>(p, md, f, g);
     const long long s = n.s;
     if (rho) rho[s] = m.rho;
     if (u) {
@@ -724,7 +915,7 @@ __global__ void __launch_bounds__(kBlock)
 
 // Equilibrium state (Eqs. 24 and 42) with rho = rho0, computed in FP64 and stored once
 // rounded in the storage format (deviations, see the storage section above).
-template <class S>
+template <class S, class L = D3Q19>
 __global__ void init_eq_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                                const double* __restrict__ T_field,
                                const double* __restrict__ u_field, double T_uniform) {
@@ -740,9 +931,9 @@ __global__ void init_eq_kernel(const __grid_constant__ KParams p, const __grid_c
     double phi = p.phi_field ? (double)p.phi_field[s] : (double)p.phi;
     double rho0 = p.rho0, usq = ux * ux + uy * uy + uz * uz;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        double eu = ex19(i) * ux + ey19(i) * uy + ez19(i) * uz;
-        double w = i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    for (int i = 0; i < L::kQ; ++i) {
+        double eu = L::ex(i) * ux + L::ey(i) * uy + L::ez(i) * uz;
+        double w = L::wd(i);
         double rel = rho0 * (3.0 * eu + 4.5 * eu * eu / phi - 1.5 * usq / phi);  // dev / w
         S::st(static_cast<typename S::T*>(pl.out[i]) + s, (float)(S::kScaled ? rel : w * rel));
     }
@@ -871,14 +1062,14 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* out)
     }
 }
 
-template <class S>
+template <class S, class L = D3Q19>
 __global__ void __launch_bounds__(kRedThreads)
     sums_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                 double* __restrict__ partials) {
     double v[2] = {0.0, 0.0};
     for (int s = blockIdx.x * kRedThreads + threadIdx.x; s < p.ns; s += gridDim.x * kRedThreads) {
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) v[0] += (double)ldp<S>(pl, p, i, s);
+        for (int i = 0; i < L::kQ; ++i) v[0] += (double)ldp<S>(pl, p, i, s);
 #pragma unroll
         for (int i = 0; i < kQT; ++i) v[1] += (double)ldg_dev<S>(pl, p, i, s);
     }
@@ -1045,6 +1236,17 @@ cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaSt
         step_kernel<false, false, StoreF32, true><<<grid, block, 0, st>>>(p, pl);
         return cudaGetLastError();
     }
+    if (p.qf == 15) {  // D3Q15 flow lattice: FP32 storage (validated on the host)
+        if (het && outflow)
+            step_kernel<true, true, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
+        else if (het)
+            step_kernel<true, false, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
+        else if (outflow)
+            step_kernel<false, true, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
+        else
+            step_kernel<false, false, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
+        return cudaGetLastError();
+    }
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
         if (het && outflow)
@@ -1068,6 +1270,17 @@ cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, floa
         macros_kernel<false, false, StoreF32, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
         return cudaGetLastError();
     }
+    if (p.qf == 15) {
+        if (het && outflow)
+            macros_kernel<true, true, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        else if (het)
+            macros_kernel<true, false, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        else if (outflow)
+            macros_kernel<false, true, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        else
+            macros_kernel<false, false, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        return cudaGetLastError();
+    }
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
         if (het && outflow)
@@ -1084,6 +1297,11 @@ cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, floa
 
 cudaError_t launch_init_eq(const KParams& p, const Planes& pl, const double* T_field,
                            const double* u_field, double T_uniform, cudaStream_t st) {
+    if (p.qf == 15) {
+        init_eq_kernel<StoreF32, D3Q15><<<blocks_for(p.ns, 128), 128, 0, st>>>(p, pl, T_field, u_field,
+                                                                              T_uniform);
+        return cudaGetLastError();
+    }
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
         init_eq_kernel<S><<<blocks_for(p.ns, 128), 128, 0, st>>>(p, pl, T_field, u_field, T_uniform);
@@ -1136,6 +1354,11 @@ cudaError_t launch_hist_reset(const KParams& p, const Planes& pl, float* hist, c
 
 cudaError_t launch_sums(const KParams& p, const Planes& pl, double* partials, int nparts,
                         double* out, cudaStream_t st) {
+    if (p.qf == 15) {
+        sums_kernel<StoreF32, D3Q15><<<nparts, kRedThreads, 0, st>>>(p, pl, partials);
+        finalize_kernel<2><<<1, kRedThreads, 0, st>>>(partials, nparts, out);
+        return cudaGetLastError();
+    }
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
         sums_kernel<S><<<nparts, kRedThreads, 0, st>>>(p, pl, partials);
