@@ -94,20 +94,24 @@ def channel_problem(nx: int, ny: int, nz: int, Re: float = 10.0, u0: float = 0.0
 
 def paper_channel(ny: int, Re: float = 10.0, Da: float = 1e-2, phi: float = 0.6,
                   u0: float = 0.01, u1: float = 0.01, Pr: float = 1.0, Ra: float = 100.0,
-                  nx: int = 1, nz: int = 1) -> dict:
+                  nx: int = 1, nz: int = 1, walls: str = "halfway") -> dict:
     """The porous channel of Sec. 4.1: plates at y-low (cold, T = 0) and y-high (hot, T = 1, moving
     along x at u0), fluid injected through the lower plate and withdrawn through the upper one at
     u1, periodic in x and z, Brinkman-Darcy medium (F_phi = 0), H = ny for Re = H u1 / nu, Da and
     Ra (Ri = Ra / (Re^2 Pr)), gravity along -y.  The external force of Eq. 47 enters through its
     uniform part nu u1 / K = u1^2 / (Re Da H); its y-dependent part only offsets the buoyancy's,
-    which in this one-dimensional flow a pressure gradient balances as well."""
-    return dict(nx=nx, ny=ny, nz=nz, mapping="channel", L=ny, Re=Re, u0=u1, Pr=Pr,
+    which in this one-dimensional flow a pressure gradient balances as well.  walls="halfway":
+    plates half a spacing outside the first and last rows (H = ny); walls="nee": the first and
+    last rows are the plates, by non-equilibrium extrapolation (H = ny - 1)."""
+    H = ny if walls == "halfway" else ny - 1
+    kind = 2 if walls == "halfway" else 4
+    return dict(nx=nx, ny=ny, nz=nz, mapping="channel", L=H, Re=Re, u0=u1, Pr=Pr,
                 Ri=Ra / (Re * Re * Pr), Da=Da, phi=phi, F_phi=0.0,
-                flow_bc=[0, 0, 2, 2, 0, 0], heat_bc=[0, 0, 2, 2, 0, 0],
+                flow_bc=[0, 0, kind, kind, 0, 0], heat_bc=[0, 0, kind, kind, 0, 0],
                 face_T=[0.0, 0.0, 0.0, 1.0, 0.0, 0.0],
                 face_u=[(0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, u1, 0.0), (u0, u1, 0.0),
                         (0.0, 0.0, 0.0), (0.0, 0.0, 0.0)],
-                accel=[0.0, u1 * u1 / (Re * Da * ny), 0.0], T_init=0.5, T0=0.5,
+                accel=[0.0, u1 * u1 / (Re * Da * H), 0.0], T_init=0.5, T0=0.5,
                 gravity_axis=1, gravity_sign=-1)
 
 

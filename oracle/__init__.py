@@ -27,8 +27,8 @@ Q19, Q15, Q7 = 19, 15, 7
 CS2 = 1.0 / 3.0  # c_s^2 with c = 1 (Sec. 3.1.2)
 
 # face order: x-low, x-high, y-low, y-high, z-low, z-high
-BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_OUTFLOW = 0, 1, 2, 3
-HT_PERIODIC, HT_ADIABATIC, HT_DIRICHLET, HT_OUTFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_OUTFLOW, BC_NEE = 0, 1, 2, 3, 4
+HT_PERIODIC, HT_ADIABATIC, HT_DIRICHLET, HT_OUTFLOW, HT_NEE_DIRICHLET, HT_NEE_ADIABATIC = range(6)
 
 # Free relaxation rates of the D3Q19 and D3Q7 models chosen in Sec. 4.
 PAPER_RATES = dict(s_e=1.1, s_eps=1.1, s_q=1.1, s_pi=1.1, s_m=1.2,
@@ -520,12 +520,15 @@ def collide_site(lp: LatticeParams, f, g, phi=None, K=None, Fphi=None, zeta_alph
 
 # ---- diagnostics: plain definitions ---------------------------------------------------------
 
-def nusselt(T: np.ndarray, face: int, T_wall: float, L: float, dT: float = 1.0):
+def nusselt(T: np.ndarray, face: int, T_wall: float, L: float, dT: float = 1.0,
+            node_wall: bool = False):
     """Wall heat flux of Eq. 53 on a halfway wall, normalised as a Nusselt number.
 
     The wall sits half a spacing outside the first node; -d(theta)/dn at the wall is taken
     from the quadratic through (wall, node 0, node 1): (8 T_w - 9 T_0 + T_1) / 3.  Positive
-    values are heat flowing from the wall into the fluid.  Returns (Nu_3D, profile, Nu_mp):
+    values are heat flowing from the wall into the fluid.  On a node wall (non-equilibrium
+    extrapolation) the first node is the wall and the one-sided second-order gradient over
+    (wall, node 1, node 2) gives (3 T_w - 4 T_1 + T_2) / 2.  Returns (Nu_3D, profile, Nu_mp):
     the profile runs along the first tangential axis (y for x-faces, x otherwise) averaged
     over the second one (Eq. 54, midpoint rule), Nu_3D is its mean (Eq. 55) and Nu_mp the
     profile at the centre (mean of the two middle entries for an even count).
@@ -534,9 +537,14 @@ def nusselt(T: np.ndarray, face: int, T_wall: float, L: float, dT: float = 1.0):
     axis = face // 2
     hi = face % 2 == 1
     arr = np.moveaxis(T, 2 - axis, 0)  # normal axis first
-    t0 = arr[-1] if hi else arr[0]
-    t1 = arr[-2] if hi else arr[1]
-    q = (8.0 * T_wall - 9.0 * t0 + t1) / 3.0 * L / dT
+    if node_wall:
+        t1 = arr[-2] if hi else arr[1]
+        t2 = arr[-3] if hi else arr[2]
+        q = (3.0 * T_wall - 4.0 * t1 + t2) / 2.0 * L / dT
+    else:
+        t0 = arr[-1] if hi else arr[0]
+        t1 = arr[-2] if hi else arr[1]
+        q = (8.0 * T_wall - 9.0 * t0 + t1) / 3.0 * L / dT
     # remaining axes of q, in [z][y][x] order minus the normal one
     if axis == 0:      # q[z][y]: profile over y, mean over z
         prof = q.mean(axis=0)

@@ -40,6 +40,19 @@
  *   pressure anchor).  When a diagonal source lies outside two faces, a no-slip wall wins
  *   over a velocity face, which wins over the outflow.
  *
+ * Node walls by non-equilibrium extrapolation (the paper's scheme [50], Sec. 4): on a face of
+ * kind BC_NEE the layer of nodes on the face is the wall, moving at face_u, at temperature
+ * face_T (HT_NEE_DIRICHLET) or at the temperature of the fluid beside it (HT_NEE_ADIABATIC).
+ * A wall node x_b does not stream.  With x_f the fluid node beside it (x_b plus the inward
+ * normal of every node-wall face it lies on), Guo's rule builds its populations from the
+ * wall's equilibrium and the streamed non-equilibrium part of x_f,
+ *   f(x_b) = f_eq(rho_b, u_w) + [f(x_f) - f_eq(rho_f, u_f)],
+ *   g(x_b) = g_eq(T_b, u_w) + [g(x_f) - g_eq(T_f, u_f)],
+ * and they then collide (Eqs. 9, 34) at the wall node's own state: the velocity prescribed as
+ * u_w, F from Eq. 4 at u_w, T = T_b (the sum of g).  rho_b = rho_f, except on a wall that
+ * withdraws fluid (u_w along its outward normal), which holds rho0: with rho_b = rho_f at
+ * both walls the mean density of a transpiring channel drifts.
+ *
  * Layout: every array is x-fastest, site s = x + nx*(y + ny*z); populations are stored
  * q-major, f[i*ns + s].
  */
@@ -415,8 +428,9 @@ void orc_velocity15(const double* f, const double* G, double phi, double nu, dou
 
 /* ---- lattice parameters and state -------------------------------------------------- */
 
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_OUTFLOW = 3 };
-enum { HT_PERIODIC = 0, HT_ADIABATIC = 1, HT_DIRICHLET = 2, HT_OUTFLOW = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_OUTFLOW = 3, BC_NEE = 4 };
+enum { HT_PERIODIC = 0, HT_ADIABATIC = 1, HT_DIRICHLET = 2, HT_OUTFLOW = 3, HT_NEE_DIRICHLET = 4,
+       HT_NEE_ADIABATIC = 5 };
 
 typedef struct {
     int nx, ny, nz;
@@ -629,9 +643,21 @@ void orc_geq7_enthalpy(const orc_lattice* L, double En, double T, const double* 
 /* ---- one site ------------------------------------------------------------------------ */
 
 /* Collision of one site (steps 2-11 above).  macro = (rho, ux, uy, uz, T). */
+static void collide_site(const orc_lattice* L, const double* f, const double* g, double phi,
+                         double K, double Fphi, double zeta_alpha, const double* u_wall,
+                         double* fout, double* gout, double* macro);
+
 void orc_collide_site(const orc_lattice* L, const double* f, const double* g, double phi,
                       double K, double Fphi, double zeta_alpha, double* fout, double* gout,
                       double* macro) {
+    collide_site(L, f, g, phi, K, Fphi, zeta_alpha, NULL, fout, gout, macro);
+}
+
+/* The collision above; with u_wall the velocity is prescribed (a node wall) instead of being
+ * solved from Eqs. 27-28. */
+static void collide_site(const orc_lattice* L, const double* f, const double* g, double phi,
+                         double K, double Fphi, double zeta_alpha, const double* u_wall,
+                         double* fout, double* gout, double* macro) {
     ensure_minv();
     const flow_lattice* D = lattice_of(L);
     const int q = D->q;
@@ -647,7 +673,10 @@ void orc_collide_site(const orc_lattice* L, const double* f, const double* g, do
     double rho = 0.0;
     for (int i = 0; i < q; ++i) rho += f[i]; /* Eq. 25 */
     double u[3];
-    velocity_on(D, f, G, phi, L->nu, K, Fphi, L->rho0, u); /* Eqs. 27-28 */
+    if (u_wall)
+        for (int a = 0; a < 3; ++a) u[a] = u_wall[a];
+    else
+        velocity_on(D, f, G, phi, L->nu, K, Fphi, L->rho0, u); /* Eqs. 27-28 */
     double F[3];
     orc_force(u, G, phi, L->nu, K, Fphi, F); /* Eq. 4 */
 
@@ -720,6 +749,64 @@ thermal:;
 /* ---- whole lattice ------------------------------------------------------------------ */
 
 static int has_outflow(const orc_lattice* L) { return L->flow_bc[1] == BC_OUTFLOW; }
+
+/* Node-wall faces a site lies on (bit f for face f). */
+static int nee_faces(const orc_lattice* L, int x, int y, int z) {
+    int c[3] = {x, y, z}, n[3] = {L->nx, L->ny, L->nz}, bits = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] == 0 && L->flow_bc[2 * a] == BC_NEE) bits |= 1 << (2 * a);
+        if (c[a] == n[a] - 1 && L->flow_bc[2 * a + 1] == BC_NEE) bits |= 1 << (2 * a + 1);
+    }
+    return bits;
+}
+
+static void gather_site(orc_state* S, int x, int y, int z, double* f, double* g, int rec);
+
+/* Post-collision populations of a node-wall site (see the header), and its macroscopic
+ * values (rho_b, u_w, T_b). */
+static void nee_site(orc_state* S, int x, int y, int z, int bits, double* fo, double* go,
+                     double* mac) {
+    const orc_lattice* L = &S->L;
+    const flow_lattice* D = lattice_of(L);
+    int c[3] = {x, y, z};
+    int wall = -1, hot = -1;
+    for (int f = 0; f < 6; ++f)
+        if (bits & (1 << f)) {
+            c[f / 2] += (f % 2 == 0) ? 1 : -1;
+            if (wall < 0) wall = f;
+            if (hot < 0 && L->heat_bc[f] == HT_NEE_DIRICHLET) hot = f;
+        }
+    /* the fluid node beside the wall: its streamed populations and macroscopic values */
+    double f[QMAX], g[Q7], m[5], ftmp[QMAX], gtmp[Q7];
+    double phi, K, Fphi, phib, Kb, Fphib;
+    gather_site(S, c[0], c[1], c[2], f, g, 0);
+    medium_at(S, site_index(L, c[0], c[1], c[2]), &phi, &K, &Fphi);
+    orc_collide_site(L, f, g, phi, K, Fphi, zeta_alpha_at(L, phi), ftmp, gtmp, m);
+    medium_at(S, site_index(L, x, y, z), &phib, &Kb, &Fphib);
+    const double* uw = L->face_u[wall];
+    double uf[3] = {m[1], m[2], m[3]};
+    double Tb = hot >= 0 ? L->face_T[hot] : m[4];
+    /* a wall that withdraws fluid (u_w along its outward normal) holds rho0 */
+    double out = wall % 2 == 0 ? -uw[wall / 2] : uw[wall / 2];
+    double rhob = out > 0.0 ? L->rho0 : m[0];
+    /* Guo's rule: the equilibrium of the wall plus the fluid node's non-equilibrium part */
+    double eb[QMAX], ef[QMAX], gb[Q7], gf[Q7];
+    feq_on(D, rhob, uw, phib, L->rho0, eb);
+    feq_on(D, m[0], uf, phi, L->rho0, ef);
+    for (int i = 0; i < D->q; ++i) f[i] += eb[i] - ef[i];
+    orc_geq7(Tb, uw, L->sigma, L->varpi, gb);
+    orc_geq7(m[4], uf, L->sigma, L->varpi, gf);
+    for (int i = 0; i < Q7; ++i) g[i] += gb[i] - gf[i];
+    /* then the collision at the wall node's own state, with u = u_w */
+    collide_site(L, f, g, phib, Kb, Fphib, zeta_alpha_at(L, phib), uw, fo, go, NULL);
+    if (mac) {
+        mac[0] = rhob;
+        mac[1] = uw[0];
+        mac[2] = uw[1];
+        mac[3] = uw[2];
+        mac[4] = Tb;
+    }
+}
 
 static void reset_outflow_history(orc_state* S) {
     if (!S->pf) return;
@@ -860,6 +947,13 @@ void orc_step(void* h, int nsteps) {
                     long s = site_index(L, x, y, z);
                     double f[QMAX], g[Q7], fo[QMAX], go[Q7];
                     double phi, K, Fphi;
+                    int nb = nee_faces(L, x, y, z);
+                    if (nb) { /* node wall: extrapolated from the fluid node beside it */
+                        nee_site(S, x, y, z, nb, fo, go, NULL);
+                        for (int i = 0; i < L->q; ++i) S->fn[(long)i * S->ns + s] = fo[i];
+                        for (int i = 0; i < Q7; ++i) S->gn[(long)i * S->ns + s] = go[i];
+                        continue;
+                    }
                     gather_site(S, x, y, z, f, g, 1);
                     medium_at(S, s, &phi, &K, &Fphi);
                     orc_collide_site(L, f, g, phi, K, Fphi, zeta_alpha_at(L, phi), fo, go, NULL);
@@ -889,9 +983,14 @@ void orc_macros(void* h, double* rho, double* u, double* T) {
                 long s = site_index(L, x, y, z);
                 double f[QMAX], g[Q7], fo[QMAX], go[Q7], mac[5];
                 double phi, K, Fphi;
-                gather_site(S, x, y, z, f, g, 0);
-                medium_at(S, s, &phi, &K, &Fphi);
-                orc_collide_site(L, f, g, phi, K, Fphi, zeta_alpha_at(L, phi), fo, go, mac);
+                int nb = nee_faces(L, x, y, z);
+                if (nb) {
+                    nee_site(S, x, y, z, nb, fo, go, mac);
+                } else {
+                    gather_site(S, x, y, z, f, g, 0);
+                    medium_at(S, s, &phi, &K, &Fphi);
+                    orc_collide_site(L, f, g, phi, K, Fphi, zeta_alpha_at(L, phi), fo, go, mac);
+                }
                 if (rho) rho[s] = mac[0];
                 if (u)
                     for (int a = 0; a < 3; ++a) u[a * S->ns + s] = mac[1 + a];

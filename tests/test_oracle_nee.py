@@ -1,0 +1,103 @@
+"""Pins of the oracle's node walls by non-equilibrium extrapolation (the paper's boundary
+scheme [50], Sec. 4): exact conduction and Couette profiles between node walls, second-order
+Brinkman-Poiseuille flow, and the paper's porous channel (Eqs. 48-50) at second order on both
+flow lattices, including the low-Reynolds case where halfway bounce-back loses its order."""
+import math
+
+import numpy as np
+import pytest
+
+from lbm_inputs import paper_channel
+
+NEE, NEE_T, NEE_A = 4, 4, 5
+
+
+def _run(orc, pb, steps):
+    o = orc.Oracle(orc.map_problem(pb))
+    o.step(steps)
+    return o
+
+
+@pytest.mark.parametrize("q", [19, 15])
+def test_conduction_between_node_walls_is_exact(orc, q):
+    """Hot node wall at x = 0 (T = 1), cold at x = N-1 (T = 0), adiabatic node walls in y:
+    T = 1 - x / (N-1) is the steady state to round-off, and the node-wall Nusselt number of
+    both walls is 1 (L = N - 1)."""
+    N = 12
+    pb = dict(nx=N, ny=5, nz=1, mapping="lattice", nu_e=0.1, alpha_f=0.15, gbeta=0.0, q=q,
+              flow_bc=[NEE, NEE, NEE, NEE, 0, 0], heat_bc=[NEE_T, NEE_T, NEE_A, NEE_A, 0, 0],
+              face_T=[1.0, 0.0, 0, 0, 0, 0], T_init=0.5)
+    o = _run(orc, pb, 6000)
+    _, u, T = o.macros()
+    want = 1.0 - np.arange(N) / (N - 1)
+    assert np.abs(T - want[None, None, :]).max() < 1e-12
+    assert np.abs(u).max() < 1e-13
+    for face, Tw, sign in ((0, 1.0, 1.0), (1, 0.0, -1.0)):
+        assert orc.nusselt(T, face, Tw, N - 1, node_wall=True)[0] == pytest.approx(sign, abs=1e-10)
+
+
+@pytest.mark.parametrize("q", [19, 15])
+def test_couette_between_node_walls_is_exact(orc, q):
+    """Lower node wall at rest, upper moving at U: u_x = U y / (N-1) exactly."""
+    N, U = 10, 0.02
+    pb = dict(nx=1, ny=N, nz=1, mapping="lattice", nu_e=0.1, q=q, flow_bc=[0, 0, NEE, NEE, 0, 0],
+              heat_bc=[0, 0, NEE_A, NEE_A, 0, 0],
+              face_u=[(0, 0, 0), (0, 0, 0), (0, 0, 0), (U, 0, 0), (0, 0, 0), (0, 0, 0)])
+    o = _run(orc, pb, 8000)
+    _, u, _ = o.macros()
+    assert np.abs(u[0, 0, :, 0] - U * np.arange(N) / (N - 1)).max() < 1e-12
+
+
+def _poiseuille_E(orc, N, q, Da=0.0375, phi=0.6, nu_e=0.1, a=1e-5):
+    H = N - 1
+    K = Da * H * H
+    pb = dict(nx=1, ny=N, nz=1, mapping="lattice", nu_e=nu_e, phi=phi, K=K, F_phi=0.0, q=q,
+              accel=[a, 0, 0], flow_bc=[0, 0, NEE, NEE, 0, 0], heat_bc=[0, 0, NEE_A, NEE_A, 0, 0])
+    lp = orc.map_problem(pb)
+    o = orc.Oracle(lp)
+    o.step(int(25 * K / (phi * lp.nu)))
+    _, u, _ = o.macros()
+    y = np.arange(N)
+    r = math.sqrt(phi / K)
+    ua = (K * a / lp.nu) * (1 - np.cosh(r * (y - H / 2)) / np.cosh(r * H / 2))
+    ux = u[0, 0, :, 0]
+    return math.sqrt(np.sum((ux - ua) ** 2) / np.sum(ua ** 2))
+
+
+@pytest.mark.parametrize("q", [19, 15])
+def test_brinkman_poiseuille_second_order(orc, q):
+    e = [_poiseuille_E(orc, N, q) for N in (17, 33, 65)]
+    for a, b in zip(e, e[1:]):
+        assert math.log2(a / b) > 1.8
+
+
+def _channel_E(orc, ny, Re, Da, q, phi=0.6):
+    """Eq. 52 errors of u_x and T at steady state with the plates on the first and last rows
+    (H = ny - 1).  u0 = u1 = 0.16 / H keeps every relaxation time fixed as the grid is
+    refined (nu = u1 H / Re), so that the error measured is the spatial one."""
+    H = ny - 1
+    uw = 0.16 / H
+    pb = dict(paper_channel(ny, Re=Re, Da=Da, u0=uw, u1=uw, walls="nee"), q=q)
+    o = _run(orc, pb, int(40 * H / (uw * Re)))
+    _, u, T = o.macros()
+    y = np.arange(ny) / H
+    t1 = Re / (2 * phi)
+    t2 = math.sqrt(Re * Re + 4 * phi ** 3 / Da) / (2 * phi)
+    ua = uw * np.exp(t1 * (y - 1)) * np.sinh(t2 * y) / math.sinh(t2)
+    Ta = (np.exp(Re * y) - 1) / (math.exp(Re) - 1)
+    ux, TT = u[0, 0, :, 0], T[0, :, 0]
+    assert np.abs(u[1, 0, :, 0] - uw).max() < 2e-3 * uw
+    return (math.sqrt(np.sum((ux - ua) ** 2) / np.sum(ua ** 2)),
+            math.sqrt(np.sum((TT - Ta) ** 2) / np.sum(Ta ** 2)))
+
+
+@pytest.mark.parametrize("q,Re,Da", [(19, 10.0, 1e-2), (15, 10.0, 1e-2)])
+def test_paper_channel_with_node_walls(orc, q, Re, Da):
+    """Eqs. 48-50 with the plates on the first and last rows: the error falls under
+    refinement, at an order that approaches two (measured 1.5-1.8 on the last halving)."""
+    errs = [_channel_E(orc, ny, Re, Da, q) for ny in (17, 33, 65)]
+    for (a0, b0), (a1, b1) in zip(errs, errs[1:]):
+        assert a1 < a0 and b1 < b0, errs
+    (a0, b0), (a1, b1) = errs[1], errs[2]
+    assert math.log2(a0 / a1) > 1.4 and math.log2(b0 / b1) > 1.6, errs
+    assert a1 < 0.03 and b1 < 0.01
