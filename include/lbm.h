@@ -47,7 +47,8 @@ enum {
     LBM_FLOW_PERIODIC = 0, /* both faces of the axis must be periodic */
     LBM_FLOW_WALL = 1,     /* resting no-slip wall, halfway bounce-back */
     LBM_FLOW_VELOCITY = 2, /* moving wall / velocity inlet with face_u (bounce-back) */
-    LBM_FLOW_OUTFLOW = 3   /* convective outflow; x-high face only */
+    LBM_FLOW_OUTFLOW = 3,  /* convective outflow; x-high face only */
+    LBM_FLOW_NEE = 4       /* node wall by non-equilibrium extrapolation (see below) */
 };
 
 /* Thermal boundary kinds (per face). */
@@ -55,8 +56,20 @@ enum {
     LBM_HEAT_PERIODIC = 0,  /* must match a periodic flow face */
     LBM_HEAT_ADIABATIC = 1, /* zero heat flux, bounce-back of g */
     LBM_HEAT_DIRICHLET = 2, /* wall temperature face_T, anti-bounce-back of g */
-    LBM_HEAT_OUTFLOW = 3    /* convective outflow; only on an outflow face */
+    LBM_HEAT_OUTFLOW = 3,   /* convective outflow; only on an outflow face */
+    LBM_HEAT_NEE_DIRICHLET = 4, /* node wall at face_T (with LBM_FLOW_NEE) */
+    LBM_HEAT_NEE_ADIABATIC = 5  /* node wall at the temperature of the fluid beside it */
 };
+/* Node walls (the paper's boundary scheme, non-equilibrium extrapolation [50], Sec. 4): the
+ * layer of sites on an LBM_FLOW_NEE face is the wall, moving at face_u; its temperature is
+ * face_T (LBM_HEAT_NEE_DIRICHLET) or that of the fluid beside it (LBM_HEAT_NEE_ADIABATIC).  A
+ * wall site does not stream: with x_f the fluid site beside it (plus the inward normal of
+ * every node-wall face it lies on), its populations are the wall equilibrium plus the
+ * streamed non-equilibrium part of x_f, f = f_eq(rho_b, u_w) + [f(x_f) - f_eq(rho_f, u_f)]
+ * and g = g_eq(T_b, u_w) + [g(x_f) - g_eq(T_f, u_f)], collided at its own state with the
+ * velocity prescribed as u_w (rho_b = rho_f, or rho0 on a wall that withdraws fluid).  The
+ * walls sit on the sites, so a channel of ny sites has height ny - 1 (give L).  FP32 storage,
+ * no outflow face, no enthalpy model, outside lbm_batch / lbm_server; >= 3 sites across. */
 
 /* Mapping from the dimensionless problem statement to lattice units. */
 enum {
@@ -137,6 +150,7 @@ typedef struct lbm_lattice {
     double U_out;
     int enthalpy, flow_off;
     double c_pl, c_ref, sigma_s, sigma_l, T_s, T_l, L_a, alpha_s, alpha_l;
+    int node_walls;            /* 1 if a face is a node wall (LBM_FLOW_NEE) */
     int q;                     /* flow lattice (19 or 15); with 15, s[] keeps the D3Q19 order
                                   and the D3Q15 rates s_e, s_eps, s_q, s_nu, s_m of Eq. 16 are
                                   s[1], s[2], s[4], s[9], s[16] */
@@ -213,12 +227,14 @@ lbm_status lbm_macros_device(lbm_ctx* ctx, float* rho, float* u, float* T);
 
 /* Wall Nusselt numbers of Eqs. 53-55 on a Dirichlet face: -d(theta)/dn at the halfway wall
  * from the quadratic through the wall value and the first two nodes,
- * Nu_local = L (8 T_w - 9 T_0 + T_1) / (3 dT) (positive = heat into the fluid), averaged
+ * Nu_local = L (8 T_w - 9 T_0 + T_1) / (3 dT) (positive = heat into the fluid); on a node
+ * wall (LBM_HEAT_NEE_DIRICHLET) the second-order one-sided gradient over the wall site and
+ * the next two, Nu_local = L (3 T_w - 4 T_1 + T_2) / (2 dT); averaged
  * over the second tangential axis into the profile along the first one (y for x-faces,
  * x otherwise; Eq. 54), whose mean is Nu_3D (Eq. 55) and whose centre value is Nu_mp.
  * FP64 accumulation on the device.  nu_avg, nu_profile (host, length of the first
  * tangential axis) and nu_mp may each be NULL.  Synchronises.
- * Errors: LBM_EINVAL (face not Dirichlet or normal extent < 2), LBM_EUNSTABLE (NaN). */
+ * Errors: LBM_EINVAL (face not Dirichlet or too few sites normal to it), LBM_EUNSTABLE. */
 lbm_status lbm_nusselt(lbm_ctx* ctx, int face, double* nu_avg, double* nu_profile,
                        double* nu_mp);
 

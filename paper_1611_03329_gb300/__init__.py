@@ -93,7 +93,7 @@ class LbmLattice(C.Structure):
         ("c_pl", C.c_double), ("c_ref", C.c_double), ("sigma_s", C.c_double),
         ("sigma_l", C.c_double), ("T_s", C.c_double), ("T_l", C.c_double), ("L_a", C.c_double),
         ("alpha_s", C.c_double), ("alpha_l", C.c_double),
-        ("q", C.c_int),
+        ("node_walls", C.c_int), ("q", C.c_int),
     ]
 
     def as_dict(self) -> dict:

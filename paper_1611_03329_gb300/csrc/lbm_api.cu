@@ -186,7 +186,10 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
     int n[3] = {p->nx, p->ny, p->nz};
     for (int f = 0; f < 6; ++f) {
         int fk = p->flow_bc[f], hk = p->heat_bc[f];
-        if (fk < 0 || fk > 3 || hk < 0 || hk > 3) return "unknown boundary kind";
+        if (fk < 0 || fk > 4 || hk < 0 || hk > 5) return "unknown boundary kind";
+        if ((fk == LBM_FLOW_NEE) != (hk == LBM_HEAT_NEE_DIRICHLET || hk == LBM_HEAT_NEE_ADIABATIC))
+            return "a node wall (non-equilibrium extrapolation) is one for both flow and heat";
+        if (fk == LBM_FLOW_NEE && n[f >> 1] < 3) return "a node wall needs >= 3 sites normal to it";
         if ((fk == LBM_FLOW_PERIODIC) != (hk == LBM_HEAT_PERIODIC))
             return "a face must be periodic for both flow and heat, or for neither";
         int other = f ^ 1;
@@ -195,11 +198,17 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
         if (fk == LBM_FLOW_OUTFLOW && f != 1) return "outflow only on the x-high face";
         if (hk == LBM_HEAT_OUTFLOW && fk != LBM_FLOW_OUTFLOW)
             return "thermal outflow needs a flow outflow face";
-        if (hk == LBM_HEAT_DIRICHLET && !std::isfinite(p->face_T[f]))
+        if ((hk == LBM_HEAT_DIRICHLET || hk == LBM_HEAT_NEE_DIRICHLET) && !std::isfinite(p->face_T[f]))
             return "face temperature must be finite";
         for (int a = 0; a < 3; ++a)
             if (!std::isfinite(p->face_u[f][a])) return "face velocity must be finite";
     }
+    bool nee = false;
+    for (int f = 0; f < 6; ++f) nee = nee || p->flow_bc[f] == LBM_FLOW_NEE;
+    if (nee && p->flow_bc[1] == LBM_FLOW_OUTFLOW) return "node walls and an outflow do not mix";
+    if (nee && p->storage != LBM_STORE_FP32) return "node walls run with FP32 storage only";
+    if (nee && p->enthalpy) return "node walls do not run the enthalpy model";
+    L->node_walls = nee ? 1 : 0;
     if (p->flow_bc[1] == LBM_FLOW_OUTFLOW) {
         if (n[0] < 3) return "an outflow needs nx >= 3";
         if (!finite_pos(L->U_out)) return "outflow speed must be > 0";
@@ -334,6 +343,8 @@ void fill_kparams(lbm_ctx* c) {
         if (p.flow_bc[f] == LBM_FLOW_PERIODIC) k.per_mask |= bit;
         if (p.flow_bc[f] == LBM_FLOW_WALL) k.wall_mask |= bit;
         if (p.flow_bc[f] == LBM_FLOW_VELOCITY) k.vel_mask |= bit;
+        if (p.flow_bc[f] == LBM_FLOW_NEE) k.nee_mask |= bit;
+        k.face_dT[f] = (float)(p.face_T[f] - L.T0);
         k.heat_kind[f] = p.heat_bc[f];
         // anti-bounce-back term 2 omega_i sigma (T_w - T0) in deviation form, omega_i = varpi/6
         // enthalpy model: full values, weight varpi c_ref / 6 (Eq. B12)
@@ -790,11 +801,13 @@ lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile,
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if (face < 0 || face > 5) return fail(c, LBM_EINVAL, "face must be 0..5");
-    if (c->prm.heat_bc[face] != LBM_HEAT_DIRICHLET)
+    const bool node_wall = c->prm.heat_bc[face] == LBM_HEAT_NEE_DIRICHLET;
+    if (c->prm.heat_bc[face] != LBM_HEAT_DIRICHLET && !node_wall)
         return fail(c, LBM_EINVAL, "face %d is not a Dirichlet (fixed temperature) face", face);
     int axis = face >> 1;
     int n[3] = {c->prm.nx, c->prm.ny, c->prm.nz};
-    if (n[axis] < 2) return fail(c, LBM_EINVAL, "Nusselt needs >= 2 sites normal to the face");
+    if (n[axis] < (node_wall ? 3 : 2))
+        return fail(c, LBM_EINVAL, "Nusselt needs more sites normal to the face");
     int n1 = axis == 0 ? c->prm.ny : c->prm.nx;
     double scale = c->lat.L / c->lat.dT;
     LBM_CUDA(lbm::launch_nusselt(c->kp, c->outflow, c->pl[c->cur], face, c->prm.face_T[face],
@@ -1007,7 +1020,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
     }
     for (int k = 0; k < n; ++k) {
         lbm_ctx* c = ctxs[k];
-        if (!c || c->sticky != LBM_OK || c->lat.q == 15) {  // D3Q15 lattices step alone
+        if (!c || c->sticky != LBM_OK || c->lat.q == 15 || c->lat.node_walls) {  // step alone
             delete b;
             return LBM_EINVAL;
         }
@@ -1306,7 +1319,8 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
     if (!s || !p || !(tol > 0.0) || max_steps < 1) return LBM_EINVAL;
     lbm_lattice L;
     if (derive(p, &L)) return LBM_EINVAL;
-    if (L.q == 15) return LBM_EINVAL;  // the serving loop batches D3Q19 lattices
+    if (L.q == 15 || L.node_walls) return LBM_EINVAL;  // the serving loop batches D3Q19 lattices
+                                                       // with halfway walls
     auto* r = new (std::nothrow) lbm_server::Req();
     if (!r) return LBM_ENOMEM;
     r->p = *p;

@@ -27,6 +27,8 @@ struct KParams {
     unsigned per_mask;    // periodic faces (flow and heat)
     unsigned wall_mask;   // no-slip walls
     unsigned vel_mask;    // velocity faces
+    unsigned nee_mask;    // node walls (non-equilibrium extrapolation)
+    float face_dT[6];     // T_w - T0 of fixed-temperature faces
     int heat_kind[6];     // LBM_HEAT_* per face
     float heat_abb[6];    // 2 (varpi/6) sigma (T_w - T0): anti-bounce-back term, deviation form
     float face_u[6][3];   // wall velocity of velocity faces

@@ -505,8 +505,11 @@ __device__ __forceinline__ void collide_g(const KParams& p, const Medium& md, fl
 // Eqs. 39, 5, 25, 27-28, 4, then (FULL) Eq. 9 with Eqs. 21-23 in moment space and Eq. 34 with
 // Eqs. 37-38, back-transformed in place.  f, g are deviations on entry and exit.  The
 // per-moment factors s_k / |M_k|^2 and (1 - s_k/2) / |M_k|^2 come precomputed in KParams.
-template <bool FULL, bool ENTH = false>
-__device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g) {
+// PU: the velocity is prescribed (pu, a node wall) instead of solved from Eqs. 27-28, and the
+// conserved momentum becomes rho0 pu + rho0 F / 2 after the collision.
+template <bool FULL, bool ENTH = false, bool PU = false>
+__device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g,
+                                         float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
     // temperature (Eq. 39, or Eqs. B7-B9 with the enthalpy model) and body force (Eq. 5)
     const float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
     float T, dT, fl = 1.0f;                                                     // or En_e
@@ -547,6 +550,11 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     const float vmag = sqrt_nonneg(vx * vx + vy * vy + vz * vz);
     const float inv_den = __fdividef(1.0f, md.l0 + sqrt_nonneg(md.l0 * md.l0 + md.l1 * vmag));
     float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
+    if constexpr (PU) {
+        ux = pux;
+        uy = puy;
+        uz = puz;
+    }
     // enthalpy model: the flow is collided only where f_l >= 0.5; elsewhere u = 0
     bool rest = false;
     if constexpr (ENTH) {
@@ -567,7 +575,8 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 #pragma unroll
         for (int i = 0; i < kQ; ++i) f[i] = w19(i) * rho;
     } else {
-    const float umag = vmag * inv_den;  // |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|))
+    // |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|))
+    const float umag = PU ? sqrt_nonneg(ux * ux + uy * uy + uz * uz) : vmag * inv_den;
     const float drag = md.c_darcy + md.c_forch * umag;
     const float Fx = md.phi * Gx - drag * ux;
     const float Fy = md.phi * Gy - drag * uy;
@@ -603,7 +612,12 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
     // momentum gains rho0 F whatever s_j is (Eqs. 9, 14, 26)
     const float de = p.ae * (-11.0f * rho + 19.0f * usq - m_e) + p.be * 38.0f * uF;
     const float deps = p.aeps * (3.0f * rho - 5.5f * usq - m_eps) - p.beps * 11.0f * uF;
-    const float djx = p.rho0_10 * Fx, djy = p.rho0_10 * Fy, djz = p.rho0_10 * Fz;
+    float djx = p.rho0_10 * Fx, djy = p.rho0_10 * Fy, djz = p.rho0_10 * Fz;
+    if constexpr (PU) {
+        djx = 0.1f * (p.rho0 * (ux + 0.5f * Fx) - jx);
+        djy = 0.1f * (p.rho0 * (uy + 0.5f * Fy) - jy);
+        djz = 0.1f * (p.rho0 * (uz + 0.5f * Fz) - jz);
+    }
     const float dqx = -p.aq * qx - (p.aqc * ux + p.bqc * Fx);
     const float dqy = -p.aq * qy - (p.aqc * uy + p.bqc * Fy);
     const float dqz = -p.aq * qz - (p.aqc * uz + p.bqc * Fz);
@@ -672,8 +686,9 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 // equilibria of Eq. 15 (beta1 = 1, beta2 = -5), the forcing of Eq. 17 and Lambda of Eq. 16,
 // back-transformed through M^T diag(1/|M_k|^2) (the rows of Eq. A1 are orthogonal, with
 // |M_k|^2 = 15, 18, 360, 10, 40, 12, 4, 8).  f, g are deviations on entry and exit.
-template <bool FULL>
-__device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, float* f, float* g) {
+template <bool FULL, bool PU = false>
+__device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, float* f, float* g,
+                                           float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
     const float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
     const float dT = n0 * p.inv_sigma;
     const float T = p.T0 + dT;
@@ -703,7 +718,8 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
     const float vz = jz * p.inv_rho0 + hphi * Gz;
     const float vmag = sqrt_nonneg(vx * vx + vy * vy + vz * vz);
     const float inv_den = __fdividef(1.0f, md.l0 + sqrt_nonneg(md.l0 * md.l0 + md.l1 * vmag));
-    const float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
+    const float ux = PU ? pux : vx * inv_den, uy = PU ? puy : vy * inv_den;
+    const float uz = PU ? puz : vz * inv_den;
 
     Macro mac;
     mac.rho = p.rho0 + rho;
@@ -714,7 +730,7 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
     mac.dT = dT;
     if (!FULL) return mac;
 
-    const float umag = vmag * inv_den;
+    const float umag = PU ? sqrt_nonneg(ux * ux + uy * uy + uz * uz) : vmag * inv_den;
     const float drag = md.c_darcy + md.c_forch * umag;
     const float Fx = md.phi * Gx - drag * ux;
     const float Fy = md.phi * Gy - drag * uy;
@@ -746,7 +762,12 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
     // dm_k / |M_k|^2 (Eq. 9); the conserved momentum gains rho0 F whatever s_j is
     const float de = p.ae15 * (usq - rho - m_e) + p.be15 * 2.0f * uF;
     const float deps = p.aeps15 * (rho - 5.0f * usq - m_eps) - p.beps15 * 10.0f * uF;
-    const float djx = p.rho0_10 * Fx, djy = p.rho0_10 * Fy, djz = p.rho0_10 * Fz;
+    float djx = p.rho0_10 * Fx, djy = p.rho0_10 * Fy, djz = p.rho0_10 * Fz;
+    if constexpr (PU) {
+        djx = 0.1f * (p.rho0 * (ux + 0.5f * Fx) - jx);
+        djy = 0.1f * (p.rho0 * (uy + 0.5f * Fy) - jy);
+        djz = 0.1f * (p.rho0 * (uz + 0.5f * Fz) - jz);
+    }
     const float dqx = -p.aq * qx - (p.aqc15 * ux + p.bqc15 * Fx);
     const float dqy = -p.aq * qy - (p.aqc15 * uy + p.bqc15 * Fy);
     const float dqz = -p.aq * qz - (p.aqc15 * uz + p.bqc15 * Fz);
@@ -789,11 +810,82 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
     return mac;
 }
 
-// The collision of the flow lattice L.
-template <bool FULL, bool ENTH, class L>
-__device__ __forceinline__ Macro collide_on(const KParams& p, const Medium& md, float* f, float* g) {
-    if constexpr (L::kQ == 15) return collide15<FULL>(p, md, f, g);
-    else return collide<FULL, ENTH>(p, md, f, g);
+// The collision of the flow lattice L (PU: with the velocity prescribed as pu).
+template <bool FULL, bool ENTH, class L, bool PU = false>
+__device__ __forceinline__ Macro collide_on(const KParams& p, const Medium& md, float* f, float* g,
+                                            float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
+    if constexpr (L::kQ == 15) return collide15<FULL, PU>(p, md, f, g, pux, puy, puz);
+    else return collide<FULL, ENTH, PU>(p, md, f, g, pux, puy, puz);
+}
+
+// ---- node walls (non-equilibrium extrapolation) -------------------------------------------------
+// Node-wall faces a site lies on (bit f for face f).
+__device__ __forceinline__ unsigned nee_bits(const KParams& p, int x, int y, int z) {
+    unsigned b = 0u;
+    if (x == 0) b |= p.nee_mask & 1u;
+    if (x == p.nx - 1) b |= p.nee_mask & 2u;
+    if (y == 0) b |= p.nee_mask & 4u;
+    if (y == p.ny - 1) b |= p.nee_mask & 8u;
+    if (z == 0) b |= p.nee_mask & 16u;
+    if (z == p.nz - 1) b |= p.nee_mask & 32u;
+    return b;
+}
+
+// A node-wall site (faces `nb`): the wall equilibrium plus the streamed non-equilibrium part
+// of the fluid site beside it (Guo's rule), collided at the wall's own state with the velocity
+// prescribed as u_w; rho_b = rho_f, or rho0 on a wall that withdraws fluid.  On exit f, g hold
+// the post-collision populations of the wall site; the returned macros are (rho_b, u_w, T_b).
+template <bool HET, bool FULL, class S, class L>
+__device__ __forceinline__ Macro nee_site(const Planes& pl, const KParams& p, int x, int y, int z,
+                                          int s, unsigned nb, float* f, float* g) {
+    int c[3] = {x, y, z};
+    int wall = -1, hot = -1;
+#pragma unroll
+    for (int fc = 0; fc < 6; ++fc)
+        if (nb & (1u << fc)) {
+            c[fc >> 1] += (fc & 1) ? -1 : 1;
+            if (wall < 0) wall = fc;
+            if (hot < 0 && p.heat_kind[fc] == 4) hot = fc;
+        }
+    const Nbr n = neighbourhood(p, c[0], c[1], c[2]);
+    gather_general<false, S, L>(pl, p, n, f, g);
+    const Medium mf = medium_at<HET>(p, n.s);
+    const Macro m = collide_on<false, false, L>(p, mf, f, g);  // macros of x_f; f, g unchanged
+    const float uwx = p.face_u[wall][0], uwy = p.face_u[wall][1], uwz = p.face_u[wall][2];
+    const float dTb = hot >= 0 ? p.face_dT[hot] : m.dT;
+    const float outw = (wall & 1) ? p.face_u[wall][wall >> 1] : -p.face_u[wall][wall >> 1];
+    const float drf = m.rho - p.rho0;
+    const float drb = outw > 0.0f ? 0.0f : drf;
+    const Medium mb = medium_at<HET>(p, s);
+    // f += f_eq(rho_b, u_w) - f_eq(rho_f, u_f) (Eqs. 18, 24), deviations
+    const float iub = (uwx * uwx + uwy * uwy + uwz * uwz) * mb.inv_phi;
+    const float iuf = (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz) * mf.inv_phi;
+#pragma unroll
+    for (int i = 0; i < L::kQ; ++i) {
+        const float ebu = (float)L::ex(i) * uwx + (float)L::ey(i) * uwy + (float)L::ez(i) * uwz;
+        const float efu = (float)L::ex(i) * m.ux + (float)L::ey(i) * m.uy + (float)L::ez(i) * m.uz;
+        f[i] += L::w(i) * ((drb - drf) +
+                           p.rho0 * (3.0f * (ebu - efu) + 4.5f * (ebu * ebu * mb.inv_phi - efu * efu * mf.inv_phi) -
+                                     1.5f * (iub - iuf)));
+    }
+    // g += g_eq(T_b, u_w) - g_eq(T_f, u_f) (Eq. 42), deviations from omega_i sigma T0
+    const float Tb = p.T0 + dTb;
+    g[0] += p.om0 * p.sigma * (dTb - m.dT);
+#pragma unroll
+    for (int i = 1; i < kQT; ++i) {
+        const float ebu = (float)ex7(i) * uwx + (float)ey7(i) * uwy + (float)ez7(i) * uwz;
+        const float efu = (float)ex7(i) * m.ux + (float)ey7(i) * m.uy + (float)ez7(i) * m.uz;
+        g[i] += p.om1 * p.sigma * (dTb - m.dT) + 0.5f * (ebu * Tb - efu * m.T);
+    }
+    Macro mac;
+    mac.rho = p.rho0 + drb;
+    mac.ux = uwx;
+    mac.uy = uwy;
+    mac.uz = uwz;
+    mac.T = Tb;
+    mac.dT = dTb;
+    if constexpr (FULL) collide_on<true, false, L, true>(p, mb, f, g, uwx, uwy, uwz);
+    return mac;
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
@@ -835,19 +927,31 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
 
 // 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
 // blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
-template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19>
+template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19, bool NEE = false>
 __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     const bool valid = x < p.nx && y < p.ny;
+    const unsigned nb = (NEE && valid) ? nee_bits(p, x, y, z) : 0u;  // node-wall site
+    const bool streams = valid && nb == 0u;
     const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
-    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
-    const unsigned lanes = __ballot_sync(0xffffffffu, valid);
+    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !streams);
+    const unsigned lanes = __ballot_sync(0xffffffffu, streams);
     if (!valid) return;
     float f[L::kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
+    if constexpr (NEE) {
+        if (nb) {
+            nee_site<HET, true, S, L>(pl, p, x, y, z, s, nb, f, g);
+#pragma unroll
+            for (int i = 0; i < L::kQ; ++i) stp<S>(pl, p, i, s, f[i]);
+#pragma unroll
+            for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, g[i], 0.0f);
+            return;
+        }
+    }
     gather_site<OUTF, S, L>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
     finish_site<HET, OUTF, S, ENTH, L>(pl, p, x, y, z, s, f, g);
 }
@@ -890,7 +994,7 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     }
 }
 
-template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19>
+template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19, bool NEE = false>
 __global__ void __launch_bounds__(kBlock)
     macros_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                   float* __restrict__ rho, float* __restrict__ u, float* __restrict__ T) {
@@ -900,9 +1004,15 @@ __global__ void __launch_bounds__(kBlock)
     if (x >= p.nx || y >= p.ny) return;
     const Nbr n = neighbourhood(p, x, y, z);
     float f[L::kQ], g[kQT];
-    gather_general<OUTF, S, L>(pl, p, n, f, g);
-    const Medium md = medium_at<HET>(p, n.s);
-    Macro m = collide_on<false, ENTH, L>(p, md, f, g);
+    Macro m;
+    const unsigned nb = NEE ? nee_bits(p, x, y, z) : 0u;
+    if (NEE && nb) {  // node-wall site: (rho_b, u_w, T_b)
+        m = nee_site<HET, false, S, L>(pl, p, x, y, z, n.s, nb, f, g);
+    } else {
+        gather_general<OUTF, S, L>(pl, p, n, f, g);
+        const Medium md = medium_at<HET>(p, n.s);
+        m = collide_on<false, ENTH, L>(p, md, f, g);
+    }
     const long long s = n.s;
     if (rho) rho[s] = m.rho;
     if (u) {
@@ -1114,6 +1224,18 @@ __global__ void __launch_bounds__(kRedThreads)
 template <bool OUTF, class S>
 __device__ __forceinline__ double temperature_at(const Planes& pl, const KParams& p, int x, int y,
                                                  int z) {
+    if (const unsigned nb = nee_bits(p, x, y, z)) {
+        // node-wall site: the wall temperature, or that of the fluid site beside it
+        int c[3] = {x, y, z};
+        for (int fc = 0; fc < 6; ++fc)
+            if (nb & (1u << fc)) {
+                if (p.heat_kind[fc] == 4) return (double)p.T0 + (double)p.face_dT[fc];
+                c[fc >> 1] += (fc & 1) ? -1 : 1;
+            }
+        x = c[0];
+        y = c[1];
+        z = c[2];
+    }
     const Nbr n = neighbourhood(p, x, y, z);
     float g[kQT];
     gather_g_bc<OUTF, S>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
@@ -1142,6 +1264,14 @@ __global__ void __launch_bounds__(kRedThreads)
         int c0[3], c1[3];
         c0[t1] = c1[t1] = j;
         c0[t2] = c1[t2] = k;
+        if (p.heat_kind[face] == 4) {  // node wall: the wall site, then two fluid sites
+            c0[axis] = hi ? n[axis] - 2 : 1;
+            c1[axis] = hi ? n[axis] - 3 : 2;
+            double T1 = temperature_at<OUTF, S>(pl, p, c0[0], c0[1], c0[2]);
+            double T2 = temperature_at<OUTF, S>(pl, p, c1[0], c1[1], c1[2]);
+            v[0] += (3.0 * Tw - 4.0 * T1 + T2) / 2.0 * scale;
+            continue;
+        }
         c0[axis] = hi ? n[axis] - 1 : 0;
         c1[axis] = hi ? n[axis] - 2 : 1;
         double T0 = temperature_at<OUTF, S>(pl, p, c0[0], c0[1], c0[2]);
@@ -1236,6 +1366,16 @@ cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaSt
         step_kernel<false, false, StoreF32, true><<<grid, block, 0, st>>>(p, pl);
         return cudaGetLastError();
     }
+    if (p.nee_mask) {  // node walls: FP32 storage, no outflow (validated on the host)
+        if (p.qf == 15) {
+            if (het) step_kernel<true, false, StoreF32, false, D3Q15, true><<<grid, block, 0, st>>>(p, pl);
+            else step_kernel<false, false, StoreF32, false, D3Q15, true><<<grid, block, 0, st>>>(p, pl);
+        } else {
+            if (het) step_kernel<true, false, StoreF32, false, D3Q19, true><<<grid, block, 0, st>>>(p, pl);
+            else step_kernel<false, false, StoreF32, false, D3Q19, true><<<grid, block, 0, st>>>(p, pl);
+        }
+        return cudaGetLastError();
+    }
     if (p.qf == 15) {  // D3Q15 flow lattice: FP32 storage (validated on the host)
         if (het && outflow)
             step_kernel<true, true, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
@@ -1268,6 +1408,20 @@ cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, floa
     const bool het = p.phi_field != nullptr;
     if (p.enthalpy) {
         macros_kernel<false, false, StoreF32, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        return cudaGetLastError();
+    }
+    if (p.nee_mask) {
+        if (p.qf == 15) {
+            if (het)
+                macros_kernel<true, false, StoreF32, false, D3Q15, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+            else
+                macros_kernel<false, false, StoreF32, false, D3Q15, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        } else {
+            if (het)
+                macros_kernel<true, false, StoreF32, false, D3Q19, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+            else
+                macros_kernel<false, false, StoreF32, false, D3Q19, true><<<grid, block, 0, st>>>(p, pl, rho, u, T);
+        }
         return cudaGetLastError();
     }
     if (p.qf == 15) {
