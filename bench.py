@@ -456,6 +456,8 @@ def run_ours(args):
     ns = wnx * wny * wnz
     with torch.cuda.stream(stream):
         lat = gb.Lattice(pb, stream=stream.cuda_stream)
+        if args.kernel != "plain":
+            lat.set_step_kernel(args.kernel)
         lat.step(args.warmup)
         lat.sync()
 
@@ -515,16 +517,19 @@ def run_ours(args):
         "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
         "data": "synthetic",
         "config": _config(args.workload, args.storage, q=q, extra=
-                          {"parallelism": f"replicas{ws}" if ws > 1 else "single"}),
+                          {"parallelism": f"replicas{ws}" if ws > 1 else "single",
+                           "step_kernel": args.kernel}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": (profiled_traffic() if (args.workload, args.storage, q) == ("channel", "fp32", 19)
+                     "traffic": (profiled_traffic()
+                                 if (args.workload, args.storage, q, args.kernel) == ("channel", "fp32", 19, "plain")
                                  else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
-                     "kernel": (f"step_kernel<false,true,D3Q{q}> (fused stream-collide, outflow)"
-                                if args.workload == "channel" else
-                                f"step_kernel<true,false,D3Q{q}> (fused stream-collide, porosity field)")},
+                     "kernel": (("tma_step_kernel" if args.kernel == "tma" else "step_kernel") +
+                                (f"<false,true,D3Q{q}> (fused stream-collide, outflow)"
+                                 if args.workload == "channel" else
+                                 f"<true,false,D3Q{q}> (fused stream-collide, porosity field)"))},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_mlups, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(fp.nbytes + gp.nbytes),
@@ -555,6 +560,8 @@ def main(argv=None):
                     help="the headline workload is the 256x64x64 channel")
     ap.add_argument("--lattice", choices=("d3q19", "d3q15"), default="d3q19",
                     help="flow lattice of the channel / cavity workloads (the headline is D3Q19)")
+    ap.add_argument("--kernel", choices=("plain", "tma"), default="plain",
+                    help="step kernel: per-thread loads, or populations staged by TMA")
     ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")
     ap.add_argument("--max-steps", type=int, default=20000, help="serve: step limit")
     ap.add_argument("--fill", type=int, default=8_000_000,

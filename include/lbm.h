@@ -202,6 +202,29 @@ lbm_status lbm_set_medium(lbm_ctx* ctx, const float* phi_field, double phi, doub
  * execution errors surface at the next synchronising call.  LBM_EINVAL for nsteps < 0. */
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 
+/* Step kernels.  Both compute the same site update (Eqs. 9-10, 34-35 with the boundary rules
+ * of lbm_step) and give bit-identical populations; they differ in how the streamed
+ * populations reach the collision.
+ *  LBM_KERNEL_PLAIN : one thread per site, each pull a load through the L1 (default).
+ *  LBM_KERNEL_TMA   : persistent blocks over tiles of 64 x 4 sites of one z-plane; for
+ *                     tiles inside the y and z ranges the Tensor Memory Accelerator copies,
+ *                     a few tiles ahead, one box per population plane (shifted by -e_i) into
+ *                     shared memory.  Needs the D3Q19 lattice, nx % 64 == 0, ny >= 4, no node
+ *                     walls and no enthalpy model.  A staged load that does not complete within
+ *                     one second stops the step early; the next lbm_sync then returns LBM_ECUDA
+ *                     (sticky). */
+#define LBM_KERNEL_PLAIN 0
+#define LBM_KERNEL_TMA 1
+
+/* Select the step kernel used by later lbm_step calls.  Prepares the kernel (tensor maps of
+ * both population copies, shared-memory limit, a 4-byte device flag owned by ctx).
+ * Errors: LBM_EINVAL (unknown kernel, or a lattice the kernel does not take; the selection is
+ * unchanged), LBM_ECUDA. */
+lbm_status lbm_set_step_kernel(lbm_ctx* ctx, int kernel);
+
+/* The context's step kernel (LBM_KERNEL_*), -1 for ctx == NULL. */
+int lbm_get_step_kernel(const lbm_ctx* ctx);
+
 /* Re-initialise the state to equilibrium (Eqs. 24 and 42) with rho = rho0 and, per site,
  * T from T_field (host, ns doubles; NULL: T_uniform) and u from u_field (host, 3 x ns
  * doubles; NULL: 0), using the current medium.  Resets the step counter.  Synchronises. */

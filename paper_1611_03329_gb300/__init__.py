@@ -37,8 +37,12 @@ ABI_SYMBOLS = (
     "lbm_residual_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_tune",
     "lbm_batch_set_block", "lbm_batch_last_error", "lbm_batch_destroy", "lbm_footprint",
     "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_poll",
-    "lbm_server_clock", "lbm_server_destroy", "lbm_server_set_fill",
+    "lbm_server_clock", "lbm_server_destroy", "lbm_server_set_fill", "lbm_set_step_kernel",
+    "lbm_get_step_kernel",
 )
+
+# Step kernels (LBM_KERNEL_*).
+STEP_KERNELS = {"plain": 0, "tma": 1}
 
 REQ_CONVERGED, REQ_MAX_STEPS, REQ_UNSTABLE, REQ_FAILED = range(4)
 REQ_STATUS = {0: "converged", 1: "max_steps", 2: "unstable", 3: "failed"}
@@ -157,6 +161,8 @@ def lib():
         L.lbm_set_medium.argtypes = [vp, fp, C.c_double, C.c_double, C.c_double, C.c_double,
                                      C.c_double]
         L.lbm_step.argtypes = [vp, C.c_int]
+        L.lbm_set_step_kernel.argtypes = [vp, C.c_int]
+        L.lbm_get_step_kernel.argtypes = [vp]
         L.lbm_init_equilibrium.argtypes = [vp, dp, dp, C.c_double]
         L.lbm_set_populations.argtypes = [vp, dp, dp]
         L.lbm_get_populations.argtypes = [vp, dp, dp]
@@ -309,6 +315,16 @@ class Lattice:
 
     def sync(self):
         self._check(lib().lbm_sync(self._h), "lbm_sync")
+
+    def set_step_kernel(self, kernel: str):
+        """Select the step kernel: "plain" (one thread per site) or "tma" (populations staged
+        into shared memory by the Tensor Memory Accelerator); both give the same populations."""
+        self._check(lib().lbm_set_step_kernel(self._h, STEP_KERNELS[kernel]), "lbm_set_step_kernel")
+
+    @property
+    def step_kernel(self) -> str:
+        k = int(lib().lbm_get_step_kernel(self._h))
+        return {v: n for n, v in STEP_KERNELS.items()}[k]
 
     @property
     def steps(self) -> int:

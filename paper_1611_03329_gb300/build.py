@@ -1,7 +1,7 @@
 """Compile the CUDA library (csrc/*.cu) for sm_103a into ``_lib/liblbm_gb300.so``.
 
-Two translation units (kernels, host C ABI) are compiled in parallel with nvcc, then linked
-into one shared library with the CUDA runtime linked statically.  The output stays in the
+The translation units (site kernels, the TMA step kernel, the host C ABI, the allocation-free
+residual entry point) are compiled in parallel with nvcc, then linked into one shared library with the CUDA runtime linked statically.  The output stays in the
 source tree (``paper_1611_03329_gb300/_lib``, git-ignored).
 """
 from __future__ import annotations
@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "liblbm_gb300.so"
 LIB = os.path.join(OUT_DIR, LIB_NAME)
-SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_tma.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

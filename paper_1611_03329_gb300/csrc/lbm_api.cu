@@ -43,6 +43,12 @@ struct lbm_ctx {
     long long steps = 0;
     lbm_status sticky = LBM_OK;
     char err[512] = {0};
+    // step kernel (LBM_KERNEL_*): for LBM_KERNEL_TMA the tensor maps of either copy, the
+    // persistent grid and the device flag of a staged load that timed out
+    int step_kernel = LBM_KERNEL_PLAIN;
+    lbm::TmaMaps tmaps[2];
+    int tma_blocks = 0;
+    int* tma_err = nullptr;
 };
 
 namespace {
@@ -506,6 +512,58 @@ lbm_status init_state(lbm_ctx* c, const double* T_dev, const double* u_dev, doub
     return LBM_OK;
 }
 
+// cuTensorMapEncodeTiled, taken from the driver through the runtime (no link to libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps of both population copies for the TMA step kernel: the Q + 7 planes of a copy
+// as (x, y, z, plane) with strides nx, nx ny and sq elements, and the FP32 temperature plane
+// of the 16-bit formats as (x, y, z); boxes of 64 and 72 x 4 sites.  Out-of-range box
+// elements are filled with zeros (the kernel never uses them).
+lbm_status encode_tma_maps(lbm_ctx* c) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(c, LBM_EINVAL, "cuTensorMapEncodeTiled is not available");
+    const EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+    const lbm_params& p = c->prm;
+    const cuuint64_t es = c->elem;
+    const cuuint64_t nplanes = (cuuint64_t)(flow_q(c) + lbm::kQT);
+    const cuuint64_t pdim[4] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz, nplanes};
+    const cuuint64_t pstr[3] = {p.nx * es, (cuuint64_t)p.nx * p.ny * es, (cuuint64_t)c->sq * es};
+    const cuuint64_t tdim[3] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, (cuuint64_t)p.nz};
+    const cuuint64_t tstr[2] = {p.nx * 4ull, (cuuint64_t)p.nx * p.ny * 4ull};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt =
+        es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    for (int k = 0; k < 2; ++k) {
+        lbm::TmaMaps& m = c->tmaps[k];
+        std::memset(&m, 0, sizeof(m));
+        for (int wide = 0; wide < 2; ++wide) {
+            const cuuint32_t bx = wide ? 72 : 64;
+            const cuuint32_t pbox[4] = {bx, (cuuint32_t)lbm::kTmaTileY, 1, 1};
+            CUresult r = encode(wide ? &m.pop72 : &m.pop64, dt, 4, c->pop[k], pdim, pstr, pbox,
+                                ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(c, LBM_EINVAL, "cuTensorMapEncodeTiled(populations) failed: %d", (int)r);
+            if (!c->tplane[k]) continue;
+            r = encode(wide ? &m.t72 : &m.t64, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->tplane[k],
+                       tdim, tstr, pbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(c, LBM_EINVAL, "cuTensorMapEncodeTiled(temperature) failed: %d", (int)r);
+        }
+    }
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -597,6 +655,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFreeHost(c->hres);
     cudaFree(c->stage);
     cudaFree(c->mac);
+    cudaFree(c->tma_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -653,7 +712,11 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
     for (int t = 0; t < nsteps; ++t) {
         int nxt = c->cur ^ 1;
-        LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pl[c->cur], c->stream));
+        if (c->step_kernel == LBM_KERNEL_TMA)
+            LBM_CUDA(lbm::launch_step_tma(c->kp, c->outflow, c->pl[c->cur], c->tmaps[c->cur],
+                                          c->tma_blocks, c->tma_err, c->stream));
+        else
+            LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pl[c->cur], c->stream));
         c->cur = nxt;
         c->steps++;
     }
@@ -664,6 +727,14 @@ lbm_status lbm_sync(lbm_ctx* c) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->tma_err) {
+        int flag = 0;
+        LBM_CUDA(cudaMemcpy(&flag, c->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            c->sticky = LBM_ECUDA;
+            return fail(c, LBM_ECUDA, "a staged population load did not complete within 1 s");
+        }
+    }
     return LBM_OK;
 }
 
@@ -873,6 +944,36 @@ lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
     if (r_T) *r_T = rT;
     return LBM_OK;
 }
+
+lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if (kernel == LBM_KERNEL_PLAIN) {
+        c->step_kernel = kernel;
+        return LBM_OK;
+    }
+    if (kernel != LBM_KERNEL_TMA) return fail(c, LBM_EINVAL, "unknown step kernel %d", kernel);
+    const lbm_params& p = c->prm;
+    if (flow_q(c) != 19 || c->lat.enthalpy || c->lat.node_walls)
+        return fail(c, LBM_EINVAL, "the TMA step kernel takes D3Q19 without node walls or enthalpy");
+    if (p.nx % lbm::kTmaTileX != 0 || p.ny < lbm::kTmaTileY)
+        return fail(c, LBM_EINVAL, "the TMA step kernel needs nx %% %d == 0 and ny >= %d",
+                    lbm::kTmaTileX, lbm::kTmaTileY);
+    if ((st = encode_tma_maps(c)) != LBM_OK) return st;
+    int blocks = 0, smem = 0;
+    LBM_CUDA(lbm::tma_prepare(c->kp, c->outflow, &blocks, &smem));
+    if (blocks <= 0) return fail(c, LBM_EINVAL, "the TMA step kernel does not fit on an SM");
+    if (!c->tma_err) {
+        LBM_CUDA(cudaMalloc(&c->tma_err, sizeof(int)));
+        LBM_CUDA(cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->stream));
+        LBM_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    c->tma_blocks = blocks;
+    c->step_kernel = kernel;
+    return LBM_OK;
+}
+
+int lbm_get_step_kernel(const lbm_ctx* c) { return c ? c->step_kernel : -1; }
 
 lbm_status lbm_get_lattice(const lbm_ctx* c, lbm_lattice* out) {
     if (!c || !out) return LBM_EINVAL;

@@ -2,6 +2,7 @@
 // (kernels and host API).  Not part of the public ABI (include/lbm.h).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -117,6 +118,25 @@ cudaError_t launch_nusselt(const KParams& p, bool outflow, const Planes& pl, int
 cudaError_t launch_residual(const float* u, const float* T, const float* up, const float* Tp,
                             long long ns, double* partials, int nparts, double* out,
                             cudaStream_t st);
+
+// TMA step kernel (lbm_tma.cu).  A copy's 26 population planes form one 4D tensor (x, y, z,
+// plane) and its FP32 temperature plane (16-bit formats) a 3D one; each has a map with boxes
+// 64 x 4 (x, y) and one with boxes 72 x 4 for the x-shifted planes.  Requires nx % 64 == 0,
+// ny >= 4, the D3Q19 lattice, no node walls and no enthalpy model.
+constexpr int kTmaTileX = 64, kTmaTileY = 4;
+struct TmaMaps {
+    CUtensorMap pop64, pop72, t64, t72;
+};
+struct TmaGrid {
+    int tiles_x, tiles_y, ntiles;
+};
+// Sets the kernel's shared-memory limit and returns its persistent grid (blocks) and its
+// dynamic shared memory per block.
+cudaError_t tma_prepare(const KParams& p, bool outflow, int* blocks, int* smem_bytes);
+// One time step reading the copy that `m` and pl.in describe; *err is set to 1 when a staged
+// load does not arrive within one second (the blocks then stop early).
+cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, const TmaMaps& m,
+                            int blocks, int* err, cudaStream_t st);
 
 int reduction_blocks();
 // One time step of every lattice of a batch group (same storage, medium kind and outflow):

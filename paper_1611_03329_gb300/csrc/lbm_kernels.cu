@@ -170,9 +170,11 @@ __device__ __forceinline__ float ldg_dev(const Planes& pl, const KParams& p, int
     if constexpr (!S::kScaled) {
         return ldp<S>(pl, p, kQ + i, idx);
     } else {
+        // explicit roundings (no contraction left to the compiler): the staged-load kernel
+        // repeats this arithmetic and must give the same bits
         const float sc = i == 0 ? p.om0 : p.om1;
-        return sc * (S::ld(static_cast<const typename S::T*>(pl.in[kQ + i]) + idx) +
-                     p.sigma * __ldg(pl.tin + idx));
+        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx),
+                                       S::ld(static_cast<const typename S::T*>(pl.in[kQ + i]) + idx)));
     }
 }
 // Stores post-collision g' (deviation from omega_i sigma T0) of a site whose temperature
@@ -184,7 +186,8 @@ __device__ __forceinline__ void stg_dev(const Planes& pl, const KParams& p, int 
         stp<S>(pl, p, kQ + i, idx, v);
     } else {
         const float isc = i == 0 ? p.iom0 : p.iom1;
-        S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + idx, v * isc - p.sigma * dT);
+        S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + idx,
+              __fmaf_rn(v, isc, -__fmul_rn(p.sigma, dT)));
     }
 }
 
@@ -368,25 +371,14 @@ __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& 
     }
 }
 
-// Pull for a warp whose sites all lie inside the y and z ranges (y, z neighbours need no
-// rule): unconditional loads with per-lane x offsets, then, only in a warp that holds an
-// x-face site, the x-face rule for the velocities that cross it.  With no x-face lane this is
-// the interior path.
-template <bool OUTF, class S, class L = D3Q19>
-__device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
-                                                   int z, int s, unsigned lanes, float* f,
-                                                   float* g) {
+// The x-face rule of a y/z-interior warp after its unconditional loads: a lane on a
+// non-periodic x face (cxm: x-low, cxp: x-high) replaces the populations that cross it.  `lanes`
+// names the lanes that call it together.
+template <bool OUTF, class S, class L>
+__device__ __forceinline__ void x_face_fixup(const Planes& pl, const KParams& p, int x, int y,
+                                             int z, int s, unsigned lanes, bool cxm, bool cxp,
+                                             float* f, float* g) {
     const int nx = p.nx, nxy = p.nx * p.ny;
-    int xm = -1, xp = 1;  // source offsets of +x and -x velocities
-    bool cxm = false, cxp = false;
-    if (x == 0) { if (p.per_mask & 1u) xm = nx - 1; else { xm = 0; cxm = true; } }
-    if (x == nx - 1) { if (p.per_mask & 2u) xp = 1 - nx; else { xp = 0; cxp = true; } }
-#pragma unroll
-    for (int i = 0; i < L::kQ; ++i)
-        f[i] = ldp<S>(pl, p, i, s + axis_off(L::ex(i), xm, xp) - (L::ey(i) * nx + L::ez(i) * nxy));
-#pragma unroll
-    for (int i = 0; i < kQT; ++i)
-        g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
     if (!__any_sync(lanes, cxm || cxp)) return;  // interior warp
     if (cxm) {
         // x-low face: wall or velocity face (an outflow is only allowed on x-high)
@@ -447,6 +439,29 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
             g[2] = bb;
         }
     }
+}
+
+
+// Pull for a warp whose sites all lie inside the y and z ranges (y, z neighbours need no
+// rule): unconditional loads with per-lane x offsets, then, only in a warp that holds an
+// x-face site, the x-face rule for the velocities that cross it.  With no x-face lane this is
+// the interior path.
+template <bool OUTF, class S, class L = D3Q19>
+__device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
+                                                   int z, int s, unsigned lanes, float* f,
+                                                   float* g) {
+    const int nx = p.nx, nxy = p.nx * p.ny;
+    int xm = -1, xp = 1;  // source offsets of +x and -x velocities
+    bool cxm = false, cxp = false;
+    if (x == 0) { if (p.per_mask & 1u) xm = nx - 1; else { xm = 0; cxm = true; } }
+    if (x == nx - 1) { if (p.per_mask & 2u) xp = 1 - nx; else { xp = 0; cxp = true; } }
+#pragma unroll
+    for (int i = 0; i < L::kQ; ++i)
+        f[i] = ldp<S>(pl, p, i, s + axis_off(L::ex(i), xm, xp) - (L::ey(i) * nx + L::ez(i) * nxy));
+#pragma unroll
+    for (int i = 0; i < kQT; ++i)
+        g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
+    x_face_fixup<OUTF, S, L>(pl, p, x, y, z, s, lanes, cxm, cxp, f, g);
 }
 
 // ---- collision -------------------------------------------------------------------------------
@@ -517,7 +532,9 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
         enthalpy_state(p, n0, T, fl);
         dT = T - p.T0;
     } else {
-        dT = n0 * p.inv_sigma;
+        // a rounded product (never contracted into an FMA with T0): every kernel that inlines
+        // the collision then computes the same T bits, whatever the surrounding code
+        dT = __fmul_rn(n0, p.inv_sigma);
         T = p.T0 + dT;
     }
     const float Gx = p.buoy[0] * dT + p.accel[0];
@@ -690,7 +707,7 @@ template <bool FULL, bool PU = false>
 __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, float* f, float* g,
                                            float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
     const float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
-    const float dT = n0 * p.inv_sigma;
+    const float dT = __fmul_rn(n0, p.inv_sigma);  // rounded product, as in collide
     const float T = p.T0 + dT;
     const float Gx = p.buoy[0] * dT + p.accel[0];
     const float Gy = p.buoy[1] * dT + p.accel[1];
@@ -1330,6 +1347,9 @@ cudaError_t with_storage(int storage, Fn&& fn) {
 
 }  // namespace
 
+// The device code above is also compiled into the TMA translation unit (lbm_tma.cu), which
+// defines LBM_DEVICE_ONLY to leave out the host launch wrappers below.
+#ifndef LBM_DEVICE_ONLY
 // ---- launch wrappers ---------------------------------------------------------------------------
 int reduction_blocks() { return kRedBlocks; }
 
@@ -1543,5 +1563,7 @@ cudaError_t launch_residual(const float* u, const float* T, const float* up, con
     finalize_kernel<5><<<1, kRedThreads, 0, st>>>(partials, nparts, out);
     return cudaGetLastError();
 }
+
+#endif  // LBM_DEVICE_ONLY
 
 }  // namespace lbm
