@@ -33,7 +33,7 @@ constexpr unsigned long long kTmaWaitNs = 1000000000ull;  // 1 s per wait
 template <class S>
 struct TmaCfg {
     using T = typename S::T;
-    static constexpr int kStages = sizeof(T) == 2 ? 4 : 3;
+    static constexpr int kStages = sizeof(T) == 2 ? 3 : 2;
     static constexpr int kW = 72;  // slot width: 64 sites and 8 columns of halo
     static constexpr int kPlane = (kTY * kW * (int)sizeof(T) + 127) / 128 * 128;  // bytes
     static constexpr int kTSlot = S::kScaled ? (kTY * kW * 4 + 127) / 128 * 128 : 0;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
 // have read it.  No barrier spans the block, so compute warps drift apart by up to the
 // pipeline depth instead of waiting for one another on every tile.
 template <bool HET, bool OUTF, class S>
-__global__ void __launch_bounds__(kTBlock, 2)
+__global__ void __launch_bounds__(kTBlock, 3)
     tma_step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
                     const __grid_constant__ TmaMaps m, const TmaGrid tg, int* __restrict__ err) {
     using C = TmaCfg<S>;
