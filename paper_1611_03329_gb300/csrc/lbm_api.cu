@@ -29,6 +29,7 @@ struct lbm_ctx {
     lbm::Planes pl[2];  // launch planes reading copy 0 / copy 1
     bool outflow = false;
     int block_threads = 64;      // site-kernel block size (LBM_BLOCK_THREADS overrides)
+    bool pdl = true;             // step launches as programmatic dependent launches (LBM_PDL=0: off)
     float* phi_dev = nullptr;
     KParams kp{};
     double* partials = nullptr;  // reduction scratch
@@ -581,6 +582,7 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     c->nyz = (long long)p->ny * p->nz;
     c->outflow = p->flow_bc[1] == LBM_FLOW_OUTFLOW;
     c->elem = p->storage == LBM_STORE_FP32 ? sizeof(float) : 2;
+    if (const char* v = std::getenv("LBM_PDL")) c->pdl = std::atoi(v) != 0;
     if (const char* bt = std::getenv("LBM_BLOCK_THREADS")) {
         int v = std::atoi(bt);
         if (v == 32 || v == 64 || v == 128 || v == 256) c->block_threads = v;
@@ -714,9 +716,9 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         int nxt = c->cur ^ 1;
         if (c->step_kernel == LBM_KERNEL_TMA)
             LBM_CUDA(lbm::launch_step_tma(c->kp, c->outflow, c->pl[c->cur], c->tmaps[c->cur],
-                                          c->tma_blocks, c->tma_err, c->stream));
+                                          c->tma_blocks, c->tma_err, c->pdl, c->stream));
         else
-            LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pl[c->cur], c->stream));
+            LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pl[c->cur], c->pdl, c->stream));
         c->cur = nxt;
         c->steps++;
     }

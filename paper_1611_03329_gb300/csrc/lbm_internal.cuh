@@ -91,7 +91,10 @@ struct BatchLattice {
 };
 
 // Launch wrappers (defined in lbm_kernels.cu).  All are asynchronous on `st`.
-cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st);
+// One time step; `pdl`: launched as a programmatic dependent launch (the kernel may be
+// scheduled while the stream's previous kernel drains, and waits for it before loading).
+cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, bool pdl,
+                        cudaStream_t st);
 cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,
                           float* T, cudaStream_t st);
 // Equilibrium state written into pl.out.
@@ -136,7 +139,7 @@ cudaError_t tma_prepare(const KParams& p, bool outflow, int* blocks, int* smem_b
 // One time step reading the copy that `m` and pl.in describe; *err is set to 1 when a staged
 // load does not arrive within one second (the blocks then stop early).
 cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, const TmaMaps& m,
-                            int blocks, int* err, cudaStream_t st);
+                            int blocks, int* err, bool pdl, cudaStream_t st);
 
 int reduction_blocks();
 // One time step of every lattice of a batch group (same storage, medium kind and outflow):

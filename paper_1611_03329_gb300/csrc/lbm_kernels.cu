@@ -942,11 +942,21 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
     if constexpr (S::kScaled) pl.tout[s] = m.dT;
 }
 
+// Programmatic dependent launch: a step kernel launched with it may be scheduled while the
+// previous kernel of the stream drains.  Each thread first waits until that kernel has
+// completed and its writes are visible (a no-op for an ordinary launch), then allows the next
+// step's grid to be scheduled in turn.
+__device__ __forceinline__ void dependent_launch_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
 // blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
 template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19, bool NEE = false>
 __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
+    dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -1378,46 +1388,49 @@ cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk
     });
 }
 
-cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, cudaStream_t st) {
+// Launch of a step kernel, with programmatic dependent launch when `pdl` is set.
+template <class... KArgs, class... Args>
+cudaError_t launch_kernel(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
+cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, bool pdl,
+                        cudaStream_t st) {
     dim3 grid, block;
     site_grid(p, &grid, &block);
     const bool het = p.phi_field != nullptr;
-    if (p.enthalpy) {  // FP32, uniform medium, no outflow (validated on the host)
-        step_kernel<false, false, StoreF32, true><<<grid, block, 0, st>>>(p, pl);
-        return cudaGetLastError();
-    }
+    if (p.enthalpy)  // FP32, uniform medium, no outflow (validated on the host)
+        return launch_kernel(pdl, step_kernel<false, false, StoreF32, true>, grid, block, 0, st, p, pl);
     if (p.nee_mask) {  // node walls: FP32 storage, no outflow (validated on the host)
-        if (p.qf == 15) {
-            if (het) step_kernel<true, false, StoreF32, false, D3Q15, true><<<grid, block, 0, st>>>(p, pl);
-            else step_kernel<false, false, StoreF32, false, D3Q15, true><<<grid, block, 0, st>>>(p, pl);
-        } else {
-            if (het) step_kernel<true, false, StoreF32, false, D3Q19, true><<<grid, block, 0, st>>>(p, pl);
-            else step_kernel<false, false, StoreF32, false, D3Q19, true><<<grid, block, 0, st>>>(p, pl);
-        }
-        return cudaGetLastError();
+        auto k = p.qf == 15 ? (het ? step_kernel<true, false, StoreF32, false, D3Q15, true>
+                                   : step_kernel<false, false, StoreF32, false, D3Q15, true>)
+                            : (het ? step_kernel<true, false, StoreF32, false, D3Q19, true>
+                                   : step_kernel<false, false, StoreF32, false, D3Q19, true>);
+        return launch_kernel(pdl, k, grid, block, 0, st, p, pl);
     }
     if (p.qf == 15) {  // D3Q15 flow lattice: FP32 storage (validated on the host)
-        if (het && outflow)
-            step_kernel<true, true, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
-        else if (het)
-            step_kernel<true, false, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
-        else if (outflow)
-            step_kernel<false, true, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
-        else
-            step_kernel<false, false, StoreF32, false, D3Q15><<<grid, block, 0, st>>>(p, pl);
-        return cudaGetLastError();
+        auto k = het ? (outflow ? step_kernel<true, true, StoreF32, false, D3Q15>
+                                : step_kernel<true, false, StoreF32, false, D3Q15>)
+                     : (outflow ? step_kernel<false, true, StoreF32, false, D3Q15>
+                                : step_kernel<false, false, StoreF32, false, D3Q15>);
+        return launch_kernel(pdl, k, grid, block, 0, st, p, pl);
     }
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
-        if (het && outflow)
-            step_kernel<true, true, S><<<grid, block, 0, st>>>(p, pl);
-        else if (het)
-            step_kernel<true, false, S><<<grid, block, 0, st>>>(p, pl);
-        else if (outflow)
-            step_kernel<false, true, S><<<grid, block, 0, st>>>(p, pl);
-        else
-            step_kernel<false, false, S><<<grid, block, 0, st>>>(p, pl);
-        return cudaGetLastError();
+        auto k = het ? (outflow ? step_kernel<true, true, S> : step_kernel<true, false, S>)
+                     : (outflow ? step_kernel<false, true, S> : step_kernel<false, false, S>);
+        return launch_kernel(pdl, k, grid, block, 0, st, p, pl);
     });
 }
 

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kTBlock, 3)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();  // the only block-wide barrier: barriers initialised
+    dependent_launch_prologue();
 
     if (warp == kTWarps) {  // loader
         if (lane != 0) return;
@@ -284,7 +285,7 @@ cudaError_t tma_prepare(const KParams& p, bool outflow, int* blocks, int* smem_b
 }
 
 cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, const TmaMaps& m,
-                            int blocks, int* err, cudaStream_t st) {
+                            int blocks, int* err, bool pdl, cudaStream_t st) {
     TmaGrid tg;
     tg.tiles_x = p.nx / kTX;
     tg.tiles_y = (p.ny + kTY - 1) / kTY;
@@ -293,16 +294,19 @@ cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, co
     const bool het = p.phi_field != nullptr;
     return with_storage(p.storage, [&](auto tag) {
         using S = decltype(tag);
-        constexpr int smem = TmaCfg<S>::kSmem;
-        if (het && outflow)
-            tma_step_kernel<true, true, S><<<blocks, kTBlock, smem, st>>>(p, pl, m, tg, err);
-        else if (het)
-            tma_step_kernel<true, false, S><<<blocks, kTBlock, smem, st>>>(p, pl, m, tg, err);
-        else if (outflow)
-            tma_step_kernel<false, true, S><<<blocks, kTBlock, smem, st>>>(p, pl, m, tg, err);
-        else
-            tma_step_kernel<false, false, S><<<blocks, kTBlock, smem, st>>>(p, pl, m, tg, err);
-        return cudaGetLastError();
+        auto k = het ? (outflow ? tma_step_kernel<true, true, S> : tma_step_kernel<true, false, S>)
+                     : (outflow ? tma_step_kernel<false, true, S> : tma_step_kernel<false, false, S>);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(kTBlock);
+        cfg.dynamicSmemBytes = TmaCfg<S>::kSmem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = pdl ? 1 : 0;
+        return cudaLaunchKernelEx(&cfg, k, p, pl, m, tg, err);
     });
 }
 
