@@ -229,7 +229,7 @@ def _oracle_run(nz: int, steps: int, warmup: int):
     return NX * NY * nz * steps / dt / 1e6, dt, oracle.max_threads()
 
 
-def cpu_baseline(budget_s: float = 10.0):
+def cpu_baseline(budget_s: float = 20.0):
     """The oracle on the host cores over a bounded sample: a z-slab of the channel (periodic
     in z as the full channel) sized so that the timed steps take about budget_s."""
     mlups1, dt1, cores = _oracle_run(8, 1, 0)
