@@ -451,13 +451,14 @@ def run_ours(args):
         return 0
     stream = torch.cuda.Stream()
     q = 15 if args.lattice == "d3q15" else 19
-    pb = _problem(storage=args.storage, workload=args.workload, q=q)
+    pb = dict(_problem(storage=args.storage, workload=args.workload, q=q), scheme=args.scheme)
     wnx, wny, wnz = WORKLOADS[args.workload]
     ns = wnx * wny * wnz
     with torch.cuda.stream(stream):
         lat = gb.Lattice(pb, stream=stream.cuda_stream)
         if args.kernel != "plain":
             lat.set_step_kernel(args.kernel)
+        aa = lat.lattice()["scheme"] == 1
         lat.step(args.warmup)
         lat.sync()
 
@@ -518,7 +519,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": _config(args.workload, args.storage, q=q, extra=
                           {"parallelism": f"replicas{ws}" if ws > 1 else "single",
-                           "step_kernel": args.kernel}),
+                           "step_kernel": args.kernel, "scheme": args.scheme}),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "traffic": (profiled_traffic()
@@ -526,7 +527,9 @@ def run_ours(args):
                                  else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
-                     "kernel": (("tma_step_kernel" if args.kernel == "tma" else "step_kernel") +
+                     "kernel": ("aa_pull_kernel<true> / aa_local_kernel<true> alternating (AA, one "
+                                "copy in place, porosity field)" if aa else
+                                ("tma_step_kernel" if args.kernel == "tma" else "step_kernel") +
                                 (f"<false,true,D3Q{q}> (fused stream-collide, outflow)"
                                  if args.workload == "channel" else
                                  f"<true,false,D3Q{q}> (fused stream-collide, porosity field)"))},
@@ -560,6 +563,8 @@ def main(argv=None):
                     help="the headline workload is the 256x64x64 channel")
     ap.add_argument("--lattice", choices=("d3q19", "d3q15"), default="d3q19",
                     help="flow lattice of the channel / cavity workloads (the headline is D3Q19)")
+    ap.add_argument("--scheme", choices=("pingpong", "aa", "auto"), default="pingpong",
+                    help="population scheme: two copies, or one copy updated in place (AA)")
     ap.add_argument("--kernel", choices=("plain", "tma"), default="plain",
                     help="step kernel: per-thread loads, or populations staged by TMA")
     ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")

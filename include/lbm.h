@@ -131,7 +131,32 @@ typedef struct lbm_params {
      * FP32 storage, without the enthalpy model, and outside lbm_batch / lbm_server; its f
      * arrays in lbm_set_populations / lbm_get_populations hold 15 planes. */
     int q_flow;
+    /* population scheme: LBM_SCHEME_PINGPONG (0, the default), LBM_SCHEME_AA or
+     * LBM_SCHEME_AUTO, see below */
+    int scheme;
 } lbm_params;
+
+/* Population schemes.  Both compute the same site update and give bit-identical populations.
+ *  LBM_SCHEME_PINGPONG : two copies of the populations; every step pulls from one copy and
+ *                        writes the other.
+ *  LBM_SCHEME_AA       : one copy, updated in place by alternating two kinds of step: a pull
+ *                        step that gathers like ping-pong and pushes each post-collision
+ *                        population to the plane the next step reads it from, and a local step
+ *                        that reads and writes its own site only.  Half the population memory,
+ *                        the same bytes moved per step.  Needs FP32 storage, the D3Q19 lattice,
+ *                        no outflow face, no node walls and no enthalpy model; such contexts
+ *                        run outside lbm_batch / lbm_server and with LBM_KERNEL_PLAIN.  After an
+ *                        odd number of steps, the first call that reads the state (populations,
+ *                        macros, Nusselt, sums, residual) first rearranges the copy (a pure
+ *                        permutation, no arithmetic) into the layout a pull step reads.
+ *  LBM_SCHEME_AUTO     : ping-pong while its footprint fits in the device memory free at
+ *                        lbm_create (the environment variable LBM_MEM_LIMIT, in bytes, caps
+ *                        that figure), else AA where the lattice allows it; lbm_derive_lattice
+ *                        reports ping-pong for it; lbm_server runs ping-pong.  The scheme in
+ *                        use is lbm_lattice.scheme (lbm_get_lattice). */
+#define LBM_SCHEME_PINGPONG 0
+#define LBM_SCHEME_AA 1
+#define LBM_SCHEME_AUTO 2
 
 /*
  * Lattice-unit parameters derived from an lbm_params (Eq. 32, Eq. 41, Eq. 51 or Eq. 56,
@@ -154,6 +179,7 @@ typedef struct lbm_lattice {
     int q;                     /* flow lattice (19 or 15); with 15, s[] keeps the D3Q19 order
                                   and the D3Q15 rates s_e, s_eps, s_q, s_nu, s_m of Eq. 16 are
                                   s[1], s[2], s[4], s[9], s[16] */
+    int scheme;                /* the scheme in use: LBM_SCHEME_PINGPONG or LBM_SCHEME_AA */
 } lbm_lattice;
 
 /* Fill p with the paper's defaults (Sec. 4: rho0 = 1, J = sigma = Gamma = 1, varpi = 1/2,

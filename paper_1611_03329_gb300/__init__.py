@@ -41,6 +41,9 @@ ABI_SYMBOLS = (
     "lbm_get_step_kernel",
 )
 
+# Population schemes (LBM_SCHEME_*).
+SCHEMES = {"pingpong": 0, "aa": 1, "auto": 2}
+
 # Step kernels (LBM_KERNEL_*).
 STEP_KERNELS = {"plain": 0, "tma": 1}
 
@@ -74,7 +77,7 @@ class LbmParams(C.Structure):
         ("T_m", C.c_double), ("T_s", C.c_double), ("T_l", C.c_double), ("St", C.c_double),
         ("c_pl", C.c_double), ("c_ps", C.c_double), ("sigma_s", C.c_double),
         ("sigma_l", C.c_double), ("alpha_ratio", C.c_double),
-        ("q_flow", C.c_int),
+        ("q_flow", C.c_int), ("scheme", C.c_int),
     ]
 
 
@@ -97,7 +100,7 @@ class LbmLattice(C.Structure):
         ("c_pl", C.c_double), ("c_ref", C.c_double), ("sigma_s", C.c_double),
         ("sigma_l", C.c_double), ("T_s", C.c_double), ("T_l", C.c_double), ("L_a", C.c_double),
         ("alpha_s", C.c_double), ("alpha_l", C.c_double),
-        ("node_walls", C.c_int), ("q", C.c_int),
+        ("node_walls", C.c_int), ("q", C.c_int), ("scheme", C.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -229,6 +232,7 @@ def params_from_problem(pb: dict) -> LbmParams:
     if "T_init" not in pb:
         p.T_init = p.T0
     p.q_flow = int(pb.get("q", 19))
+    p.scheme = SCHEMES[pb.get("scheme", "pingpong")]
     p.enthalpy = int(bool(pb.get("enthalpy", False)))
     p.flow_off = int(bool(pb.get("flow_off", False)))
     for k in ("T_m", "T_s", "T_l", "St", "c_pl", "c_ps", "sigma_s", "sigma_l", "alpha_ratio"):

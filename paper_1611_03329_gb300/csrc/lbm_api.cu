@@ -30,6 +30,12 @@ struct lbm_ctx {
     bool outflow = false;
     int block_threads = 64;      // site-kernel block size (LBM_BLOCK_THREADS overrides)
     bool pdl = true;             // step launches as programmatic dependent launches (LBM_PDL=0: off)
+    // AA scheme: one copy (pop[0]); pl[0] = (in: permuted, out: identity) for pull steps and
+    // readers, pl[1] = (in: identity, out: permuted) for local steps and the initial state,
+    // pw.in = permuted; aa_phase 0: swapped layout (next step pulls), 1: streamed layout
+    bool aa = false;
+    lbm::Planes pw;
+    int aa_phase = 0;
     float* phi_dev = nullptr;
     KParams kp{};
     double* partials = nullptr;  // reduction scratch
@@ -86,6 +92,14 @@ double or_default(double v, double d) { return v > 0.0 ? v : d; }
 
 // Eq. 56 / Eq. 51 / lattice units -> lbm_lattice (default medium).  Returns an error text or
 // nullptr.
+// Whether a problem can run the AA scheme (L: its lattice so far, with q and node_walls set).
+bool aa_eligible(const lbm_params* p, const lbm_lattice& L) {
+    return L.q == 19 && p->storage == LBM_STORE_FP32 && !L.node_walls && !p->enthalpy &&
+           p->flow_bc[1] != LBM_FLOW_OUTFLOW;
+}
+
+unsigned long long footprint_of(const lbm_params* p, const lbm_lattice& L, int has_phi_field);
+
 const char* derive(const lbm_params* p, lbm_lattice* L) {
     std::memset(L, 0, sizeof(*L));
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
@@ -220,6 +234,13 @@ const char* derive(const lbm_params* p, lbm_lattice* L) {
         if (n[0] < 3) return "an outflow needs nx >= 3";
         if (!finite_pos(L->U_out)) return "outflow speed must be > 0";
     }
+    if (p->scheme < LBM_SCHEME_PINGPONG || p->scheme > LBM_SCHEME_AUTO)
+        return "scheme must be LBM_SCHEME_PINGPONG, LBM_SCHEME_AA or LBM_SCHEME_AUTO";
+    if (p->scheme == LBM_SCHEME_AA && !aa_eligible(p, *L))
+        return "the AA scheme needs FP32 storage, D3Q19, no outflow, no node walls and no "
+               "enthalpy model";
+    // AUTO resolves to ping-pong here; lbm_create switches it to AA when two copies do not fit
+    L->scheme = p->scheme == LBM_SCHEME_AA ? LBM_SCHEME_AA : LBM_SCHEME_PINGPONG;
     if (!std::isfinite(p->T_init)) return "T_init must be finite";
     L->enthalpy = p->enthalpy ? 1 : 0;
     L->flow_off = p->flow_off ? 1 : 0;
@@ -467,8 +488,26 @@ bool has_plane(const lbm_ctx* c, int q) { return q < flow_q(c) || q >= lbm::kQ; 
 
 // Start of logical population plane q of copy k (copies hold Q + 7 planes).
 void* plane_ptr(const lbm_ctx* c, int k, int q) {
+    if (c->aa) q = lbm::aa_swapped_plane(q);  // the state at rest is in the swapped layout
     const int phys = q < lbm::kQ ? q : flow_q(c) + (q - lbm::kQ);
     return static_cast<char*>(c->pop[k]) + (size_t)phys * (size_t)c->sq * c->elem;
+}
+
+// Plane tables of an AA context's single copy: `in_perm` / `out_perm` select the swapped
+// layout (logical plane q at physical plane opp(q)) for the input / output side.
+lbm::Planes aa_planes(const lbm_ctx* c, bool in_perm, bool out_perm) {
+    lbm::Planes pl;
+    for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
+        const int pp = lbm::aa_swapped_plane(q);
+        char* base = static_cast<char*>(c->pop[0]);
+        pl.in[q] = base + (size_t)(in_perm ? pp : q) * (size_t)c->sq * c->elem;
+        pl.out[q] = base + (size_t)(out_perm ? pp : q) * (size_t)c->sq * c->elem;
+    }
+    pl.hin = nullptr;
+    pl.hout = nullptr;
+    pl.tin = nullptr;
+    pl.tout = nullptr;
+    return pl;
 }
 
 // Planes of a step that reads copy `from` and writes the other copy.
@@ -496,6 +535,14 @@ lbm_status ensure_mac(lbm_ctx* c) {
     return LBM_OK;
 }
 
+// AA: the swapped layout every reader expects (a permutation after an odd number of steps).
+lbm_status aa_settle(lbm_ctx* c) {
+    if (!c->aa || c->aa_phase == 0) return LBM_OK;
+    LBM_CUDA(lbm::launch_aa_normalize(c->kp, c->pl[0], c->stream));
+    c->aa_phase = 0;
+    return LBM_OK;
+}
+
 lbm_status reset_hist(lbm_ctx* c) {
     if (!c->outflow) return LBM_OK;
     LBM_CUDA(lbm::launch_hist_reset(c->kp, c->pl[c->cur], cur_hist(c), c->stream));
@@ -510,6 +557,7 @@ lbm_status init_state(lbm_ctx* c, const double* T_dev, const double* u_dev, doub
     if (s != LBM_OK) return s;
     c->steps = 0;
     c->have_prev = false;
+    c->aa_phase = 0;
     return LBM_OK;
 }
 
@@ -601,8 +649,26 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamCreate");
         else c->own_stream = true;
     }
+    // AUTO: ping-pong while both copies fit in the free device memory (LBM_MEM_LIMIT, in
+    // bytes, caps that figure), else AA where the lattice allows it
+    if (st == LBM_OK && p->scheme == LBM_SCHEME_AUTO && aa_eligible(p, c->lat)) {
+        size_t fr = 0, tot = 0;
+        e = cudaMemGetInfo(&fr, &tot);
+        if (e != cudaSuccess) {
+            st = cuda_fail(c, e, "cudaMemGetInfo");
+        } else {
+            unsigned long long avail = fr;
+            if (const char* v = std::getenv("LBM_MEM_LIMIT")) {
+                const unsigned long long lim = std::strtoull(v, nullptr, 10);
+                if (lim > 0 && lim < avail) avail = lim;
+            }
+            if (footprint_of(p, c->lat, 0) > avail) c->lat.scheme = LBM_SCHEME_AA;
+        }
+    }
+    c->aa = c->lat.scheme == LBM_SCHEME_AA;
+    L = c->lat;
     size_t pop_bytes = c->elem * (size_t)((L.q == 15 ? 15 : lbm::kQ) + lbm::kQT) * (size_t)c->sq;
-    for (int k = 0; k < 2 && st == LBM_OK; ++k) {
+    for (int k = 0; k < (c->aa ? 1 : 2) && st == LBM_OK; ++k) {
         e = cudaMalloc(&c->pop[k], pop_bytes);
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaMalloc(populations)");
         if (st == LBM_OK && c->outflow) {
@@ -625,8 +691,14 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     }
     if (st == LBM_OK) {
         fill_kparams(c);
-        c->pl[0] = planes(c, 0);
-        c->pl[1] = planes(c, 1);
+        if (c->aa) {
+            c->pl[0] = aa_planes(c, true, false);
+            c->pl[1] = aa_planes(c, false, true);
+            c->pw = aa_planes(c, true, true);
+        } else {
+            c->pl[0] = planes(c, 0);
+            c->pl[1] = planes(c, 1);
+        }
         st = init_state(c, nullptr, nullptr, p->T_init);
     }
     if (st == LBM_OK) {
@@ -712,6 +784,16 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
+    if (c->aa) {
+        for (int t = 0; t < nsteps; ++t) {
+            const bool local = c->aa_phase == 1;
+            LBM_CUDA(lbm::launch_aa_step(c->kp, local, c->pl[local ? 1 : 0], c->pw, c->pdl,
+                                         c->stream));
+            c->aa_phase ^= 1;
+            c->steps++;
+        }
+        return LBM_OK;
+    }
     for (int t = 0; t < nsteps; ++t) {
         int nxt = c->cur ^ 1;
         if (c->step_kernel == LBM_KERNEL_TMA)
@@ -811,6 +893,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
     }
     if ((st = reset_hist(c)) != LBM_OK) return st;
     c->have_prev = false;
+    c->aa_phase = 0;  // the whole state was written in the swapped layout
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -818,6 +901,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
 lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
+    if ((st = aa_settle(c)) != LBM_OK) return st;
     if ((st = ensure_stage(c)) != LBM_OK) return st;
     const bool tshift = c->prm.storage != LBM_STORE_FP32;
     const int nq = tshift ? lbm::kQ : lbm::kQ + lbm::kQT;
@@ -846,6 +930,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
 lbm_status lbm_macros_device(lbm_ctx* c, float* rho, float* u, float* T) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
+    if ((st = aa_settle(c)) != LBM_OK) return st;
     LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, c->pl[c->cur], rho, u, T, c->stream));
     return LBM_OK;
 }
@@ -853,6 +938,7 @@ lbm_status lbm_macros_device(lbm_ctx* c, float* rho, float* u, float* T) {
 lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* T) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
+    if ((st = aa_settle(c)) != LBM_OK) return st;
     if ((st = ensure_mac(c)) != LBM_OK) return st;
     float* half = c->mac + (size_t)(c->snap ^ 1) * 4 * c->ns;  // the half not holding the snapshot
     float* du = half;
@@ -873,6 +959,7 @@ lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* T) {
 lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile, double* nu_mp) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
+    if ((st = aa_settle(c)) != LBM_OK) return st;
     if (face < 0 || face > 5) return fail(c, LBM_EINVAL, "face must be 0..5");
     const bool node_wall = c->prm.heat_bc[face] == LBM_HEAT_NEE_DIRICHLET;
     if (c->prm.heat_bc[face] != LBM_HEAT_DIRICHLET && !node_wall)
@@ -900,6 +987,7 @@ lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile,
 lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
+    if ((st = aa_settle(c)) != LBM_OK) return st;
     int nr = lbm::reduction_blocks();
     LBM_CUDA(lbm::launch_sums(c->kp, c->pl[c->cur], c->partials, nr, c->dres, c->stream));
     LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 2, cudaMemcpyDeviceToHost,
@@ -915,6 +1003,7 @@ lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
 lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
+    if ((st = aa_settle(c)) != LBM_OK) return st;
     if ((st = ensure_mac(c)) != LBM_OK) return st;
     float* cu = c->mac + (size_t)(c->snap ^ 1) * 4 * c->ns;  // new fields
     float* cT = cu + 3 * c->ns;
@@ -958,6 +1047,7 @@ lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
     const lbm_params& p = c->prm;
     if (flow_q(c) != 19 || c->lat.enthalpy || c->lat.node_walls)
         return fail(c, LBM_EINVAL, "the TMA step kernel takes D3Q19 without node walls or enthalpy");
+    if (c->aa) return fail(c, LBM_EINVAL, "the TMA step kernel runs the ping-pong scheme");
     if (p.nx % lbm::kTmaTileX != 0 || p.ny < lbm::kTmaTileY)
         return fail(c, LBM_EINVAL, "the TMA step kernel needs nx %% %d == 0 and ny >= %d",
                     lbm::kTmaTileX, lbm::kTmaTileY);
@@ -1123,7 +1213,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
     }
     for (int k = 0; k < n; ++k) {
         lbm_ctx* c = ctxs[k];
-        if (!c || c->sticky != LBM_OK || c->lat.q == 15 || c->lat.node_walls) {  // step alone
+        if (!c || c->sticky != LBM_OK || c->lat.q == 15 || c->lat.node_walls || c->aa) {  // step alone
             delete b;
             return LBM_EINVAL;
         }
@@ -1301,7 +1391,8 @@ unsigned long long footprint_of(const lbm_params* p, const lbm_lattice& L, int h
     const unsigned long long sq = (ns + 63) / 64 * 64;
     const unsigned long long elem = p->storage == LBM_STORE_FP32 ? 4 : 2;
     const unsigned long long nq = (L.q == 15 ? 15 : lbm::kQ) + lbm::kQT;
-    unsigned long long b = 2ull * nq * elem * sq;  // two population copies
+    // two population copies (one with the AA scheme)
+    unsigned long long b = (L.scheme == LBM_SCHEME_AA ? 1ull : 2ull) * nq * elem * sq;
     if (p->flow_bc[1] == LBM_FLOW_OUTFLOW) b += 2ull * lbm::kOutSlots * 4 * p->ny * p->nz;
     if (p->storage != LBM_STORE_FP32) b += 2ull * 4 * ns;  // temperature planes
     if (has_phi_field) b += 4 * ns;
@@ -1424,9 +1515,11 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
     if (derive(p, &L)) return LBM_EINVAL;
     if (L.q == 15 || L.node_walls) return LBM_EINVAL;  // the serving loop batches D3Q19 lattices
                                                        // with halfway walls
+    if (p->scheme == LBM_SCHEME_AA) return LBM_EINVAL;  // and ping-pong copies
     auto* r = new (std::nothrow) lbm_server::Req();
     if (!r) return LBM_ENOMEM;
     r->p = *p;
+    r->p.scheme = LBM_SCHEME_PINGPONG;
     if (m) {
         r->phi = m->phi;
         r->K = m->K;

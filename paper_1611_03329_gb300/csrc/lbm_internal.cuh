@@ -95,6 +95,13 @@ struct BatchLattice {
 // scheduled while the stream's previous kernel drains, and waits for it before loading).
 cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, bool pdl,
                         cudaStream_t st);
+// AA pattern (FP32, D3Q19, no outflow; one copy).  Pull step (local = false): pl.in is the
+// permuted table of the copy (logical plane q at physical opp(q)), pl.out the identity table.
+// Local step (local = true): pl = (in: identity, out: permuted), pw.in = the permuted table.
+cudaError_t launch_aa_step(const KParams& p, bool local, const Planes& pl, const Planes& pw,
+                           bool pdl, cudaStream_t st);
+// The streamed layout left by a pull step back to the swapped layout (pl.out: identity table).
+cudaError_t launch_aa_normalize(const KParams& p, const Planes& pl, cudaStream_t st);
 cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,
                           float* T, cudaStream_t st);
 // Equilibrium state written into pl.out.
@@ -142,6 +149,9 @@ cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, co
                             int blocks, int* err, bool pdl, cudaStream_t st);
 
 int reduction_blocks();
+// Physical plane of logical D3Q19 + D3Q7 plane q in the AA scheme's swapped layout: the plane
+// of the opposite velocity.
+int aa_swapped_plane(int q);
 // One time step of every lattice of a batch group (same storage, medium kind and outflow):
 // lattice l reads its planes pl[cur ^ flip]; blk_lat maps each of the nblocks blocks to its
 // lattice.

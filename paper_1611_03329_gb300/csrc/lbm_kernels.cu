@@ -983,6 +983,194 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     finish_site<HET, OUTF, S, ENTH, L>(pl, p, x, y, z, s, f, g);
 }
 
+// ---- AA pattern: one population copy, updated in place (FP32, D3Q19, no outflow) ----------
+// Two layouts of the single copy alternate.  W ("swapped"): physical plane opp(i) at x holds
+// the post-collision f*_i(x), i.e. the ping-pong state with its planes permuted.  N
+// ("streamed"): physical plane i at x holds the pre-collision f_i(x) that a pull would gather,
+// except where the pull of i crosses a non-periodic face: there it holds the raw f*_opp(i)(x)
+// and the face rule is applied when it is read.
+//  pull step (W -> N): the ping-pong gather through a permuted plane table, the collision, and
+//    a push of f*_j to plane j at x + e_j (plane opp(j) at x when x + e_j lies outside);
+//  local step (N -> W): own-site loads (face rule on crossing directions), the collision, and
+//    stores to plane opp(i) at x.
+// A thread writes exactly the locations it reads, so both steps are race-free in one copy, and
+// each gathers the same values as the ping-pong pull: the populations agree bit for bit.
+struct StoreF32InPlace {  // FP32 loads through the coherent path: the copy is written in place
+    using T = float;
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float ld(const T* q) { return *q; }
+    static __device__ __forceinline__ void st(T* q, float v) { *q = v; }
+};
+
+template <int J>
+__device__ __forceinline__ void aa_push_f(const Planes& pl, const Nbr& n, float v) {
+    constexpr int I = opp19(J);  // f*_J leaves towards x + e_J, the pull source of opp(J)
+    constexpr int ex = ex19(I), ey = ey19(I), ez = ez19(I);
+    const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
+                        axis_cross(ez, n.cross, 16u, 32u);
+    if (cr == 0u)
+        static_cast<float*>(pl.out[J])[n.s + axis_off(ex, n.xm, n.xp) + axis_off(ey, n.ym, n.yp) +
+                                        axis_off(ez, n.zm, n.zp)] = v;
+    else
+        static_cast<float*>(pl.out[I])[n.s] = v;
+}
+template <int J>
+__device__ __forceinline__ void aa_push_g(const Planes& pl, const Nbr& n, float v) {
+    constexpr int I = opp7(J);
+    constexpr int ex = ex7(I), ey = ey7(I), ez = ez7(I);
+    const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
+                        axis_cross(ez, n.cross, 16u, 32u);
+    if (cr == 0u)
+        static_cast<float*>(pl.out[kQ + J])[n.s + axis_off(ex, n.xm, n.xp) +
+                                             axis_off(ey, n.ym, n.yp) + axis_off(ez, n.zm, n.zp)] = v;
+    else
+        static_cast<float*>(pl.out[kQ + I])[n.s] = v;
+}
+template <int... J>
+__device__ __forceinline__ void aa_push_all(const Planes& pl, const Nbr& n, const float* f,
+                                            const float* g, std::integer_sequence<int, J...>) {
+    (aa_push_f<J>(pl, n, f[J]), ...);
+    ((J < kQT ? aa_push_g<(J < kQT ? J : 0)>(pl, n, g[J < kQT ? J : 0]) : void()), ...);
+}
+
+// Local-step read of f_I at site n: plane I at x; on a crossing direction plane I holds the
+// raw f*_opp(I)(x), to which the ping-pong face rule is applied (pull_f through the permuted
+// table `pw`, whose logical plane opp(I) is physical plane I).
+template <int I>
+__device__ __forceinline__ float aa_local_f(const Planes& pl, const Planes& pw, const KParams& p,
+                                            const Nbr& n) {
+    constexpr int ex = ex19(I), ey = ey19(I), ez = ez19(I);
+    const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
+                        axis_cross(ez, n.cross, 16u, 32u);
+    bool via = false;
+    if (cr == 0u) return ldp<StoreF32InPlace>(pl, p, I, n.s);
+    return pull_f<D3Q19, I, false, StoreF32InPlace>(pw, p, n, &via);
+}
+template <int I>
+__device__ __forceinline__ float aa_local_g(const Planes& pl, const Planes& pw, const KParams& p,
+                                            const Nbr& n) {
+    constexpr int ex = ex7(I), ey = ey7(I), ez = ez7(I);
+    const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
+                        axis_cross(ez, n.cross, 16u, 32u);
+    if (cr == 0u) return ldp<StoreF32InPlace>(pl, p, kQ + I, n.s);
+    return pull_g<I, false, StoreF32InPlace>(pw, p, n);
+}
+template <int... I>
+__device__ __forceinline__ void aa_local_all(const Planes& pl, const Planes& pw, const KParams& p,
+                                             const Nbr& n, float* f, float* g,
+                                             std::integer_sequence<int, I...>) {
+    ((f[I] = aa_local_f<I>(pl, pw, p, n)), ...);
+    ((I < kQT ? (void)(g[I < kQT ? I : 0] = aa_local_g<(I < kQT ? I : 0)>(pl, pw, p, n)) : void()),
+     ...);
+}
+
+// Pull step (W -> N): pl.in is the permuted table (logical q at physical opp(q)), pl.out the
+// identity table of the same copy.
+template <bool HET>
+__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
+    aa_pull_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
+    dependent_launch_prologue();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x < p.nx && y < p.ny;
+    const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
+    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+    const unsigned lanes = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
+    float f[kQ], g[kQT];
+    const int s = x + p.nx * (y + p.ny * z);
+    gather_site<false, StoreF32InPlace, D3Q19>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
+    const Medium md = medium_at<HET>(p, s);
+    collide_on<true, false, D3Q19>(p, md, f, g);
+    const Nbr n = neighbourhood(p, x, y, z);
+    aa_push_all(pl, n, f, g, std::make_integer_sequence<int, kQ>{});
+}
+
+// Local step (N -> W): pl = (in: identity, out: permuted), pw = the permuted table as input.
+template <bool HET>
+__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
+    aa_local_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
+                    const __grid_constant__ Planes pw) {
+    dependent_launch_prologue();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    float f[kQ], g[kQT];
+    const Nbr n = neighbourhood(p, x, y, z);
+    if (n.cross == 0u) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) f[i] = ldp<StoreF32InPlace>(pl, p, i, n.s);
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) g[i] = ldp<StoreF32InPlace>(pl, p, kQ + i, n.s);
+    } else {
+        aa_local_all(pl, pw, p, n, f, g, std::make_integer_sequence<int, kQ>{});
+    }
+    const Medium md = medium_at<HET>(p, n.s);
+    collide_on<true, false, D3Q19>(p, md, f, g);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) stp<StoreF32InPlace>(pl, p, i, n.s, f[i]);
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) stp<StoreF32InPlace>(pl, p, kQ + i, n.s, g[i]);
+}
+
+// N -> W without a collision: f*_j(x) sits in plane j at x + e_j (N) and belongs in plane
+// opp(j) at x (W), while f*_opp(j)(x + e_j) sits in the latter and belongs in the former, so
+// the two are swapped; each pair is swapped once, by the site x of its direction j < opp(j).
+// Crossing directions already hold the raw value where W wants it.  Pure data movement.
+// pl.out: the identity plane table of the copy.
+template <int J>
+__device__ __forceinline__ void aa_swap_f(const Planes& pl, const Nbr& n) {
+    if constexpr (J < opp19(J)) {
+        constexpr int I = opp19(J);
+        constexpr int ex = ex19(I), ey = ey19(I), ez = ez19(I);
+        const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
+                            axis_cross(ez, n.cross, 16u, 32u);
+        if (cr == 0u) {
+            float* a = static_cast<float*>(pl.out[J]) + n.s + axis_off(ex, n.xm, n.xp) +
+                       axis_off(ey, n.ym, n.yp) + axis_off(ez, n.zm, n.zp);
+            float* b = static_cast<float*>(pl.out[I]) + n.s;
+            const float va = *a, vb = *b;
+            *a = vb;
+            *b = va;
+        }
+    }
+}
+template <int J>
+__device__ __forceinline__ void aa_swap_g(const Planes& pl, const Nbr& n) {
+    if constexpr (J < opp7(J)) {
+        constexpr int I = opp7(J);
+        constexpr int ex = ex7(I), ey = ey7(I), ez = ez7(I);
+        const unsigned cr = axis_cross(ex, n.cross, 1u, 2u) | axis_cross(ey, n.cross, 4u, 8u) |
+                            axis_cross(ez, n.cross, 16u, 32u);
+        if (cr == 0u) {
+            float* a = static_cast<float*>(pl.out[kQ + J]) + n.s + axis_off(ex, n.xm, n.xp) +
+                       axis_off(ey, n.ym, n.yp) + axis_off(ez, n.zm, n.zp);
+            float* b = static_cast<float*>(pl.out[kQ + I]) + n.s;
+            const float va = *a, vb = *b;
+            *a = vb;
+            *b = va;
+        }
+    }
+}
+template <int... J>
+__device__ __forceinline__ void aa_swap_all(const Planes& pl, const Nbr& n,
+                                            std::integer_sequence<int, J...>) {
+    (aa_swap_f<J>(pl, n), ...);
+    ((J < kQT ? aa_swap_g<(J < kQT ? J : 0)>(pl, n) : void()), ...);
+}
+
+__global__ void __launch_bounds__(kBlock) aa_normalize_kernel(const __grid_constant__ KParams p,
+                                                              const __grid_constant__ Planes pl) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const Nbr n = neighbourhood(p, x, y, z);
+    aa_swap_all(pl, n, std::make_integer_sequence<int, kQ>{});
+}
+
 // Batched step: one flat grid over the blocks of many lattices.  blk_lat[b] names the lattice
 // of block b; the lattice's parameters and planes are read in place through the read-only
 // cache (uniform over the block).  A block covers `rows` consecutive z-planes of one
@@ -1363,6 +1551,8 @@ cudaError_t with_storage(int storage, Fn&& fn) {
 // ---- launch wrappers ---------------------------------------------------------------------------
 int reduction_blocks() { return kRedBlocks; }
 
+int aa_swapped_plane(int q) { return q < kQ ? opp19(q) : kQ + opp7(q - kQ); }
+
 int block_x(int nx, int block_threads) { return block_x_of(nx, block_threads); }
 
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
@@ -1432,6 +1622,25 @@ cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, bool p
                      : (outflow ? step_kernel<false, true, S> : step_kernel<false, false, S>);
         return launch_kernel(pdl, k, grid, block, 0, st, p, pl);
     });
+}
+
+cudaError_t launch_aa_step(const KParams& p, bool local, const Planes& pl, const Planes& pw,
+                           bool pdl, cudaStream_t st) {
+    dim3 grid, block;
+    site_grid(p, &grid, &block);
+    const bool het = p.phi_field != nullptr;
+    if (local)
+        return launch_kernel(pdl, het ? aa_local_kernel<true> : aa_local_kernel<false>, grid, block,
+                             0, st, p, pl, pw);
+    return launch_kernel(pdl, het ? aa_pull_kernel<true> : aa_pull_kernel<false>, grid, block, 0,
+                         st, p, pl);
+}
+
+cudaError_t launch_aa_normalize(const KParams& p, const Planes& pl, cudaStream_t st) {
+    dim3 grid, block;
+    site_grid(p, &grid, &block);
+    aa_normalize_kernel<<<grid, block, 0, st>>>(p, pl);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_macros(const KParams& p, bool outflow, const Planes& pl, float* rho, float* u,

@@ -115,3 +115,27 @@ def test_relaxation_rate_bound(gb):
     pb = dict(nx=4, ny=4, nz=4, mapping="lattice", nu_e=0.1, alpha_f=-0.0, Pr=-1.0)
     with pytest.raises(gb.LbmError):
         gb.derive_lattice(pb)
+
+
+def test_aa_scheme_resolution_and_footprint(gb):
+    """The AA scheme applies to FP32, D3Q19 lattices without outflow, node walls or the
+    enthalpy model and is rejected elsewhere; LBM_SCHEME_AUTO derives as ping-pong (the
+    device-memory test that may switch it to AA happens at lbm_create); an AA lattice holds
+    one population copy instead of two (26 planes of sq = ceil(ns / 64) * 64 floats fewer)."""
+    from lbm_inputs import channel_problem
+
+    cav = cavity_problem(20, Ra=1e4, Da=1e-2, phi=0.6)
+    assert gb.derive_lattice(dict(cav, scheme="aa"))["scheme"] == 1
+    assert gb.derive_lattice(dict(cav, scheme="auto"))["scheme"] == 0
+    assert gb.derive_lattice(dict(cav, scheme="pingpong"))["scheme"] == 0
+    assert gb.derive_lattice(dict(cav, scheme="auto", storage="bf16"))["scheme"] == 0
+    ch = channel_problem(32, 8, 4)
+    assert gb.derive_lattice(dict(ch, scheme="auto"))["scheme"] == 0
+    for bad in (dict(ch, scheme="aa"), dict(cav, scheme="aa", storage="fp16"),
+                dict(cav, scheme="aa", q=15)):
+        with pytest.raises(gb.LbmError):
+            gb.derive_lattice(bad)
+    ns = 20 ** 3
+    sq = (ns + 63) // 64 * 64
+    assert gb.footprint(dict(cav, scheme="pingpong")) - gb.footprint(dict(cav, scheme="aa")) \
+        == 26 * 4 * sq
