@@ -122,21 +122,28 @@ static_assert(ex19(opp19(13)) == -ex19(13) && ez19(opp19(13)) == -ez19(13), "opp
 // formats hold it divided by the weight, (f - w_i rho0) / w_i and (g - omega_i sigma T0) /
 // omega_i, so that every plane carries values of the order of the Mach number.  Arithmetic is
 // FP32 in every case; 16-bit values are rounded to nearest on store.
+// kStrided: plane q is addressed as plane 0 + q * sq (the planes of a copy are contiguous)
+// instead of through its own pointer.  Fewer pointer loads from the parameter block (which go
+// through the address-divergence pipe) for more integer adds; the 16-bit step measured 13 %
+// faster, FP32 the same, so only the 16-bit formats use it.
 struct StoreF32 {
     using T = float;
     static constexpr bool kScaled = false;
+    static constexpr bool kStrided = false;
     static __device__ __forceinline__ float ld(const T* q) { return __ldg(q); }
     static __device__ __forceinline__ void st(T* q, float v) { *q = v; }
 };
 struct StoreF16 {
     using T = __half;
     static constexpr bool kScaled = true;
+    static constexpr bool kStrided = true;
     static __device__ __forceinline__ float ld(const T* q) { return __half2float(__ldg(q)); }
     static __device__ __forceinline__ void st(T* q, float v) { *q = __float2half_rn(v); }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
     static constexpr bool kScaled = true;
+    static constexpr bool kStrided = true;
     static __device__ __forceinline__ float ld(const T* q) { return __bfloat162float(__ldg(q)); }
     static __device__ __forceinline__ void st(T* q, float v) { *q = __float2bfloat16_rn(v); }
 };
@@ -152,14 +159,25 @@ __device__ __forceinline__ float plane_inv_scale(const KParams& p, int q) {
     if constexpr (!S::kScaled) return 1.0f;
     else return q < kQ ? 1.0f / w19(q) : (q == kQ ? p.iom0 : p.iom1);
 }
+// Start of plane q of the planes being read / written.
+template <class S>
+__device__ __forceinline__ const typename S::T* plane_in(const Planes& pl, const KParams& p, int q) {
+    if constexpr (S::kStrided) return static_cast<const typename S::T*>(pl.in[0]) + q * p.sq;
+    else return static_cast<const typename S::T*>(pl.in[q]);
+}
+template <class S>
+__device__ __forceinline__ typename S::T* plane_out(const Planes& pl, const KParams& p, int q) {
+    if constexpr (S::kStrided) return static_cast<typename S::T*>(pl.out[0]) + q * p.sq;
+    else return static_cast<typename S::T*>(pl.out[q]);
+}
 // Deviation of plane q at site index idx of the planes being read / written.
 template <class S>
 __device__ __forceinline__ float ldp(const Planes& pl, const KParams& p, int q, int idx) {
-    return S::ld(static_cast<const typename S::T*>(pl.in[q]) + idx) * plane_scale<S>(p, q);
+    return S::ld(plane_in<S>(pl, p, q) + idx) * plane_scale<S>(p, q);
 }
 template <class S>
 __device__ __forceinline__ void stp(const Planes& pl, const KParams& p, int q, int idx, float v) {
-    S::st(static_cast<typename S::T*>(pl.out[q]) + idx, v * plane_inv_scale<S>(p, q));
+    S::st(plane_out<S>(pl, p, q) + idx, v * plane_inv_scale<S>(p, q));
 }
 // D3Q7 population i at site idx as the deviation g_i - omega_i sigma T0.  The 16-bit formats
 // store (g_i - omega_i sigma T_x) / omega_i against the site's own temperature T_x, whose
@@ -174,7 +192,7 @@ __device__ __forceinline__ float ldg_dev(const Planes& pl, const KParams& p, int
         // repeats this arithmetic and must give the same bits
         const float sc = i == 0 ? p.om0 : p.om1;
         return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx),
-                                       S::ld(static_cast<const typename S::T*>(pl.in[kQ + i]) + idx)));
+                                       S::ld(plane_in<S>(pl, p, kQ + i) + idx)));
     }
 }
 // Stores post-collision g' (deviation from omega_i sigma T0) of a site whose temperature
@@ -186,8 +204,7 @@ __device__ __forceinline__ void stg_dev(const Planes& pl, const KParams& p, int 
         stp<S>(pl, p, kQ + i, idx, v);
     } else {
         const float isc = i == 0 ? p.iom0 : p.iom1;
-        S::st(static_cast<typename S::T*>(pl.out[kQ + i]) + idx,
-              __fmaf_rn(v, isc, -__fmul_rn(p.sigma, dT)));
+        S::st(plane_out<S>(pl, p, kQ + i) + idx, __fmaf_rn(v, isc, -__fmul_rn(p.sigma, dT)));
     }
 }
 
@@ -998,6 +1015,7 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
 struct StoreF32InPlace {  // FP32 loads through the coherent path: the copy is written in place
     using T = float;
     static constexpr bool kScaled = false;
+    static constexpr bool kStrided = false;  // the plane tables are permuted
     static __device__ __forceinline__ float ld(const T* q) { return *q; }
     static __device__ __forceinline__ void st(T* q, float v) { *q = v; }
 };
