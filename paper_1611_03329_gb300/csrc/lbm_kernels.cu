@@ -390,12 +390,13 @@ __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& 
 
 // The x-face rule of a y/z-interior warp after its unconditional loads: a lane on a
 // non-periodic x face (cxm: x-low, cxp: x-high) replaces the populations that cross it.  `lanes`
-// names the lanes that call it together.
+// names the lanes that call it together; oym, oyp, ozm, ozp are the site offsets of the pull
+// sources of velocities with e_y = +1, -1 and e_z = +1, -1 (wrapped across periodic faces).
 template <bool OUTF, class S, class L>
 __device__ __forceinline__ void x_face_fixup(const Planes& pl, const KParams& p, int x, int y,
                                              int z, int s, unsigned lanes, bool cxm, bool cxp,
-                                             float* f, float* g) {
-    const int nx = p.nx, nxy = p.nx * p.ny;
+                                             int oym, int oyp, int ozm, int ozp, float* f,
+                                             float* g) {
     if (!__any_sync(lanes, cxm || cxp)) return;  // interior warp
     if (cxm) {
         // x-low face: wall or velocity face (an outflow is only allowed on x-high)
@@ -432,7 +433,8 @@ __device__ __forceinline__ void x_face_fixup(const Planes& pl, const KParams& p,
 #pragma unroll
             for (int i = 0; i < L::kQ; ++i) {
                 if (L::ex(i) != -1) continue;
-                float inner = ldp<S>(pl, p, i, s - (L::ey(i) * nx + L::ez(i) * nxy));
+                float inner = ldp<S>(pl, p, i, s + axis_off(L::ey(i), oym, oyp) +
+                                                   axis_off(L::ez(i), ozm, ozp));
                 float old = __ldg(pl.hin + L::slot(i) * p.nyz + yz);
                 f[i] = p.out_a * old + p.out_b * inner;
             }
@@ -459,10 +461,18 @@ __device__ __forceinline__ void x_face_fixup(const Planes& pl, const KParams& p,
 }
 
 
-// Pull for a warp whose sites all lie inside the y and z ranges (y, z neighbours need no
-// rule): unconditional loads with per-lane x offsets, then, only in a warp that holds an
-// x-face site, the x-face rule for the velocities that cross it.  With no x-face lane this is
-// the interior path.
+// Whether the y and z neighbours of a site need no face rule: they lie inside the ranges, or
+// across a periodic face (faces are periodic in pairs), where the fast pull wraps the offset.
+__device__ __forceinline__ bool yz_fast(const KParams& p, int y, int z) {
+    const bool y_ok = (y > 0 && y < p.ny - 1) || (p.per_mask & 12u) == 12u;
+    const bool z_ok = (z > 0 && z < p.nz - 1) || (p.per_mask & 48u) == 48u;
+    return y_ok && z_ok;
+}
+
+// Pull for a warp whose sites all satisfy yz_fast (y, z neighbours need no rule; the y and z
+// offsets are uniform over the warp): unconditional loads with per-lane x offsets, then, only
+// in a warp that holds an x-face site, the x-face rule for the velocities that cross it.  With
+// no x-face lane this is the interior path.
 template <bool OUTF, class S, class L = D3Q19>
 __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
                                                    int z, int s, unsigned lanes, float* f,
@@ -472,13 +482,20 @@ __device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KPara
     bool cxm = false, cxp = false;
     if (x == 0) { if (p.per_mask & 1u) xm = nx - 1; else { xm = 0; cxm = true; } }
     if (x == nx - 1) { if (p.per_mask & 2u) xp = 1 - nx; else { xp = 0; cxp = true; } }
+    // y and z source offsets, wrapped on periodic faces (the only faces yz_fast lets through)
+    const int ym = y == 0 ? nx * (p.ny - 1) : -nx;
+    const int yp = y == p.ny - 1 ? -nx * (p.ny - 1) : nx;
+    const int zm = z == 0 ? nxy * (p.nz - 1) : -nxy;
+    const int zp = z == p.nz - 1 ? -nxy * (p.nz - 1) : nxy;
 #pragma unroll
     for (int i = 0; i < L::kQ; ++i)
-        f[i] = ldp<S>(pl, p, i, s + axis_off(L::ex(i), xm, xp) - (L::ey(i) * nx + L::ez(i) * nxy));
+        f[i] = ldp<S>(pl, p, i, s + axis_off(L::ex(i), xm, xp) + axis_off(L::ey(i), ym, yp) +
+                                    axis_off(L::ez(i), zm, zp));
 #pragma unroll
     for (int i = 0; i < kQT; ++i)
-        g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) - (ey7(i) * nx + ez7(i) * nxy));
-    x_face_fixup<OUTF, S, L>(pl, p, x, y, z, s, lanes, cxm, cxp, f, g);
+        g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) + axis_off(ey7(i), ym, yp) +
+                                        axis_off(ez7(i), zm, zp));
+    x_face_fixup<OUTF, S, L>(pl, p, x, y, z, s, lanes, cxm, cxp, ym, yp, zm, zp, f, g);
 }
 
 // ---- collision -------------------------------------------------------------------------------
@@ -980,8 +997,7 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     const bool valid = x < p.nx && y < p.ny;
     const unsigned nb = (NEE && valid) ? nee_bits(p, x, y, z) : 0u;  // node-wall site
     const bool streams = valid && nb == 0u;
-    const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
-    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !streams);
+    const bool warp_yz_in = __all_sync(0xffffffffu, yz_fast(p, y, z) || !streams);
     const unsigned lanes = __ballot_sync(0xffffffffu, streams);
     if (!valid) return;
     float f[L::kQ], g[kQT];
@@ -1092,8 +1108,7 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     const bool valid = x < p.nx && y < p.ny;
-    const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
-    const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+    const bool warp_yz_in = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
     const unsigned lanes = __ballot_sync(0xffffffffu, valid);
     if (!valid) return;
     float f[kQ], g[kQT];
@@ -1209,12 +1224,10 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     const int y = (rest % gy) * by + ty;
     const int z0 = (rest / gy) * rows;
     const bool valid = x < p.nx && y < p.ny;
-    const bool y_in = y > 0 && y < p.ny - 1;
     for (int r = 0; r < rows; ++r) {
         const int z = z0 + r;
         if (z >= p.nz) break;  // uniform over the block
-        const bool yz_in = y_in && z > 0 && z < p.nz - 1;
-        const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+        const bool warp_yz_in = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
         // every lane of the warp reaches the two votes above; only the valid lanes go on, so
         // the votes inside the site update name exactly those lanes
         const unsigned lanes = __ballot_sync(0xffffffffu, valid);

@@ -145,8 +145,11 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
     using C = TmaCfg<S>;
     using T = typename S::T;
     const bool valid = y < p.ny;  // x < nx: nx is a multiple of 64
+    // staged boxes do not wrap: only rows strictly inside the y and z ranges use them; the
+    // global-memory path takes the wider yz_fast set on its fast branch
     const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
     const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
+    const bool warp_fast = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
     const unsigned lanes = __ballot_sync(0xffffffffu, valid);
     const bool xface = x == 0 || x == p.nx - 1;
     const bool periodic_x_face = (p.per_mask & 3u) && __any_sync(0xffffffffu, valid && xface);
@@ -154,7 +157,7 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
     if (!warp_yz_in || periodic_x_face) {
-        gather_site<OUTF, S, D3Q19>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
+        gather_site<OUTF, S, D3Q19>(pl, p, x, y, z, s, warp_fast, lanes, f, g);
     } else {
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
@@ -174,7 +177,9 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
                 g[j] = v * plane_scale<S>(p, kQ + j);
             }
         }
-        x_face_fixup<OUTF, S, D3Q19>(pl, p, x, y, z, s, lanes, x == 0, x == p.nx - 1, f, g);
+        const int nxy = p.nx * p.ny;
+        x_face_fixup<OUTF, S, D3Q19>(pl, p, x, y, z, s, lanes, x == 0, x == p.nx - 1, -p.nx, p.nx,
+                                     -nxy, nxy, f, g);
     }
     finish_site<HET, OUTF, S, false, D3Q19>(pl, p, x, y, z, s, f, g);
 }
