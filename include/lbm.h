@@ -266,6 +266,22 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g);
  * 15, full values); either pointer may be NULL.  Synchronises. */
 lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* g);
 
+/* Raw state I/O (checkpoint / restart, and a lossless host round trip of the state).  The
+ * state blob holds a 128-byte header (magic "LBMSTATE", version, the lattice extents, flow
+ * lattice, storage format, scheme and step count) followed by the populations of the current
+ * copy exactly as stored (the Q + 7 planes of sq = ceil(ns / 64) * 64 elements each, in the
+ * storage format, FP32 deviations or 16-bit scaled deviations), the FP32 temperature plane of
+ * the 16-bit formats (ns floats) and the outflow history (6 x ny x nz floats) when the
+ * lattice has them.  lbm_state_bytes gives its size.  No conversion runs on either side: one
+ * asynchronous copy per region on the context's stream.  The host buffer (pinned memory
+ * gives full copy bandwidth) must stay valid and unchanged until the next synchronising call.
+ * lbm_load_state accepts only a blob of a context with the same extents, flow lattice,
+ * storage format and scheme (LBM_EINVAL otherwise, nothing changed); it restores the step
+ * count.  An AA context saves after rearranging an odd-step copy (see LBM_SCHEME_AA). */
+lbm_status lbm_state_bytes(const lbm_ctx* ctx, unsigned long long* bytes);
+lbm_status lbm_save_state(lbm_ctx* ctx, void* host, unsigned long long bytes);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* host, unsigned long long bytes);
+
 /* Macroscopic fields at the current time, computed from the streamed populations exactly
  * as the step does: rho (Eq. 25), u (Eqs. 27-28), T (Eq. 39).  Host pointers: rho and T
  * ns floats, u 3 x ns floats; any may be NULL.  Synchronises. */

@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "lbm_batch_set_block", "lbm_batch_last_error", "lbm_batch_destroy", "lbm_footprint",
     "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_poll",
     "lbm_server_clock", "lbm_server_destroy", "lbm_server_set_fill", "lbm_set_step_kernel",
-    "lbm_get_step_kernel",
+    "lbm_get_step_kernel", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
 )
 
 # Population schemes (LBM_SCHEME_*).
@@ -165,6 +165,9 @@ def lib():
                                      C.c_double]
         L.lbm_step.argtypes = [vp, C.c_int]
         L.lbm_set_step_kernel.argtypes = [vp, C.c_int]
+        L.lbm_state_bytes.argtypes = [vp, C.POINTER(C.c_ulonglong)]
+        L.lbm_save_state.argtypes = [vp, vp, C.c_ulonglong]
+        L.lbm_load_state.argtypes = [vp, vp, C.c_ulonglong]
         L.lbm_get_step_kernel.argtypes = [vp]
         L.lbm_init_equilibrium.argtypes = [vp, dp, dp, C.c_double]
         L.lbm_set_populations.argtypes = [vp, dp, dp]
@@ -319,6 +322,32 @@ class Lattice:
 
     def sync(self):
         self._check(lib().lbm_sync(self._h), "lbm_sync")
+
+    def state_bytes(self) -> int:
+        n = C.c_ulonglong()
+        self._check(lib().lbm_state_bytes(self._h, C.byref(n)), "lbm_state_bytes")
+        return int(n.value)
+
+    def save_state(self, out: Optional[np.ndarray] = None, sync: bool = True) -> np.ndarray:
+        """The raw state blob (lbm_save_state) into `out` (a C-contiguous uint8 array of at
+        least state_bytes(), ideally pinned) or a new array."""
+        n = self.state_bytes()
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size >= n
+        self._check(lib().lbm_save_state(self._h, out.ctypes.data_as(C.c_void_p), out.size),
+                    "lbm_save_state")
+        if sync:
+            self.sync()
+        return out
+
+    def load_state(self, blob: np.ndarray, sync: bool = True):
+        """Restore a blob of save_state (lbm_load_state); asynchronous unless `sync`."""
+        assert blob.dtype == np.uint8 and blob.flags.c_contiguous
+        self._check(lib().lbm_load_state(self._h, blob.ctypes.data_as(C.c_void_p), blob.size),
+                    "lbm_load_state")
+        if sync:
+            self.sync()
 
     def set_step_kernel(self, kernel: str):
         """Select the step kernel: "plain" (one thread per site) or "tma" (populations staged

@@ -927,6 +927,100 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
     return LBM_OK;
 }
 
+// ---- raw state I/O -------------------------------------------------------------------------
+namespace {
+struct StateHeader {  // 128 bytes at the start of a state blob
+    char magic[8];    // "LBMSTATE"
+    int version;      // 1
+    int nx, ny, nz;
+    int q, storage, scheme;
+    long long steps;
+    unsigned long long pop_bytes, tplane_bytes, hist_bytes;
+    char reserved[56];
+};
+static_assert(sizeof(StateHeader) == 128, "state header size");
+
+StateHeader state_header(const lbm_ctx* c) {
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "LBMSTATE", 8);
+    h.version = 1;
+    h.nx = c->prm.nx;
+    h.ny = c->prm.ny;
+    h.nz = c->prm.nz;
+    h.q = flow_q(c);
+    h.storage = c->prm.storage;
+    h.scheme = c->lat.scheme;
+    h.steps = c->steps;
+    h.pop_bytes = (unsigned long long)(flow_q(c) + lbm::kQT) * (unsigned long long)c->sq * c->elem;
+    h.tplane_bytes = c->tplane[0] ? sizeof(float) * (unsigned long long)c->ns : 0ull;
+    h.hist_bytes = c->outflow ? sizeof(float) * lbm::kOutSlots * (unsigned long long)c->nyz : 0ull;
+    return h;
+}
+}  // namespace
+
+lbm_status lbm_state_bytes(const lbm_ctx* c, unsigned long long* bytes) {
+    if (!c || !bytes) return LBM_EINVAL;
+    const StateHeader h = state_header(c);
+    *bytes = sizeof(StateHeader) + h.pop_bytes + h.tplane_bytes + h.hist_bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* host, unsigned long long bytes) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    const StateHeader h = state_header(c);
+    if (!host || bytes < sizeof(h) + h.pop_bytes + h.tplane_bytes + h.hist_bytes)
+        return fail(c, LBM_EINVAL, "state buffer missing or smaller than lbm_state_bytes");
+    if ((st = aa_settle(c)) != LBM_OK) return st;
+    char* out = static_cast<char*>(host);
+    std::memcpy(out, &h, sizeof(h));
+    out += sizeof(h);
+    LBM_CUDA(cudaMemcpyAsync(out, c->pop[c->cur], h.pop_bytes, cudaMemcpyDeviceToHost, c->stream));
+    out += h.pop_bytes;
+    if (h.tplane_bytes) {
+        LBM_CUDA(cudaMemcpyAsync(out, c->tplane[c->cur], h.tplane_bytes, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        out += h.tplane_bytes;
+    }
+    if (h.hist_bytes)
+        LBM_CUDA(cudaMemcpyAsync(out, c->hist[c->cur], h.hist_bytes, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* host, unsigned long long bytes) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    const StateHeader mine = state_header(c);
+    StateHeader h;
+    if (!host || bytes < sizeof(h)) return fail(c, LBM_EINVAL, "state buffer missing");
+    std::memcpy(&h, host, sizeof(h));
+    if (std::memcmp(h.magic, mine.magic, 8) != 0 || h.version != mine.version)
+        return fail(c, LBM_EINVAL, "not a state blob of this library version");
+    if (h.nx != mine.nx || h.ny != mine.ny || h.nz != mine.nz || h.q != mine.q ||
+        h.storage != mine.storage || h.scheme != mine.scheme || h.pop_bytes != mine.pop_bytes ||
+        h.tplane_bytes != mine.tplane_bytes || h.hist_bytes != mine.hist_bytes)
+        return fail(c, LBM_EINVAL, "state blob of a different lattice, format or scheme");
+    if (bytes < sizeof(h) + h.pop_bytes + h.tplane_bytes + h.hist_bytes)
+        return fail(c, LBM_EINVAL, "state buffer shorter than its header says");
+    const char* in = static_cast<const char*>(host) + sizeof(h);
+    LBM_CUDA(cudaMemcpyAsync(c->pop[c->cur], in, h.pop_bytes, cudaMemcpyHostToDevice, c->stream));
+    in += h.pop_bytes;
+    if (h.tplane_bytes) {
+        LBM_CUDA(cudaMemcpyAsync(c->tplane[c->cur], in, h.tplane_bytes, cudaMemcpyHostToDevice,
+                                 c->stream));
+        in += h.tplane_bytes;
+    }
+    if (h.hist_bytes)
+        LBM_CUDA(cudaMemcpyAsync(c->hist[c->cur], in, h.hist_bytes, cudaMemcpyHostToDevice,
+                                 c->stream));
+    c->steps = h.steps;
+    c->have_prev = false;
+    c->aa_phase = 0;
+    return LBM_OK;
+}
+
 lbm_status lbm_macros_device(lbm_ctx* c, float* rho, float* u, float* T) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
