@@ -39,7 +39,9 @@ typedef enum {
     LBM_ENOMEM = 2,    /* device allocation failed; the context is unusable */
     LBM_ECUDA = 3,     /* a CUDA call failed (sticky, see lbm_last_error) */
     LBM_EUNSTABLE = 4, /* a reduction found NaN or Inf in the state */
-    LBM_ESTATE = 5     /* call not allowed in the context's current state */
+    LBM_ESTATE = 5,    /* call not allowed in the context's current state */
+    LBM_ETIMEOUT = 6   /* a bounded device-side wait ran out and the step stopped early
+                          (sticky, see LBM_KERNEL_TMA) */
 } lbm_status;
 
 /* Flow boundary kinds (per face). */
@@ -237,8 +239,11 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  *                     a few tiles ahead, one box per population plane (shifted by -e_i) into
  *                     shared memory.  Needs the D3Q19 lattice, nx % 64 == 0, ny >= 4, no node
  *                     walls and no enthalpy model.  A staged load that does not complete within
- *                     one second stops the step early; the next lbm_sync then returns LBM_ECUDA
- *                     (sticky). */
+ *                     one second stops the step early; the next lbm_sync then returns
+ *                     LBM_ETIMEOUT (sticky).  For tests of that path, the environment variable
+ *                     LBM_TMA_EXPECT_EXTRA (bytes, read by lbm_set_step_kernel) makes every
+ *                     stage wait for that many bytes more than its loads bring, so that its
+ *                     waits run out. */
 #define LBM_KERNEL_PLAIN 0
 #define LBM_KERNEL_TMA 1
 

@@ -19,7 +19,7 @@ from . import build as _build
 
 Q19, Q7 = 19, 7
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = range(6)
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_ETIMEOUT = range(7)
 FLOW_PERIODIC, FLOW_WALL, FLOW_VELOCITY, FLOW_OUTFLOW = range(4)
 HEAT_PERIODIC, HEAT_ADIABATIC, HEAT_DIRICHLET, HEAT_OUTFLOW = range(4)
 MAP_CAVITY, MAP_CHANNEL, MAP_LATTICE = range(3)

@@ -56,6 +56,7 @@ struct lbm_ctx {
     lbm::TmaMaps tmaps[2];
     int tma_blocks = 0;
     int* tma_err = nullptr;
+    int tma_extra_tx = 0;  // test hook: bytes each stage waits for beyond its loads
 };
 
 namespace {
@@ -318,6 +319,7 @@ const char* lbm_status_string(lbm_status s) {
         case LBM_ECUDA: return "CUDA error";
         case LBM_EUNSTABLE: return "non-finite state";
         case LBM_ESTATE: return "call not allowed in the current state";
+        case LBM_ETIMEOUT: return "a device-side wait timed out";
     }
     return "unknown status";
 }
@@ -798,7 +800,8 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         int nxt = c->cur ^ 1;
         if (c->step_kernel == LBM_KERNEL_TMA)
             LBM_CUDA(lbm::launch_step_tma(c->kp, c->outflow, c->pl[c->cur], c->tmaps[c->cur],
-                                          c->tma_blocks, c->tma_err, c->pdl, c->stream));
+                                          c->tma_blocks, c->tma_extra_tx, c->tma_err, c->pdl,
+                                          c->stream));
         else
             LBM_CUDA(lbm::launch_step(c->kp, c->outflow, c->pl[c->cur], c->pdl, c->stream));
         c->cur = nxt;
@@ -815,8 +818,8 @@ lbm_status lbm_sync(lbm_ctx* c) {
         int flag = 0;
         LBM_CUDA(cudaMemcpy(&flag, c->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (flag) {
-            c->sticky = LBM_ECUDA;
-            return fail(c, LBM_ECUDA, "a staged population load did not complete within 1 s");
+            c->sticky = LBM_ETIMEOUT;
+            return fail(c, LBM_ETIMEOUT, "a staged population load did not complete within 1 s");
         }
     }
     return LBM_OK;
@@ -1155,6 +1158,11 @@ lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
         LBM_CUDA(cudaStreamSynchronize(c->stream));
     }
     c->tma_blocks = blocks;
+    c->tma_extra_tx = 0;
+    if (const char* v = std::getenv("LBM_TMA_EXPECT_EXTRA")) {
+        const int extra = std::atoi(v);
+        if (extra > 0 && extra <= 4096) c->tma_extra_tx = extra;
+    }
     c->step_kernel = kernel;
     return LBM_OK;
 }

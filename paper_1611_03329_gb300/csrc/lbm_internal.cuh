@@ -139,14 +139,15 @@ struct TmaMaps {
 };
 struct TmaGrid {
     int tiles_x, tiles_y, ntiles;
+    int extra_tx;  // bytes a stage waits for beyond its loads (0; > 0 only to test timeouts)
 };
 // Sets the kernel's shared-memory limit and returns its persistent grid (blocks) and its
 // dynamic shared memory per block.
 cudaError_t tma_prepare(const KParams& p, bool outflow, int* blocks, int* smem_bytes);
 // One time step reading the copy that `m` and pl.in describe; *err is set to 1 when a staged
-// load does not arrive within one second (the blocks then stop early).
+// load does not arrive within one second (the blocks then stop early).  extra_tx: see TmaGrid.
 cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, const TmaMaps& m,
-                            int blocks, int* err, bool pdl, cudaStream_t st);
+                            int blocks, int extra_tx, int* err, bool pdl, cudaStream_t st);
 
 int reduction_blocks();
 // Physical plane of logical D3Q19 + D3Q7 plane q in the AA scheme's swapped layout: the plane

@@ -120,7 +120,7 @@ __device__ __forceinline__ void tma_issue(const KParams& p, const TmaGrid& tg, i
 #pragma unroll
     for (int j = 0; j < kQT; ++j)
         bytes += kTY * (ex7(j) ? 72 : 64) * (unsigned)(sizeof(T) + (S::kScaled ? 4 : 0));
-    bar_expect(b, bytes);
+    bar_expect(b, bytes + (unsigned)tg.extra_tx);
 #pragma unroll
     for (int i = 0; i < kQ; ++i)
         tma4(stage + i * C::kPlane, ex19(i) ? &m.pop72 : &m.pop64, box_x(x0, ex19(i)),
@@ -290,8 +290,9 @@ cudaError_t tma_prepare(const KParams& p, bool outflow, int* blocks, int* smem_b
 }
 
 cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, const TmaMaps& m,
-                            int blocks, int* err, bool pdl, cudaStream_t st) {
+                            int blocks, int extra_tx, int* err, bool pdl, cudaStream_t st) {
     TmaGrid tg;
+    tg.extra_tx = extra_tx;
     tg.tiles_x = p.nx / kTX;
     tg.tiles_y = (p.ny + kTY - 1) / kTY;
     tg.ntiles = tg.tiles_x * tg.tiles_y * p.nz;

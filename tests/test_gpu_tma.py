@@ -128,3 +128,30 @@ def test_selection_rules(gb):
     lat.set_step_kernel("tma")
     lat.set_step_kernel("plain")
     assert lat.step_kernel == "plain"
+
+
+def test_wait_timeout_is_reported(gb, monkeypatch):
+    """Failure detection of the bounded waits: with every stage told to wait for 16 bytes its
+    loads never bring (LBM_TMA_EXPECT_EXTRA), each wait runs out after about a second, the
+    kernel sets its flag and stops, lbm_sync reports LBM_ETIMEOUT and the context refuses
+    further steps.  Nothing faults or hangs: a new context on the same device steps normally
+    and matches the plain kernel."""
+    from paper_1611_03329_gb300 import LbmError
+
+    pb = channel_problem(64, 8, 6)
+    monkeypatch.setenv("LBM_TMA_EXPECT_EXTRA", "16")
+    lat = gb.Lattice(pb)
+    lat.set_step_kernel("tma")
+    monkeypatch.delenv("LBM_TMA_EXPECT_EXTRA")
+    lat.step(1)
+    with pytest.raises(LbmError) as ei:
+        lat.sync()
+    assert ei.value.status == gb.LBM_ETIMEOUT
+    with pytest.raises(LbmError):
+        lat.step(1)
+    lat.close()
+    ok, ref = gb.Lattice(pb), gb.Lattice(pb)
+    ok.set_step_kernel("tma")
+    ok.step(3)
+    ref.step(3)
+    assert np.array_equal(ok.populations()[0], ref.populations()[0])
