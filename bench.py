@@ -37,6 +37,7 @@ WORKLOADS = {
     "cavity256": (256, 256, 256),
     "batch64": (0, 0, 0),  # 64 cavities of edge 32..128 in one batched launch per step
     "serve": (0, 0, 0),    # Poisson stream of cavity and channel solves, continuous batching
+    "sweep": (0, 0, 0),    # precision sweep: heterogeneous cavities to steady state, 3 formats
 }
 
 
@@ -318,6 +319,67 @@ def run_batch(args, gb, torch):
         "path": "lbm_step per lattice, lattices one after another"}, block, unstable
 
 
+# ---- precision sweep -------------------------------------------------------------------------
+def _field_err(a, ref):
+    """max|a - ref| / max|ref| (field-normalised, as in the parity tests)."""
+    import numpy as np
+
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = float(np.max(np.abs(ref)))
+    return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - ref))) / (scale or 1.0)
+
+
+def run_sweep(args, gb):
+    """Heterogeneous porous cavities (edge E, Ra in {1e4, 1e5, 1e6}, Da in {1e-4, 1e-2}, the
+    seeded porosity field of mean 0.6) with FP32, FP16- and BF16-deviation storage, each run
+    to the steady-state residual r <= 1e-7 (k = 100 steps) or the step cap; Nu_3D of the hot
+    wall and the errors of the 16-bit runs against the FP32 run of the same case."""
+    import numpy as np
+
+    from lbm_inputs import cavity_problem, porosity_field
+
+    edge, cap, tol, chunk = args.sweep_edge, args.max_steps, 1e-7, 2000
+    phi = porosity_field(edge, edge, edge, seed=20161110).astype("float32")
+    cases = []
+    t_all = time.perf_counter()
+    for Ra in args.sweep_ra:
+        for Da in args.sweep_da:
+            if (Ra, Da) in args.sweep_skip:
+                continue
+            pb = cavity_problem(edge, Ra=Ra, Da=Da, phi=0.6, Pr=0.71, phi_field=phi,
+                                phi_ref=0.6)
+            ref = None
+            for storage in ("fp32", "fp16", "bf16"):
+                lat = gb.Lattice(dict(pb, storage=storage))
+                t0 = time.perf_counter()
+                steps, ru, rT = 0, float("inf"), float("inf")
+                while steps < cap:
+                    n = min(chunk, cap - steps)
+                    lat.step(n - 100)
+                    lat.residual()  # snapshot of step steps + n - 100
+                    lat.step(100)
+                    ru, rT = lat.residual()
+                    steps += n
+                    if max(ru, rT) <= tol:
+                        break
+                wall = time.perf_counter() - t0
+                _, u, T = lat.macros()
+                nu = lat.nusselt(0)[0]
+                rec = {"Ra": Ra, "Da": Da, "storage": storage, "steps": steps,
+                       "r_u": ru, "r_T": rT, "converged": max(ru, rT) <= tol,
+                       "Nu_hot": round(nu, 6), "wall_s": round(wall, 2),
+                       "mlups": round(edge ** 3 * steps / wall / 1e6, 1)}
+                if storage == "fp32":
+                    ref = (u, T, nu)
+                else:
+                    rec.update({"err_u_vs_fp32": _field_err(u, ref[0]),
+                                "err_T_vs_fp32": _field_err(T, ref[1]),
+                                "err_Nu_vs_fp32": abs(nu - ref[2]) / abs(ref[2])})
+                cases.append(rec)
+                lat.close()
+    return cases, time.perf_counter() - t_all
+
+
 # ---- serving workload ------------------------------------------------------------------------
 def _serve_stream(gb, reqs, budget, chunk, tol, max_steps, alone, fill=0):
     """Submit each request at its arrival time and run the serving loop; with alone=True each
@@ -405,6 +467,22 @@ def run_ours(args):
     dist = _init_dist(ws)
     gb.build.build()
     torch.cuda.set_device(0)
+    if args.workload == "sweep":
+        cases, wall = run_sweep(args, gb)
+        if rank != 0:
+            return 0
+        line = {"metric": "steady-state Nu and 16-bit storage error (precision sweep)",
+                "value": None, "unit": None, "n_gpus": ws, "steps": None, "warmup": 0,
+                "higher_is_better": None, "dtype": "f32-math, fp32 / fp16 / bf16 storage",
+                "data": "synthetic",
+                "config": {"workload": f"porous cavities {args.sweep_edge}^3, seeded porosity "
+                                       "field (mean 0.6, std 0.05, [0.4, 0.9]), Pr 0.71, "
+                                       f"Ra in {args.sweep_ra}, Da in {args.sweep_da}"
+                                       + (f", without {args.sweep_skip}" if args.sweep_skip else ""),
+                           "tol": 1e-7, "k": 100, "max_steps": args.max_steps},
+                "wall_s": round(wall, 1), "cases": cases}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "serve":
         mixed, solo, n, tol, max_steps, uncapped = run_serve(args, gb)
         if rank != 0:
@@ -587,7 +665,15 @@ def main(argv=None):
     ap.add_argument("--kernel", choices=("plain", "tma"), default="plain",
                     help="step kernel: per-thread loads, or populations staged by TMA")
     ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")
-    ap.add_argument("--max-steps", type=int, default=20000, help="serve: step limit")
+    ap.add_argument("--max-steps", type=int, default=20000, help="serve / sweep: step limit")
+    ap.add_argument("--sweep-edge", type=int, default=128, help="sweep: cavity edge")
+    ap.add_argument("--sweep-ra", type=lambda t: [float(v) for v in t.split(",")],
+                    default=[1e4, 1e5, 1e6], help="sweep: Rayleigh numbers (comma list)")
+    ap.add_argument("--sweep-da", type=lambda t: [float(v) for v in t.split(",")],
+                    default=[1e-4, 1e-2], help="sweep: Darcy numbers (comma list)")
+    ap.add_argument("--sweep-skip", type=lambda t: [tuple(float(x) for x in c.split(":"))
+                                                    for c in t.split(",") if c],
+                    default=[], help="sweep: Ra:Da cases to leave out (comma list)")
     ap.add_argument("--fill", type=int, default=8_000_000,
                     help="serve: cap on the lattice sites admitted at once (0: none)")
     args = ap.parse_args(argv)
