@@ -338,7 +338,7 @@ def run_sweep(args, gb):
 
     from lbm_inputs import cavity_problem, porosity_field
 
-    edge, cap, tol, chunk = args.sweep_edge, args.max_steps, 1e-7, 2000
+    edge, cap, tol, chunk = args.sweep_edge, args.max_steps or 200000, 1e-7, 2000
     phi = porosity_field(edge, edge, edge, seed=20161110).astype("float32")
     cases = []
     t_all = time.perf_counter()
@@ -443,7 +443,7 @@ def run_serve(args, gb):
     from lbm_inputs import serving_mix
 
     reqs = serving_mix(args.requests, seed=5)
-    tol, max_steps, chunk = 1e-6, args.max_steps, 100
+    tol, max_steps, chunk = 1e-6, args.max_steps or 50000, 100
     mixed, _ = _serve_stream(gb, reqs, 0, chunk, tol, max_steps, alone=False, fill=args.fill)
     uncapped = None
     if args.fill:
@@ -479,7 +479,7 @@ def run_ours(args):
                                        "field (mean 0.6, std 0.05, [0.4, 0.9]), Pr 0.71, "
                                        f"Ra in {args.sweep_ra}, Da in {args.sweep_da}"
                                        + (f", without {args.sweep_skip}" if args.sweep_skip else ""),
-                           "tol": 1e-7, "k": 100, "max_steps": args.max_steps},
+                           "tol": 1e-7, "k": 100, "max_steps": args.max_steps or 200000},
                 "wall_s": round(wall, 1), "cases": cases}
         print(json.dumps(line), flush=True)
         return 0
@@ -665,7 +665,8 @@ def main(argv=None):
     ap.add_argument("--kernel", choices=("plain", "tma"), default="plain",
                     help="step kernel: per-thread loads, or populations staged by TMA")
     ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")
-    ap.add_argument("--max-steps", type=int, default=20000, help="serve / sweep: step limit")
+    ap.add_argument("--max-steps", type=int, default=None,
+                    help="serve / sweep: step limit per solve (default 50000 / 200000)")
     ap.add_argument("--sweep-edge", type=int, default=128, help="sweep: cavity edge")
     ap.add_argument("--sweep-ra", type=lambda t: [float(v) for v in t.split(",")],
                     default=[1e4, 1e5, 1e6], help="sweep: Rayleigh numbers (comma list)")
