@@ -353,8 +353,12 @@ def run_sweep(args, gb):
                 lat = gb.Lattice(dict(pb, storage=storage))
                 t0 = time.perf_counter()
                 steps, ru, rT = 0, float("inf"), float("inf")
-                while steps < cap:
-                    n = min(chunk, cap - steps)
+                # with --sweep-match, the 16-bit runs stop where the FP32 run converged
+                run_cap = cap
+                if storage != "fp32" and args.sweep_match and ref is not None and ref[3]:
+                    run_cap = ref[4]
+                while steps < run_cap:
+                    n = min(chunk, run_cap - steps)
                     lat.step(n - 100)
                     lat.residual()  # snapshot of step steps + n - 100
                     lat.step(100)
@@ -370,7 +374,7 @@ def run_sweep(args, gb):
                        "Nu_hot": round(nu, 6), "wall_s": round(wall, 2),
                        "mlups": round(edge ** 3 * steps / wall / 1e6, 1)}
                 if storage == "fp32":
-                    ref = (u, T, nu)
+                    ref = (u, T, nu, rec["converged"], steps)
                 else:
                     rec.update({"err_u_vs_fp32": _field_err(u, ref[0]),
                                 "err_T_vs_fp32": _field_err(T, ref[1]),
@@ -675,6 +679,8 @@ def main(argv=None):
     ap.add_argument("--sweep-skip", type=lambda t: [tuple(float(x) for x in c.split(":"))
                                                     for c in t.split(",") if c],
                     default=[], help="sweep: Ra:Da cases to leave out (comma list)")
+    ap.add_argument("--sweep-match", action="store_true",
+                    help="sweep: stop the 16-bit runs at the step count of the converged FP32 run")
     ap.add_argument("--fill", type=int, default=8_000_000,
                     help="serve: cap on the lattice sites admitted at once (0: none)")
     args = ap.parse_args(argv)
