@@ -18,7 +18,9 @@
 //
 // Every wait on an mbarrier is bounded by the global timer.  One that runs out sets an error
 // flag and stops the warp; the loader then stops issuing and waits (bounded again) for the
-// loads it has in flight before it leaves.
+// loads it has in flight before it leaves.  TmaGrid::extra_tx (zero in normal use) adds bytes
+// to every stage's expected count that no load brings, so that a test can make the waits run
+// out without any fault.
 #define LBM_DEVICE_ONLY
 #include "lbm_kernels.cu"
 
