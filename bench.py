@@ -312,8 +312,8 @@ def run_batch(args, gb, torch):
         except gb.LbmError:
             unstable += 1
     batch.close()
-    bytes_site = 26 * 2 * gb.STORAGE_BYTES[args.storage]
-    achieved = bytes_site * sites / (ms / args.steps * 1e-3) / 1e9
+    step_bytes = sum(gb.algorithmic_bytes_per_site(pb) * l.ns for pb, l in zip(pbs, lats))
+    achieved = step_bytes / (ms / args.steps * 1e-3) / 1e9
     return mlups, ms, sites, achieved, clk.summary(), {
         "value": round(mlups1, 2), "unit": UNIT, "steps": n1,
         "path": "lbm_step per lattice, lattices one after another"}, block, unstable

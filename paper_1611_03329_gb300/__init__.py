@@ -573,10 +573,12 @@ def medium_args(pb: dict) -> dict:
 
 def algorithmic_bytes_per_site(pb: dict) -> int:
     """Bytes one time step must move per site: the Q + 7 populations (26 for D3Q19, 22 for
-    D3Q15) read and written in the storage format (4 or 2 bytes each), plus the FP32
-    porosity of a heterogeneous medium."""
+    D3Q15) read and written in the storage format (4 or 2 bytes each), the FP32 temperature
+    plane of the 16-bit formats (read and written: the thermal populations are stored against
+    it), plus the FP32 porosity of a heterogeneous medium."""
     npop = (15 if int(pb.get("q", 19)) == 15 else 19) + 7
-    return (npop * 2 * STORAGE_BYTES[pb.get("storage", "fp32")]
+    storage = pb.get("storage", "fp32")
+    return (npop * 2 * STORAGE_BYTES[storage] + (8 if storage != "fp32" else 0)
             + (4 if pb.get("phi_field") is not None else 0))
 
 
