@@ -624,6 +624,11 @@ def run_ours(args):
                                  else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
+                     "limiter": ("memory latency at the HBM roofline's side (ncu: DRAM traffic = "
+                                 "algorithmic bytes, long-scoreboard stalls first)"
+                                 if args.storage == "fp32" else
+                                 "instruction issue (ncu on the channel: issue 72 %, DRAM 22 %; "
+                                 "profiles/step_kernel_channel_256x64x64_fp16.md)"),
                      "kernel": ("aa_pull_kernel<true> / aa_local_kernel<true> alternating (AA, one "
                                 "copy in place, porosity field)" if aa else
                                 ("tma_step_kernel" if args.kernel == "tma" else "step_kernel") +
