@@ -624,8 +624,9 @@ def run_ours(args):
                                  else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
-                     "limiter": ("memory latency at the HBM roofline's side (ncu: DRAM traffic = "
-                                 "algorithmic bytes, long-scoreboard stalls first)"
+                     "limiter": ("memory latency (ncu: DRAM traffic equals the algorithmic "
+                                 "bytes, long-scoreboard stalls first) and the drain of each "
+                                 "launch (profiles/step_kernel_channel_256x64x64.md)"
                                  if args.storage == "fp32" else
                                  "instruction issue (ncu on the channel: issue 72 %, DRAM 22 %; "
                                  "profiles/step_kernel_channel_256x64x64_fp16.md)"),
