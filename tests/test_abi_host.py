@@ -139,3 +139,19 @@ def test_aa_scheme_resolution_and_footprint(gb):
     sq = (ns + 63) // 64 * 64
     assert gb.footprint(dict(cav, scheme="pingpong")) - gb.footprint(dict(cav, scheme="aa")) \
         == 26 * 4 * sq
+
+
+def test_algorithmic_bytes_per_site(gb):
+    """The roofline's bytes per site update: the populations read and written in their storage
+    format, the FP32 temperature plane of the 16-bit formats (read and written), and the FP32
+    porosity of a heterogeneous medium."""
+    import numpy as np
+    from lbm_inputs import channel_problem
+
+    ch = channel_problem(16, 8, 4)
+    assert gb.algorithmic_bytes_per_site(ch) == 26 * 4 * 2
+    assert gb.algorithmic_bytes_per_site(dict(ch, storage="fp16")) == 26 * 2 * 2 + 8
+    assert gb.algorithmic_bytes_per_site(dict(ch, storage="bf16")) == 26 * 2 * 2 + 8
+    assert gb.algorithmic_bytes_per_site(dict(ch, q=15)) == 22 * 4 * 2
+    het = cavity_problem(8, Ra=1e4, Da=1e-2, phi=0.6, phi_field=np.full((8, 8, 8), 0.6))
+    assert gb.algorithmic_bytes_per_site(het) == 26 * 4 * 2 + 4
