@@ -282,7 +282,10 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* g);
  * gives full copy bandwidth) must stay valid and unchanged until the next synchronising call.
  * lbm_load_state accepts only a blob of a context with the same extents, flow lattice,
  * storage format and scheme (LBM_EINVAL otherwise, nothing changed); it restores the step
- * count.  An AA context saves after rearranging an odd-step copy (see LBM_SCHEME_AA). */
+ * count.  The parameters and the medium (lbm_set_medium) are not in the blob: a restart
+ * context is created from the same lbm_params and given the same medium.  An AA context saves
+ * after rearranging an odd-step copy (see LBM_SCHEME_AA).  Errors: LBM_EINVAL (NULL or short
+ * buffer, a foreign or truncated blob; nothing changed), LBM_ECUDA. */
 lbm_status lbm_state_bytes(const lbm_ctx* ctx, unsigned long long* bytes);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* host, unsigned long long bytes);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* host, unsigned long long bytes);
@@ -454,7 +457,8 @@ lbm_status lbm_get_lattice(const lbm_ctx* ctx, lbm_lattice* out);
 /* Number of time steps taken since create / init. */
 long long lbm_steps_done(const lbm_ctx* ctx);
 
-/* Block the host until the context's stream is idle. */
+/* Block the host until the context's stream is idle.  Returns LBM_ETIMEOUT (sticky) when a
+ * bounded device-side wait of a TMA step ran out since the last check (see LBM_KERNEL_TMA). */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
 /* Text of the last error of the context (never NULL; "" when none).  Owned by ctx. */
