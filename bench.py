@@ -63,10 +63,11 @@ def _workload_text(workload, storage, q=19):
             f"{storage.upper()} storage")
 
 
-def _config(workload="channel", storage="fp32", extra=None, q=19):
+def _config(workload="channel", storage="fp32", extra=None, q=19, scheme="pingpong"):
     if workload == "batch64":
         cfg = {"workload": _workload_text(workload, storage), "lattices": 64,
-               "storage": f"{storage}-deviation", "scheme": "ping-pong pull, batched",
+               "storage": f"{storage}-deviation",
+               "scheme": ("AA in place" if scheme == "aa" else "ping-pong pull") + ", batched",
                "seed": 2016, "l2": "inputs larger than L2 (GBs of populations), no flush"}
         cfg.update(extra or {})
         return cfg
@@ -275,7 +276,7 @@ def run_batch(args, gb, torch):
     steps), against the same lattices solved one at a time (each lattice's own launches)."""
     from lbm_inputs import batch_cavities
 
-    pbs = [dict(pb, storage=args.storage) for pb in batch_cavities(64)]
+    pbs = [dict(pb, storage=args.storage, scheme=args.scheme) for pb in batch_cavities(64)]
     stream = torch.cuda.Stream()
     lats = [gb.Lattice(pb, stream=stream.cuda_stream) for pb in pbs]
     sites = sum(l.ns for l in lats)
@@ -520,9 +521,10 @@ def run_ours(args):
                 "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math",
                           "bf16": "bf16-storage/f32-math"}[args.storage],
                 "data": "synthetic",
-                "config": _config("batch64", args.storage, {"sites": sites, "block_threads": block[0],
-                                                            "planes_per_block": block[1],
-                                                            "unstable_lattices": unstable}),
+                "config": _config("batch64", args.storage, scheme=args.scheme,
+                                  extra={"sites": sites, "block_threads": block[0],
+                                         "planes_per_block": block[1],
+                                         "unstable_lattices": unstable}),
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak[0],
                              "unit": "GB/s", "frac": round(achieved / peak[0], 4),
                              "traffic": None, "peak_source": peak[1]},

@@ -147,7 +147,8 @@ typedef struct lbm_params {
  *                        that reads and writes its own site only.  Half the population memory,
  *                        the same bytes moved per step.  Needs FP32 storage, the D3Q19 lattice,
  *                        no outflow face, no node walls and no enthalpy model; such contexts
- *                        run outside lbm_batch / lbm_server and with LBM_KERNEL_PLAIN.  After an
+ *                        run with LBM_KERNEL_PLAIN, in lbm_batch (their own groups) but not in
+ *                        lbm_server.  After an
  *                        odd number of steps, the first call that reads the state (populations,
  *                        macros, Nusselt, sums, residual) first rearranges the copy (a pure
  *                        permutation, no arithmetic) into the layout a pull step reads.
@@ -350,7 +351,8 @@ lbm_status lbm_residual_noalloc(const float* u, const float* T, const float* u_p
 
 /* ---- batched launches -----------------------------------------------------------------
  * A batch advances many independent lattices (contexts) with one fused launch per time step
- * and kernel variant (storage format, uniform or field medium, outflow or not): the step of
+ * and kernel variant (storage format, uniform or field medium, outflow or not, ping-pong or
+ * AA scheme; an AA lattice takes its own pull or local step in the shared launch): the step of
  * Sec. 3 at every site of every lattice, exactly as lbm_step computes it, so a lattice's
  * results are identical alone and in a batch.  Multi-step sequences are recorded once per
  * step count as a CUDA graph and replayed.  The contexts keep owning their state; after
@@ -370,7 +372,9 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 /* Time the batched step at 32, 64, 128 and 256 threads per block and 1, 2 and 4 z-planes
  * per block and keep the fastest shape (written to *block_threads and *rows when non-NULL).
  * The timed launches write only the buffers that the next step overwrites, so the lattices'
- * state is unchanged.  Synchronises. */
+ * state is unchanged; AA lattices, updated in place, are therefore not timed, and a batch of
+ * AA lattices only takes 32 threads x 4 planes (measured fastest for them) without timing.
+ * Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows);
 
 /* Set the block shape of the batched step: threads (32, 64, 128 or 256) and z-planes per

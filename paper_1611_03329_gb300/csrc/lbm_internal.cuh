@@ -159,6 +159,10 @@ int aa_swapped_plane(int q);
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
                               bool enthalpy, int flip, cudaStream_t st);
+// One time step of the AA lattices of a batch group (FP32, D3Q19, no outflow): lattice l runs a
+// pull step when (cur ^ flip) is 0, else a local step; cur holds its AA phase.
+cudaError_t launch_batch_aa(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
+                            int block_threads, int rows, bool het, int flip, cudaStream_t st);
 // x-extent of a site-kernel block for a lattice of width nx within block_threads threads.
 int block_x(int nx, int block_threads);  // number of partial sums the reductions write (<= partials size)
 

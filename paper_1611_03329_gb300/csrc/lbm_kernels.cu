@@ -1098,38 +1098,26 @@ __device__ __forceinline__ void aa_local_all(const Planes& pl, const Planes& pw,
      ...);
 }
 
-// Pull step (W -> N): pl.in is the permuted table (logical q at physical opp(q)), pl.out the
-// identity table of the same copy.
+// Pull-step update of one valid site (W -> N): pl.in is the permuted table (logical q at
+// physical opp(q)), pl.out the identity table of the same copy; warp_fast and lanes as in
+// step_kernel.
 template <bool HET>
-__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
-    aa_pull_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
-    dependent_launch_prologue();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    const bool valid = x < p.nx && y < p.ny;
-    const bool warp_yz_in = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
-    const unsigned lanes = __ballot_sync(0xffffffffu, valid);
-    if (!valid) return;
+__device__ __forceinline__ void aa_pull_site(const KParams& p, const Planes& pl, int x, int y,
+                                             int z, bool warp_fast, unsigned lanes) {
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
-    gather_site<false, StoreF32InPlace, D3Q19>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
+    gather_site<false, StoreF32InPlace, D3Q19>(pl, p, x, y, z, s, warp_fast, lanes, f, g);
     const Medium md = medium_at<HET>(p, s);
     collide_on<true, false, D3Q19>(p, md, f, g);
     const Nbr n = neighbourhood(p, x, y, z);
     aa_push_all(pl, n, f, g, std::make_integer_sequence<int, kQ>{});
 }
 
-// Local step (N -> W): pl = (in: identity, out: permuted), pw = the permuted table as input.
+// Local-step update of one valid site (N -> W): pl = (in: identity, out: permuted), pw = the
+// permuted table as input.
 template <bool HET>
-__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
-    aa_local_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
-                    const __grid_constant__ Planes pw) {
-    dependent_launch_prologue();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
+__device__ __forceinline__ void aa_local_site(const KParams& p, const Planes& pl, const Planes& pw,
+                                              int x, int y, int z) {
     float f[kQ], g[kQT];
     const Nbr n = neighbourhood(p, x, y, z);
     if (n.cross == 0u) {
@@ -1146,6 +1134,32 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     for (int i = 0; i < kQ; ++i) stp<StoreF32InPlace>(pl, p, i, n.s, f[i]);
 #pragma unroll
     for (int i = 0; i < kQT; ++i) stp<StoreF32InPlace>(pl, p, kQ + i, n.s, g[i]);
+}
+
+// Pull step over one lattice (3D launch as step_kernel).
+template <bool HET>
+__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
+    aa_pull_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
+    dependent_launch_prologue();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = x < p.nx && y < p.ny;
+    const bool warp_fast = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
+    const unsigned lanes = __ballot_sync(0xffffffffu, valid);
+    if (valid) aa_pull_site<HET>(p, pl, x, y, z, warp_fast, lanes);
+}
+
+// Local step over one lattice.
+template <bool HET>
+__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
+    aa_local_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl,
+                    const __grid_constant__ Planes pw) {
+    dependent_launch_prologue();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x < p.nx && y < p.ny) aa_local_site<HET>(p, pl, pw, x, y, z);
 }
 
 // N -> W without a collision: f*_j(x) sits in plane j at x + e_j (N) and belongs in plane
@@ -1237,6 +1251,40 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
             gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
             finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
         }
+    }
+}
+
+// Batched AA step: one flat grid over the blocks of the AA lattices of a group (FP32, D3Q19,
+// no outflow), each lattice in its own phase.  Lattice L runs a pull step when
+// (L->cur ^ flip) is 0 (its copy in the swapped layout) and a local step otherwise; L->pl[0] =
+// (in: permuted, out: identity) and L->pl[1] = (in: identity, out: permuted) are the plane
+// tables of its single copy, and pl[0] doubles as the local step's permuted input table.  The
+// block -> site mapping is that of batch_step_kernel.
+template <bool HET>
+__global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
+    batch_aa_kernel(const BatchLattice* __restrict__ tab,
+                    const unsigned short* __restrict__ blk_lat, int flip, int rows) {
+    const BatchLattice* L = tab + __ldg(blk_lat + blockIdx.x);
+    const KParams& p = L->p;
+    const bool local = ((L->cur ^ flip) & 1) != 0;  // uniform over the block
+    const int bx = L->bx, gx = L->gx, gy = L->gy;
+    const int loc = (int)blockIdx.x - L->block_begin;
+    const int by = blockDim.x / bx;
+    const int tx = threadIdx.x & (bx - 1), ty = threadIdx.x / bx;
+    const int bxi = loc % gx, rest = loc / gx;
+    const int x = bxi * bx + tx;
+    const int y = (rest % gy) * by + ty;
+    const int z0 = (rest / gy) * rows;
+    const bool valid = x < p.nx && y < p.ny;
+    for (int r = 0; r < rows; ++r) {
+        const int z = z0 + r;
+        if (z >= p.nz) break;  // uniform over the block
+        // every lane reaches the votes; only the valid lanes update a site
+        const bool warp_fast = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
+        const unsigned lanes = __ballot_sync(0xffffffffu, valid);
+        if (!valid) continue;
+        if (local) aa_local_site<HET>(p, L->pl[1], L->pl[0], x, y, z);
+        else aa_pull_site<HET>(p, L->pl[0], x, y, z, warp_fast, lanes);
     }
 }
 
@@ -1607,6 +1655,14 @@ cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk
             batch_step_kernel<false, false, S><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_batch_aa(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
+                            int block_threads, int rows, bool het, int flip, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (het) batch_aa_kernel<true><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+    else batch_aa_kernel<false><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+    return cudaGetLastError();
 }
 
 // Launch of a step kernel, with programmatic dependent launch when `pdl` is set.
