@@ -10,9 +10,9 @@
  * anchored convective outflow.
  *
  * Conventions shared by every call:
- *  - Every call returns an lbm_status; nothing throws across the ABI.  A CUDA failure is
- *    sticky: once a call returns LBM_ECUDA the context only accepts lbm_destroy,
- *    lbm_last_error and lbm_status_string.
+ *  - Every call returns an lbm_status; nothing throws across the ABI.  A CUDA failure and a
+ *    timed-out device wait are sticky: once a call returns LBM_ECUDA or LBM_ETIMEOUT the
+ *    context only accepts lbm_destroy, lbm_last_error and lbm_status_string.
  *  - Field arrays are x-fastest: site s = x + nx*(y + ny*z); population arrays are
  *    q-major, f[i*ns + s] with ns = nx*ny*nz and the velocity order of Eq. 19 (D3Q19) and
  *    of the first seven columns of Eq. 12 (D3Q7).  Vector fields are [3][ns].
