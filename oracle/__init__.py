@@ -79,6 +79,8 @@ def lib():
         L.orc_steps_done.restype = C.c_long
         L.orc_steps_done.argtypes = [C.c_void_p]
         L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_gate_margin.argtypes = [C.c_void_p, dp]
+        L.orc_gate_margin_reset.argtypes = [C.c_void_p]
         L.orc_max_threads.restype = C.c_int
         L.orc_sizeof_lattice.restype = C.c_int
         L.orc_tables.argtypes = [dp] * 7
@@ -473,6 +475,18 @@ class Oracle:
     @property
     def steps(self) -> int:
         return int(lib().orc_steps_done(self._h))
+
+    def gate_margin(self) -> np.ndarray:
+        """Enthalpy model: per site, the smallest |f_l - 1/2| the flow gate met in the steps
+        since the last reset (0.5 for a site that stayed in one phase, and everywhere without
+        the model), shaped [z][y][x].  A site whose margin is below the resolution of a
+        lower-precision implementation's f_l may legitimately be gated differently there."""
+        out = np.zeros(self.shape)
+        lib().orc_gate_margin(self._h, _p(out))
+        return out
+
+    def reset_gate_margin(self):
+        lib().orc_gate_margin_reset(self._h)
 
     def macros(self):
         """(rho, u[3], T) at the current time, each shaped [z][y][x]."""

@@ -26,7 +26,10 @@
  *  12. store f*, g* in the other array.
  * With the enthalpy model (App. B) step 2 becomes En_e = sum g (Eq. B7) with T and f_l from
  * Eqs. B8-B9, the flow is collided only where f_l >= 0.5 (elsewhere f rests at f_eq(rho, 0)
- * and u = 0), and step 11 uses n_eq of Eq. B6 with zeta_alpha from Eq. B11.
+ * and u = 0; the FP64 value of f_l decides), and step 11 uses n_eq of Eq. B6 with
+ * zeta_alpha from Eq. B11.  The oracle records, per site, how close f_l came to the gate
+ * (orc_gate_margin), so that a check against a lower-precision implementation can tell the
+ * sites where the two may legitimately decide differently.
  *
  * Boundary rules (the paper uses non-equilibrium extrapolation; this oracle follows the
  * halfway rules that the GPU library implements, Eqs. 10 and 35 in pull form):
@@ -477,6 +480,9 @@ typedef struct {
     double* pfn;
     double* pgn;
     long steps;
+    /* enthalpy model: per site, the smallest |f_l - 1/2| met by the flow gate in the steps
+     * since the last orc_gate_margin_reset (0.5 for a site that never left a pure phase) */
+    double* gate_margin;
 } orc_state;
 
 /* Directions that enter the domain across the x-high face (e_x = -1): 2, 8, 10, 12 and 14
@@ -681,9 +687,8 @@ static void collide_site(const orc_lattice* L, const double* f, const double* g,
     orc_force(u, G, phi, L->nu, K, Fphi, F); /* Eq. 4 */
 
     double m[QMAX], feq[QMAX], meq[QMAX], S[QMAX], ms[QMAX];
-    /* the liquid-fraction gate is a discrete decision: taken on the FP32 value of f_l, the
-     * precision the GPU kernel decides in */
-    if (L->enthalpy && (L->flow_off || (float)fl < 0.5f)) {
+    /* the liquid-fraction gate of the flow (f_l >= 1/2 flows), decided on the FP64 value */
+    if (L->enthalpy && (L->flow_off || fl < 0.5)) {
         /* solid (or no flow): the flow is not collided; the populations rest at f_eq(rho, 0) */
         u[0] = u[1] = u[2] = 0.0;
         double zero[3] = {0.0, 0.0, 0.0};
@@ -838,6 +843,10 @@ void* orc_create(const orc_lattice* L, const double* phi_field) {
         S->phi_site = (double*)malloc(sizeof(double) * S->ns);
         memcpy(S->phi_site, phi_field, sizeof(double) * S->ns);
     }
+    if (L->enthalpy) {
+        S->gate_margin = (double*)malloc(sizeof(double) * S->ns);
+        for (long s = 0; s < S->ns; ++s) S->gate_margin[s] = 0.5;
+    }
     if (has_outflow(L)) {
         long nyz = (long)L->ny * L->nz;
         S->pf = (double*)calloc(5 * nyz, sizeof(double));
@@ -860,6 +869,7 @@ void orc_destroy(void* h) {
     free(S->pg);
     free(S->pfn);
     free(S->pgn);
+    free(S->gate_margin);
     free(S);
 }
 
@@ -956,6 +966,14 @@ void orc_step(void* h, int nsteps) {
                     }
                     gather_site(S, x, y, z, f, g, 1);
                     medium_at(S, s, &phi, &K, &Fphi);
+                    if (S->gate_margin && !L->flow_off) {
+                        /* distance of this step's f_l (Eqs. B7-B9) from the gate at 1/2 */
+                        double En = 0.0, T, fl;
+                        for (int i = 0; i < Q7; ++i) En += g[i];
+                        orc_enthalpy_state(L, phi, En, &T, &fl);
+                        double d = fabs(fl - 0.5);
+                        if (d < S->gate_margin[s]) S->gate_margin[s] = d;
+                    }
                     orc_collide_site(L, f, g, phi, K, Fphi, zeta_alpha_at(L, phi), fo, go, NULL);
                     for (int i = 0; i < L->q; ++i) S->fn[(long)i * S->ns + s] = fo[i];
                     for (int i = 0; i < Q7; ++i) S->gn[(long)i * S->ns + s] = go[i];
@@ -999,6 +1017,19 @@ void orc_macros(void* h, double* rho, double* u, double* T) {
 }
 
 long orc_steps_done(void* h) { return ((orc_state*)h)->steps; }
+
+/* Enthalpy model: copy the per-site gate margins (ns doubles, see orc_state.gate_margin) to
+ * out; 0.5 everywhere without the model or with flow_off (no gate). */
+void orc_gate_margin(void* h, double* out) {
+    orc_state* S = (orc_state*)h;
+    for (long s = 0; s < S->ns; ++s) out[s] = S->gate_margin ? S->gate_margin[s] : 0.5;
+}
+
+void orc_gate_margin_reset(void* h) {
+    orc_state* S = (orc_state*)h;
+    if (S->gate_margin)
+        for (long s = 0; s < S->ns; ++s) S->gate_margin[s] = 0.5;
+}
 
 void orc_set_threads(int n) {
 #ifdef _OPENMP

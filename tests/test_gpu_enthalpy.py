@@ -1,4 +1,19 @@
-"""The enthalpy-based phase-change model (App. B) on the GPU against the FP64 oracle."""
+"""The enthalpy-based phase-change model (App. B) on the GPU against the FP64 oracle.
+
+The flow is collided where the liquid fraction f_l (Eq. B9) is at least 1/2.  The oracle
+decides that on the FP64 value of f_l, the FP32 kernel on its FP32 value; the two may differ
+only at a site whose f_l lies within the FP32 resolution of f_l from 1/2.  That resolution,
+for one step from the same stored state: the seven g_i are stored in FP32 (relative rounding
+u = 2^-24 each), summed in FP32 (three levels of a pairwise tree) and mapped through
+f_l = (En - En_s) / (En_l - En_s) in FP32, so
+    |f_l(FP32) - f_l(exact)| <= (4 u sum|g_i| + u |En_s|) / (En_l - En_s) + 3 u.
+With sum|g_i| <= 3, En_s = 0.5 and En_l - En_s = L_a = 1 (St = 1, c_pl = 1, phi = 1) this is
+below 1.0e-6; the tests use the band GATE_BAND_STEP = 1e-5.  Sites whose oracle margin
+(Oracle.gate_margin) lies inside the band are counted and left out of the comparison; every
+other site is compared at 1e-5.  Runs compared without re-synchronising the two states use
+GATE_BAND_RUN = 1e-4: populations that agree to 1e-5 of max|g| ~ 1.5 give f_l within
+7 x 1.5e-5 ~ 1e-4.
+"""
 
 import numpy as np
 import pytest
@@ -6,6 +21,9 @@ import pytest
 from lbm_inputs import random_macros, uniform
 
 pytestmark = pytest.mark.gpu
+
+GATE_BAND_STEP = 1e-5
+GATE_BAND_RUN = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -45,13 +63,18 @@ def test_single_step_mixed_phases(gb, orc):
     _, ug, Tg = lat.macros()
     _, uo, To = o.macros()
     assert orc.field_error(Tg, To) < 1e-5 and orc.field_error(ug, uo) < 1e-5
+    o.reset_gate_margin()
     lat.step(1)
     o.step(1)
     fa, ga = lat.populations()
     fb, gbo = o.populations()
     w = orc.tables()["w19"].reshape(19, 1, 1, 1)
-    assert np.abs(fa - fb).max() < 1e-5 * np.abs(fb - w).max()
-    assert np.abs(ga - gbo).max() < 1e-5 * np.abs(gbo).max()
+    keep = o.gate_margin() >= GATE_BAND_STEP  # sites whose gate both precisions decide alike
+    near = int((~keep).sum())
+    print(f"single step: {near} of {keep.size} sites within {GATE_BAND_STEP} of f_l = 1/2")
+    assert near <= keep.size // 100
+    assert np.abs(fa - fb)[:, keep].max() < 1e-5 * np.abs(fb - w).max()
+    assert np.abs(ga - gbo)[:, keep].max() < 1e-5 * np.abs(gbo).max()
 
 
 def test_two_region_melting_matches_oracle(gb, orc):
@@ -61,6 +84,7 @@ def test_two_region_melting_matches_oracle(gb, orc):
     lat.step(t)
     o = orc.Oracle(orc.map_problem(pb))
     o.step(t)
+    assert o.gate_margin().min() == 0.5  # no flow (flow_off): no gate, a zero-width band
     _, ug, Tg = lat.macros()
     _, _, To = o.macros()
     assert orc.field_error(Tg, To) < 1e-5
@@ -70,19 +94,57 @@ def test_two_region_melting_matches_oracle(gb, orc):
     assert h == pytest.approx(g.sum(), rel=1e-5)
 
 
-def test_convection_melting_cavity(gb, orc):
+def test_convection_melting_cavity_free_run(gb, orc):
+    """1,300 steps of both sides on their own: the oracle shows that no gate decision of the
+    run comes within GATE_BAND_RUN of 1/2, so both sides gate every site alike and u, T and
+    Nu agree at 1e-5."""
     pb = _convection(16)
+    steps = 1300
     lat = gb.Lattice(pb)
-    lat.step(2000)
+    lat.step(steps)
     o = orc.Oracle(orc.map_problem(pb))
-    o.step(2000)
+    o.step(steps)
+    margin = o.gate_margin().min()
+    assert margin > GATE_BAND_RUN, margin
     _, ug, Tg = lat.macros()
     _, uo, To = o.macros()
-    assert orc.field_error(Tg, To) < 1e-4
-    assert orc.field_error(ug, uo) < 1e-3
+    assert np.abs(uo).max() > 1e-5  # the melt has started to move
+    assert orc.field_error(Tg, To) < 1e-5
+    assert orc.field_error(ug, uo) < 1e-5
     nu_g = lat.nusselt(0)[0]
     nu_o = orc.nusselt(To, 0, 1.0, 16)[0]
-    assert nu_g == pytest.approx(nu_o, rel=1e-4)
+    assert nu_g == pytest.approx(nu_o, rel=1e-5)
+
+
+def test_convection_melting_cavity_every_step(gb, orc):
+    """2,000 steps along the GPU's own trajectory: before each step the oracle takes the
+    GPU's stored populations, then both take one step.  Every site whose oracle f_l lies
+    farther than GATE_BAND_STEP from 1/2 is compared at 1e-5 after every step (the melt
+    front crosses f_l = 1/2 as a plane of 128 cells near steps 1,400-1,500, with a margin of
+    1.2e-5 to 1.9e-5); the near-threshold sites are counted."""
+    pb = _convection(16)
+    lat = gb.Lattice(pb)
+    o = orc.Oracle(orc.map_problem(pb))
+    w = orc.tables()["w19"].reshape(19, 1, 1, 1)
+    near_total, worst_f, worst_g = 0, 0.0, 0.0
+    f, g = lat.populations()
+    for _ in range(2000):
+        o.set_populations(f, g)
+        o.reset_gate_margin()
+        lat.step(1)
+        o.step(1)
+        f, g = lat.populations()
+        fo, go = o.populations()
+        keep = o.gate_margin() >= GATE_BAND_STEP
+        near_total += int((~keep).sum())
+        # until the melt moves, the oracle's f deviations are FP64 round-off of an exact rest
+        # state (~1e-17); the scale floor of 1e-9 compares those steps absolutely at 1e-14
+        worst_f = max(worst_f, np.abs(f - fo)[:, keep].max() / max(np.abs(fo - w).max(), 1e-9))
+        worst_g = max(worst_g, np.abs(g - go)[:, keep].max() / np.abs(go).max())
+    print(f"2000 chained steps: {near_total} near-threshold site-steps, worst f {worst_f:.2e}, "
+          f"g {worst_g:.2e}")
+    assert near_total <= 2 * 128
+    assert worst_f < 1e-5 and worst_g < 1e-5
 
 
 def test_enthalpy_lattice_in_a_batch(gb):

@@ -113,3 +113,28 @@ def test_solid_cells_do_not_flow(orc):
     assert solid.any() and liquid.any()
     assert np.abs(u[:, solid]).max() == 0.0
     assert np.abs(u[:, liquid]).max() > 1e-5
+
+
+def test_gate_margin_records_the_distance_of_f_l_from_one_half(orc):
+    """Oracle.gate_margin: in a closed adiabatic box at rest with a uniform mushy enthalpy
+    (f_l = 0.3 or 0.62 by Eq. B9) nothing changes, so after a step every site's margin is
+    |f_l - 1/2|; phase-pure sites read 0.5; with flow_off there is no gate (0.5)."""
+    pb = dict(nx=4, ny=3, nz=2, mapping="lattice", nu_e=0.1, alpha_f=0.04, enthalpy=True,
+              T_m=0.0, St=1.0, T0=0.0, flow_bc=[1] * 6, heat_bc=[1] * 6)
+    for flow_off in (False, True):
+        lp = orc.map_problem(dict(pb, flow_off=flow_off))
+        Es = lp.sigma_s * lp.c_pl * lp.T_s
+        El = lp.sigma_l * lp.c_pl * lp.T_l + lp.L_a
+        for fl, want in ((0.3, 0.2), (0.62, 0.12), (1.0, 0.5), (0.0, 0.5)):
+            En = Es + fl * (El - Es) + (0.2 if fl == 1.0 else -0.2 if fl == 0.0 else 0.0)
+            o = orc.Oracle(lp)
+            f = np.broadcast_to(orc.feq19(1.0, [0, 0, 0], 1.0)[:, None, None, None],
+                                (19,) + o.shape).copy()
+            g = np.broadcast_to(orc.geq7_enthalpy(lp, En, 0.0, [0, 0, 0])[:, None, None, None],
+                                (7,) + o.shape).copy()
+            o.set_populations(f, g)
+            o.step(1)
+            m = o.gate_margin()
+            assert np.allclose(m, 0.5 if flow_off else want, atol=1e-12), (fl, m.min(), m.max())
+            o.reset_gate_margin()
+            assert (o.gate_margin() == 0.5).all()
