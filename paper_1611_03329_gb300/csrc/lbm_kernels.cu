@@ -284,6 +284,45 @@ __device__ __forceinline__ Medium medium_at(const KParams& p, int s) {
 }
 
 // ---- streaming with boundary rules ------------------------------------------------------------
+// The three value rules of a pull that crosses a face, each written with explicit roundings so
+// that every kernel that inlines them (plain, batched, AA, staged) computes the same bits.
+// Moving wall / velocity inlet (halfway bounce-back with the wall's momentum):
+// f_I = f*_opp(I)(x) + 2 w_I rho0 (e_I . u_w) / c_s^2, u_w the velocity of `face`.
+template <class L, int I>
+__device__ __forceinline__ float bounce_moving(const KParams& p, int face, float bb) {
+    // e_I has components in {-1, 0, 1}: the products are exact, the two sums round in order
+    const float eu = __fadd_rn(__fadd_rn((float)L::ex(I) * p.face_u[face][0],
+                                         (float)L::ey(I) * p.face_u[face][1]),
+                               (float)L::ez(I) * p.face_u[face][2]);
+    return __fmaf_rn(__fmul_rn(6.0f * L::w(I), p.rho0), eu, bb);
+}
+// Convective outflow: p(N-1, t+1) = (p(N-1, t) + U p(N-2, t+1)) / (1 + U) = a old + b inner.
+__device__ __forceinline__ float outflow_blend(const KParams& p, float old, float inner) {
+    return __fmaf_rn(p.out_a, old, __fmul_rn(p.out_b, inner));
+}
+// Pressure anchor of the outlet: the populations set by the outflow rule (`via`) are shifted by
+// w_i (rho0 - rho) / sum(w_i) so that the outlet density is rho0; f holds deviations, so
+// rho0 - rho = -sum f.  With all five entering velocities set by the rule, sum(w_i) = 1/6 on
+// both lattices and the shift is w_i (-6 rho).
+template <class L>
+__device__ __forceinline__ void outflow_anchor(float* f, const bool* via) {
+    float rho = 0.0f, wsum = 0.0f;
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < L::kQ; ++i) {
+        rho += f[i];
+        if (via[i]) {
+            wsum += L::w(i);
+            ++n;
+        }
+    }
+    if (n == 0) return;
+    const float corr = n == 5 ? __fmul_rn(-6.0f, rho) : -rho / wsum;
+#pragma unroll
+    for (int i = 0; i < L::kQ; ++i)
+        if (via[i]) f[i] = __fmaf_rn(L::w(i), corr, f[i]);
+}
+
 // Pull of f_I at site n: the post-collision population at x - e_I, or the wall rule when that
 // source lies outside (a no-slip wall wins over a velocity face, which wins over the outflow).
 template <class L, int I, bool OUTF, class S>
@@ -297,31 +336,15 @@ __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, cons
     const float bb = ldp<S>(pl, p, L::opp(I), n.s);
     if (cr & p.wall_mask) return bb;
     unsigned vm = cr & p.vel_mask;
-    if (vm) {
-        int face = __ffs(vm) - 1;
-        float eu = (float)ex * p.face_u[face][0] + (float)ey * p.face_u[face][1] +
-                   (float)ez * p.face_u[face][2];
-        return bb + 6.0f * L::w(I) * p.rho0 * eu;  // 2 w_i rho0 (e_i . u_w) / c_s^2
-    }
+    if (vm) return bounce_moving<L, I>(p, __ffs(vm) - 1, bb);
     if constexpr (OUTF && ex == -1) {
-        // convective outflow: p(N-1, t+1) = (p(N-1, t) + U p(N-2, t+1)) / (1 + U), with
-        // p(N-2, t+1) pulled at the inner neighbour (same y, z, so the same y/z crossings)
+        // convective outflow with p(N-2, t+1) pulled at the inner neighbour: the source of
+        // x - 1 along -x is x itself, at the same y/z offsets (a y/z face crossed here is a
+        // wall or velocity face, taken above)
         *via = true;
-        float inner;
-        if (cyz == 0u) {
-            inner = ldp<S>(pl, p, I, n.s + oyz);  // source of x-1 along -x is x itself
-        } else {
-            inner = ldp<S>(pl, p, L::opp(I), n.s - 1);
-            unsigned vmi = cyz & p.vel_mask;
-            if (!(cyz & p.wall_mask) && vmi) {
-                int face = __ffs(vmi) - 1;
-                float eu = (float)ex * p.face_u[face][0] + (float)ey * p.face_u[face][1] +
-                           (float)ez * p.face_u[face][2];
-                inner += 6.0f * L::w(I) * p.rho0 * eu;
-            }
-        }
-        float old = __ldg(pl.hin + L::slot(I) * p.nyz + n.y + p.ny * n.z);
-        return p.out_a * old + p.out_b * inner;
+        const float inner = ldp<S>(pl, p, I, n.s + oyz);
+        const float old = __ldg(pl.hin + L::slot(I) * p.nyz + n.y + p.ny * n.z);
+        return outflow_blend(p, old, inner);
     }
     return bb;  // not reached for validated boundary sets
 }
@@ -334,18 +357,17 @@ __device__ __forceinline__ float pull_g(const Planes& pl, const KParams& p, cons
     if (cr == 0u)
         return ldg_dev<S>(pl, p, I, n.s + axis_off(ex, n.xm, n.xp) + axis_off(ey, n.ym, n.yp) +
                      axis_off(ez, n.zm, n.zp));
-    const float bb = ldg_dev<S>(pl, p, opp7(I), n.s);
     const int face = __ffs(cr) - 1;  // a D3Q7 velocity crosses one face at most
     const int kind = p.heat_kind[face];
-    if (kind == 2) return -bb + p.heat_abb[face];  // Dirichlet: anti-bounce-back
     if constexpr (OUTF && ex == -1) {
-        if (kind == 3) {
-            float inner = ldg_dev<S>(pl, p, I, n.s);  // g_I(N-2, t+1) = g*_I(N-1, t)
-            float old = __ldg(pl.hin + 5 * p.nyz + n.y + p.ny * n.z);
-            return p.out_a * old + p.out_b * inner;
+        if (kind == 3) {  // g_I(N-2, t+1) = g*_I(N-1, t)
+            const float inner = ldg_dev<S>(pl, p, I, n.s);
+            return outflow_blend(p, __ldg(pl.hin + 5 * p.nyz + n.y + p.ny * n.z), inner);
         }
     }
-    return bb;  // adiabatic: bounce-back
+    const float bb = ldg_dev<S>(pl, p, opp7(I), n.s);
+    if (kind == 2) return -bb + p.heat_abb[face];  // Dirichlet: anti-bounce-back
+    return bb;                                      // adiabatic: bounce-back
 }
 
 template <class L, bool OUTF, class S, int... I>
@@ -361,7 +383,8 @@ __device__ __forceinline__ void gather_g_bc(float* g, const Planes& pl, const KP
     ((g[I] = pull_g<I, OUTF, S>(pl, p, n)), ...);
 }
 
-// Predicated pull of all populations (any site), with the outflow's pressure anchor.
+// Predicated pull of all populations (any site), with the outflow's pressure anchor.  Used
+// where a site is gathered on its own (macroscopic fields, node walls, AA local steps).
 template <bool OUTF, class S, class L = D3Q19>
 __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& p, const Nbr& n,
                                                float* f, float* g) {
@@ -370,96 +393,69 @@ __device__ __forceinline__ void gather_general(const Planes& pl, const KParams& 
     for (int i = 0; i < L::kQ; ++i) via[i] = false;
     gather_f_bc<L, OUTF, S>(f, via, pl, p, n, std::make_integer_sequence<int, L::kQ>{});
     gather_g_bc<OUTF, S>(g, pl, p, n, std::make_integer_sequence<int, kQT>{});
-    if (OUTF && n.x == p.nx - 1) {
-        // pressure anchor: shift the populations set by the outflow rule by
-        // w_i (rho0 - rho) / sum(w_i) so that the outlet density is rho0
-        float rho = 0.0f, wsum = 0.0f;
-#pragma unroll
-        for (int i = 0; i < L::kQ; ++i) {
-            rho += f[i];
-            if (via[i]) wsum += L::w(i);
-        }
-        if (wsum > 0.0f) {
-            float corr = -rho / wsum;
-#pragma unroll
-            for (int i = 0; i < L::kQ; ++i)
-                if (via[i]) f[i] += L::w(i) * corr;
-        }
-    }
+    if (OUTF && n.x == p.nx - 1) outflow_anchor<L>(f, via);
 }
 
-// The x-face rule of a y/z-interior warp after its unconditional loads: a lane on a
-// non-periodic x face (cxm: x-low, cxp: x-high) replaces the populations that cross it.  `lanes`
-// names the lanes that call it together; oym, oyp, ozm, ozp are the site offsets of the pull
-// sources of velocities with e_y = +1, -1 and e_z = +1, -1 (wrapped across periodic faces).
+// The x-face rule after loads that ignored it (the staged-tile path of the TMA kernel): a lane
+// on a non-periodic x face (cxm: x-low, cxp: x-high) replaces the populations that cross it.
+// `lanes` names the lanes that call it together; oym, oyp, ozm, ozp are the site offsets of
+// the pull sources of velocities with e_y = +1, -1 and e_z = +1, -1.
+template <bool OUTF, class S, class L, int... I>
+__device__ __forceinline__ void x_face_f(const Planes& pl, const KParams& p, int s, bool cxm,
+                                         bool cxp, bool out, int oym, int oyp, int ozm, int ozp,
+                                         int yz, float* f, bool* via,
+                                         std::integer_sequence<int, I...>) {
+    (([&] {
+         if constexpr (L::ex(I) == 1) {
+             if (cxm) {
+                 const float bb = ldp<S>(pl, p, L::opp(I), s);
+                 f[I] = ((p.vel_mask & 1u) && !(p.wall_mask & 1u)) ? bounce_moving<L, I>(p, 0, bb) : bb;
+             }
+         } else if constexpr (L::ex(I) == -1) {
+             if (cxp) {
+                 if (out) {
+                     const float inner = ldp<S>(pl, p, I, s + axis_off(L::ey(I), oym, oyp) +
+                                                              axis_off(L::ez(I), ozm, ozp));
+                     f[I] = outflow_blend(p, __ldg(pl.hin + L::slot(I) * p.nyz + yz), inner);
+                     via[I] = true;
+                 } else {
+                     const float bb = ldp<S>(pl, p, L::opp(I), s);
+                     f[I] = ((p.vel_mask & 2u) && !(p.wall_mask & 2u)) ? bounce_moving<L, I>(p, 1, bb) : bb;
+                 }
+             }
+         }
+     }()),
+     ...);
+}
+
 template <bool OUTF, class S, class L>
 __device__ __forceinline__ void x_face_fixup(const Planes& pl, const KParams& p, int x, int y,
                                              int z, int s, unsigned lanes, bool cxm, bool cxp,
                                              int oym, int oyp, int ozm, int ozp, float* f,
                                              float* g) {
     if (!__any_sync(lanes, cxm || cxp)) return;  // interior warp
-    if (cxm) {
-        // x-low face: wall or velocity face (an outflow is only allowed on x-high)
-        const bool vel = (p.vel_mask & 1u) && !(p.wall_mask & 1u);
+    const bool out = OUTF && !(p.wall_mask & 2u) && !(p.vel_mask & 2u);
+    const int yz = y + p.ny * z;
+    bool via[L::kQ];
 #pragma unroll
-        for (int i = 0; i < L::kQ; ++i) {
-            if (L::ex(i) != 1) continue;
-            float v = ldp<S>(pl, p, L::opp(i), s);
-            if (vel)
-                v += 6.0f * L::w(i) * p.rho0 *
-                     (p.face_u[0][0] + (float)L::ey(i) * p.face_u[0][1] + (float)L::ez(i) * p.face_u[0][2]);
-            f[i] = v;
-        }
+    for (int i = 0; i < L::kQ; ++i) via[i] = false;
+    x_face_f<OUTF, S, L>(pl, p, s, cxm, cxp, out, oym, oyp, ozm, ozp, yz, f, via,
+                         std::make_integer_sequence<int, L::kQ>{});
+    if (OUTF && cxp && out) outflow_anchor<L>(f, via);
+    if (cxm) {  // x-low: wall / velocity face (an outflow is only allowed on x-high)
         const float bb = ldg_dev<S>(pl, p, 2, s);
         g[1] = p.heat_kind[0] == 2 ? -bb + p.heat_abb[0] : bb;
     }
     if (cxp) {
-        const bool wall = p.wall_mask & 2u, vel = p.vel_mask & 2u;
-        if (!OUTF || wall || vel) {
-#pragma unroll
-            for (int i = 0; i < L::kQ; ++i) {
-                if (L::ex(i) != -1) continue;
-                float v = ldp<S>(pl, p, L::opp(i), s);
-                if (vel && !wall)
-                    v += 6.0f * L::w(i) * p.rho0 *
-                         (-p.face_u[1][0] + (float)L::ey(i) * p.face_u[1][1] +
-                          (float)L::ez(i) * p.face_u[1][2]);
-                f[i] = v;
-            }
-        } else {
-            // convective outflow of every -x velocity (their y/z sources are inside), then the
-            // pressure anchor: shift them by w_i (rho0 - rho) / sum(w_i), sum(w_i) = 1/6
-            const int yz = y + p.ny * z;
-#pragma unroll
-            for (int i = 0; i < L::kQ; ++i) {
-                if (L::ex(i) != -1) continue;
-                float inner = ldp<S>(pl, p, i, s + axis_off(L::ey(i), oym, oyp) +
-                                                   axis_off(L::ez(i), ozm, ozp));
-                float old = __ldg(pl.hin + L::slot(i) * p.nyz + yz);
-                f[i] = p.out_a * old + p.out_b * inner;
-            }
-            float rho = 0.0f;
-#pragma unroll
-            for (int i = 0; i < L::kQ; ++i) rho += f[i];
-            const float corr = -6.0f * rho;
-#pragma unroll
-            for (int i = 0; i < L::kQ; ++i)
-                if (L::ex(i) == -1) f[i] += L::w(i) * corr;
-        }
-        const float bb = ldg_dev<S>(pl, p, 1, s);
         const int kind = p.heat_kind[1];
-        if (kind == 2) {
-            g[2] = -bb + p.heat_abb[1];
-        } else if (OUTF && kind == 3) {
-            float inner = ldg_dev<S>(pl, p, 2, s);
-            float old = __ldg(pl.hin + 5 * p.nyz + y + p.ny * z);
-            g[2] = p.out_a * old + p.out_b * inner;
+        if (OUTF && kind == 3) {
+            g[2] = outflow_blend(p, __ldg(pl.hin + 5 * p.nyz + yz), ldg_dev<S>(pl, p, 2, s));
         } else {
-            g[2] = bb;
+            const float bb = ldg_dev<S>(pl, p, 1, s);
+            g[2] = kind == 2 ? -bb + p.heat_abb[1] : bb;
         }
     }
 }
-
 
 // Whether the y and z neighbours of a site need no face rule: they lie inside the ranges, or
 // across a periodic face (faces are periodic in pairs), where the fast pull wraps the offset.
@@ -468,34 +464,154 @@ __device__ __forceinline__ bool yz_fast(const KParams& p, int y, int z) {
     const bool z_ok = (z > 0 && z < p.nz - 1) || (p.per_mask & 48u) == 48u;
     return y_ok && z_ok;
 }
+// Whether no pull of a site crosses a non-periodic face.
+__device__ __forceinline__ bool site_no_cross(const KParams& p, int x, int y, int z) {
+    return yz_fast(p, y, z) && ((x > 0 && x < p.nx - 1) || (p.per_mask & 3u) == 3u);
+}
 
-// Pull for a warp whose sites all satisfy yz_fast (y, z neighbours need no rule; the y and z
-// offsets are uniform over the warp): unconditional loads with per-lane x offsets, then, only
-// in a warp that holds an x-face site, the x-face rule for the velocities that cross it.  With
-// no x-face lane this is the interior path.
-template <bool OUTF, class S, class L = D3Q19>
-__device__ __forceinline__ void gather_yz_interior(const Planes& pl, const KParams& p, int x, int y,
-                                                   int z, int s, unsigned lanes, float* f,
-                                                   float* g) {
+// Source offsets of the six axis directions of a site (wrapped across periodic faces, 0 on a
+// crossed face) and its crossing bits (x-low, x-high, y-low, y-high, z-low, z-high).
+struct AxisOff {
+    int xm, xp, ym, yp, zm, zp;
+    unsigned cross;
+};
+__device__ __forceinline__ AxisOff axis_offsets(const KParams& p, int x, int y, int z) {
     const int nx = p.nx, nxy = p.nx * p.ny;
-    int xm = -1, xp = 1;  // source offsets of +x and -x velocities
-    bool cxm = false, cxp = false;
-    if (x == 0) { if (p.per_mask & 1u) xm = nx - 1; else { xm = 0; cxm = true; } }
-    if (x == nx - 1) { if (p.per_mask & 2u) xp = 1 - nx; else { xp = 0; cxp = true; } }
-    // y and z source offsets, wrapped on periodic faces (the only faces yz_fast lets through)
-    const int ym = y == 0 ? nx * (p.ny - 1) : -nx;
-    const int yp = y == p.ny - 1 ? -nx * (p.ny - 1) : nx;
-    const int zm = z == 0 ? nxy * (p.nz - 1) : -nxy;
-    const int zp = z == p.nz - 1 ? -nxy * (p.nz - 1) : nxy;
+    AxisOff o;
+    o.cross = 0u;
+    o.xm = -1;
+    o.xp = 1;
+    o.ym = -nx;
+    o.yp = nx;
+    o.zm = -nxy;
+    o.zp = nxy;
+    if (x == 0) { if (p.per_mask & 1u) o.xm = nx - 1; else { o.xm = 0; o.cross |= 1u; } }
+    if (x == nx - 1) { if (p.per_mask & 2u) o.xp = 1 - nx; else { o.xp = 0; o.cross |= 2u; } }
+    if (y == 0) { if (p.per_mask & 4u) o.ym = nx * (p.ny - 1); else { o.ym = 0; o.cross |= 4u; } }
+    if (y == p.ny - 1) { if (p.per_mask & 8u) o.yp = -nx * (p.ny - 1); else { o.yp = 0; o.cross |= 8u; } }
+    if (z == 0) { if (p.per_mask & 16u) o.zm = nxy * (p.nz - 1); else { o.zm = 0; o.cross |= 16u; } }
+    if (z == p.nz - 1) { if (p.per_mask & 32u) o.zp = -nxy * (p.nz - 1); else { o.zp = 0; o.cross |= 32u; } }
+    return o;
+}
+template <int EX, int EY, int EZ>
+__device__ __forceinline__ int src_off(const AxisOff& o) {
+    return axis_off(EX, o.xm, o.xp) + axis_off(EY, o.ym, o.yp) + axis_off(EZ, o.zm, o.zp);
+}
+template <int EX, int EY, int EZ>
+__device__ __forceinline__ unsigned src_cross(unsigned cr) {
+    return axis_cross(EX, cr, 1u, 2u) | axis_cross(EY, cr, 4u, 8u) | axis_cross(EZ, cr, 16u, 32u);
+}
+
+// Pull of a site none of whose pulls crosses a non-periodic face: unconditional loads.
+template <class S, class L = D3Q19>
+__device__ __forceinline__ void gather_interior(const Planes& pl, const KParams& p, int x, int y,
+                                                int z, int s, float* f, float* g) {
+    const AxisOff o = axis_offsets(p, x, y, z);
 #pragma unroll
     for (int i = 0; i < L::kQ; ++i)
-        f[i] = ldp<S>(pl, p, i, s + axis_off(L::ex(i), xm, xp) + axis_off(L::ey(i), ym, yp) +
-                                    axis_off(L::ez(i), zm, zp));
+        f[i] = ldp<S>(pl, p, i, s + axis_off(L::ex(i), o.xm, o.xp) + axis_off(L::ey(i), o.ym, o.yp) +
+                                    axis_off(L::ez(i), o.zm, o.zp));
 #pragma unroll
     for (int i = 0; i < kQT; ++i)
-        g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), xm, xp) + axis_off(ey7(i), ym, yp) +
-                                        axis_off(ez7(i), zm, zp));
-    x_face_fixup<OUTF, S, L>(pl, p, x, y, z, s, lanes, cxm, cxp, ym, yp, zm, zp, f, g);
+        g[i] = ldg_dev<S>(pl, p, i, s + axis_off(ex7(i), o.xm, o.xp) + axis_off(ey7(i), o.ym, o.yp) +
+                                        axis_off(ez7(i), o.zm, o.zp));
+}
+
+// Load of plane I at idx, or of plane J (the opposite velocity, same weight) when `other`.
+template <class S>
+__device__ __forceinline__ float ldp_either(const Planes& pl, const KParams& p, int I, int J,
+                                            bool other, int idx) {
+    const typename S::T* q = other ? plane_in<S>(pl, p, J) : plane_in<S>(pl, p, I);
+    return S::ld(q + idx) * plane_scale<S>(p, I);
+}
+template <class S>
+__device__ __forceinline__ float ldg_either(const Planes& pl, const KParams& p, int I, int J,
+                                            bool other, int idx) {
+    if constexpr (!S::kScaled) {
+        return ldp_either<S>(pl, p, kQ + I, kQ + J, other, idx);
+    } else {
+        const float sc = I == 0 ? p.om0 : p.om1;
+        const typename S::T* q = other ? plane_in<S>(pl, p, kQ + J) : plane_in<S>(pl, p, kQ + I);
+        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx), S::ld(q + idx)));
+    }
+}
+
+// Pull of any site of a lattice without node walls, with every load issued in one round: the
+// source of each population is chosen per lane (the neighbour, the opposite plane of the site
+// itself for a bounce-back, the inner source for the outflow), then the value rules of the
+// crossed faces are applied to the loaded values.
+template <bool OUTF, class S, class L, int... I>
+__device__ __forceinline__ void sel_load_f(const Planes& pl, const KParams& p, int s,
+                                           const AxisOff& o, float* f,
+                                           std::integer_sequence<int, I...>) {
+    (([&] {
+         constexpr int ex = L::ex(I), ey = L::ey(I), ez = L::ez(I);
+         const unsigned c = src_cross<ex, ey, ez>(o.cross);
+         // the outflow rule reads plane I at the source with the x offset of the crossed
+         // face (0), i.e. the inner neighbour's pull source; the other rules the opposite plane
+         const bool bounce =
+             c != 0u && !(OUTF && ex == -1 && !(c & (p.wall_mask | p.vel_mask)));
+         f[I] = ldp_either<S>(pl, p, I, L::opp(I), bounce, bounce ? s : s + src_off<ex, ey, ez>(o));
+     }()),
+     ...);
+}
+template <bool OUTF, class S, class L, int... I>
+__device__ __forceinline__ void sel_fix_f(const KParams& p, const AxisOff& o, const float* hf,
+                                          float* f, bool* via, std::integer_sequence<int, I...>) {
+    (([&] {
+         constexpr int ex = L::ex(I), ey = L::ey(I), ez = L::ez(I);
+         const unsigned c = src_cross<ex, ey, ez>(o.cross);
+         via[I] = false;
+         if (c != 0u && !(c & p.wall_mask)) {
+             const unsigned vm = c & p.vel_mask;
+             if (vm) {
+                 f[I] = bounce_moving<L, I>(p, __ffs(vm) - 1, f[I]);
+             } else if constexpr (OUTF && ex == -1) {
+                 f[I] = outflow_blend(p, hf[L::slot(I)], f[I]);
+                 via[I] = true;
+             }
+         }
+     }()),
+     ...);
+}
+template <bool OUTF, class S, class L>
+__device__ __forceinline__ void gather_sel(const Planes& pl, const KParams& p, int x, int y, int z,
+                                           int s, float* f, float* g) {
+    const AxisOff o = axis_offsets(p, x, y, z);
+    sel_load_f<OUTF, S, L>(pl, p, s, o, f, std::make_integer_sequence<int, L::kQ>{});
+    // D3Q7: one face at most per velocity; the outflow rule (x-high, kind 3) reads plane 2 at
+    // the site itself, the other rules the opposite plane of the site
+    const bool gout = OUTF && (o.cross & 2u) && p.heat_kind[1] == 3;
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) {
+        const unsigned c = axis_cross(ex7(i), o.cross, 1u, 2u) | axis_cross(ey7(i), o.cross, 4u, 8u) |
+                           axis_cross(ez7(i), o.cross, 16u, 32u);
+        const bool bounce = c != 0u && !(i == 2 && gout);
+        g[i] = ldg_either<S>(pl, p, i, opp7(i), bounce,
+                             c != 0u ? s : s + axis_off(ex7(i), o.xm, o.xp) +
+                                               axis_off(ey7(i), o.ym, o.yp) +
+                                               axis_off(ez7(i), o.zm, o.zp));
+    }
+    float hf[kOutSlots];  // outflow history of the lanes on the x-high face, same round
+    if constexpr (OUTF) {
+        const bool xo = (o.cross & 2u) != 0u;
+        const int yz = y + p.ny * z;
+#pragma unroll
+        for (int k = 0; k < kOutSlots; ++k) hf[k] = xo ? __ldg(pl.hin + k * p.nyz + yz) : 0.0f;
+    }
+    if (o.cross == 0u) return;  // no face rule at this site
+    bool via[L::kQ];
+    sel_fix_f<OUTF, S, L>(p, o, hf, f, via, std::make_integer_sequence<int, L::kQ>{});
+    if (OUTF && (o.cross & 2u)) outflow_anchor<L>(f, via);
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) {
+        const unsigned c = axis_cross(ex7(i), o.cross, 1u, 2u) | axis_cross(ey7(i), o.cross, 4u, 8u) |
+                           axis_cross(ez7(i), o.cross, 16u, 32u);
+        if (c == 0u) continue;
+        const int face = __ffs(c) - 1;
+        if (i == 2 && gout) g[i] = outflow_blend(p, hf[5], g[i]);
+        else if (p.heat_kind[face] == 2) g[i] = -g[i] + p.heat_abb[face];  // anti-bounce-back
+    }
 }
 
 // ---- collision -------------------------------------------------------------------------------
@@ -940,18 +1056,14 @@ __device__ __forceinline__ Macro nee_site(const Planes& pl, const KParams& p, in
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
-// Pull of one site (interior or general path; the warp-uniform choice is made by the caller).
-// `lanes` is the mask of the warp's lanes that call it together (the valid sites).
+// Pull of one site: unconditional loads when no lane of the warp crosses a non-periodic face
+// (`warp_fast`, a warp-uniform choice made by the caller with site_no_cross), else the
+// one-round select path.
 template <bool OUTF, class S, class L = D3Q19>
 __device__ __forceinline__ void gather_site(const Planes& pl, const KParams& p, int x, int y, int z,
-                                            int s, bool warp_yz_in, unsigned lanes, float* f,
-                                            float* g) {
-    if (warp_yz_in) {
-        gather_yz_interior<OUTF, S, L>(pl, p, x, y, z, s, lanes, f, g);
-    } else {
-        const Nbr n = neighbourhood(p, x, y, z);
-        gather_general<OUTF, S, L>(pl, p, n, f, g);
-    }
+                                            int s, bool warp_fast, float* f, float* g) {
+    if (warp_fast) gather_interior<S, L>(pl, p, x, y, z, s, f, g);
+    else gather_sel<OUTF, S, L>(pl, p, x, y, z, s, f, g);
 }
 
 // Outflow history, collision and store of one gathered site.
@@ -987,8 +1099,11 @@ __device__ __forceinline__ void dependent_launch_prologue() {
 
 // 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
 // blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
+// Registers: 64 per thread (32 resident warps per SM with 64-thread blocks); 72 with a porosity
+// field, whose medium terms need more (28 warps; at 80 the field kernel lost 4 % on the 256^3
+// cavity).
 template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19, bool NEE = false>
-__global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlocks)
+__global__ void __maxnreg__(HET ? 72 : 64)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -997,8 +1112,7 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     const bool valid = x < p.nx && y < p.ny;
     const unsigned nb = (NEE && valid) ? nee_bits(p, x, y, z) : 0u;  // node-wall site
     const bool streams = valid && nb == 0u;
-    const bool warp_yz_in = __all_sync(0xffffffffu, yz_fast(p, y, z) || !streams);
-    const unsigned lanes = __ballot_sync(0xffffffffu, streams);
+    const bool warp_fast = __all_sync(0xffffffffu, !streams || site_no_cross(p, x, y, z));
     if (!valid) return;
     float f[L::kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
@@ -1012,7 +1126,7 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
             return;
         }
     }
-    gather_site<OUTF, S, L>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
+    gather_site<OUTF, S, L>(pl, p, x, y, z, s, warp_fast, f, g);
     finish_site<HET, OUTF, S, ENTH, L>(pl, p, x, y, z, s, f, g);
 }
 
@@ -1099,14 +1213,13 @@ __device__ __forceinline__ void aa_local_all(const Planes& pl, const Planes& pw,
 }
 
 // Pull-step update of one valid site (W -> N): pl.in is the permuted table (logical q at
-// physical opp(q)), pl.out the identity table of the same copy; warp_fast and lanes as in
-// step_kernel.
+// physical opp(q)), pl.out the identity table of the same copy; warp_fast as in step_kernel.
 template <bool HET>
 __device__ __forceinline__ void aa_pull_site(const KParams& p, const Planes& pl, int x, int y,
-                                             int z, bool warp_fast, unsigned lanes) {
+                                             int z, bool warp_fast) {
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
-    gather_site<false, StoreF32InPlace, D3Q19>(pl, p, x, y, z, s, warp_fast, lanes, f, g);
+    gather_site<false, StoreF32InPlace, D3Q19>(pl, p, x, y, z, s, warp_fast, f, g);
     const Medium md = medium_at<HET>(p, s);
     collide_on<true, false, D3Q19>(p, md, f, g);
     const Nbr n = neighbourhood(p, x, y, z);
@@ -1145,9 +1258,8 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     const bool valid = x < p.nx && y < p.ny;
-    const bool warp_fast = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
-    const unsigned lanes = __ballot_sync(0xffffffffu, valid);
-    if (valid) aa_pull_site<HET>(p, pl, x, y, z, warp_fast, lanes);
+    const bool warp_fast = __all_sync(0xffffffffu, !valid || site_no_cross(p, x, y, z));
+    if (valid) aa_pull_site<HET>(p, pl, x, y, z, warp_fast);
 }
 
 // Local step over one lattice.
@@ -1241,14 +1353,13 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     for (int r = 0; r < rows; ++r) {
         const int z = z0 + r;
         if (z >= p.nz) break;  // uniform over the block
-        const bool warp_yz_in = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
-        // every lane of the warp reaches the two votes above; only the valid lanes go on, so
-        // the votes inside the site update name exactly those lanes
-        const unsigned lanes = __ballot_sync(0xffffffffu, valid);
+        // every lane of the warp reaches the vote; only the valid lanes update a site (the
+        // site update itself holds no warp-wide vote)
+        const bool warp_fast = __all_sync(0xffffffffu, !valid || site_no_cross(p, x, y, z));
         if (valid) {
             float f[kQ], g[kQT];
             const int s = x + p.nx * (y + p.ny * z);
-            gather_site<OUTF, S>(pl, p, x, y, z, s, warp_yz_in, lanes, f, g);
+            gather_site<OUTF, S>(pl, p, x, y, z, s, warp_fast, f, g);
             finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
         }
     }
@@ -1279,12 +1390,11 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     for (int r = 0; r < rows; ++r) {
         const int z = z0 + r;
         if (z >= p.nz) break;  // uniform over the block
-        // every lane reaches the votes; only the valid lanes update a site
-        const bool warp_fast = __all_sync(0xffffffffu, yz_fast(p, y, z) || !valid);
-        const unsigned lanes = __ballot_sync(0xffffffffu, valid);
+        // every lane reaches the vote; only the valid lanes update a site
+        const bool warp_fast = __all_sync(0xffffffffu, !valid || site_no_cross(p, x, y, z));
         if (!valid) continue;
         if (local) aa_local_site<HET>(p, L->pl[1], L->pl[0], x, y, z);
-        else aa_pull_site<HET>(p, L->pl[0], x, y, z, warp_fast, lanes);
+        else aa_pull_site<HET>(p, L->pl[0], x, y, z, warp_fast);
     }
 }
 
