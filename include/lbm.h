@@ -80,11 +80,16 @@ enum {
     LBM_MAP_LATTICE = 2  /* lattice units given directly (nu_e, alpha_f, gbeta) */
 };
 
-/* Storage of the populations (arithmetic is FP32 in every case):
- *  LBM_STORE_FP32     : FP32 deviations f_i - w_i rho0 and g_i - omega_i sigma T0 (208 B/site);
- *  LBM_STORE_FP16_DEV : FP16 scaled deviations (f_i - w_i rho0) / w_i and
- *                       (g_i - omega_i sigma T0) / omega_i, rounded to nearest (104 B/site);
- *  LBM_STORE_BF16_DEV : the same in BF16 (104 B/site). */
+/* Storage of the populations (arithmetic is FP32 in every case).  Bytes per site are those a
+ * time step reads and writes (each population once each way):
+ *  LBM_STORE_FP32     : FP32 deviations f_i - w_i rho0 and g_i - omega_i sigma T0 (208 B/site;
+ *                       D3Q15: 176 B/site);
+ *  LBM_STORE_FP16_DEV : FP16 scaled deviations, rounded to nearest: (f_i - w_i rho0) / w_i, and
+ *                       for the D3Q7 planes (g_i - omega_i sigma T_x) / omega_i against the
+ *                       site's own temperature T_x, whose deviation T_x - T0 is kept in an FP32
+ *                       temperature plane (26 x 2 B + 4 B, read and written: 112 B/site);
+ *  LBM_STORE_BF16_DEV : the same in BF16 (112 B/site).
+ * A porosity field (lbm_set_medium) adds 4 B/site read. */
 enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16_DEV = 1, LBM_STORE_BF16_DEV = 2 };
 
 /*
@@ -136,6 +141,9 @@ typedef struct lbm_params {
     /* population scheme: LBM_SCHEME_PINGPONG (0, the default), LBM_SCHEME_AA or
      * LBM_SCHEME_AUTO, see below */
     int scheme;
+    /* LBM_SCHEME_AUTO: cap, in bytes, on the free device memory that lbm_create counts when
+     * it chooses the scheme (0, the default: no cap) */
+    unsigned long long auto_mem_limit;
 } lbm_params;
 
 /* Population schemes.  Both compute the same site update and give bit-identical populations.
@@ -153,8 +161,8 @@ typedef struct lbm_params {
  *                        macros, Nusselt, sums, residual) first rearranges the copy (a pure
  *                        permutation, no arithmetic) into the layout a pull step reads.
  *  LBM_SCHEME_AUTO     : ping-pong while its footprint fits in the device memory free at
- *                        lbm_create (the environment variable LBM_MEM_LIMIT, in bytes, caps
- *                        that figure), else AA where the lattice allows it; lbm_derive_lattice
+ *                        lbm_create (lbm_params.auto_mem_limit, when above 0, caps that
+ *                        figure), else AA where the lattice allows it; lbm_derive_lattice
  *                        reports ping-pong for it; lbm_server runs ping-pong.  The scheme in
  *                        use is lbm_lattice.scheme (lbm_get_lattice). */
 #define LBM_SCHEME_PINGPONG 0
@@ -240,11 +248,10 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  *                     a few tiles ahead, one box per population plane (shifted by -e_i) into
  *                     shared memory.  Needs the D3Q19 lattice, nx % 64 == 0, ny >= 4, no node
  *                     walls and no enthalpy model.  A staged load that does not complete within
- *                     one second stops the step early; the next lbm_sync then returns
- *                     LBM_ETIMEOUT (sticky).  For tests of that path, the environment variable
- *                     LBM_TMA_EXPECT_EXTRA (bytes, read by lbm_set_step_kernel) makes every
- *                     stage wait for that many bytes more than its loads bring, so that its
- *                     waits run out. */
+ *                     one second stops the step early; the next call that synchronises the
+ *                     context's stream (lbm_sync, lbm_macros, lbm_residual, lbm_sums,
+ *                     lbm_nusselt, lbm_get_populations, ...) then returns LBM_ETIMEOUT
+ *                     (sticky).  lbm_test_tma_extra_wait exercises that path. */
 #define LBM_KERNEL_PLAIN 0
 #define LBM_KERNEL_TMA 1
 
@@ -256,6 +263,22 @@ lbm_status lbm_set_step_kernel(lbm_ctx* ctx, int kernel);
 
 /* The context's step kernel (LBM_KERNEL_*), -1 for ctx == NULL. */
 int lbm_get_step_kernel(const lbm_ctx* ctx);
+
+/* Launch settings of the context's single-lattice site kernels, for measurements:
+ *  block_threads    : threads per block, 32, 64 (the default), 128 or 256; 0 keeps the
+ *                     current value;
+ *  dependent_launch : 1 (the default) launches each step kernel as a programmatic dependent
+ *                     launch (its blocks may be scheduled while the previous step drains; they
+ *                     wait for it before their first load), 0 as an ordinary launch, -1 keeps
+ *                     the current setting.
+ * Results do not depend on either.  Errors: LBM_EINVAL (a value out of range; nothing changed). */
+lbm_status lbm_set_launch(lbm_ctx* ctx, int block_threads, int dependent_launch);
+
+/* TEST ONLY: makes every pipeline stage of the TMA step kernel wait for `bytes` (0 .. 4096)
+ * more than its loads bring, so that its bounded waits run out and the failure path of
+ * LBM_KERNEL_TMA can be exercised without a fault; 0 (the default) turns it off.  Takes effect
+ * from the next lbm_step with LBM_KERNEL_TMA.  Errors: LBM_EINVAL for bytes out of range. */
+lbm_status lbm_test_tma_extra_wait(lbm_ctx* ctx, int bytes);
 
 /* Re-initialise the state to equilibrium (Eqs. 24 and 42) with rho = rho0 and, per site,
  * T from T_field (host, ns doubles; NULL: T_uniform) and u from u_field (host, 3 x ns
@@ -329,9 +352,8 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
 
 /* Allocation-free steady-state residual.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- an application that gives the
- * library a fixed arena and forbids cudaMalloc after start-up, a loop in which an
- * allocation (which may synchronise the device) would stall, or work recorded into a CUDA
- * stream capture, where allocation calls are not permitted.
+ * library a fixed arena and forbids cudaMalloc after start-up, or a loop in which an
+ * allocation (which may synchronise the device) would stall.
  * It computes what lbm_residual computes, r_u = ||u - u_prev||_2 / ||u||_2 and the same for
  * T (FP64 accumulation), from fields the caller holds, e.g. two results of
  * lbm_macros_device:
@@ -339,8 +361,12 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
  *  ns        : 1 .. LBM_NOALLOC_MAX_SITES, else LBM_EINVAL and nothing is launched;
  *  out       : device, 3 doubles, written asynchronously: r_u, r_T (0 for a field that is
  *              zero and unchanged, +inf for one that is zero after changing) and the number
- *              of non-finite values met;
+ *              of non-finite values met; when that number is above 0, r_u and r_T are NaN
+ *              (a blown-up field never passes a test r < tol);
  *  stream    : cudaStream_t to queue on (NULL: the current device's default stream).
+ * The call runs on the stream's device and leaves the calling thread's current device as it
+ * found it.  Each of its two launches is checked through its own return code; an error left
+ * on the thread by an earlier call is neither reported nor cleared.
  * It allocates nothing: its partial sums live in a static 320 KiB device array that every
  * GPU loading the library holds until exit.  The first call on a device looks up that
  * array's device address (cudaGetSymbolAddress); make that first call before any stream
@@ -440,6 +466,13 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
  * requests after the round (either pointer may be NULL).  Synchronises. */
 lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued);
 
+/* Give a queued or admitted request host buffers for its final fields: u (3 x ns floats,
+ * [3][ns]) and T (ns floats), either may be NULL.  When the request finishes (converged, step
+ * limit or unstable) the server writes its macroscopic fields at the final time there, as
+ * lbm_macros computes them, before releasing its state.  The buffers are the caller's and must
+ * stay valid until the result has been polled.  LBM_EINVAL for an unknown or finished id. */
+lbm_status lbm_server_set_output(lbm_server* s, long long id, float* u, float* T);
+
 /* Move up to `max` finished results into out; *n receives how many. */
 lbm_status lbm_server_poll(lbm_server* s, lbm_result* out, int max, int* n);
 
@@ -462,7 +495,8 @@ lbm_status lbm_get_lattice(const lbm_ctx* ctx, lbm_lattice* out);
 long long lbm_steps_done(const lbm_ctx* ctx);
 
 /* Block the host until the context's stream is idle.  Returns LBM_ETIMEOUT (sticky) when a
- * bounded device-side wait of a TMA step ran out since the last check (see LBM_KERNEL_TMA). */
+ * bounded device-side wait of a TMA step ran out since the last check (see LBM_KERNEL_TMA);
+ * every other call that synchronises the stream checks the same. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
 /* Text of the last error of the context (never NULL; "" when none).  Owned by ctx. */

@@ -1,12 +1,11 @@
 // Allocation-free steady-state residual for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc: an application that hands the library a fixed
-// device-memory arena and forbids allocations after start-up, a real-time loop in which an
-// allocation would stall (cudaMalloc may synchronise the device), or code that records its
-// work into a CUDA stream capture, where allocation calls are not permitted.  This file gives
-// them one entry point, lbm_residual_noalloc, that computes the same relative change of the
-// velocity and temperature fields as lbm_residual from fields the caller already holds, and
-// keeps its per-block partial sums in a fixed, file-scope device array instead.
+// device-memory arena and forbids allocations after start-up, or a real-time loop in which an
+// allocation would stall (cudaMalloc may synchronise the device).  This file gives them one
+// entry point, lbm_residual_noalloc, that computes the same relative change of the velocity
+// and temperature fields as lbm_residual from fields the caller already holds, and keeps its
+// per-block partial sums in a fixed, file-scope device array instead.
 //
 // The array lives for as long as the library is loaded, on every GPU that loads it.  Every
 // call shares it and it keeps the last call's contents; each call writes every slot it
@@ -96,8 +95,13 @@ __global__ void __launch_bounds__(kThreads)
         for (int k = 0; k < kVals; ++k)
             t[k] = warp_sum(threadIdx.x < kThreads / 32 ? sh[k][threadIdx.x] : 0.0);
         if (threadIdx.x == 0) {
-            out[0] = t[1] > 0.0 ? sqrt(t[0] / t[1]) : (t[0] > 0.0 ? HUGE_VAL : 0.0);
-            out[1] = t[3] > 0.0 ? sqrt(t[2] / t[3]) : (t[2] > 0.0 ? HUGE_VAL : 0.0);
+            if (t[4] > 0.0) {  // a non-finite value: no residual, and never below a tolerance
+                out[0] = nan("");
+                out[1] = nan("");
+            } else {
+                out[0] = t[1] > 0.0 ? sqrt(t[0] / t[1]) : (t[0] > 0.0 ? HUGE_VAL : 0.0);
+                out[1] = t[3] > 0.0 ? sqrt(t[2] / t[3]) : (t[2] > 0.0 ? HUGE_VAL : 0.0);
+            }
             out[2] = t[4];
         }
     }
@@ -121,6 +125,26 @@ cudaError_t scratch_for_device(int dev, double** ptr) {
     return cudaSuccess;
 }
 
+// Makes `dev` the calling thread's current device for the lifetime of the guard and restores
+// the device that was current before on every exit.
+class DeviceGuard {
+  public:
+    cudaError_t enter(int dev) {
+        cudaError_t e = cudaGetDevice(&prev_);
+        if (e != cudaSuccess) return e;
+        have_prev_ = true;
+        return prev_ == dev ? cudaSuccess : cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (have_prev_ && cudaGetDevice(&now) == cudaSuccess && now != prev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0;
+    bool have_prev_ = false;
+};
+
 }  // namespace
 
 extern "C" lbm_status lbm_residual_noalloc(const float* u, const float* T, const float* u_prev,
@@ -133,11 +157,23 @@ extern "C" lbm_status lbm_residual_noalloc(const float* u, const float* T, const
     cudaError_t e = st ? cudaStreamGetDevice(st, &dev) : cudaGetDevice(&dev);
     if (e != cudaSuccess) return LBM_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return LBM_EINVAL;
-    if ((e = cudaSetDevice(dev)) != cudaSuccess) return LBM_ECUDA;
+    DeviceGuard guard;  // the caller's current device is back in place on every return
+    if (guard.enter(dev) != cudaSuccess) return LBM_ECUDA;
     double* scratch = nullptr;
-    if ((e = scratch_for_device(dev, &scratch)) != cudaSuccess) return LBM_ECUDA;
-    int nblocks = (int)((ns + kSitesPerBlock - 1) / kSitesPerBlock);
-    residual_partials_kernel<<<nblocks, kThreads, 0, st>>>(u, T, u_prev, T_prev, ns, scratch);
-    residual_finish_kernel<<<1, kThreads, 0, st>>>(scratch, nblocks, out);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    if (scratch_for_device(dev, &scratch) != cudaSuccess) return LBM_ECUDA;
+    const int nblocks = (int)((ns + kSitesPerBlock - 1) / kSitesPerBlock);
+    // each launch is checked through its own return code, so an error left on the thread by
+    // an earlier, unrelated call is neither reported as this call's nor cleared
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cfg.gridDim = dim3(nblocks);
+    if (cudaLaunchKernelEx(&cfg, residual_partials_kernel, u, T, u_prev, T_prev, ns, scratch) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    cfg.gridDim = dim3(1);
+    if (cudaLaunchKernelEx(&cfg, residual_finish_kernel, (const double*)scratch, nblocks, out) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    return LBM_OK;
 }

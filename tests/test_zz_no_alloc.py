@@ -1,9 +1,10 @@
 """The allocation-free residual entry point against the existing one.
 
-lbm_residual_noalloc serves callers that cannot allocate device memory (a fixed arena,
-an allocation-free loop, a stream capture); it keeps its partial sums in a static device
-array.  This file runs last so that a failure here leaves every other test already run;
-it also passes on its own in a fresh process.
+lbm_residual_noalloc serves callers that cannot allocate device memory (an application that
+hands the library a fixed arena and forbids cudaMalloc after start-up, or a loop in which an
+allocation would stall); it keeps its partial sums in a static device array.  This file runs
+last so that a failure here leaves every other test already run; it also passes on its own in
+a fresh process.
 """
 import pytest
 
@@ -64,3 +65,46 @@ def test_noalloc_rejects_sizes_beyond_the_maximum(env):
         assert ei.value.status == gb.LBM_EINVAL
     with pytest.raises(gb.LbmError):
         gb.residual_noalloc(0, p, p, p, 8, out.data_ptr())
+
+
+def test_noalloc_reports_non_finite_fields(env):
+    """A NaN or Inf in a field is counted in out[2] and makes both residuals NaN, so a caller
+    that tests r < tol never takes a blown-up solve for a converged one; the next call on
+    finite fields is unaffected (the shared array keeps nothing that matters)."""
+    gb, torch = env
+    ns = 5000
+    stream = torch.cuda.current_stream()
+    u = torch.linspace(0.1, 0.2, 3 * ns, device="cuda")
+    up = u * 0.999
+    T = torch.linspace(0.0, 1.0, ns, device="cuda")
+    Tp = T.clone()
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for bad, where in ((float("nan"), "u"), (float("inf"), "T")):
+        ub, Tb = u.clone(), T.clone()
+        (ub if where == "u" else Tb)[1234] = bad
+        gb.residual_noalloc(ub.data_ptr(), Tb.data_ptr(), up.data_ptr(), Tp.data_ptr(), ns,
+                            out.data_ptr(), stream.cuda_stream)
+        r = out.cpu().tolist()
+        assert r[2] == 1.0
+        assert r[0] != r[0] and r[1] != r[1]  # NaN
+        assert not (r[0] < 1e-6) and not (r[1] < 1e-6)
+    gb.residual_noalloc(u.data_ptr(), T.data_ptr(), up.data_ptr(), Tp.data_ptr(), ns,
+                        out.data_ptr(), stream.cuda_stream)
+    r = out.cpu().tolist()
+    want_u = float(torch.linalg.vector_norm(u.double() - up.double()) /
+                   torch.linalg.vector_norm(u.double()))
+    assert r[2] == 0.0 and r[1] == 0.0
+    assert r[0] == pytest.approx(want_u, rel=1e-5)
+
+
+def test_noalloc_keeps_the_current_device(env):
+    """The call runs on its stream's device and leaves the thread's current device as it was."""
+    gb, torch = env
+    ns = 64
+    buf = torch.ones(3 * ns, device="cuda")
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    before = torch.cuda.current_device()
+    gb.residual_noalloc(buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), ns,
+                        out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.current_device() == before
