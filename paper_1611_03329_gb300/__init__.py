@@ -39,6 +39,7 @@ ABI_SYMBOLS = (
     "lbm_server_create", "lbm_server_submit", "lbm_server_advance", "lbm_server_poll",
     "lbm_server_clock", "lbm_server_destroy", "lbm_server_set_fill", "lbm_set_step_kernel",
     "lbm_get_step_kernel", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
+    "lbm_set_launch", "lbm_test_tma_extra_wait", "lbm_server_set_output",
 )
 
 # Population schemes (LBM_SCHEME_*).
@@ -78,6 +79,7 @@ class LbmParams(C.Structure):
         ("c_pl", C.c_double), ("c_ps", C.c_double), ("sigma_s", C.c_double),
         ("sigma_l", C.c_double), ("alpha_ratio", C.c_double),
         ("q_flow", C.c_int), ("scheme", C.c_int),
+        ("auto_mem_limit", C.c_ulonglong),
     ]
 
 
@@ -169,6 +171,8 @@ def lib():
         L.lbm_save_state.argtypes = [vp, vp, C.c_ulonglong]
         L.lbm_load_state.argtypes = [vp, vp, C.c_ulonglong]
         L.lbm_get_step_kernel.argtypes = [vp]
+        L.lbm_set_launch.argtypes = [vp, C.c_int, C.c_int]
+        L.lbm_test_tma_extra_wait.argtypes = [vp, C.c_int]
         L.lbm_init_equilibrium.argtypes = [vp, dp, dp, C.c_double]
         L.lbm_set_populations.argtypes = [vp, dp, dp]
         L.lbm_get_populations.argtypes = [vp, dp, dp]
@@ -200,6 +204,7 @@ def lib():
                                         C.POINTER(C.c_longlong)]
         L.lbm_server_advance.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.lbm_server_poll.argtypes = [vp, C.POINTER(LbmResult), C.c_int, C.POINTER(C.c_int)]
+        L.lbm_server_set_output.argtypes = [vp, C.c_longlong, fp, fp]
         L.lbm_server_set_fill.argtypes = [vp, C.c_longlong]
         L.lbm_server_clock.argtypes = [vp]
         L.lbm_server_clock.restype = C.c_double
@@ -236,6 +241,7 @@ def params_from_problem(pb: dict) -> LbmParams:
         p.T_init = p.T0
     p.q_flow = int(pb.get("q", 19))
     p.scheme = SCHEMES[pb.get("scheme", "pingpong")]
+    p.auto_mem_limit = int(pb.get("auto_mem_limit", 0))
     p.enthalpy = int(bool(pb.get("enthalpy", False)))
     p.flow_off = int(bool(pb.get("flow_off", False)))
     for k in ("T_m", "T_s", "T_l", "St", "c_pl", "c_ps", "sigma_s", "sigma_l", "alpha_ratio"):
@@ -353,6 +359,15 @@ class Lattice:
         """Select the step kernel: "plain" (one thread per site) or "tma" (populations staged
         into shared memory by the Tensor Memory Accelerator); both give the same populations."""
         self._check(lib().lbm_set_step_kernel(self._h, STEP_KERNELS[kernel]), "lbm_set_step_kernel")
+
+    def set_launch(self, block_threads: int = 0, dependent_launch: int = -1):
+        """lbm_set_launch: block size (0 keeps) and programmatic dependent launch (-1 keeps)."""
+        self._check(lib().lbm_set_launch(self._h, int(block_threads), int(dependent_launch)),
+                    "lbm_set_launch")
+
+    def test_tma_extra_wait(self, nbytes: int):
+        """lbm_test_tma_extra_wait (test only): TMA stages wait for nbytes more than arrive."""
+        self._check(lib().lbm_test_tma_extra_wait(self._h, int(nbytes)), "lbm_test_tma_extra_wait")
 
     @property
     def step_kernel(self) -> str:
@@ -532,6 +547,16 @@ class Server:
         if st != LBM_OK:
             raise LbmError(st, f"lbm_server_submit: {lib().lbm_status_string(st).decode()}")
         return rid.value
+
+    def set_output(self, rid: int, u: Optional[np.ndarray], T: Optional[np.ndarray]):
+        """lbm_server_set_output: float32 host arrays (u: 3 x ns, T: ns) that receive the
+        request's final fields; the caller keeps them alive until the result is polled."""
+        for a in (u, T):
+            assert a is None or (a.dtype == np.float32 and a.flags["C_CONTIGUOUS"])
+        st = lib().lbm_server_set_output(self._h, int(rid), None if u is None else _fp(u),
+                                         None if T is None else _fp(T))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_server_set_output")
 
     def advance(self):
         """One scheduling round; returns (admitted, queued)."""

@@ -28,8 +28,8 @@ struct lbm_ctx {
     int cur = 0;
     lbm::Planes pl[2];  // launch planes reading copy 0 / copy 1
     bool outflow = false;
-    int block_threads = 64;      // site-kernel block size (LBM_BLOCK_THREADS overrides)
-    bool pdl = true;             // step launches as programmatic dependent launches (LBM_PDL=0: off)
+    int block_threads = 64;      // site-kernel block size (lbm_set_launch)
+    bool pdl = true;             // step launches as programmatic dependent launches (lbm_set_launch)
     // AA scheme: one copy (pop[0]); pl[0] = (in: permuted, out: identity) for pull steps and
     // readers, pl[1] = (in: identity, out: permuted) for local steps and the initial state,
     // pw.in = permuted; aa_phase 0: swapped layout (next step pulls), 1: streamed layout
@@ -473,6 +473,22 @@ void fill_kparams(lbm_ctx* c) {
     }
 }
 
+// Waits for the context's stream; a staged load of the TMA step kernel that ran out of time
+// since the last check (the kernel's device flag) makes the context LBM_ETIMEOUT (sticky), so
+// that no call returns results computed from a step that stopped early.
+lbm_status sync_ctx(lbm_ctx* c) {
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->tma_err) {
+        int flag = 0;
+        LBM_CUDA(cudaMemcpy(&flag, c->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            c->sticky = LBM_ETIMEOUT;
+            return fail(c, LBM_ETIMEOUT, "a staged population load did not complete within 1 s");
+        }
+    }
+    return LBM_OK;
+}
+
 lbm_status usable(lbm_ctx* c) {
     if (!c) return LBM_EINVAL;
     if (c->sticky != LBM_OK) return c->sticky;
@@ -632,11 +648,6 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     c->nyz = (long long)p->ny * p->nz;
     c->outflow = p->flow_bc[1] == LBM_FLOW_OUTFLOW;
     c->elem = p->storage == LBM_STORE_FP32 ? sizeof(float) : 2;
-    if (const char* v = std::getenv("LBM_PDL")) c->pdl = std::atoi(v) != 0;
-    if (const char* bt = std::getenv("LBM_BLOCK_THREADS")) {
-        int v = std::atoi(bt);
-        if (v == 32 || v == 64 || v == 128 || v == 256) c->block_threads = v;
-    }
     lbm_status st = LBM_OK;
     // the device of a caller's stream, else the calling thread's current device
     cudaError_t e = stream ? cudaStreamGetDevice((cudaStream_t)stream, &c->device)
@@ -651,7 +662,7 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
         if (e != cudaSuccess) st = cuda_fail(c, e, "cudaStreamCreate");
         else c->own_stream = true;
     }
-    // AUTO: ping-pong while both copies fit in the free device memory (LBM_MEM_LIMIT, in
+    // AUTO: ping-pong while both copies fit in the free device memory (auto_mem_limit, in
     // bytes, caps that figure), else AA where the lattice allows it
     if (st == LBM_OK && p->scheme == LBM_SCHEME_AUTO && aa_eligible(p, c->lat)) {
         size_t fr = 0, tot = 0;
@@ -660,10 +671,7 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
             st = cuda_fail(c, e, "cudaMemGetInfo");
         } else {
             unsigned long long avail = fr;
-            if (const char* v = std::getenv("LBM_MEM_LIMIT")) {
-                const unsigned long long lim = std::strtoull(v, nullptr, 10);
-                if (lim > 0 && lim < avail) avail = lim;
-            }
+            if (p->auto_mem_limit > 0 && p->auto_mem_limit < avail) avail = p->auto_mem_limit;
             if (footprint_of(p, c->lat, 0) > avail) c->lat.scheme = LBM_SCHEME_AA;
         }
     }
@@ -776,7 +784,7 @@ lbm_status lbm_set_medium(lbm_ctx* c, const float* phi_field, double phi, double
         LBM_CUDA(cudaMemcpyAsync(c->phi_dev, phi_field, sizeof(float) * (size_t)c->ns,
                                  cudaMemcpyHostToDevice, c->stream));
     }
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     c->lat = L;
     fill_kparams(c);
     return LBM_OK;
@@ -813,16 +821,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
 lbm_status lbm_sync(lbm_ctx* c) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
-    if (c->tma_err) {
-        int flag = 0;
-        LBM_CUDA(cudaMemcpy(&flag, c->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (flag) {
-            c->sticky = LBM_ETIMEOUT;
-            return fail(c, LBM_ETIMEOUT, "a staged population load did not complete within 1 s");
-        }
-    }
-    return LBM_OK;
+    return sync_ctx(c);
 }
 
 lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* T_field, const double* u_field,
@@ -846,7 +845,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* T_field, const double*
         }
     }
     if ((st = init_state(c, Td, ud, T_uniform)) != LBM_OK) return st;
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     return LBM_OK;
 }
 
@@ -897,7 +896,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* g) {
     if ((st = reset_hist(c)) != LBM_OK) return st;
     c->have_prev = false;
     c->aa_phase = 0;  // the whole state was written in the swapped layout
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     return LBM_OK;
 }
 
@@ -926,7 +925,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
         LBM_CUDA(cudaMemcpyAsync(g, c->stage, sizeof(double) * lbm::kQT * c->ns,
                                  cudaMemcpyDeviceToHost, c->stream));
     }
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     return LBM_OK;
 }
 
@@ -1049,7 +1048,7 @@ lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* T) {
         LBM_CUDA(cudaMemcpyAsync(u, du, sizeof(float) * 3 * c->ns, cudaMemcpyDeviceToHost, c->stream));
     if (T)
         LBM_CUDA(cudaMemcpyAsync(T, dT, sizeof(float) * c->ns, cudaMemcpyDeviceToHost, c->stream));
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     return LBM_OK;
 }
 
@@ -1074,7 +1073,7 @@ lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile,
     if (nu_profile)
         LBM_CUDA(cudaMemcpyAsync(nu_profile, c->profile, sizeof(double) * n1,
                                  cudaMemcpyDeviceToHost, c->stream));
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     if (!std::isfinite(c->hres[0])) return fail(c, LBM_EUNSTABLE, "Nusselt number is not finite");
     if (nu_avg) *nu_avg = c->hres[0];
     if (nu_mp) *nu_mp = c->hres[1];
@@ -1089,7 +1088,7 @@ lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
     LBM_CUDA(lbm::launch_sums(c->kp, c->pl[c->cur], c->partials, nr, c->dres, c->stream));
     LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 2, cudaMemcpyDeviceToHost,
                              c->stream));
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     if (mass_dev) *mass_dev = c->hres[0];
     if (heat_dev) *heat_dev = c->hres[1];
     if (!std::isfinite(c->hres[0]) || !std::isfinite(c->hres[1]))
@@ -1117,7 +1116,7 @@ lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
     LBM_CUDA(lbm::launch_residual(cu, cT, pu, pT, c->ns, c->partials, nr, c->dres, c->stream));
     LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 5, cudaMemcpyDeviceToHost,
                              c->stream));
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (lbm_status s_ = sync_ctx(c)) return s_;
     const double* h = c->hres;
     c->snap ^= 1;
     c->have_prev = true;
@@ -1155,19 +1154,36 @@ lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
     if (!c->tma_err) {
         LBM_CUDA(cudaMalloc(&c->tma_err, sizeof(int)));
         LBM_CUDA(cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->stream));
-        LBM_CUDA(cudaStreamSynchronize(c->stream));
+        if (lbm_status s_ = sync_ctx(c)) return s_;
     }
     c->tma_blocks = blocks;
-    c->tma_extra_tx = 0;
-    if (const char* v = std::getenv("LBM_TMA_EXPECT_EXTRA")) {
-        const int extra = std::atoi(v);
-        if (extra > 0 && extra <= 4096) c->tma_extra_tx = extra;
-    }
     c->step_kernel = kernel;
     return LBM_OK;
 }
 
 int lbm_get_step_kernel(const lbm_ctx* c) { return c ? c->step_kernel : -1; }
+
+lbm_status lbm_set_launch(lbm_ctx* c, int block_threads, int dependent_launch) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if (block_threads != 0 && block_threads != 32 && block_threads != 64 && block_threads != 128 &&
+        block_threads != 256)
+        return fail(c, LBM_EINVAL, "block_threads must be 0, 32, 64, 128 or 256");
+    if (dependent_launch < -1 || dependent_launch > 1)
+        return fail(c, LBM_EINVAL, "dependent_launch must be -1, 0 or 1");
+    if (block_threads) c->block_threads = block_threads;
+    if (dependent_launch >= 0) c->pdl = dependent_launch != 0;
+    fill_kparams(c);  // the block size travels in the kernel parameters
+    return LBM_OK;
+}
+
+lbm_status lbm_test_tma_extra_wait(lbm_ctx* c, int bytes) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if (bytes < 0 || bytes > 4096) return fail(c, LBM_EINVAL, "bytes must be 0 .. 4096");
+    c->tma_extra_tx = bytes;
+    return LBM_OK;
+}
 
 lbm_status lbm_get_lattice(const lbm_ctx* c, lbm_lattice* out) {
     if (!c || !out) return LBM_EINVAL;
@@ -1546,6 +1562,8 @@ struct lbm_server {
         double t_submit = 0.0, t_admit = 0.0;
         lbm_ctx* ctx = nullptr;
         double r_u = HUGE_VAL, r_T = HUGE_VAL;
+        float* out_u = nullptr;  // caller's host buffers for the final fields (or NULL)
+        float* out_T = nullptr;
     };
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -1579,6 +1597,7 @@ void server_finish(lbm_server* s, size_t k, int status) {
         if (r->p.heat_bc[0] == LBM_HEAT_DIRICHLET && r->p.nx >= 2)
             lbm_nusselt(r->ctx, 0, &res.nu_avg, nullptr, &res.nu_mp);
         lbm_sums(r->ctx, &res.mass_dev, &res.heat_dev);
+        if (r->out_u || r->out_T) lbm_macros(r->ctx, nullptr, r->out_u, r->out_T);
     }
     res.t_submit = r->t_submit;
     res.t_admit = r->t_admit;
@@ -1725,6 +1744,23 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
     if (n_active) *n_active = (int)s->active.size();
     if (n_queued) *n_queued = (int)s->queue.size();
     return LBM_OK;
+}
+
+lbm_status lbm_server_set_output(lbm_server* s, long long id, float* u, float* T) {
+    if (!s) return LBM_EINVAL;
+    for (auto* r : s->queue)
+        if (r->id == id) {
+            r->out_u = u;
+            r->out_T = T;
+            return LBM_OK;
+        }
+    for (auto* r : s->active)
+        if (r->id == id) {
+            r->out_u = u;
+            r->out_T = T;
+            return LBM_OK;
+        }
+    return LBM_EINVAL;  // unknown or already finished
 }
 
 lbm_status lbm_server_poll(lbm_server* s, lbm_result* out, int max, int* n) {

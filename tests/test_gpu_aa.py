@@ -138,7 +138,7 @@ def test_cavity_128_bit_identical(gb):
         assert np.array_equal(a, b)
 
 
-def test_scheme_rules(gb, monkeypatch):
+def test_scheme_rules(gb):
     from paper_1611_03329_gb300 import LbmError
 
     with pytest.raises(LbmError):  # outflow face
@@ -151,12 +151,11 @@ def test_scheme_rules(gb, monkeypatch):
     # AUTO: ping-pong while two copies fit, AA when the memory cap leaves room for one only
     assert gb.Lattice(pb).lattice()["scheme"] == 0
     one_copy = gb.footprint(dict(pb, scheme="aa"))
-    monkeypatch.setenv("LBM_MEM_LIMIT", str(one_copy + 1024))
-    cav = gb.Lattice(pb)
+    cav = gb.Lattice(dict(pb, auto_mem_limit=one_copy + 1024))
     assert cav.lattice()["scheme"] == 1
-    ch = gb.Lattice(dict(channel_problem(64, 8, 4), scheme="auto"))  # outflow: ping-pong
+    ch = gb.Lattice(dict(channel_problem(64, 8, 4), scheme="auto",
+                         auto_mem_limit=one_copy + 1024))  # outflow: ping-pong
     assert ch.lattice()["scheme"] == 0
-    monkeypatch.delenv("LBM_MEM_LIMIT")
     with pytest.raises(LbmError):  # the TMA kernel runs ping-pong copies
         cav.set_step_kernel("tma")
 

@@ -130,22 +130,24 @@ def test_selection_rules(gb):
     assert lat.step_kernel == "plain"
 
 
-def test_wait_timeout_is_reported(gb, monkeypatch):
+@pytest.mark.parametrize("reader", ["sync", "macros", "residual"])
+def test_wait_timeout_is_reported(gb, reader):
     """Failure detection of the bounded waits: with every stage told to wait for 16 bytes its
-    loads never bring (LBM_TMA_EXPECT_EXTRA), each wait runs out after about a second, the
-    kernel sets its flag and stops, lbm_sync reports LBM_ETIMEOUT and the context refuses
-    further steps.  Nothing faults or hangs: a new context on the same device steps normally
-    and matches the plain kernel."""
+    loads never bring (lbm_test_tma_extra_wait), each wait runs out after about a second, the
+    kernel sets its flag and stops, and the next call that synchronises the stream -- lbm_sync,
+    or a reader of the state such as lbm_macros or lbm_residual -- reports LBM_ETIMEOUT instead
+    of results from the step that stopped early; the context then refuses further steps.
+    Nothing faults or hangs: a new context on the same device steps normally and matches the
+    plain kernel."""
     from paper_1611_03329_gb300 import LbmError
 
     pb = channel_problem(64, 8, 6)
-    monkeypatch.setenv("LBM_TMA_EXPECT_EXTRA", "16")
     lat = gb.Lattice(pb)
     lat.set_step_kernel("tma")
-    monkeypatch.delenv("LBM_TMA_EXPECT_EXTRA")
+    lat.test_tma_extra_wait(16)
     lat.step(1)
     with pytest.raises(LbmError) as ei:
-        lat.sync()
+        {"sync": lat.sync, "macros": lat.macros, "residual": lat.residual}[reader]()
     assert ei.value.status == gb.LBM_ETIMEOUT
     with pytest.raises(LbmError):
         lat.step(1)
