@@ -39,17 +39,33 @@ def test_replica_timing_takes_the_max_over_ranks():
     assert got == [(0, 15.0), (1, 15.0)]
 
 
-def test_traffic_gate_follows_the_kernel_source(tmp_path, monkeypatch):
+def test_traffic_gate_follows_the_kernel_source(monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
 
     h = bench.kernel_source_hash()
-    prof = tmp_path / "p.md"
-    prof.write_text(f"kernel_source_sha256: {h}\ndram_bytes_per_launch: 123\n")
-    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(prof))
+    monkeypatch.setattr(bench, "STEP_TRAFFIC", {"kernel_source_sha256": h,
+                                                "dram_bytes_per_launch": 123})
     assert bench.profiled_traffic() == 123
-    prof.write_text("kernel_source_sha256: 0000\ndram_bytes_per_launch: 123\n")
+    monkeypatch.setattr(bench, "STEP_TRAFFIC", {"kernel_source_sha256": "0000",
+                                                "dram_bytes_per_launch": 123})
     assert bench.profiled_traffic() is None
+
+
+def test_bench_reads_no_profile_files():
+    """The emitted line is built from measurements and constants, never from profiles/."""
+    with open(os.path.join(ROOT, "bench.py")) as fh:
+        src = fh.read()
+    assert "profiles/" not in src
+
+
+def test_window_count_covers_a_second_and_five_windows():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.window_count(1000.0) == bench.MIN_WINDOWS  # long windows: five of them
+    assert bench.window_count(0.78) == 1283                  # 20 channel steps: >= 1 s in all
+    assert bench.window_count(1e-9) == bench.MAX_WINDOWS
 
 
 def test_reference_arm_prints_one_json_line():
