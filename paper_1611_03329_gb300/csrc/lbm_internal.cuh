@@ -23,6 +23,7 @@ struct KParams {
     int block_threads;  // threads per block of the site kernels (host launch setting)
     long long ns;   // sites
     long long sq;   // elements between consecutive population planes (>= ns, padded)
+    int off32;      // every element offset within a population copy fits an int
 
     // boundaries (face bits: 1 << face, faces x-low, x-high, y-low, y-high, z-low, z-high)
     unsigned per_mask;    // periodic faces (flow and heat)
@@ -74,6 +75,13 @@ struct Planes {
     float* hout;
     const float* tin;  // T - T0 per site (16-bit formats only): planes in / out
     float* tout;
+    // The same planes as element offsets from one base per side (the planes of a copy are one
+    // allocation): plane q of the planes read starts at base_in + off_in[q] elements.  Used by
+    // the kernels instantiated with 32-bit offsets, when KParams::off32 is set.
+    const void* base_in;
+    void* base_out;
+    int off_in[kQ + kQT];
+    int off_out[kQ + kQT];
 };
 
 // One lattice of a batched launch: its parameters, its launch planes for either parity, the
@@ -158,7 +166,7 @@ int aa_swapped_plane(int q);
 // lattice.
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
-                              bool enthalpy, int flip, cudaStream_t st);
+                              bool enthalpy, bool off32, int flip, cudaStream_t st);
 // One time step of the AA lattices of a batch group (FP32, D3Q19, no outflow): lattice l runs a
 // pull step when (cur ^ flip) is 0, else a local step; cur holds its AA phase.
 cudaError_t launch_batch_aa(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,

@@ -126,10 +126,15 @@ static_assert(ex19(opp19(13)) == -ex19(13) && ez19(opp19(13)) == -ez19(13), "opp
 // instead of through its own pointer.  Fewer pointer loads from the parameter block (which go
 // through the address-divergence pipe) for more integer adds; the 16-bit step measured 13 %
 // faster, FP32 the same, so only the 16-bit formats use it.
+// kOff32: plane q at element offset Planes::off_in[q] / off_out[q] from one base pointer per
+// side, the offset and the site index added in 32 bits and widened once (two integer
+// instructions per access, no pointer read from the parameter block); used by the hot
+// kernels when every offset of a copy fits an int (KParams::off32).
 struct StoreF32 {
     using T = float;
     static constexpr bool kScaled = false;
     static constexpr bool kStrided = false;
+    static constexpr bool kOff32 = false;
     static __device__ __forceinline__ float ld(const T* q) { return __ldg(q); }
     static __device__ __forceinline__ void st(T* q, float v) { *q = v; }
 };
@@ -137,6 +142,7 @@ struct StoreF16 {
     using T = __half;
     static constexpr bool kScaled = true;
     static constexpr bool kStrided = true;
+    static constexpr bool kOff32 = false;
     static __device__ __forceinline__ float ld(const T* q) { return __half2float(__ldg(q)); }
     static __device__ __forceinline__ void st(T* q, float v) { *q = __float2half_rn(v); }
 };
@@ -144,9 +150,18 @@ struct StoreBF16 {
     using T = __nv_bfloat16;
     static constexpr bool kScaled = true;
     static constexpr bool kStrided = true;
+    static constexpr bool kOff32 = false;
     static __device__ __forceinline__ float ld(const T* q) { return __bfloat162float(__ldg(q)); }
     static __device__ __forceinline__ void st(T* q, float v) { *q = __float2bfloat16_rn(v); }
 };
+// A storage format addressed by 32-bit offsets (see kOff32 above).
+template <class B>
+struct Off32 : B {
+    static constexpr bool kOff32 = true;
+};
+using StoreF32o = Off32<StoreF32>;
+using StoreF16o = Off32<StoreF16>;
+using StoreBF16o = Off32<StoreBF16>;
 
 // Weight that multiplies the stored value of plane q (q < 19: f, else g).
 template <class S>
@@ -170,14 +185,40 @@ __device__ __forceinline__ typename S::T* plane_out(const Planes& pl, const KPar
     if constexpr (S::kStrided) return static_cast<typename S::T*>(pl.out[0]) + q * p.sq;
     else return static_cast<typename S::T*>(pl.out[q]);
 }
+// Element idx of plane q of the planes being read / written; the `either` form takes plane J
+// instead of I when `other` is set.
+template <class S>
+__device__ __forceinline__ const typename S::T* at_in(const Planes& pl, const KParams& p, int q,
+                                                      int idx) {
+    if constexpr (S::kOff32)
+        return static_cast<const typename S::T*>(pl.base_in) + (unsigned)(pl.off_in[q] + idx);
+    else
+        return plane_in<S>(pl, p, q) + idx;
+}
+template <class S>
+__device__ __forceinline__ typename S::T* at_out(const Planes& pl, const KParams& p, int q, int idx) {
+    if constexpr (S::kOff32)
+        return static_cast<typename S::T*>(pl.base_out) + (unsigned)(pl.off_out[q] + idx);
+    else
+        return plane_out<S>(pl, p, q) + idx;
+}
+template <class S>
+__device__ __forceinline__ const typename S::T* at_in_either(const Planes& pl, const KParams& p,
+                                                             int I, int J, bool other, int idx) {
+    if constexpr (S::kOff32)
+        return static_cast<const typename S::T*>(pl.base_in) +
+               (unsigned)((other ? pl.off_in[J] : pl.off_in[I]) + idx);
+    else
+        return (other ? plane_in<S>(pl, p, J) : plane_in<S>(pl, p, I)) + idx;
+}
 // Deviation of plane q at site index idx of the planes being read / written.
 template <class S>
 __device__ __forceinline__ float ldp(const Planes& pl, const KParams& p, int q, int idx) {
-    return S::ld(plane_in<S>(pl, p, q) + idx) * plane_scale<S>(p, q);
+    return S::ld(at_in<S>(pl, p, q, idx)) * plane_scale<S>(p, q);
 }
 template <class S>
 __device__ __forceinline__ void stp(const Planes& pl, const KParams& p, int q, int idx, float v) {
-    S::st(plane_out<S>(pl, p, q) + idx, v * plane_inv_scale<S>(p, q));
+    S::st(at_out<S>(pl, p, q, idx), v * plane_inv_scale<S>(p, q));
 }
 // D3Q7 population i at site idx as the deviation g_i - omega_i sigma T0.  The 16-bit formats
 // store (g_i - omega_i sigma T_x) / omega_i against the site's own temperature T_x, whose
@@ -192,7 +233,7 @@ __device__ __forceinline__ float ldg_dev(const Planes& pl, const KParams& p, int
         // repeats this arithmetic and must give the same bits
         const float sc = i == 0 ? p.om0 : p.om1;
         return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx),
-                                       S::ld(plane_in<S>(pl, p, kQ + i) + idx)));
+                                       S::ld(at_in<S>(pl, p, kQ + i, idx))));
     }
 }
 // Stores post-collision g' (deviation from omega_i sigma T0) of a site whose temperature
@@ -204,7 +245,7 @@ __device__ __forceinline__ void stg_dev(const Planes& pl, const KParams& p, int 
         stp<S>(pl, p, kQ + i, idx, v);
     } else {
         const float isc = i == 0 ? p.iom0 : p.iom1;
-        S::st(plane_out<S>(pl, p, kQ + i) + idx, __fmaf_rn(v, isc, -__fmul_rn(p.sigma, dT)));
+        S::st(at_out<S>(pl, p, kQ + i, idx), __fmaf_rn(v, isc, -__fmul_rn(p.sigma, dT)));
     }
 }
 
@@ -296,6 +337,38 @@ __device__ __forceinline__ float bounce_moving(const KParams& p, int face, float
                                (float)L::ez(I) * p.face_u[face][2]);
     return __fmaf_rn(__fmul_rn(6.0f * L::w(I), p.rho0), eu, bb);
 }
+// The same for a pull of I that crosses the velocity faces vm (non-zero): the lowest-numbered
+// one applies.  The candidate faces are those along I's non-zero components, known at compile
+// time, so the face velocity is picked with selects of parameter values instead of an
+// indexed read of the parameter block.
+template <class L, int I>
+__device__ __forceinline__ float bounce_moving_on(const KParams& p, unsigned vm, float bb) {
+    constexpr int ex = L::ex(I), ey = L::ey(I), ez = L::ez(I);
+    constexpr int fx = ex == 1 ? 0 : 1, fy = ey == 1 ? 2 : 3, fz = ez == 1 ? 4 : 5;
+    float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+    bool found = false;
+    if constexpr (ex != 0) {
+        if (vm & (1u << fx)) {
+            u0 = p.face_u[fx][0]; u1 = p.face_u[fx][1]; u2 = p.face_u[fx][2];
+            found = true;
+        }
+    }
+    if constexpr (ey != 0) {
+        if (!found && (vm & (1u << fy))) {
+            u0 = p.face_u[fy][0]; u1 = p.face_u[fy][1]; u2 = p.face_u[fy][2];
+            found = true;
+        }
+    }
+    if constexpr (ez != 0) {
+        if (!found) { u0 = p.face_u[fz][0]; u1 = p.face_u[fz][1]; u2 = p.face_u[fz][2]; }
+    }
+    const float eu = __fadd_rn(__fadd_rn((float)ex * u0, (float)ey * u1), (float)ez * u2);
+    return __fmaf_rn(__fmul_rn(6.0f * L::w(I), p.rho0), eu, bb);
+}
+// Face a D3Q7 velocity crosses (each has one non-zero component): x-low, x-high, y-low, ...
+constexpr int face7(int i) {
+    return ex7(i) == 1 ? 0 : ex7(i) == -1 ? 1 : ey7(i) == 1 ? 2 : ey7(i) == -1 ? 3 : ez7(i) == 1 ? 4 : 5;
+}
 // Convective outflow: p(N-1, t+1) = (p(N-1, t) + U p(N-2, t+1)) / (1 + U) = a old + b inner.
 __device__ __forceinline__ float outflow_blend(const KParams& p, float old, float inner) {
     return __fmaf_rn(p.out_a, old, __fmul_rn(p.out_b, inner));
@@ -336,7 +409,7 @@ __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, cons
     const float bb = ldp<S>(pl, p, L::opp(I), n.s);
     if (cr & p.wall_mask) return bb;
     unsigned vm = cr & p.vel_mask;
-    if (vm) return bounce_moving<L, I>(p, __ffs(vm) - 1, bb);
+    if (vm) return bounce_moving_on<L, I>(p, vm, bb);
     if constexpr (OUTF && ex == -1) {
         // convective outflow with p(N-2, t+1) pulled at the inner neighbour: the source of
         // x - 1 along -x is x itself, at the same y/z offsets (a y/z face crossed here is a
@@ -357,7 +430,7 @@ __device__ __forceinline__ float pull_g(const Planes& pl, const KParams& p, cons
     if (cr == 0u)
         return ldg_dev<S>(pl, p, I, n.s + axis_off(ex, n.xm, n.xp) + axis_off(ey, n.ym, n.yp) +
                      axis_off(ez, n.zm, n.zp));
-    const int face = __ffs(cr) - 1;  // a D3Q7 velocity crosses one face at most
+    constexpr int face = face7(I);  // a D3Q7 velocity crosses one face at most
     const int kind = p.heat_kind[face];
     if constexpr (OUTF && ex == -1) {
         if (kind == 3) {  // g_I(N-2, t+1) = g*_I(N-1, t)
@@ -521,8 +594,7 @@ __device__ __forceinline__ void gather_interior(const Planes& pl, const KParams&
 template <class S>
 __device__ __forceinline__ float ldp_either(const Planes& pl, const KParams& p, int I, int J,
                                             bool other, int idx) {
-    const typename S::T* q = other ? plane_in<S>(pl, p, J) : plane_in<S>(pl, p, I);
-    return S::ld(q + idx) * plane_scale<S>(p, I);
+    return S::ld(at_in_either<S>(pl, p, I, J, other, idx)) * plane_scale<S>(p, I);
 }
 template <class S>
 __device__ __forceinline__ float ldg_either(const Planes& pl, const KParams& p, int I, int J,
@@ -531,8 +603,8 @@ __device__ __forceinline__ float ldg_either(const Planes& pl, const KParams& p, 
         return ldp_either<S>(pl, p, kQ + I, kQ + J, other, idx);
     } else {
         const float sc = I == 0 ? p.om0 : p.om1;
-        const typename S::T* q = other ? plane_in<S>(pl, p, kQ + J) : plane_in<S>(pl, p, kQ + I);
-        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx), S::ld(q + idx)));
+        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx),
+                                       S::ld(at_in_either<S>(pl, p, kQ + I, kQ + J, other, idx))));
     }
 }
 
@@ -565,7 +637,7 @@ __device__ __forceinline__ void sel_fix_f(const KParams& p, const AxisOff& o, co
          if (c != 0u && !(c & p.wall_mask)) {
              const unsigned vm = c & p.vel_mask;
              if (vm) {
-                 f[I] = bounce_moving<L, I>(p, __ffs(vm) - 1, f[I]);
+                 f[I] = bounce_moving_on<L, I>(p, vm, f[I]);
              } else if constexpr (OUTF && ex == -1) {
                  f[I] = outflow_blend(p, hf[L::slot(I)], f[I]);
                  via[I] = true;
@@ -574,6 +646,20 @@ __device__ __forceinline__ void sel_fix_f(const KParams& p, const AxisOff& o, co
      }()),
      ...);
 }
+template <int... I>
+__device__ __forceinline__ void sel_fix_g(const KParams& p, const AxisOff& o, bool gout,
+                                          const float* hf, float* g,
+                                          std::integer_sequence<int, I...>) {
+    (([&] {
+         const unsigned c = src_cross<ex7(I), ey7(I), ez7(I)>(o.cross);
+         if (c == 0u) return;
+         constexpr int face = face7(I);
+         if (I == 2 && gout) g[I] = outflow_blend(p, hf[5], g[I]);
+         else if (p.heat_kind[face] == 2) g[I] = -g[I] + p.heat_abb[face];  // anti-bounce-back
+     }()),
+     ...);
+}
+
 template <bool OUTF, class S, class L>
 __device__ __forceinline__ void gather_sel(const Planes& pl, const KParams& p, int x, int y, int z,
                                            int s, float* f, float* g) {
@@ -603,15 +689,7 @@ __device__ __forceinline__ void gather_sel(const Planes& pl, const KParams& p, i
     bool via[L::kQ];
     sel_fix_f<OUTF, S, L>(p, o, hf, f, via, std::make_integer_sequence<int, L::kQ>{});
     if (OUTF && (o.cross & 2u)) outflow_anchor<L>(f, via);
-#pragma unroll
-    for (int i = 0; i < kQT; ++i) {
-        const unsigned c = axis_cross(ex7(i), o.cross, 1u, 2u) | axis_cross(ey7(i), o.cross, 4u, 8u) |
-                           axis_cross(ez7(i), o.cross, 16u, 32u);
-        if (c == 0u) continue;
-        const int face = __ffs(c) - 1;
-        if (i == 2 && gout) g[i] = outflow_blend(p, hf[5], g[i]);
-        else if (p.heat_kind[face] == 2) g[i] = -g[i] + p.heat_abb[face];  // anti-bounce-back
-    }
+    sel_fix_g(p, o, gout, hf, g, std::make_integer_sequence<int, kQT>{});
 }
 
 // ---- collision -------------------------------------------------------------------------------
@@ -1056,13 +1134,107 @@ __device__ __forceinline__ Macro nee_site(const Planes& pl, const KParams& p, in
 }
 
 // ---- kernels ---------------------------------------------------------------------------------
-// Pull of one site: unconditional loads when no lane of the warp crosses a non-periodic face
-// (`warp_fast`, a warp-uniform choice made by the caller with site_no_cross), else the
-// one-round select path.
+// Pull of a site whose y and z neighbours need no rule (yz_fast) but which may lie on a
+// non-periodic x face: the populations with e_x = 0 are plain loads; those with e_x = +1
+// (-1) read the opposite plane of the site itself on a lane at the x-low (x-high) face, or,
+// for the outflow, plane I at the inner source.  One round of loads, then the rules of the
+// two x faces, whose parameters are compile-time entries of the parameter block.
+template <bool OUTF, class S, class L, int... I>
+__device__ __forceinline__ void xsel_load_f(const Planes& pl, const KParams& p, int s,
+                                            const AxisOff& o, bool cxm, bool cxp, bool xout,
+                                            float* f, std::integer_sequence<int, I...>) {
+    (([&] {
+         constexpr int ex = L::ex(I), ey = L::ey(I), ez = L::ez(I);
+         const int src = s + src_off<ex, ey, ez>(o);
+         if constexpr (ex == 0) {
+             f[I] = ldp<S>(pl, p, I, src);
+         } else {
+             const bool bounce = ex == 1 ? cxm : (cxp && !xout);
+             f[I] = ldp_either<S>(pl, p, I, L::opp(I), bounce, bounce ? s : src);
+         }
+     }()),
+     ...);
+}
+template <bool OUTF, class S, class L, int... I>
+__device__ __forceinline__ void xsel_fix_f(const KParams& p, bool cxm, bool cxp, bool xout,
+                                           const float* hf, float* f, bool* via,
+                                           std::integer_sequence<int, I...>) {
+    const bool vlo = (p.vel_mask & 1u) && !(p.wall_mask & 1u);
+    const bool vhi = (p.vel_mask & 2u) && !(p.wall_mask & 2u);
+    (([&] {
+         constexpr int ex = L::ex(I);
+         via[I] = false;
+         if constexpr (ex == 1) {
+             if (cxm && vlo) f[I] = bounce_moving<L, I>(p, 0, f[I]);
+         } else if constexpr (ex == -1) {
+             if (cxp) {
+                 if (xout) {
+                     if constexpr (OUTF) {
+                         f[I] = outflow_blend(p, hf[L::slot(I)], f[I]);
+                         via[I] = true;
+                     }
+                 } else if (vhi) {
+                     f[I] = bounce_moving<L, I>(p, 1, f[I]);
+                 }
+             }
+         }
+     }()),
+     ...);
+}
+template <bool OUTF, class S, class L>
+__device__ __forceinline__ void gather_xsel(const Planes& pl, const KParams& p, int x, int y,
+                                            int z, int s, float* f, float* g) {
+    const AxisOff o = axis_offsets(p, x, y, z);
+    const bool cxm = (o.cross & 1u) != 0u, cxp = (o.cross & 2u) != 0u;
+    // the x-high face applies the outflow rule (it is the outflow face, and not a wall or
+    // velocity face, whose rules win)
+    const bool xout = OUTF && !(p.wall_mask & 2u) && !(p.vel_mask & 2u);
+    xsel_load_f<OUTF, S, L>(pl, p, s, o, cxm, cxp, xout, f, std::make_integer_sequence<int, L::kQ>{});
+    const bool gout = OUTF && cxp && p.heat_kind[1] == 3;
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) {
+        const int src = s + axis_off(ex7(i), o.xm, o.xp) + axis_off(ey7(i), o.ym, o.yp) +
+                        axis_off(ez7(i), o.zm, o.zp);
+        if (ex7(i) == 0) {
+            g[i] = ldg_dev<S>(pl, p, i, src);
+        } else {
+            const bool bounce = ex7(i) == 1 ? cxm : (cxp && !gout);
+            g[i] = ldg_either<S>(pl, p, i, opp7(i), bounce, bounce ? s : src);
+        }
+    }
+    float hf[kOutSlots];
+    if constexpr (OUTF) {
+        const int yz = y + p.ny * z;
+#pragma unroll
+        for (int k = 0; k < kOutSlots; ++k) hf[k] = cxp ? __ldg(pl.hin + k * p.nyz + yz) : 0.0f;
+    }
+    if (!(cxm || cxp)) return;
+    bool via[L::kQ];
+    xsel_fix_f<OUTF, S, L>(p, cxm, cxp, xout, hf, f, via, std::make_integer_sequence<int, L::kQ>{});
+    if (OUTF && cxp && xout) outflow_anchor<L>(f, via);
+    if (cxm && p.heat_kind[0] == 2) g[1] = -g[1] + p.heat_abb[0];
+    if (cxp) {
+        if (gout) g[2] = outflow_blend(p, hf[5], g[2]);
+        else if (p.heat_kind[1] == 2) g[2] = -g[2] + p.heat_abb[1];
+    }
+}
+
+// How the sites of a warp gather: kGatherInterior when no pull of any of its sites crosses a
+// non-periodic face, kGatherX when only x faces are crossed (the y and z neighbours of every
+// site need no rule), else kGatherAny.  Warp-uniform: the caller votes (warp_gather_mode).
+enum { kGatherInterior = 0, kGatherX = 1, kGatherAny = 2 };
+__device__ __forceinline__ int warp_gather_mode(const KParams& p, int x, int y, int z, bool active) {
+    if (__all_sync(0xffffffffu, !active || site_no_cross(p, x, y, z))) return kGatherInterior;
+    if (__all_sync(0xffffffffu, !active || yz_fast(p, y, z))) return kGatherX;
+    return kGatherAny;
+}
+
+// Pull of one site in the gather mode of its warp.
 template <bool OUTF, class S, class L = D3Q19>
 __device__ __forceinline__ void gather_site(const Planes& pl, const KParams& p, int x, int y, int z,
-                                            int s, bool warp_fast, float* f, float* g) {
-    if (warp_fast) gather_interior<S, L>(pl, p, x, y, z, s, f, g);
+                                            int s, int mode, float* f, float* g) {
+    if (mode == kGatherInterior) gather_interior<S, L>(pl, p, x, y, z, s, f, g);
+    else if (mode == kGatherX) gather_xsel<OUTF, S, L>(pl, p, x, y, z, s, f, g);
     else gather_sel<OUTF, S, L>(pl, p, x, y, z, s, f, g);
 }
 
@@ -1112,7 +1284,7 @@ __global__ void __maxnreg__(HET ? 72 : 64)
     const bool valid = x < p.nx && y < p.ny;
     const unsigned nb = (NEE && valid) ? nee_bits(p, x, y, z) : 0u;  // node-wall site
     const bool streams = valid && nb == 0u;
-    const bool warp_fast = __all_sync(0xffffffffu, !streams || site_no_cross(p, x, y, z));
+    const int mode = warp_gather_mode(p, x, y, z, streams);
     if (!valid) return;
     float f[L::kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
@@ -1126,7 +1298,7 @@ __global__ void __maxnreg__(HET ? 72 : 64)
             return;
         }
     }
-    gather_site<OUTF, S, L>(pl, p, x, y, z, s, warp_fast, f, g);
+    gather_site<OUTF, S, L>(pl, p, x, y, z, s, mode, f, g);
     finish_site<HET, OUTF, S, ENTH, L>(pl, p, x, y, z, s, f, g);
 }
 
@@ -1146,6 +1318,7 @@ struct StoreF32InPlace {  // FP32 loads through the coherent path: the copy is w
     using T = float;
     static constexpr bool kScaled = false;
     static constexpr bool kStrided = false;  // the plane tables are permuted
+    static constexpr bool kOff32 = false;
     static __device__ __forceinline__ float ld(const T* q) { return *q; }
     static __device__ __forceinline__ void st(T* q, float v) { *q = v; }
 };
@@ -1213,13 +1386,13 @@ __device__ __forceinline__ void aa_local_all(const Planes& pl, const Planes& pw,
 }
 
 // Pull-step update of one valid site (W -> N): pl.in is the permuted table (logical q at
-// physical opp(q)), pl.out the identity table of the same copy; warp_fast as in step_kernel.
+// physical opp(q)), pl.out the identity table of the same copy; mode as in step_kernel.
 template <bool HET>
 __device__ __forceinline__ void aa_pull_site(const KParams& p, const Planes& pl, int x, int y,
-                                             int z, bool warp_fast) {
+                                             int z, int mode) {
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
-    gather_site<false, StoreF32InPlace, D3Q19>(pl, p, x, y, z, s, warp_fast, f, g);
+    gather_site<false, StoreF32InPlace, D3Q19>(pl, p, x, y, z, s, mode, f, g);
     const Medium md = medium_at<HET>(p, s);
     collide_on<true, false, D3Q19>(p, md, f, g);
     const Nbr n = neighbourhood(p, x, y, z);
@@ -1258,8 +1431,8 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     const bool valid = x < p.nx && y < p.ny;
-    const bool warp_fast = __all_sync(0xffffffffu, !valid || site_no_cross(p, x, y, z));
-    if (valid) aa_pull_site<HET>(p, pl, x, y, z, warp_fast);
+    const int mode = warp_gather_mode(p, x, y, z, valid);
+    if (valid) aa_pull_site<HET>(p, pl, x, y, z, mode);
 }
 
 // Local step over one lattice.
@@ -1353,13 +1526,13 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     for (int r = 0; r < rows; ++r) {
         const int z = z0 + r;
         if (z >= p.nz) break;  // uniform over the block
-        // every lane of the warp reaches the vote; only the valid lanes update a site (the
+        // every lane of the warp reaches the votes; only the valid lanes update a site (the
         // site update itself holds no warp-wide vote)
-        const bool warp_fast = __all_sync(0xffffffffu, !valid || site_no_cross(p, x, y, z));
+        const int mode = warp_gather_mode(p, x, y, z, valid);
         if (valid) {
             float f[kQ], g[kQT];
             const int s = x + p.nx * (y + p.ny * z);
-            gather_site<OUTF, S>(pl, p, x, y, z, s, warp_fast, f, g);
+            gather_site<OUTF, S>(pl, p, x, y, z, s, mode, f, g);
             finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
         }
     }
@@ -1390,11 +1563,11 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     for (int r = 0; r < rows; ++r) {
         const int z = z0 + r;
         if (z >= p.nz) break;  // uniform over the block
-        // every lane reaches the vote; only the valid lanes update a site
-        const bool warp_fast = __all_sync(0xffffffffu, !valid || site_no_cross(p, x, y, z));
+        // every lane reaches the votes; only the valid lanes update a site
+        const int mode = warp_gather_mode(p, x, y, z, valid);
         if (!valid) continue;
         if (local) aa_local_site<HET>(p, L->pl[1], L->pl[0], x, y, z);
-        else aa_pull_site<HET>(p, L->pl[0], x, y, z, warp_fast);
+        else aa_pull_site<HET>(p, L->pl[0], x, y, z, mode);
     }
 }
 
@@ -1746,14 +1919,20 @@ int block_x(int nx, int block_threads) { return block_x_of(nx, block_threads); }
 
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
-                              bool enthalpy, int flip, cudaStream_t st) {
+                              bool enthalpy, bool off32, int flip, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
     if (enthalpy) {
         batch_step_kernel<false, false, StoreF32, true>
             <<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
         return cudaGetLastError();
     }
-    return with_storage(storage, [&](auto tag) {
+    auto pick = [&](auto&& fn) {
+        if (!off32) return with_storage(storage, fn);
+        if (storage == 1) return fn(StoreF16o{});
+        if (storage == 2) return fn(StoreBF16o{});
+        return fn(StoreF32o{});
+    };
+    return pick([&](auto tag) {
         using S = decltype(tag);
         if (het && outflow)
             batch_step_kernel<true, true, S><<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
@@ -1813,12 +1992,18 @@ cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, bool p
                                 : step_kernel<false, false, StoreF32, false, D3Q15>);
         return launch_kernel(pdl, k, grid, block, 0, st, p, pl);
     }
-    return with_storage(p.storage, [&](auto tag) {
+    auto go = [&](auto tag) {
         using S = decltype(tag);
         auto k = het ? (outflow ? step_kernel<true, true, S> : step_kernel<true, false, S>)
                      : (outflow ? step_kernel<false, true, S> : step_kernel<false, false, S>);
         return launch_kernel(pdl, k, grid, block, 0, st, p, pl);
-    });
+    };
+    if (p.off32) {  // 32-bit plane offsets (every lattice below ~82 M sites)
+        if (p.storage == 1) return go(StoreF16o{});
+        if (p.storage == 2) return go(StoreBF16o{});
+        return go(StoreF32o{});
+    }
+    return with_storage(p.storage, go);
 }
 
 cudaError_t launch_aa_step(const KParams& p, bool local, const Planes& pl, const Planes& pw,

@@ -151,7 +151,7 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
     // global-memory path takes the wider yz_fast set on its fast branch
     const bool yz_in = y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1;
     const bool warp_yz_in = __all_sync(0xffffffffu, yz_in || !valid);
-    const bool warp_fast = __all_sync(0xffffffffu, !valid || site_no_cross(p, x, y, z));
+    const int mode = warp_gather_mode(p, x, y, z, valid);
     const unsigned lanes = __ballot_sync(0xffffffffu, valid);
     const bool xface = x == 0 || x == p.nx - 1;
     const bool periodic_x_face = (p.per_mask & 3u) && __any_sync(0xffffffffu, valid && xface);
@@ -159,7 +159,7 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
     float f[kQ], g[kQT];
     const int s = x + p.nx * (y + p.ny * z);
     if (!warp_yz_in || periodic_x_face) {
-        gather_site<OUTF, S, D3Q19>(pl, p, x, y, z, s, warp_fast, f, g);
+        gather_site<OUTF, S, D3Q19>(pl, p, x, y, z, s, mode, f, g);
     } else {
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
