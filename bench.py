@@ -465,31 +465,50 @@ def run_sweep(args, gb):
 
 
 # ---- serving workload ------------------------------------------------------------------------
-def _serve_stream(gb, reqs, budget, chunk, tol, max_steps, alone, fill=0):
-    """Submit each request at its arrival time and run the serving loop; with alone=True each
-    request gets a server of its own once the previous one is done (one solve at a time)."""
+def _served_storage(gb, pb, tol):
+    """The storage a request is served in: a 16-bit format whose residual floor lies above the
+    tolerance is replaced by FP32 (the rule of lbm_server_submit)."""
+    st = pb.get("storage", "fp32")
+    return "fp32" if st in gb.RESIDUAL_FLOOR and tol < gb.RESIDUAL_FLOOR[st] else st
+
+
+def _solo_stream(gb, reqs, chunk, tol, max_steps):
+    """One solve at a time: each request, in arrival order and not before it arrives, is
+    solved alone through the single-lattice path (lbm_step, a residual every `chunk` steps)
+    until it converges or reaches its step limit."""
     t0 = time.perf_counter()
     results = []
-    if alone:
-        for arrival, pb in reqs:
-            while time.perf_counter() - t0 < arrival:
-                time.sleep(0.0005)
-            srv = gb.Server(budget_bytes=budget, chunk=chunk)
-            sub = time.perf_counter() - t0
-            srv.submit(pb, tol=tol, max_steps=max_steps)
-            while True:
-                na, nq = srv.advance()
-                got = srv.poll()
-                if got:
-                    r = got[0]
-                    r["arrival"] = arrival
-                    r["finished"] = sub + (r["t_done"] - r["t_submit"])
-                    results.append(r)
-                if na == 0 and nq == 0:
-                    break
-            srv.close()
-        return results, time.perf_counter() - t0
-    srv = gb.Server(budget_bytes=budget, chunk=chunk, max_active_sites=fill)
+    for arrival, pb in reqs:
+        while time.perf_counter() - t0 < arrival:
+            time.sleep(0.0005)
+        start = time.perf_counter() - t0
+        storage = _served_storage(gb, pb, tol)
+        lat = gb.Lattice(dict(pb, storage=storage))
+        steps, status = 0, "max_steps"
+        while True:
+            lat.step(chunk)
+            steps += chunk
+            try:
+                ru, rT = lat.residual()
+            except gb.LbmError:
+                status = "unstable"
+                break
+            if ru < tol and rT < tol:
+                status = "converged"
+                break
+            if steps >= max_steps:
+                break
+        lat.close()
+        results.append({"arrival": arrival, "started": start, "finished": time.perf_counter() - t0,
+                        "sites": lat.ns, "steps": steps, "status": status, "storage": storage})
+    return results, time.perf_counter() - t0
+
+
+def _serve_stream(gb, reqs, budget, chunk, tol, max_steps, fill=0, policy="fifo"):
+    """Submit each request at its arrival time and run the serving loop (continuous batching)."""
+    t0 = time.perf_counter()
+    results = []
+    srv = gb.Server(budget_bytes=budget, chunk=chunk, max_active_sites=fill, policy=policy)
     offset = None
     pending = list(reqs)
     arrivals = {}
@@ -520,7 +539,9 @@ def _latency_summary(results):
     return {"p50_s": round(pct(0.5), 4), "p99_s": round(pct(0.99), 4),
             "mlups": round(lups / span / 1e6, 2), "makespan_s": round(span, 3),
             "statuses": {s: sum(1 for r in results if r["status"] == s)
-                         for s in sorted({r["status"] for r in results})}}
+                         for s in sorted({r["status"] for r in results})},
+            "storage": {s: sum(1 for r in results if r.get("storage") == s)
+                        for s in sorted({r.get("storage") for r in results})}}
 
 
 def run_serve(args, gb):
@@ -528,14 +549,13 @@ def run_serve(args, gb):
 
     reqs = serving_mix(args.requests, seed=5)
     tol, max_steps, chunk = 1e-6, args.max_steps or 50000, 100
-    mixed, _ = _serve_stream(gb, reqs, 0, chunk, tol, max_steps, alone=False, fill=args.fill)
-    uncapped = None
-    if args.fill:
-        uncapped = _latency_summary(_serve_stream(gb, reqs, 0, chunk, tol, max_steps,
-                                                  alone=False, fill=0)[0])
-    solo, _ = _serve_stream(gb, reqs, 0, chunk, tol, max_steps, alone=True)
-    return (_latency_summary(mixed), _latency_summary(solo), len(reqs), tol, max_steps,
-            uncapped)
+    runs = {}
+    runs["fifo"] = _latency_summary(_serve_stream(gb, reqs, 0, chunk, tol, max_steps,
+                                                  fill=args.fill, policy="fifo")[0])
+    runs["backfill"] = _latency_summary(_serve_stream(gb, reqs, 0, chunk, tol, max_steps,
+                                                      fill=args.fill, policy="backfill")[0])
+    runs["one_at_a_time"] = _latency_summary(_solo_stream(gb, reqs, chunk, tol, max_steps)[0])
+    return runs, len(reqs), tol, max_steps
 
 
 # ---- our arm ---------------------------------------------------------------------------------
@@ -568,23 +588,26 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
         return 0
     if args.workload == "serve":
-        mixed, solo, n, tol, max_steps, uncapped = run_serve(args, gb)
+        runs, n, tol, max_steps = run_serve(args, gb)
         if rank != 0:
             return 0
+        best = max(("fifo", "backfill"), key=lambda k: runs[k]["mlups"])
         line = {"metric": "time-to-steady-state p50/p99 and aggregate MLUPS (serving)",
-                "value": mixed["mlups"], "unit": UNIT, "n_gpus": ws, "steps": None,
+                "value": runs[best]["mlups"], "unit": UNIT, "n_gpus": ws, "steps": None,
                 "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32-math, fp32 or fp16 storage per request", "data": "synthetic",
                 "config": {"workload": f"{n} requests, Poisson 20/s (seed 5): porous cavities "
                                        "32^3-192^3, 4WxWxW channels (W 32, 64) and, one "
                                        "in ten, melting cavities (enthalpy model)",
                            "tol": tol, "max_steps": max_steps, "chunk": 100,
-                           "admission": "FIFO by device footprint (80% of free memory)"
-                                        + (f", at most {args.fill} sites admitted" if args.fill else "")},
-                "latency": {"p50_s": mixed["p50_s"], "p99_s": mixed["p99_s"]},
-                "serving": mixed, "serving_uncapped": uncapped, "one_at_a_time": solo,
-                "speedup_mlups": round(mixed["mlups"] / solo["mlups"], 3),
-                "speedup_p50": round(solo["p50_s"] / mixed["p50_s"], 3)}
+                           "admission": "by device footprint (80% of free memory)"
+                                        + (f", at most {args.fill} sites admitted" if args.fill else ""),
+                           "storage_rule": "16-bit requests whose tolerance lies below the "
+                                           "format's residual floor are served in FP32"},
+                "policy": best, "latency": {"p50_s": runs[best]["p50_s"], "p99_s": runs[best]["p99_s"]},
+                "serving": runs,
+                "speedup_mlups": round(runs[best]["mlups"] / runs["one_at_a_time"]["mlups"], 3),
+                "speedup_p50": round(runs["one_at_a_time"]["p50_s"] / runs[best]["p50_s"], 3)}
         print(json.dumps(line), flush=True)
         return 0
     if args.workload == "batch64":

@@ -421,7 +421,8 @@ lbm_status lbm_footprint(const lbm_params* p, int has_phi_field, unsigned long l
  * A server takes solve requests as they arrive, admits them in arrival order while their
  * device footprint fits its memory budget, keeps their populations resident and advances all
  * admitted lattices together with batched launches (lbm_batch_*) in chunks of `chunk` steps.
- * After every chunk each lattice's steady-state residual (lbm_residual) is checked; a request
+ * After every chunk each lattice's steady-state residual (lbm_residual; one synchronisation of
+ * the server's stream for all of them) is checked; a request
  * finishes when both residuals fall below its tolerance, when it reaches its step limit, or
  * when its state stops being finite, and its memory is released for the next request.  A
  * request's result depends only on its own problem: it is the same alone and in the mix. */
@@ -435,6 +436,20 @@ typedef struct lbm_medium {
 
 enum { LBM_REQ_CONVERGED = 0, LBM_REQ_MAX_STEPS = 1, LBM_REQ_UNSTABLE = 2, LBM_REQ_FAILED = 3 };
 
+/* Residual floors of the 16-bit formats: the rounding of the stored deviations keeps the
+ * steady-state residual of a 16-bit solve above about these values (measured on the porous
+ * cavities of the precision sweep: FP16 0.8e-4 .. 1.4e-4 in u, BF16 0.7e-3 .. 1.1e-3).  A request
+ * whose tolerance lies below the floor of its storage format is served in FP32 storage
+ * (lbm_result.storage), so that it can converge at the accuracy it asks for. */
+#define LBM_RESIDUAL_FLOOR_FP16 2e-4
+#define LBM_RESIDUAL_FLOOR_BF16 2e-3
+
+/* Admission policies (lbm_server_set_policy).  FIFO: requests are admitted strictly in
+ * arrival order; the first one that does not fit (memory budget or fill cap) stops admission.
+ * BACKFILL: later requests that fit may be admitted ahead of one that does not, until that
+ * one has waited 20 rounds with others passing it; then admission is FIFO again until it is in. */
+enum { LBM_ADMIT_FIFO = 0, LBM_ADMIT_BACKFILL = 1 };
+
 /* Result of a finished request.  Times are seconds on the server's host clock since
  * lbm_server_create: submitted, admitted (state allocated), finished. */
 typedef struct lbm_result {
@@ -447,6 +462,7 @@ typedef struct lbm_result {
     double t_submit, t_admit, t_done;
     unsigned long long bytes;   /* device footprint */
     long long sites;
+    int storage;                /* LBM_STORE_* the request was served in */
 } lbm_result;
 
 /* Create a server on the current device with a device-memory budget in bytes (0: 80 % of
@@ -475,6 +491,9 @@ lbm_status lbm_server_set_output(lbm_server* s, long long id, float* u, float* T
 
 /* Move up to `max` finished results into out; *n receives how many. */
 lbm_status lbm_server_poll(lbm_server* s, lbm_result* out, int max, int* n);
+
+/* Admission policy: LBM_ADMIT_FIFO (the default) or LBM_ADMIT_BACKFILL.  LBM_EINVAL otherwise. */
+lbm_status lbm_server_set_policy(lbm_server* s, int policy);
 
 /* Cap the lattice sites admitted at once (0, the default: no cap).  Beyond the sites that
  * fill the GPU, admitting more requests adds no throughput and only delays the earlier

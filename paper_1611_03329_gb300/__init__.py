@@ -40,7 +40,11 @@ ABI_SYMBOLS = (
     "lbm_server_clock", "lbm_server_destroy", "lbm_server_set_fill", "lbm_set_step_kernel",
     "lbm_get_step_kernel", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
     "lbm_set_launch", "lbm_test_tma_extra_wait", "lbm_server_set_output",
+    "lbm_server_set_policy",
 )
+
+ADMIT_POLICIES = {"fifo": 0, "backfill": 1}
+RESIDUAL_FLOOR = {"fp16": 2e-4, "bf16": 2e-3}  # LBM_RESIDUAL_FLOOR_FP16 / _BF16
 
 # Population schemes (LBM_SCHEME_*).
 SCHEMES = {"pingpong": 0, "aa": 1, "auto": 2}
@@ -125,11 +129,12 @@ class LbmResult(C.Structure):
                 ("r_u", C.c_double), ("r_T", C.c_double), ("nu_avg", C.c_double),
                 ("nu_mp", C.c_double), ("mass_dev", C.c_double), ("heat_dev", C.c_double),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
-                ("bytes", C.c_ulonglong), ("sites", C.c_longlong)]
+                ("bytes", C.c_ulonglong), ("sites", C.c_longlong), ("storage", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {name: getattr(self, name) for name, _ in self._fields_}
         d["status"] = REQ_STATUS.get(self.status, str(self.status))
+        d["storage"] = {v: k for k, v in _STORAGE.items()}.get(self.storage, str(self.storage))
         return d
 
 
@@ -205,6 +210,7 @@ def lib():
         L.lbm_server_advance.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.lbm_server_poll.argtypes = [vp, C.POINTER(LbmResult), C.c_int, C.POINTER(C.c_int)]
         L.lbm_server_set_output.argtypes = [vp, C.c_longlong, fp, fp]
+        L.lbm_server_set_policy.argtypes = [vp, C.c_int]
         L.lbm_server_set_fill.argtypes = [vp, C.c_longlong]
         L.lbm_server_clock.argtypes = [vp]
         L.lbm_server_clock.restype = C.c_double
@@ -518,7 +524,7 @@ class Server:
     call advance() repeatedly, poll() finished results."""
 
     def __init__(self, budget_bytes: int = 0, chunk: int = 100, stream: Optional[int] = None,
-                 max_active_sites: int = 0):
+                 max_active_sites: int = 0, policy: str = "fifo"):
         self._h = C.c_void_p()
         st = lib().lbm_server_create(C.c_ulonglong(budget_bytes), int(chunk),
                                      C.c_void_p(stream or 0), C.byref(self._h))
@@ -528,6 +534,9 @@ class Server:
             st = lib().lbm_server_set_fill(self._h, C.c_longlong(max_active_sites))
             if st != LBM_OK:
                 raise LbmError(st, "lbm_server_set_fill")
+        st = lib().lbm_server_set_policy(self._h, ADMIT_POLICIES[policy])
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_server_set_policy")
 
     def submit(self, pb: dict, tol: float = 1e-6, max_steps: int = 50000) -> int:
         m = LbmMedium()

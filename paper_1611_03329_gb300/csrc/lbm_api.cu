@@ -2,6 +2,7 @@
 // validation, device memory of a context and the launch sequence of each call.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -343,6 +344,8 @@ void fill_kparams(lbm_ctx* c) {
     k.nz = p.nz;
     k.nyz = p.ny * p.nz;
     k.block_threads = c->block_threads;
+    // all 26 planes of a copy and a site index within one plane addressed by an int offset
+    k.off32 = (long long)(lbm::kQ + lbm::kQT + 1) * c->sq <= (long long)INT_MAX ? 1 : 0;
     k.enthalpy = L.enthalpy;
     k.flow_off = L.flow_off;
     if (L.enthalpy) {
@@ -511,15 +514,27 @@ void* plane_ptr(const lbm_ctx* c, int k, int q) {
     return static_cast<char*>(c->pop[k]) + (size_t)phys * (size_t)c->sq * c->elem;
 }
 
+// Element offset of a plane from the start of its copy (0 for a plane the lattice lacks).
+int plane_off(const lbm_ctx* c, const void* base, const void* plane) {
+    if (!plane) return 0;
+    const long long off = (static_cast<const char*>(plane) - static_cast<const char*>(base)) /
+                          (long long)c->elem;
+    return off <= INT_MAX ? (int)off : 0;  // only used when KParams::off32 says all fit
+}
+
 // Plane tables of an AA context's single copy: `in_perm` / `out_perm` select the swapped
 // layout (logical plane q at physical plane opp(q)) for the input / output side.
 lbm::Planes aa_planes(const lbm_ctx* c, bool in_perm, bool out_perm) {
     lbm::Planes pl;
+    pl.base_in = c->pop[0];
+    pl.base_out = c->pop[0];
     for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
         const int pp = lbm::aa_swapped_plane(q);
         char* base = static_cast<char*>(c->pop[0]);
         pl.in[q] = base + (size_t)(in_perm ? pp : q) * (size_t)c->sq * c->elem;
         pl.out[q] = base + (size_t)(out_perm ? pp : q) * (size_t)c->sq * c->elem;
+        pl.off_in[q] = plane_off(c, pl.base_in, pl.in[q]);
+        pl.off_out[q] = plane_off(c, pl.base_out, pl.out[q]);
     }
     pl.hin = nullptr;
     pl.hout = nullptr;
@@ -532,9 +547,13 @@ lbm::Planes aa_planes(const lbm_ctx* c, bool in_perm, bool out_perm) {
 lbm::Planes planes(const lbm_ctx* c, int from) {
     lbm::Planes pl;
     const int to = from ^ 1;
+    pl.base_in = c->pop[from];
+    pl.base_out = c->pop[to];
     for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
         pl.in[q] = has_plane(c, q) ? plane_ptr(c, from, q) : nullptr;
         pl.out[q] = has_plane(c, q) ? plane_ptr(c, to, q) : nullptr;
+        pl.off_in[q] = plane_off(c, pl.base_in, pl.in[q]);
+        pl.off_out[q] = plane_off(c, pl.base_out, pl.out[q]);
     }
     pl.hin = c->hist[from];
     pl.hout = c->hist[to];
@@ -628,6 +647,49 @@ lbm_status encode_tma_maps(lbm_ctx* c) {
                 return fail(c, LBM_EINVAL, "cuTensorMapEncodeTiled(temperature) failed: %d", (int)r);
         }
     }
+    return LBM_OK;
+}
+
+// The steady-state residual in two halves, so that a caller holding many contexts on one
+// stream (the serving loop) synchronises once for all of them.  residual_launch queues the
+// macroscopic fields of the current state, the reduction against the previous snapshot and
+// the copy of its sums into the pinned mirror; residual_collect (after the stream has been
+// synchronised) turns the sums into r_u, r_T and makes the new fields the snapshot.
+lbm_status residual_launch(lbm_ctx* c) {
+    lbm_status st = usable(c);
+    if (st != LBM_OK) return st;
+    if ((st = aa_settle(c)) != LBM_OK) return st;
+    if ((st = ensure_mac(c)) != LBM_OK) return st;
+    float* cu = c->mac + (size_t)(c->snap ^ 1) * 4 * c->ns;  // new fields
+    float* cT = cu + 3 * c->ns;
+    const float* pu = c->mac + (size_t)c->snap * 4 * c->ns;  // snapshot of the previous call
+    const float* pT = pu + 3 * c->ns;
+    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, c->pl[c->cur], nullptr, cu, cT, c->stream));
+    if (!c->have_prev) {  // first call: no snapshot yet, compare the fields with themselves
+        pu = cu;
+        pT = cT;
+    }
+    int nr = lbm::reduction_blocks();
+    LBM_CUDA(lbm::launch_residual(cu, cT, pu, pT, c->ns, c->partials, nr, c->dres, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 5, cudaMemcpyDeviceToHost,
+                             c->stream));
+    return LBM_OK;
+}
+
+lbm_status residual_collect(lbm_ctx* c, double* r_u, double* r_T) {
+    const double* h = c->hres;
+    const bool first = !c->have_prev;
+    c->snap ^= 1;
+    c->have_prev = true;
+    if (h[4] > 0.0) return fail(c, LBM_EUNSTABLE, "velocity or temperature is not finite");
+    // relative change; a field that is zero and unchanged has residual 0
+    auto rel = [](double num, double den) {
+        return den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? HUGE_VAL : 0.0);
+    };
+    double ru = first ? HUGE_VAL : rel(h[0], h[1]);
+    double rT = first ? HUGE_VAL : rel(h[2], h[3]);
+    if (r_u) *r_u = ru;
+    if (r_T) *r_T = rT;
     return LBM_OK;
 }
 
@@ -1097,39 +1159,10 @@ lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
 }
 
 lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
-    lbm_status st = usable(c);
+    lbm_status st = residual_launch(c);
     if (st != LBM_OK) return st;
-    if ((st = aa_settle(c)) != LBM_OK) return st;
-    if ((st = ensure_mac(c)) != LBM_OK) return st;
-    float* cu = c->mac + (size_t)(c->snap ^ 1) * 4 * c->ns;  // new fields
-    float* cT = cu + 3 * c->ns;
-    const float* pu = c->mac + (size_t)c->snap * 4 * c->ns;  // snapshot of the previous call
-    const float* pT = pu + 3 * c->ns;
-    LBM_CUDA(lbm::launch_macros(c->kp, c->outflow, c->pl[c->cur], nullptr, cu, cT,
-                                c->stream));
-    bool first = !c->have_prev;
-    if (first) {
-        pu = cu;
-        pT = cT;
-    }
-    int nr = lbm::reduction_blocks();
-    LBM_CUDA(lbm::launch_residual(cu, cT, pu, pT, c->ns, c->partials, nr, c->dres, c->stream));
-    LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 5, cudaMemcpyDeviceToHost,
-                             c->stream));
-    if (lbm_status s_ = sync_ctx(c)) return s_;
-    const double* h = c->hres;
-    c->snap ^= 1;
-    c->have_prev = true;
-    if (h[4] > 0.0) return fail(c, LBM_EUNSTABLE, "velocity or temperature is not finite");
-    // relative change; a field that is zero and unchanged has residual 0
-    auto rel = [](double num, double den) {
-        return den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? HUGE_VAL : 0.0);
-    };
-    double ru = first ? HUGE_VAL : rel(h[0], h[1]);
-    double rT = first ? HUGE_VAL : rel(h[2], h[3]);
-    if (r_u) *r_u = ru;
-    if (r_T) *r_T = rT;
-    return LBM_OK;
+    if ((st = sync_ctx(c)) != LBM_OK) return st;
+    return residual_collect(c, r_u, r_T);
 }
 
 lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
@@ -1208,6 +1241,7 @@ struct lbm_batch {
         int storage = 0;
         bool het = false, outflow = false, enthalpy = false;
         bool aa = false;  // AA-scheme lattices (one copy each, stepped by batch_aa_kernel)
+        bool off32 = false;  // the members' planes are addressed by 32-bit offsets
         std::vector<int> members;           // indices into ctx
         lbm::BatchLattice* dtab = nullptr;  // device table
         // host mirror in pageable memory: an asynchronous copy from it stages the data before
@@ -1290,7 +1324,7 @@ lbm_status batch_launch_steps(lbm_batch* b, int nsteps, bool tuning) {
                 continue;
             }
             LBM_BCUDA(lbm::launch_batch_step(g.dtab, g.dblk, g.nblocks, b->block_threads, b->rows,
-                                             g.storage, g.het, g.outflow, g.enthalpy,
+                                             g.storage, g.het, g.outflow, g.enthalpy, g.off32,
                                              tuning ? 0 : (t & 1), b->stream));
         }
     return LBM_OK;
@@ -1373,11 +1407,11 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
         lbm_ctx* c = b->ctx[k];
         const int stg = c->prm.storage;
         const bool het = c->lat.has_phi_field != 0, outf = c->outflow;
-        const bool ent = c->lat.enthalpy != 0, aa = c->aa;
+        const bool ent = c->lat.enthalpy != 0, aa = c->aa, o32 = c->kp.off32 != 0;
         lbm_batch::Group* grp = nullptr;
         for (auto& gr : b->groups)
             if (gr.storage == stg && gr.het == het && gr.outflow == outf && gr.enthalpy == ent &&
-                gr.aa == aa)
+                gr.aa == aa && gr.off32 == o32)
                 grp = &gr;
         if (!grp) {
             b->groups.emplace_back();
@@ -1387,6 +1421,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
             grp->outflow = outf;
             grp->enthalpy = ent;
             grp->aa = aa;
+            grp->off32 = o32;
         }
         grp->members.push_back(k);
     }
@@ -1564,6 +1599,7 @@ struct lbm_server {
         double r_u = HUGE_VAL, r_T = HUGE_VAL;
         float* out_u = nullptr;  // caller's host buffers for the final fields (or NULL)
         float* out_T = nullptr;
+        int skipped = 0;  // admission rounds in which later requests were admitted before it
     };
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -1571,6 +1607,7 @@ struct lbm_server {
     unsigned long long budget = 0, used = 0;
     long long max_active_sites = 0;  // 0: no cap
     long long active_sites = 0;
+    int policy = LBM_ADMIT_FIFO;
     int chunk = 100;
     std::deque<Req*> queue;
     std::vector<Req*> active;
@@ -1604,6 +1641,7 @@ void server_finish(lbm_server* s, size_t k, int status) {
     res.t_done = now_s(s->t0);
     res.bytes = r->bytes;
     res.sites = (long long)r->p.nx * r->p.ny * r->p.nz;
+    res.storage = r->p.storage;
     s->done.push_back(res);
     lbm_destroy(r->ctx);
     s->used -= r->bytes;
@@ -1666,6 +1704,11 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
     if (!r) return LBM_ENOMEM;
     r->p = *p;
     r->p.scheme = LBM_SCHEME_PINGPONG;
+    // a 16-bit format cannot bring the residual below its floor: such a request is stored in
+    // FP32, so that it converges at the accuracy it asked for
+    if ((p->storage == LBM_STORE_FP16_DEV && tol < LBM_RESIDUAL_FLOOR_FP16) ||
+        (p->storage == LBM_STORE_BF16_DEV && tol < LBM_RESIDUAL_FLOOR_BF16))
+        r->p.storage = LBM_STORE_FP32;
     if (m) {
         r->phi = m->phi;
         r->K = m->K;
@@ -1677,7 +1720,7 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
     }
     r->tol = tol;
     r->max_steps = max_steps;
-    r->bytes = footprint_of(p, L, m && m->phi_field ? 1 : 0);
+    r->bytes = footprint_of(&r->p, L, m && m->phi_field ? 1 : 0);
     if (r->bytes > s->budget) {
         delete r;
         return LBM_EINVAL;
@@ -1692,16 +1735,28 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
 lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
     if (!s) return LBM_EINVAL;
     if (cudaSetDevice(s->device) != cudaSuccess) return LBM_ECUDA;
-    // admission in arrival order while the head of the queue fits the memory budget and, with
-    // a cap, while the admitted lattices hold fewer sites than the cap (a lone request is
-    // always admitted)
-    while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
-        lbm_server::Req* r = s->queue.front();
+    // admission in arrival order while a request fits the memory budget and, with a cap, the
+    // admitted lattices hold fewer sites than the cap (a lone request is always admitted).
+    // FIFO stops at the first request that does not fit; BACKFILL lets later requests that fit
+    // go ahead of it, until it has been passed over in kMaxSkips rounds.
+    constexpr int kMaxSkips = 20;
+    bool passed = false;
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        lbm_server::Req* r = *it;
         const long long sites = (long long)r->p.nx * r->p.ny * r->p.nz;
-        if (s->max_active_sites > 0 && s->active_sites > 0 &&
-            s->active_sites + sites > s->max_active_sites)
-            break;
-        s->queue.pop_front();
+        const bool fits = s->used + r->bytes <= s->budget &&
+                          !(s->max_active_sites > 0 && s->active_sites > 0 &&
+                            s->active_sites + sites > s->max_active_sites);
+        if (!fits) {
+            if (s->policy != LBM_ADMIT_BACKFILL) break;
+            if (!passed) {  // the oldest waiting request: later ones may pass it ...
+                passed = true;
+                if (++r->skipped > kMaxSkips) break;  // ... but not for ever
+            }
+            ++it;
+            continue;
+        }
+        it = s->queue.erase(it);
         s->active_sites += sites;
         r->t_admit = now_s(s->t0);
         lbm_status st = lbm_create(&r->p, s->stream, &r->ctx);
@@ -1725,17 +1780,21 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
         }
         lbm_status st = lbm_batch_step(s->batch, s->chunk);
         if (st != LBM_OK) return st;
-        for (size_t k = 0; k < s->active.size();) {
+        // every residual queued behind the chunk, then one synchronisation for all of them
+        std::vector<lbm_status> launched(s->active.size());
+        for (size_t k = 0; k < s->active.size(); ++k) launched[k] = residual_launch(s->active[k]->ctx);
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
+        std::vector<int> status(s->active.size(), -1);
+        for (size_t k = 0; k < s->active.size(); ++k) {
             lbm_server::Req* r = s->active[k];
-            st = lbm_residual(r->ctx, &r->r_u, &r->r_T);
-            int status = -1;
-            if (st == LBM_EUNSTABLE) status = LBM_REQ_UNSTABLE;
-            else if (st != LBM_OK) status = LBM_REQ_FAILED;
-            else if (r->r_u < r->tol && r->r_T < r->tol) status = LBM_REQ_CONVERGED;
-            else if (r->ctx->steps >= r->max_steps) status = LBM_REQ_MAX_STEPS;
-            if (status >= 0) server_finish(s, k, status);
-            else ++k;
+            st = launched[k] == LBM_OK ? residual_collect(r->ctx, &r->r_u, &r->r_T) : launched[k];
+            if (st == LBM_EUNSTABLE) status[k] = LBM_REQ_UNSTABLE;
+            else if (st != LBM_OK) status[k] = LBM_REQ_FAILED;
+            else if (r->r_u < r->tol && r->r_T < r->tol) status[k] = LBM_REQ_CONVERGED;
+            else if (r->ctx->steps >= r->max_steps) status[k] = LBM_REQ_MAX_STEPS;
         }
+        for (size_t k = s->active.size(); k-- > 0;)
+            if (status[k] >= 0) server_finish(s, k, status[k]);
     }
     if (s->active.empty() && s->batch) {
         lbm_batch_destroy(s->batch);
@@ -1743,6 +1802,12 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
     }
     if (n_active) *n_active = (int)s->active.size();
     if (n_queued) *n_queued = (int)s->queue.size();
+    return LBM_OK;
+}
+
+lbm_status lbm_server_set_policy(lbm_server* s, int policy) {
+    if (!s || (policy != LBM_ADMIT_FIFO && policy != LBM_ADMIT_BACKFILL)) return LBM_EINVAL;
+    s->policy = policy;
     return LBM_OK;
 }
 

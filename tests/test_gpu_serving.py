@@ -30,7 +30,13 @@ def _requests():
     ]
 
 
-KEYS = ("status", "steps", "r_u", "r_T", "nu_avg", "nu_mp", "mass_dev", "heat_dev")
+KEYS = ("status", "steps", "r_u", "r_T", "nu_avg", "nu_mp", "mass_dev", "heat_dev", "storage")
+
+
+def _tol(pb):
+    """A tolerance each storage format can reach (above the 16-bit residual floors), so the
+    16-bit requests stay 16-bit."""
+    return {"fp16": 5e-4, "bf16": 5e-3}.get(pb.get("storage", "fp32"), 1e-6)
 
 
 def _drain(srv, limit=10000):
@@ -55,22 +61,23 @@ def _same(a, b):
 def test_result_is_the_same_alone_and_in_the_mix(gb):
     pbs = _requests()
     srv = gb.Server(chunk=100)
-    ids = [srv.submit(pb, tol=1e-6, max_steps=2500) for pb in pbs[:3]]
+    ids = [srv.submit(pb, tol=_tol(pb), max_steps=2500) for pb in pbs[:3]]
     done = []
     for _ in range(3):  # three rounds with the first arrivals, then the rest arrive
         srv.advance()
         done += srv.poll()
-    ids += [srv.submit(pb, tol=1e-6, max_steps=2500) for pb in pbs[3:]]
+    ids += [srv.submit(pb, tol=_tol(pb), max_steps=2500) for pb in pbs[3:]]
     done += _drain(srv)
     srv.close()
     assert sorted(r["id"] for r in done) == sorted(ids)
     mixed = {r["id"]: r for r in done}
     for rid, pb in zip(ids, pbs):
         solo = gb.Server(chunk=100)
-        solo.submit(pb, tol=1e-6, max_steps=2500)
+        solo.submit(pb, tol=_tol(pb), max_steps=2500)
         (r,) = _drain(solo)
         solo.close()
         _same(mixed[rid], r)
+        assert r["storage"] == pb.get("storage", "fp32")
         assert r["status"] in ("converged", "max_steps")
         assert r["steps"] % 100 == 0 and 200 <= r["steps"] <= 2500
         assert mixed[rid]["t_done"] >= mixed[rid]["t_admit"] >= mixed[rid]["t_submit"]
@@ -122,3 +129,42 @@ def test_unstable_request_is_reported_alone(gb):
     srv.close()
     assert res[ib]["status"] == "unstable"
     assert res[ig]["status"] == "max_steps" and np.isfinite(res[ig]["nu_avg"])
+
+
+def test_tolerance_below_a_16bit_floor_is_served_in_fp32(gb):
+    """A 16-bit request whose tolerance lies below its format's residual floor is stored in
+    FP32 (it could not converge otherwise); above the floor it keeps its format."""
+    base = cavity_problem(12, Ra=1e4, Da=1e-2, phi=0.7, Pr=0.71)
+    cases = [("fp16", 1e-6, "fp32"), ("fp16", 5e-4, "fp16"), ("bf16", 1e-3, "fp32"),
+             ("bf16", 5e-3, "bf16"), ("fp32", 1e-6, "fp32")]
+    assert gb.RESIDUAL_FLOOR["fp16"] == 2e-4 and gb.RESIDUAL_FLOOR["bf16"] == 2e-3
+    srv = gb.Server(chunk=100)
+    ids = {srv.submit(dict(base, storage=st), tol=tol, max_steps=200): want
+           for st, tol, want in cases}
+    res = _drain(srv)
+    srv.close()
+    for r in res:
+        assert r["storage"] == ids[r["id"]], r
+
+
+@pytest.mark.parametrize("policy", ["fifo", "backfill"])
+def test_backfill_lets_small_requests_pass(gb, policy):
+    """With a fill cap that the first request fills, a large second request waits; under
+    BACKFILL a small third request that fits is admitted ahead of it, under FIFO it is not.
+    Results do not depend on the policy."""
+    a = cavity_problem(16, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71)
+    big = cavity_problem(20, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71)
+    small = cavity_problem(8, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71)
+    srv = gb.Server(chunk=100, max_active_sites=16 ** 3 + 8 ** 3, policy=policy)
+    ia = srv.submit(a, tol=1e-12, max_steps=400)
+    ib = srv.submit(big, tol=1e-12, max_steps=200)
+    ic = srv.submit(small, tol=1e-12, max_steps=200)
+    res = {r["id"]: r for r in _drain(srv)}
+    srv.close()
+    assert res[ia]["t_admit"] < res[ib]["t_admit"]
+    if policy == "backfill":
+        assert res[ic]["t_admit"] < res[ib]["t_admit"]
+    else:
+        assert res[ic]["t_admit"] >= res[ib]["t_admit"]
+    for r in res.values():
+        assert r["status"] == "max_steps"
