@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <utility>
+#include <type_traits>
 
 #include "lbm_internal.cuh"
 
@@ -214,11 +215,14 @@ __device__ __forceinline__ const typename S::T* at_in_either(const Planes& pl, c
 // Deviation of plane q at site index idx of the planes being read / written.
 template <class S>
 __device__ __forceinline__ float ldp(const Planes& pl, const KParams& p, int q, int idx) {
-    return S::ld(at_in<S>(pl, p, q, idx)) * plane_scale<S>(p, q);
+    const float v = S::ld(at_in<S>(pl, p, q, idx));
+    if constexpr (S::kScaled) return __fmul_rn(v, plane_scale<S>(p, q));
+    else return v;
 }
 template <class S>
 __device__ __forceinline__ void stp(const Planes& pl, const KParams& p, int q, int idx, float v) {
-    S::st(at_out<S>(pl, p, q, idx), v * plane_inv_scale<S>(p, q));
+    if constexpr (S::kScaled) S::st(at_out<S>(pl, p, q, idx), __fmul_rn(v, plane_inv_scale<S>(p, q)));
+    else S::st(at_out<S>(pl, p, q, idx), v);
 }
 // D3Q7 population i at site idx as the deviation g_i - omega_i sigma T0.  The 16-bit formats
 // store (g_i - omega_i sigma T_x) / omega_i against the site's own temperature T_x, whose
@@ -289,39 +293,96 @@ __device__ __forceinline__ unsigned axis_cross(int e, unsigned cr, unsigned lo, 
     return e == 1 ? (cr & lo) : (e == -1 ? (cr & hi) : 0u);
 }
 
-struct Medium {
-    float phi, inv_phi, l0, l1, c_darcy, c_forch, zeta_alpha;
+// ---- arithmetic on one site or on an x-adjacent pair of sites --------------------------------
+// The collision is written once over a lane type: L1 carries one site (FP32 instructions), L2
+// two sites (the paired FP32 instructions FADD2, FMUL2, FFMA2 of sm_100).  Every operation
+// rounds explicitly -- nothing is left to the compiler to contract into an FMA -- so a site
+// gives the same bits updated alone or paired, in whatever kernel inlines the update.
+struct L1 {
+    float v;
 };
+struct L2 {
+    float2 v;
+};
+__device__ __forceinline__ L1 operator+(L1 a, L1 b) { return {__fadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ L1 operator-(L1 a, L1 b) { return {__fsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ L1 operator*(L1 a, L1 b) { return {__fmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ L1 operator-(L1 a) { return {-a.v}; }
+__device__ __forceinline__ L1 fma(L1 a, L1 b, L1 c) { return {__fmaf_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ L2 operator+(L2 a, L2 b) { return {__fadd2_rn(a.v, b.v)}; }
+// a - b as b * (-1) + a: one rounding of the exact difference, as __fsub_rn
+__device__ __forceinline__ L2 operator-(L2 a, L2 b) {
+    return {__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)};
+}
+__device__ __forceinline__ L2 operator*(L2 a, L2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ L2 operator-(L2 a) { return {make_float2(-a.v.x, -a.v.y)}; }
+__device__ __forceinline__ L2 fma(L2 a, L2 b, L2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+// a constant on every lane
+template <class V> __device__ __forceinline__ V K(float c);
+template <> __device__ __forceinline__ L1 K<L1>(float c) { return {c}; }
+template <> __device__ __forceinline__ L2 K<L2>(float c) { return {make_float2(c, c)}; }
+// lane-wise application of a scalar function (the special-function steps)
+template <class F> __device__ __forceinline__ L1 lanes(L1 a, F fn) { return {fn(a.v)}; }
+template <class F> __device__ __forceinline__ L2 lanes(L2 a, F fn) {
+    return {make_float2(fn(a.v.x), fn(a.v.y))};
+}
+template <class F> __device__ __forceinline__ L1 lanes(L1 a, L1 b, F fn) { return {fn(a.v, b.v)}; }
+template <class F> __device__ __forceinline__ L2 lanes(L2 a, L2 b, F fn) {
+    return {make_float2(fn(a.v.x, b.v.x), fn(a.v.y, b.v.y))};
+}
+
+// sqrt of a non-negative value through the hardware reciprocal square root (exact zero kept).
+__device__ __forceinline__ float sqrt_nonneg(float v) {
+    return v > 0.0f ? __fmul_rn(v, rsqrtf(v)) : 0.0f;
+}
+
+template <class V>
+struct MediumT {
+    V phi, inv_phi, l0, l1, c_darcy, c_forch, zeta_alpha;
+};
+using Medium = MediumT<L1>;
 
 // Eq. 4 / Eq. 28 coefficients at a site; Eq. 6 (Kozeny-Carman K, Ergun F_phi) for a field.
 template <bool HET>
 __device__ __forceinline__ Medium medium_at(const KParams& p, int s) {
     Medium m;
     if (!HET) {
-        m.phi = p.phi;
-        m.inv_phi = p.inv_phi;
-        m.l0 = p.l0;
-        m.l1 = p.l1;
-        m.c_darcy = p.c_darcy;
-        m.c_forch = p.c_forch;
-        m.zeta_alpha = p.zeta_alpha;
+        m.phi = {p.phi};
+        m.inv_phi = {p.inv_phi};
+        m.l0 = {p.l0};
+        m.l1 = {p.l1};
+        m.c_darcy = {p.c_darcy};
+        m.c_forch = {p.c_forch};
+        m.zeta_alpha = {p.zeta_alpha};
     } else {
-        float ph = __ldg(p.phi_field + s);
-        float ph3 = ph * ph * ph;
-        float omp = 1.0f - ph;
-        float Fp = p.F_phi < 0.0f ? 1.75f * rsqrtf(150.0f * ph3) : p.F_phi;
-        float inv_sqrtK = p.kinf ? 0.0f : omp * rsqrtf(p.cK * ph3);  // 1/sqrt(K(phi))
-        m.phi = ph;
-        m.inv_phi = __fdividef(1.0f, ph);
-        m.c_darcy = ph * p.nu * inv_sqrtK * inv_sqrtK;  // phi nu / K
-        m.c_forch = ph * Fp * inv_sqrtK;                // phi F_phi / sqrt(K)
-        m.l0 = 0.5f * (1.0f + 0.5f * m.c_darcy);
-        m.l1 = 0.5f * m.c_forch;
-        m.zeta_alpha = p.hetero_alpha
-                           ? 1.0f / (0.5f + (ph * p.alpha_f + omp * p.alpha_m) * p.inv_sig_csT2)
-                           : p.zeta_alpha;
+        const float ph = __ldg(p.phi_field + s);
+        const float ph3 = __fmul_rn(__fmul_rn(ph, ph), ph);
+        const float omp = __fsub_rn(1.0f, ph);
+        const float Fp = p.F_phi < 0.0f ? __fmul_rn(1.75f, rsqrtf(__fmul_rn(150.0f, ph3))) : p.F_phi;
+        const float inv_sqrtK = p.kinf ? 0.0f : __fmul_rn(omp, rsqrtf(__fmul_rn(p.cK, ph3)));
+        m.phi = {ph};
+        m.inv_phi = {__fdividef(1.0f, ph)};
+        const float cd = __fmul_rn(__fmul_rn(__fmul_rn(ph, p.nu), inv_sqrtK), inv_sqrtK);  // phi nu / K
+        const float cf = __fmul_rn(__fmul_rn(ph, Fp), inv_sqrtK);  // phi F_phi / sqrt(K)
+        m.c_darcy = {cd};
+        m.c_forch = {cf};
+        m.l0 = {__fmul_rn(0.5f, __fmaf_rn(0.5f, cd, 1.0f))};
+        m.l1 = {__fmul_rn(0.5f, cf)};
+        m.zeta_alpha = {p.hetero_alpha
+                            ? __fdividef(1.0f, __fmaf_rn(__fmaf_rn(ph, p.alpha_f,
+                                                                   __fmul_rn(omp, p.alpha_m)),
+                                                         p.inv_sig_csT2, 0.5f))
+                            : p.zeta_alpha};
     }
     return m;
+}
+// The medium of the two sites of a pair (each computed as medium_at computes it).
+template <bool HET>
+__device__ __forceinline__ MediumT<L2> medium_pair(const KParams& p, int sa) {
+    const Medium a = medium_at<HET>(p, sa), b = medium_at<HET>(p, sa + 1);
+    auto pk = [](L1 x, L1 y) { return L2{make_float2(x.v, y.v)}; };
+    return {pk(a.phi, b.phi), pk(a.inv_phi, b.inv_phi), pk(a.l0, b.l0), pk(a.l1, b.l1),
+            pk(a.c_darcy, b.c_darcy), pk(a.c_forch, b.c_forch), pk(a.zeta_alpha, b.zeta_alpha)};
 }
 
 // ---- streaming with boundary rules ------------------------------------------------------------
@@ -594,7 +655,9 @@ __device__ __forceinline__ void gather_interior(const Planes& pl, const KParams&
 template <class S>
 __device__ __forceinline__ float ldp_either(const Planes& pl, const KParams& p, int I, int J,
                                             bool other, int idx) {
-    return S::ld(at_in_either<S>(pl, p, I, J, other, idx)) * plane_scale<S>(p, I);
+    const float v = S::ld(at_in_either<S>(pl, p, I, J, other, idx));
+    if constexpr (S::kScaled) return __fmul_rn(v, plane_scale<S>(p, I));
+    else return v;
 }
 template <class S>
 __device__ __forceinline__ float ldg_either(const Planes& pl, const KParams& p, int I, int J,
@@ -696,119 +759,138 @@ __device__ __forceinline__ void gather_sel(const Planes& pl, const KParams& p, i
 // Eqs. B8-B9: temperature and liquid fraction from the effective enthalpy.
 __device__ __forceinline__ void enthalpy_state(const KParams& p, float En, float& T, float& fl) {
     if (En <= p.ent_Es) {
-        T = En * p.ent_is;
+        T = __fmul_rn(En, p.ent_is);
         fl = 0.0f;
     } else if (En >= p.ent_El) {
-        T = p.ent_Tl + (En - p.ent_El) * p.ent_il;
+        T = __fmaf_rn(__fsub_rn(En, p.ent_El), p.ent_il, p.ent_Tl);
         fl = 1.0f;
     } else {
-        fl = (En - p.ent_Es) * p.ent_idE;
-        T = p.ent_Ts + fl * (p.ent_Tl - p.ent_Ts);
+        fl = __fmul_rn(__fsub_rn(En, p.ent_Es), p.ent_idE);
+        T = __fmaf_rn(fl, __fsub_rn(p.ent_Tl, p.ent_Ts), p.ent_Ts);
     }
 }
 
+template <class V>
+struct MacroT {
+    V rho, ux, uy, uz, T, dT;  // dT = T - T0
+};
 struct Macro {
     float rho, ux, uy, uz, T, dT;  // dT = T - T0
 };
 
-// sqrt of a non-negative value through the hardware reciprocal square root (exact zero kept).
-__device__ __forceinline__ float sqrt_nonneg(float v) { return v > 0.0f ? v * rsqrtf(v) : 0.0f; }
-
 // D3Q7: n = N g (Eq. 36), n_eq = T (sigma, u, varpi sigma, 0, 0) (Eq. 37), Eq. 34, Eq. 43;
-// enthalpy model: n_eq = (En_e, c_pl T u, varpi c_ref T, 0, 0) (Eq. B6) on full values,
-// zeta_alpha from Eq. B11 with alpha_e = f_l alpha_l + (1 - f_l) alpha_s.  n0 = sum g (the
-// deviation sigma (T - T0), or En_e), u the flow's velocity; g is updated in place.
+// enthalpy model (one site at a time): n_eq = (En_e, c_pl T u, varpi c_ref T, 0, 0) (Eq. B6)
+// on full values, zeta_alpha from Eq. B11 with alpha_e = f_l alpha_l + (1 - f_l) alpha_s.
+// n0 = sum g (the deviation sigma (T - T0), or En_e), u the flow's velocity; g is updated in
+// place.
+template <class V, bool ENTH>
+__device__ __forceinline__ void collide_g_t(const KParams& p, const MediumT<V>& md, V* g, V n0, V T,
+                                            float fl, V ux, V uy, V uz) {
+    const V g12 = g[1] + g[2], g34 = g[3] + g[4], g56 = g[5] + g[6];
+    const V n4 = (g12 + g34) + g56;  // minus varpi sigma T0 (standard model)
+    V tu = T, n4eq = K<V>(p.varpi) * n0, za = md.zeta_alpha;
+    if constexpr (ENTH) {
+        tu = K<V>(p.c_pl) * T;
+        n4eq = K<V>(__fmul_rn(p.varpi, p.c_ref)) * T;
+        za = K<V>(__fdividef(1.0f, __fmaf_rn(__fmaf_rn(fl, p.alpha_l,
+                                                       __fmul_rn(__fsub_rn(1.0f, fl), p.alpha_s)),
+                                             p.inv_csT2, 0.5f)));
+    }
+    const V dn1 = za * fma(tu, ux, -(g[1] - g[2]));
+    const V dn2 = za * fma(tu, uy, -(g[3] - g[4]));
+    const V dn3 = za * fma(tu, uz, -(g[5] - g[6]));
+    const V c4 = K<V>(p.ze6) * (n4eq - n4);   // dn4 / 6
+    const V c5 = K<V>(-p.zn6) * (g12 - g34);  // dn5 / 6
+    const V c6 = K<V>(-p.zn6) * (g12 - g56);  // dn6 / 6
+    g[0] = fma(K<V>(-6.0f), c4, g[0]);
+    const V c46 = c4 + c6;
+    const V gx = c46 + c5, gy = fma(K<V>(-2.0f), c5, c46), gz = fma(K<V>(-2.0f), c6, c4 + c5);
+    const V h1 = K<V>(0.5f) * dn1, h2 = K<V>(0.5f) * dn2, h3 = K<V>(0.5f) * dn3;
+    g[1] = g[1] + (gx + h1);
+    g[2] = g[2] + (gx - h1);
+    g[3] = g[3] + (gy + h2);
+    g[4] = g[4] + (gy - h2);
+    g[5] = g[5] + (gz + h3);
+    g[6] = g[6] + (gz - h3);
+}
 template <bool ENTH>
 __device__ __forceinline__ void collide_g(const KParams& p, const Medium& md, float* g, float n0,
                                           float T, float fl, float ux, float uy, float uz) {
-    const float g12 = g[1] + g[2], g34 = g[3] + g[4], g56 = g[5] + g[6];
-    const float n4 = g12 + g34 + g56;  // minus varpi sigma T0 (standard model)
-    float tu = T, n4eq = p.varpi * n0, za = md.zeta_alpha;
-    if constexpr (ENTH) {
-        tu = p.c_pl * T;
-        n4eq = p.varpi * p.c_ref * T;
-        za = __fdividef(1.0f, 0.5f + (fl * p.alpha_l + (1.0f - fl) * p.alpha_s) * p.inv_csT2);
-    }
-    const float dn1 = za * (tu * ux - (g[1] - g[2]));
-    const float dn2 = za * (tu * uy - (g[3] - g[4]));
-    const float dn3 = za * (tu * uz - (g[5] - g[6]));
-    const float c4 = p.ze6 * (n4eq - n4);  // dn4 / 6
-    const float c5 = -p.zn6 * (g12 - g34);         // dn5 / 6
-    const float c6 = -p.zn6 * (g12 - g56);         // dn6 / 6
-    g[0] -= 6.0f * c4;
-    const float gx = c4 + c5 + c6, gy = c4 - 2.0f * c5 + c6, gz = c4 + c5 - 2.0f * c6;
-    g[1] += gx + 0.5f * dn1;
-    g[2] += gx - 0.5f * dn1;
-    g[3] += gy + 0.5f * dn2;
-    g[4] += gy - 0.5f * dn2;
-    g[5] += gz + 0.5f * dn3;
-    g[6] += gz - 0.5f * dn3;
+    collide_g_t<L1, ENTH>(p, md, reinterpret_cast<L1*>(g), L1{n0}, L1{T}, fl, L1{ux}, L1{uy},
+                          L1{uz});
 }
 
 // Eqs. 39, 5, 25, 27-28, 4, then (FULL) Eq. 9 with Eqs. 21-23 in moment space and Eq. 34 with
-// Eqs. 37-38, back-transformed in place.  f, g are deviations on entry and exit.  The
-// per-moment factors s_k / |M_k|^2 and (1 - s_k/2) / |M_k|^2 come precomputed in KParams.
-// PU: the velocity is prescribed (pu, a node wall) instead of solved from Eqs. 27-28, and the
-// conserved momentum becomes rho0 pu + rho0 F / 2 after the collision.
-template <bool FULL, bool ENTH = false, bool PU = false>
-__device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g,
-                                         float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
+// Eqs. 37-38, back-transformed in place, on one site (L1) or a pair (L2).  f, g are
+// deviations on entry and exit.  The per-moment factors s_k / |M_k|^2 and (1 - s_k/2) /
+// |M_k|^2 come precomputed in KParams.  PU (one site): the velocity is prescribed (pu, a node
+// wall) instead of solved from Eqs. 27-28, and the conserved momentum becomes
+// rho0 pu + rho0 F / 2 after the collision.  ENTH (one site): the enthalpy model.
+template <class V, bool FULL, bool ENTH = false, bool PU = false>
+__device__ __forceinline__ MacroT<V> collide_t(const KParams& p, const MediumT<V>& md, V* f, V* g,
+                                               float pux = 0.0f, float puy = 0.0f,
+                                               float puz = 0.0f) {
+    static_assert(std::is_same<V, L1>::value || !(ENTH || PU), "paired sites: standard model");
     // temperature (Eq. 39, or Eqs. B7-B9 with the enthalpy model) and body force (Eq. 5)
-    const float n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
-    float T, dT, fl = 1.0f;                                                     // or En_e
+    const V n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
+    V T, dT;                                                                 // or En_e
+    float fl = 1.0f;
     if constexpr (ENTH) {
-        enthalpy_state(p, n0, T, fl);
-        dT = T - p.T0;
+        float t;
+        enthalpy_state(p, n0.v, t, fl);
+        T = L1{t};
+        dT = L1{__fsub_rn(t, p.T0)};
     } else {
-        // a rounded product (never contracted into an FMA with T0): every kernel that inlines
-        // the collision then computes the same T bits, whatever the surrounding code
-        dT = __fmul_rn(n0, p.inv_sigma);
-        T = p.T0 + dT;
+        dT = n0 * K<V>(p.inv_sigma);
+        T = K<V>(p.T0) + dT;
     }
-    const float Gx = p.buoy[0] * dT + p.accel[0];
-    const float Gy = p.buoy[1] * dT + p.accel[1];
-    const float Gz = p.buoy[2] * dT + p.accel[2];
+    const V Gx = fma(K<V>(p.buoy[0]), dT, K<V>(p.accel[0]));
+    const V Gy = fma(K<V>(p.buoy[1]), dT, K<V>(p.accel[1]));
+    const V Gz = fma(K<V>(p.buoy[2]), dT, K<V>(p.accel[2]));
 
     // symmetric / antisymmetric sums over opposite pairs
-    const float s1 = f[1] + f[2], d1 = f[1] - f[2];
-    const float s2 = f[3] + f[4], d2 = f[3] - f[4];
-    const float s3 = f[5] + f[6], d3 = f[5] - f[6];
-    const float s4 = f[7] + f[10], d4 = f[7] - f[10];   // ( 1, 1, 0)
-    const float s5 = f[8] + f[9], d5 = f[8] - f[9];     // (-1, 1, 0)
-    const float s6 = f[11] + f[14], d6 = f[11] - f[14]; // ( 1, 0, 1)
-    const float s7 = f[12] + f[13], d7 = f[12] - f[13]; // (-1, 0, 1)
-    const float s8 = f[15] + f[18], d8 = f[15] - f[18]; // ( 0, 1, 1)
-    const float s9 = f[16] + f[17], d9 = f[16] - f[17]; // ( 0,-1, 1)
-    const float A = s1 + s2 + s3;
-    const float Dxy = s4 + s5, Dxz = s6 + s7, Dyz = s8 + s9;
-    const float D = Dxy + Dxz + Dyz;
-    const float rho = f[0] + A + D;  // rho - rho0 (Eq. 25)
-    const float jx = d1 + (d4 - d5) + (d6 - d7);
-    const float jy = d2 + (d4 + d5) + (d8 - d9);
-    const float jz = d3 + (d6 + d7) + (d8 + d9);
+    const V s1 = f[1] + f[2], d1 = f[1] - f[2];
+    const V s2 = f[3] + f[4], d2 = f[3] - f[4];
+    const V s3 = f[5] + f[6], d3 = f[5] - f[6];
+    const V s4 = f[7] + f[10], d4 = f[7] - f[10];   // ( 1, 1, 0)
+    const V s5 = f[8] + f[9], d5 = f[8] - f[9];     // (-1, 1, 0)
+    const V s6 = f[11] + f[14], d6 = f[11] - f[14]; // ( 1, 0, 1)
+    const V s7 = f[12] + f[13], d7 = f[12] - f[13]; // (-1, 0, 1)
+    const V s8 = f[15] + f[18], d8 = f[15] - f[18]; // ( 0, 1, 1)
+    const V s9 = f[16] + f[17], d9 = f[16] - f[17]; // ( 0,-1, 1)
+    const V A = (s1 + s2) + s3;
+    const V Dxy = s4 + s5, Dxz = s6 + s7, Dyz = s8 + s9;
+    const V D = (Dxy + Dxz) + Dyz;
+    const V rho = (f[0] + A) + D;  // rho - rho0 (Eq. 25)
+    const V d45 = d4 - d5, d67 = d6 - d7, d89 = d8 - d9;
+    const V e45 = d4 + d5, e67 = d6 + d7, e89 = d8 + d9;
+    const V jx = (d1 + d45) + d67;
+    const V jy = (d2 + e45) + d89;
+    const V jz = (d3 + e67) + e89;
 
     // velocity (Eqs. 27-28) and total force (Eq. 4)
-    const float hphi = 0.5f * md.phi;
-    const float vx = jx * p.inv_rho0 + hphi * Gx;
-    const float vy = jy * p.inv_rho0 + hphi * Gy;
-    const float vz = jz * p.inv_rho0 + hphi * Gz;
-    const float vmag = sqrt_nonneg(vx * vx + vy * vy + vz * vz);
-    const float inv_den = __fdividef(1.0f, md.l0 + sqrt_nonneg(md.l0 * md.l0 + md.l1 * vmag));
-    float ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
+    const V hphi = K<V>(0.5f) * md.phi;
+    const V vx = fma(jx, K<V>(p.inv_rho0), hphi * Gx);
+    const V vy = fma(jy, K<V>(p.inv_rho0), hphi * Gy);
+    const V vz = fma(jz, K<V>(p.inv_rho0), hphi * Gz);
+    const V vmag = lanes(fma(vz, vz, fma(vy, vy, vx * vx)), sqrt_nonneg);
+    const V root = lanes(fma(md.l1, vmag, md.l0 * md.l0), sqrt_nonneg);
+    const V inv_den = lanes(md.l0 + root, [](float d) { return __fdividef(1.0f, d); });
+    V ux = vx * inv_den, uy = vy * inv_den, uz = vz * inv_den;
     if constexpr (PU) {
-        ux = pux;
-        uy = puy;
-        uz = puz;
+        ux = L1{pux};
+        uy = L1{puy};
+        uz = L1{puz};
     }
     // enthalpy model: the flow is collided only where f_l >= 0.5; elsewhere u = 0
     bool rest = false;
     if constexpr (ENTH) {
         rest = p.flow_off || fl < 0.5f;
-        if (rest) ux = uy = uz = 0.0f;
+        if (rest) ux = uy = uz = L1{0.0f};
     }
 
-    Macro mac;
-    mac.rho = p.rho0 + rho;
+    MacroT<V> mac;
+    mac.rho = K<V>(p.rho0) + rho;
     mac.ux = ux;
     mac.uy = uy;
     mac.uz = uz;
@@ -818,113 +900,132 @@ __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, flo
 
     if (rest) {  // f_eq(rho, 0) in deviation form: w_i (rho - rho0)
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) f[i] = w19(i) * rho;
+        for (int i = 0; i < kQ; ++i) f[i] = K<V>(w19(i)) * rho;
     } else {
     // |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|))
-    const float umag = PU ? sqrt_nonneg(ux * ux + uy * uy + uz * uz) : vmag * inv_den;
-    const float drag = md.c_darcy + md.c_forch * umag;
-    const float Fx = md.phi * Gx - drag * ux;
-    const float Fy = md.phi * Gy - drag * uy;
-    const float Fz = md.phi * Gz - drag * uz;
+    V umag;
+    if constexpr (PU) umag = lanes(fma(uz, uz, fma(uy, uy, ux * ux)), sqrt_nonneg);
+    else umag = vmag * inv_den;
+    const V drag = fma(md.c_forch, umag, md.c_darcy);
+    const V Fx = fma(md.phi, Gx, -(drag * ux));
+    const V Fy = fma(md.phi, Gy, -(drag * uy));
+    const V Fz = fma(md.phi, Gz, -(drag * uz));
 
     // moments of Eq. 20 (rows of Eq. A2) that relax
-    const float m_e = -30.0f * f[0] - 11.0f * A + 8.0f * D;
-    const float m_eps = 12.0f * f[0] - 4.0f * A + D;
-    const float qx = jx - 5.0f * d1, qy = jy - 5.0f * d2, qz = jz - 5.0f * d3;
-    const float m_pxx = 2.0f * s1 - s2 - s3 + Dxy + Dxz - 2.0f * Dyz;
-    const float m_pixx = -4.0f * s1 + 2.0f * (s2 + s3) + Dxy + Dxz - 2.0f * Dyz;
-    const float m_pww = s2 - s3 + Dxy - Dxz;
-    const float m_piww = 2.0f * (s3 - s2) + Dxy - Dxz;
-    const float m_pxy = s4 - s5, m_pyz = s8 - s9, m_pzx = s6 - s7;
-    const float m_mx = (d4 - d5) - (d6 - d7);
-    const float m_my = (d8 - d9) - (d4 + d5);
-    const float m_mz = (d6 + d7) - (d8 + d9);
+    const V m_e = fma(K<V>(-30.0f), f[0], fma(K<V>(-11.0f), A, K<V>(8.0f) * D));
+    const V m_eps = fma(K<V>(12.0f), f[0], fma(K<V>(-4.0f), A, D));
+    const V qx = fma(K<V>(-5.0f), d1, jx), qy = fma(K<V>(-5.0f), d2, jy),
+            qz = fma(K<V>(-5.0f), d3, jz);
+    const V s23 = s2 + s3;
+    const V Dw = fma(K<V>(-2.0f), Dyz, Dxy + Dxz);  // Dxy + Dxz - 2 Dyz
+    const V m_pxx = fma(K<V>(2.0f), s1, Dw - s23);
+    const V m_pixx = fma(K<V>(-4.0f), s1, fma(K<V>(2.0f), s23, Dw));
+    const V Dv = Dxy - Dxz;
+    const V m_pww = (s2 - s3) + Dv;
+    const V m_piww = fma(K<V>(2.0f), s3 - s2, Dv);
+    const V m_pxy = s4 - s5, m_pyz = s8 - s9, m_pzx = s6 - s7;
+    const V m_mx = d45 - d67;
+    const V m_my = d89 - e45;
+    const V m_mz = e67 - e89;
 
     // equilibria (Eq. 21, beta1 = 3, beta2 = -11/2, beta3 = -1/2) and forcing (Eq. 23), with
     // the velocity scaled by rho0 / phi once: w = rho0 u / phi
-    const float r0p = p.rho0 * md.inv_phi;
-    const float wx = r0p * ux, wy = r0p * uy, wz = r0p * uz;
-    const float pxx = wx * ux, pyy = wy * uy, pzz = wz * uz;  // rho0 u_a^2 / phi
-    const float fxx = wx * Fx, fyy = wy * Fy, fzz = wz * Fz;  // rho0 u_a F_a / phi
-    const float usq = pxx + pyy + pzz;
-    const float uF = fxx + fyy + fzz;
-    const float eq_pxx = 2.0f * pxx - pyy - pzz;
-    const float eq_pww = pyy - pzz;
-    const float S_pxx = 2.0f * (2.0f * fxx - fyy - fzz);
-    const float S_pww = 2.0f * (fyy - fzz);
+    const V r0p = K<V>(p.rho0) * md.inv_phi;
+    const V wx = r0p * ux, wy = r0p * uy, wz = r0p * uz;
+    const V pxx = wx * ux, pyy = wy * uy, pzz = wz * uz;  // rho0 u_a^2 / phi
+    const V fxx = wx * Fx, fyy = wy * Fy, fzz = wz * Fz;  // rho0 u_a F_a / phi
+    const V usq = (pxx + pyy) + pzz;
+    const V uF = (fxx + fyy) + fzz;
+    const V pyz = pyy + pzz, fyz = fyy + fzz;
+    const V eq_pxx = fma(K<V>(2.0f), pxx, -pyz);
+    const V eq_pww = pyy - pzz;
+    const V S_pxx = K<V>(2.0f) * fma(K<V>(2.0f), fxx, -fyz);
+    const V S_pww = K<V>(2.0f) * (fyy - fzz);
 
     // dm_k / |M_k|^2 = -s_k (m_k - m_k^eq) / |M_k|^2 + (1 - s_k/2) S_k / |M_k|^2; the conserved
     // momentum gains rho0 F whatever s_j is (Eqs. 9, 14, 26)
-    const float de = p.ae * (-11.0f * rho + 19.0f * usq - m_e) + p.be * 38.0f * uF;
-    const float deps = p.aeps * (3.0f * rho - 5.5f * usq - m_eps) - p.beps * 11.0f * uF;
-    float djx = p.rho0_10 * Fx, djy = p.rho0_10 * Fy, djz = p.rho0_10 * Fz;
+    const V de = fma(K<V>(p.ae), fma(K<V>(-11.0f), rho, fma(K<V>(19.0f), usq, -m_e)),
+                     K<V>(__fmul_rn(38.0f, p.be)) * uF);
+    const V deps = fma(K<V>(p.aeps), fma(K<V>(3.0f), rho, fma(K<V>(-5.5f), usq, -m_eps)),
+                       K<V>(__fmul_rn(-11.0f, p.beps)) * uF);
+    V djx = K<V>(p.rho0_10) * Fx, djy = K<V>(p.rho0_10) * Fy, djz = K<V>(p.rho0_10) * Fz;
     if constexpr (PU) {
-        djx = 0.1f * (p.rho0 * (ux + 0.5f * Fx) - jx);
-        djy = 0.1f * (p.rho0 * (uy + 0.5f * Fy) - jy);
-        djz = 0.1f * (p.rho0 * (uz + 0.5f * Fz) - jz);
+        djx = K<V>(0.1f) * fma(K<V>(p.rho0), fma(K<V>(0.5f), Fx, ux), -jx);
+        djy = K<V>(0.1f) * fma(K<V>(p.rho0), fma(K<V>(0.5f), Fy, uy), -jy);
+        djz = K<V>(0.1f) * fma(K<V>(p.rho0), fma(K<V>(0.5f), Fz, uz), -jz);
     }
-    const float dqx = -p.aq * qx - (p.aqc * ux + p.bqc * Fx);
-    const float dqy = -p.aq * qy - (p.aqc * uy + p.bqc * Fy);
-    const float dqz = -p.aq * qz - (p.aqc * uz + p.bqc * Fz);
-    const float dpxx = p.anu36 * (eq_pxx - m_pxx) + p.bnu36 * S_pxx;
-    const float dpixx = -p.api72 * (0.5f * eq_pxx + m_pixx) - p.hbpi72 * S_pxx;
-    const float dpww = p.anu12 * (eq_pww - m_pww) + p.bnu12 * S_pww;
-    const float dpiww = -p.api24 * (0.5f * eq_pww + m_piww) - p.hbpi24 * S_pww;
-    const float dpxy = p.anu4 * (wx * uy - m_pxy) + p.bnu4 * (wx * Fy + wy * Fx);
-    const float dpyz = p.anu4 * (wy * uz - m_pyz) + p.bnu4 * (wy * Fz + wz * Fy);
-    const float dpzx = p.anu4 * (wz * ux - m_pzx) + p.bnu4 * (wz * Fx + wx * Fz);
-    const float dmx = -p.am8 * m_mx;
-    const float dmy = -p.am8 * m_my;
-    const float dmz = -p.am8 * m_mz;
+    const V dqx = fma(K<V>(-p.aq), qx, -fma(K<V>(p.aqc), ux, K<V>(p.bqc) * Fx));
+    const V dqy = fma(K<V>(-p.aq), qy, -fma(K<V>(p.aqc), uy, K<V>(p.bqc) * Fy));
+    const V dqz = fma(K<V>(-p.aq), qz, -fma(K<V>(p.aqc), uz, K<V>(p.bqc) * Fz));
+    const V dpxx = fma(K<V>(p.anu36), eq_pxx - m_pxx, K<V>(p.bnu36) * S_pxx);
+    const V dpixx = fma(K<V>(-p.api72), fma(K<V>(0.5f), eq_pxx, m_pixx), K<V>(-p.hbpi72) * S_pxx);
+    const V dpww = fma(K<V>(p.anu12), eq_pww - m_pww, K<V>(p.bnu12) * S_pww);
+    const V dpiww = fma(K<V>(-p.api24), fma(K<V>(0.5f), eq_pww, m_piww), K<V>(-p.hbpi24) * S_pww);
+    const V dpxy = fma(K<V>(p.anu4), fma(wx, uy, -m_pxy), K<V>(p.bnu4) * fma(wx, Fy, wy * Fx));
+    const V dpyz = fma(K<V>(p.anu4), fma(wy, uz, -m_pyz), K<V>(p.bnu4) * fma(wy, Fz, wz * Fy));
+    const V dpzx = fma(K<V>(p.anu4), fma(wz, ux, -m_pzx), K<V>(p.bnu4) * fma(wz, Fx, wx * Fz));
+    const V dmx = K<V>(-p.am8) * m_mx;
+    const V dmy = K<V>(-p.am8) * m_my;
+    const V dmz = K<V>(-p.am8) * m_mz;
 
     // f* = f + M^T diag(1/|M_k|^2) dm
-    f[0] += -30.0f * de + 12.0f * deps;
-    const float Eax = -11.0f * de - 4.0f * deps;
-    const float Ex = Eax + 2.0f * dpxx - 4.0f * dpixx;
-    const float Eyz2 = Eax - dpxx + 2.0f * dpixx;
-    const float Pw = dpww - 2.0f * dpiww;
-    const float Ey = Eyz2 + Pw;
-    const float Ez = Eyz2 - Pw;
-    const float Ox = djx - 4.0f * dqx, Oy = djy - 4.0f * dqy, Oz = djz - 4.0f * dqz;
-    f[1] += Ex + Ox;
-    f[2] += Ex - Ox;
-    f[3] += Ey + Oy;
-    f[4] += Ey - Oy;
-    f[5] += Ez + Oz;
-    f[6] += Ez - Oz;
-    const float Cd = 8.0f * de + deps;
-    const float Cp = Cd + dpxx + dpixx;
-    const float Pww = dpww + dpiww;
-    const float Exy = Cp + Pww;
-    const float Exz = Cp - Pww;
-    const float Eyz = Cd - 2.0f * (dpxx + dpixx);
-    const float Jx = djx + dqx, Jy = djy + dqy, Jz = djz + dqz;
-    const float O7 = Jx + Jy + dmx - dmy;
-    const float O8 = -Jx + Jy - dmx - dmy;
-    const float O11 = Jx + Jz - dmx + dmz;
-    const float O12 = -Jx + Jz + dmx + dmz;
-    const float O15 = Jy + Jz + dmy - dmz;
-    const float O16 = -Jy + Jz - dmy - dmz;
-    const float Ea = Exy + dpxy, Eb = Exy - dpxy;
-    const float Ec = Exz + dpzx, Ed = Exz - dpzx;
-    const float Ee = Eyz + dpyz, Ef = Eyz - dpyz;
-    f[7] += Ea + O7;
-    f[10] += Ea - O7;
-    f[8] += Eb + O8;
-    f[9] += Eb - O8;
-    f[11] += Ec + O11;
-    f[14] += Ec - O11;
-    f[12] += Ed + O12;
-    f[13] += Ed - O12;
-    f[15] += Ee + O15;
-    f[18] += Ee - O15;
-    f[16] += Ef + O16;
-    f[17] += Ef - O16;
+    f[0] = f[0] + fma(K<V>(-30.0f), de, K<V>(12.0f) * deps);
+    const V Eax = fma(K<V>(-11.0f), de, K<V>(-4.0f) * deps);
+    const V Ex = fma(K<V>(2.0f), dpxx, fma(K<V>(-4.0f), dpixx, Eax));
+    const V Eyz2 = fma(K<V>(2.0f), dpixx, Eax - dpxx);
+    const V Pw = fma(K<V>(-2.0f), dpiww, dpww);
+    const V Ey = Eyz2 + Pw;
+    const V Ez = Eyz2 - Pw;
+    const V Ox = fma(K<V>(-4.0f), dqx, djx), Oy = fma(K<V>(-4.0f), dqy, djy),
+            Oz = fma(K<V>(-4.0f), dqz, djz);
+    f[1] = f[1] + (Ex + Ox);
+    f[2] = f[2] + (Ex - Ox);
+    f[3] = f[3] + (Ey + Oy);
+    f[4] = f[4] + (Ey - Oy);
+    f[5] = f[5] + (Ez + Oz);
+    f[6] = f[6] + (Ez - Oz);
+    const V Cd = fma(K<V>(8.0f), de, deps);
+    const V pp = dpxx + dpixx;
+    const V Cp = Cd + pp;
+    const V Pww = dpww + dpiww;
+    const V Exy = Cp + Pww;
+    const V Exz = Cp - Pww;
+    const V Eyz = fma(K<V>(-2.0f), pp, Cd);
+    const V Jx = djx + dqx, Jy = djy + dqy, Jz = djz + dqz;
+    const V mxy = dmx - dmy, mxz = dmz - dmx, myz = dmy - dmz;
+    const V O7 = (Jx + Jy) + mxy;
+    const V O8 = (Jy - Jx) - (dmx + dmy);
+    const V O11 = (Jx + Jz) + mxz;
+    const V O12 = (Jz - Jx) + (dmx + dmz);
+    const V O15 = (Jy + Jz) + myz;
+    const V O16 = (Jz - Jy) - (dmy + dmz);
+    const V Ea = Exy + dpxy, Eb = Exy - dpxy;
+    const V Ec = Exz + dpzx, Ed = Exz - dpzx;
+    const V Ee = Eyz + dpyz, Ef = Eyz - dpyz;
+    f[7] = f[7] + (Ea + O7);
+    f[10] = f[10] + (Ea - O7);
+    f[8] = f[8] + (Eb + O8);
+    f[9] = f[9] + (Eb - O8);
+    f[11] = f[11] + (Ec + O11);
+    f[14] = f[14] + (Ec - O11);
+    f[12] = f[12] + (Ed + O12);
+    f[13] = f[13] + (Ed - O12);
+    f[15] = f[15] + (Ee + O15);
+    f[18] = f[18] + (Ee - O15);
+    f[16] = f[16] + (Ef + O16);
+    f[17] = f[17] + (Ef - O16);
 
     }  // flow collision
 
-    collide_g<ENTH>(p, md, g, n0, T, fl, ux, uy, uz);
+    collide_g_t<V, ENTH>(p, md, g, n0, T, fl, ux, uy, uz);
     return mac;
+}
+template <bool FULL, bool ENTH = false, bool PU = false>
+__device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g,
+                                         float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
+    const MacroT<L1> m = collide_t<L1, FULL, ENTH, PU>(p, md, reinterpret_cast<L1*>(f),
+                                                       reinterpret_cast<L1*>(g), pux, puy, puz);
+    return {m.rho.v, m.ux.v, m.uy.v, m.uz.v, m.T.v, m.dT.v};
 }
 
 // D3Q15 (Sec. 3.1.1): the same steps with the moments of Eq. 13 (rows of Eq. A1), the
@@ -957,12 +1058,12 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
     const float jz = d3 + (da + db) + (dc + dd);
 
     // velocity (Eqs. 27-28) and total force (Eq. 4)
-    const float hphi = 0.5f * md.phi;
+    const float hphi = 0.5f * md.phi.v;
     const float vx = jx * p.inv_rho0 + hphi * Gx;
     const float vy = jy * p.inv_rho0 + hphi * Gy;
     const float vz = jz * p.inv_rho0 + hphi * Gz;
     const float vmag = sqrt_nonneg(vx * vx + vy * vy + vz * vz);
-    const float inv_den = __fdividef(1.0f, md.l0 + sqrt_nonneg(md.l0 * md.l0 + md.l1 * vmag));
+    const float inv_den = __fdividef(1.0f, md.l0.v + sqrt_nonneg(md.l0.v * md.l0.v + md.l1.v * vmag));
     const float ux = PU ? pux : vx * inv_den, uy = PU ? puy : vy * inv_den;
     const float uz = PU ? puz : vz * inv_den;
 
@@ -976,10 +1077,10 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
     if (!FULL) return mac;
 
     const float umag = PU ? sqrt_nonneg(ux * ux + uy * uy + uz * uz) : vmag * inv_den;
-    const float drag = md.c_darcy + md.c_forch * umag;
-    const float Fx = md.phi * Gx - drag * ux;
-    const float Fy = md.phi * Gy - drag * uy;
-    const float Fz = md.phi * Gz - drag * uz;
+    const float drag = md.c_darcy.v + md.c_forch.v * umag;
+    const float Fx = md.phi.v * Gx - drag * ux;
+    const float Fy = md.phi.v * Gy - drag * uy;
+    const float Fz = md.phi.v * Gz - drag * uz;
 
     // moments of Eq. 13 (rows of Eq. A1) that relax
     const float m_e = -2.0f * f[0] - A + Cs;
@@ -993,7 +1094,7 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
     const float m_xyz = (da + dd) - (db + dc);
 
     // equilibria (Eq. 15) and forcing (Eq. 17) with w = rho0 u / phi
-    const float r0p = p.rho0 * md.inv_phi;
+    const float r0p = p.rho0 * md.inv_phi.v;
     const float wx = r0p * ux, wy = r0p * uy, wz = r0p * uz;
     const float pxx = wx * ux, pyy = wy * uy, pzz = wz * uz;
     const float fxx = wx * Fx, fyy = wy * Fy, fzz = wz * Fz;
@@ -1103,14 +1204,14 @@ __device__ __forceinline__ Macro nee_site(const Planes& pl, const KParams& p, in
     const float drb = outw > 0.0f ? 0.0f : drf;
     const Medium mb = medium_at<HET>(p, s);
     // f += f_eq(rho_b, u_w) - f_eq(rho_f, u_f) (Eqs. 18, 24), deviations
-    const float iub = (uwx * uwx + uwy * uwy + uwz * uwz) * mb.inv_phi;
-    const float iuf = (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz) * mf.inv_phi;
+    const float iub = (uwx * uwx + uwy * uwy + uwz * uwz) * mb.inv_phi.v;
+    const float iuf = (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz) * mf.inv_phi.v;
 #pragma unroll
     for (int i = 0; i < L::kQ; ++i) {
         const float ebu = (float)L::ex(i) * uwx + (float)L::ey(i) * uwy + (float)L::ez(i) * uwz;
         const float efu = (float)L::ex(i) * m.ux + (float)L::ey(i) * m.uy + (float)L::ez(i) * m.uz;
         f[i] += L::w(i) * ((drb - drf) +
-                           p.rho0 * (3.0f * (ebu - efu) + 4.5f * (ebu * ebu * mb.inv_phi - efu * efu * mf.inv_phi) -
+                           p.rho0 * (3.0f * (ebu - efu) + 4.5f * (ebu * ebu * mb.inv_phi.v - efu * efu * mf.inv_phi.v) -
                                      1.5f * (iub - iuf)));
     }
     // g += g_eq(T_b, u_w) - g_eq(T_f, u_f) (Eq. 42), deviations from omega_i sigma T0
@@ -1300,6 +1401,145 @@ __global__ void __maxnreg__(HET ? 72 : 64)
     }
     gather_site<OUTF, S, L>(pl, p, x, y, z, s, mode, f, g);
     finish_site<HET, OUTF, S, ENTH, L>(pl, p, x, y, z, s, f, g);
+}
+
+// ---- paired sites: two x-adjacent sites per thread ----------------------------------------------
+// One thread updates the sites x and x + 1 (x even, nx even) with the collision on L2 (the
+// paired FP32 instructions).  A plane whose velocity has e_x = 0 holds the two sources next to
+// each other, so it is read and written as one aligned 2-element access; the planes with
+// e_x = +-1 read their two sources separately.  Warps with a boundary site gather each site on
+// its own (gather_site) and pair the results.  The update is that of step_kernel, bit for bit.
+template <class S>
+__device__ __forceinline__ float2 ld2_raw(const typename S::T* a) {
+    if constexpr (std::is_same<typename S::T, float>::value) {
+        return __ldg(reinterpret_cast<const float2*>(a));
+    } else if constexpr (std::is_same<typename S::T, __half>::value) {
+        return __half22float2(__ldg(reinterpret_cast<const __half2*>(a)));
+    } else {
+        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(a)));
+    }
+}
+template <class S>
+__device__ __forceinline__ void st2_raw(typename S::T* a, float2 v) {
+    if constexpr (std::is_same<typename S::T, float>::value) {
+        *reinterpret_cast<float2*>(a) = v;
+    } else if constexpr (std::is_same<typename S::T, __half>::value) {
+        *reinterpret_cast<__half2*>(a) = __float22half2_rn(v);
+    } else {
+        *reinterpret_cast<__nv_bfloat162*>(a) = __float22bfloat162_rn(v);
+    }
+}
+// Plane q (flow) at the aligned pair idx, idx + 1, as ldp reads each.
+template <class S>
+__device__ __forceinline__ L2 ldp2(const Planes& pl, const KParams& p, int q, int idx) {
+    const L2 v{ld2_raw<S>(at_in<S>(pl, p, q, idx))};
+    if constexpr (S::kScaled) return v * K<L2>(plane_scale<S>(p, q));
+    else return v;
+}
+// D3Q7 population i at the aligned pair idx, idx + 1, as ldg_dev reads each.
+template <class S>
+__device__ __forceinline__ L2 ldg2(const Planes& pl, const KParams& p, int i, int idx) {
+    if constexpr (!S::kScaled) {
+        return ldp2<S>(pl, p, kQ + i, idx);
+    } else {
+        const L2 st{ld2_raw<S>(at_in<S>(pl, p, kQ + i, idx))};
+        const L2 tin{__ldg(reinterpret_cast<const float2*>(pl.tin + idx))};
+        return K<L2>(i == 0 ? p.om0 : p.om1) * fma(K<L2>(p.sigma), tin, st);
+    }
+}
+template <class S>
+__device__ __forceinline__ void stp2(const Planes& pl, const KParams& p, int q, int idx, L2 v) {
+    if constexpr (S::kScaled) v = v * K<L2>(plane_inv_scale<S>(p, q));
+    st2_raw<S>(at_out<S>(pl, p, q, idx), v.v);
+}
+template <class S>
+__device__ __forceinline__ void stg2(const Planes& pl, const KParams& p, int i, int idx, L2 v, L2 dT) {
+    if constexpr (!S::kScaled) {
+        stp2<S>(pl, p, kQ + i, idx, v);
+    } else {
+        const L2 w = fma(v, K<L2>(i == 0 ? p.iom0 : p.iom1), -(K<L2>(p.sigma) * dT));
+        st2_raw<S>(at_out<S>(pl, p, kQ + i, idx), w.v);
+    }
+}
+__device__ __forceinline__ L2 pair(float a, float b) { return {make_float2(a, b)}; }
+
+// Pull of the pair when no pull of either site crosses a non-periodic face.
+template <class S>
+__device__ __forceinline__ void gather_pair_interior(const Planes& pl, const KParams& p, int xa,
+                                                     int y, int z, int sa, L2* f, L2* g) {
+    const AxisOff o = axis_offsets(p, xa, y, z);  // site a; site b differs only along +x
+    const int xpb = (xa + 1 == p.nx - 1) ? 1 - p.nx : 1;  // periodic wrap of site b's +x source
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int oyz = axis_off(D3Q19::ey(i), o.ym, o.yp) + axis_off(D3Q19::ez(i), o.zm, o.zp);
+        if (D3Q19::ex(i) == 0) {
+            f[i] = ldp2<S>(pl, p, i, sa + oyz);
+        } else if (D3Q19::ex(i) == 1) {  // sources x - 1: sa + xm (a), sa (b)
+            f[i] = pair(ldp<S>(pl, p, i, sa + o.xm + oyz), ldp<S>(pl, p, i, sa + oyz));
+        } else {  // sources x + 1: sa + 1 (a), sa + 1 + xpb (b)
+            f[i] = pair(ldp<S>(pl, p, i, sa + 1 + oyz), ldp<S>(pl, p, i, sa + 1 + xpb + oyz));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) {
+        const int oyz = axis_off(ey7(i), o.ym, o.yp) + axis_off(ez7(i), o.zm, o.zp);
+        if (ex7(i) == 0) {
+            g[i] = ldg2<S>(pl, p, i, sa + oyz);
+        } else if (ex7(i) == 1) {
+            g[i] = pair(ldg_dev<S>(pl, p, i, sa + o.xm + oyz), ldg_dev<S>(pl, p, i, sa + oyz));
+        } else {
+            g[i] = pair(ldg_dev<S>(pl, p, i, sa + 1 + oyz), ldg_dev<S>(pl, p, i, sa + 1 + xpb + oyz));
+        }
+    }
+}
+
+// The gather mode of a warp of pairs (warp_gather_mode over both sites of every lane).
+__device__ __forceinline__ int warp_pair_mode(const KParams& p, int xa, int y, int z, bool active) {
+    const bool quiet = site_no_cross(p, xa, y, z) && site_no_cross(p, xa + 1, y, z);
+    if (__all_sync(0xffffffffu, !active || quiet)) return kGatherInterior;
+    if (__all_sync(0xffffffffu, !active || yz_fast(p, y, z))) return kGatherX;
+    return kGatherAny;
+}
+
+template <bool HET, bool OUTF, class S>
+__global__ void __launch_bounds__(kBlock)
+    step_pair_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
+    dependent_launch_prologue();
+    const int xa = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool valid = xa < p.nx && y < p.ny;  // nx even: x + 1 < nx as well
+    const int mode = warp_pair_mode(p, xa, y, z, valid);
+    if (!valid) return;
+    const int sa = xa + p.nx * (y + p.ny * z);
+    L2 f[kQ], g[kQT];
+    if (mode == kGatherInterior) {
+        gather_pair_interior<S>(pl, p, xa, y, z, sa, f, g);
+    } else {
+        float fa[kQ], ga[kQT], fb[kQ], gb[kQT];
+        gather_site<OUTF, S>(pl, p, xa, y, z, sa, mode, fa, ga);
+        gather_site<OUTF, S>(pl, p, xa + 1, y, z, sa + 1, mode, fb, gb);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) f[i] = pair(fa[i], fb[i]);
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) g[i] = pair(ga[i], gb[i]);
+    }
+    if (OUTF && xa + 1 == p.nx - 1) {  // site b on the outflow face: its pre-collision pulls
+        const int yz = y + p.ny * z;
+        pl.hout[0 * p.nyz + yz] = f[2].v.y;
+        pl.hout[1 * p.nyz + yz] = f[8].v.y;
+        pl.hout[2 * p.nyz + yz] = f[10].v.y;
+        pl.hout[3 * p.nyz + yz] = f[12].v.y;
+        pl.hout[4 * p.nyz + yz] = f[14].v.y;
+        pl.hout[5 * p.nyz + yz] = g[2].v.y;
+    }
+    const MediumT<L2> md = medium_pair<HET>(p, sa);
+    const MacroT<L2> m = collide_t<L2, true>(p, md, f, g);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) stp2<S>(pl, p, i, sa, f[i]);
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) stg2<S>(pl, p, i, sa, g[i], m.dT);
+    if constexpr (S::kScaled) *reinterpret_cast<float2*>(pl.tout + sa) = m.dT.v;
 }
 
 // ---- AA pattern: one population copy, updated in place (FP32, D3Q19, no outflow) ----------
@@ -2004,6 +2244,25 @@ cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, bool p
         return go(StoreF32o{});
     }
     return with_storage(p.storage, go);
+}
+
+cudaError_t launch_step_pair(const KParams& p, bool outflow, const Planes& pl, bool pdl,
+                             cudaStream_t st) {
+    int nt = p.block_threads >= 32 && p.block_threads <= kBlock ? p.block_threads : 64;
+    const int npx = p.nx / 2;
+    const int bx = block_x_of(npx, nt);
+    const int by = nt / bx > 0 ? nt / bx : 1;
+    const dim3 block(bx, by, 1), grid((npx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
+    const bool het = p.phi_field != nullptr;
+    auto go = [&](auto tag) {
+        using S = decltype(tag);
+        auto k = het ? (outflow ? step_pair_kernel<true, true, S> : step_pair_kernel<true, false, S>)
+                     : (outflow ? step_pair_kernel<false, true, S> : step_pair_kernel<false, false, S>);
+        return launch_kernel(pdl, k, grid, block, 0, st, p, pl);
+    };
+    if (p.storage == 1) return go(StoreF16o{});
+    if (p.storage == 2) return go(StoreBF16o{});
+    return go(StoreF32o{});
 }
 
 cudaError_t launch_aa_step(const KParams& p, bool local, const Planes& pl, const Planes& pw,
