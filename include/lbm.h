@@ -251,9 +251,15 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  *                     one second stops the step early; the next call that synchronises the
  *                     context's stream (lbm_sync, lbm_macros, lbm_residual, lbm_sums,
  *                     lbm_nusselt, lbm_get_populations, ...) then returns LBM_ETIMEOUT
- *                     (sticky).  lbm_test_tma_extra_wait exercises that path. */
+ *                     (sticky).  lbm_test_tma_extra_wait exercises that path.
+ *  LBM_KERNEL_PAIRED : one thread per pair of x-adjacent sites; planes whose velocity has
+ *                     e_x = 0 are read and written as aligned 2-element accesses and the
+ *                     collision runs on the paired FP32 instructions of sm_100 (two sites per
+ *                     instruction).  Needs the D3Q19 lattice, the ping-pong scheme, an even
+ *                     nx, fewer than ~82 M sites, no node walls and no enthalpy model. */
 #define LBM_KERNEL_PLAIN 0
 #define LBM_KERNEL_TMA 1
+#define LBM_KERNEL_PAIRED 2
 
 /* Select the step kernel used by later lbm_step calls.  Prepares the kernel (tensor maps of
  * both population copies, shared-memory limit, a 4-byte device flag owned by ctx).

@@ -50,7 +50,7 @@ RESIDUAL_FLOOR = {"fp16": 2e-4, "bf16": 2e-3}  # LBM_RESIDUAL_FLOOR_FP16 / _BF16
 SCHEMES = {"pingpong": 0, "aa": 1, "auto": 2}
 
 # Step kernels (LBM_KERNEL_*).
-STEP_KERNELS = {"plain": 0, "tma": 1}
+STEP_KERNELS = {"plain": 0, "tma": 1, "paired": 2}
 
 REQ_CONVERGED, REQ_MAX_STEPS, REQ_UNSTABLE, REQ_FAILED = range(4)
 REQ_STATUS = {0: "converged", 1: "max_steps", 2: "unstable", 3: "failed"}

@@ -10,8 +10,21 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges reach a profiler only when one is attached
+
 #include "../../include/lbm.h"
 #include "lbm_internal.cuh"
+
+namespace {
+// NVTX range for the lifetime of the object: the host calls that queue or wait for GPU work
+// show up as named ranges on a profiler's timeline (no cost without a profiler).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 using lbm::KParams;
 
@@ -853,6 +866,7 @@ lbm_status lbm_set_medium(lbm_ctx* c, const float* phi_field, double phi, double
 }
 
 lbm_status lbm_step(lbm_ctx* c, int nsteps) {
+    NvtxRange range_("lbm_step");
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
@@ -868,7 +882,9 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     }
     for (int t = 0; t < nsteps; ++t) {
         int nxt = c->cur ^ 1;
-        if (c->step_kernel == LBM_KERNEL_TMA)
+        if (c->step_kernel == LBM_KERNEL_PAIRED)
+            LBM_CUDA(lbm::launch_step_pair(c->kp, c->outflow, c->pl[c->cur], c->pdl, c->stream));
+        else if (c->step_kernel == LBM_KERNEL_TMA)
             LBM_CUDA(lbm::launch_step_tma(c->kp, c->outflow, c->pl[c->cur], c->tmaps[c->cur],
                                           c->tma_blocks, c->tma_extra_tx, c->tma_err, c->pdl,
                                           c->stream));
@@ -1031,6 +1047,7 @@ lbm_status lbm_state_bytes(const lbm_ctx* c, unsigned long long* bytes) {
 }
 
 lbm_status lbm_save_state(lbm_ctx* c, void* host, unsigned long long bytes) {
+    NvtxRange range_("lbm_save_state");
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     const StateHeader h = state_header(c);
@@ -1054,6 +1071,7 @@ lbm_status lbm_save_state(lbm_ctx* c, void* host, unsigned long long bytes) {
 }
 
 lbm_status lbm_load_state(lbm_ctx* c, const void* host, unsigned long long bytes) {
+    NvtxRange range_("lbm_load_state");
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     const StateHeader mine = state_header(c);
@@ -1094,6 +1112,7 @@ lbm_status lbm_macros_device(lbm_ctx* c, float* rho, float* u, float* T) {
 }
 
 lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* T) {
+    NvtxRange range_("lbm_macros");
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if ((st = aa_settle(c)) != LBM_OK) return st;
@@ -1115,6 +1134,7 @@ lbm_status lbm_macros(lbm_ctx* c, float* rho, float* u, float* T) {
 }
 
 lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile, double* nu_mp) {
+    NvtxRange range_("lbm_nusselt");
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if ((st = aa_settle(c)) != LBM_OK) return st;
@@ -1143,6 +1163,7 @@ lbm_status lbm_nusselt(lbm_ctx* c, int face, double* nu_avg, double* nu_profile,
 }
 
 lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
+    NvtxRange range_("lbm_sums");
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if ((st = aa_settle(c)) != LBM_OK) return st;
@@ -1159,6 +1180,7 @@ lbm_status lbm_sums(lbm_ctx* c, double* mass_dev, double* heat_dev) {
 }
 
 lbm_status lbm_residual(lbm_ctx* c, double* r_u, double* r_T) {
+    NvtxRange range_("lbm_residual");
     lbm_status st = residual_launch(c);
     if (st != LBM_OK) return st;
     if ((st = sync_ctx(c)) != LBM_OK) return st;
@@ -1169,6 +1191,16 @@ lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;
     if (kernel == LBM_KERNEL_PLAIN) {
+        c->step_kernel = kernel;
+        return LBM_OK;
+    }
+    if (kernel == LBM_KERNEL_PAIRED) {
+        if (flow_q(c) != 19 || c->lat.enthalpy || c->lat.node_walls || c->aa)
+            return fail(c, LBM_EINVAL, "the paired step kernel takes D3Q19 ping-pong lattices "
+                                       "without node walls or enthalpy");
+        if (c->prm.nx % 2 != 0 || !c->kp.off32)
+            return fail(c, LBM_EINVAL, "the paired step kernel needs an even nx and fewer "
+                                       "than ~82 M sites");
         c->step_kernel = kernel;
         return LBM_OK;
     }
@@ -1454,6 +1486,7 @@ void lbm_batch_destroy(lbm_batch* b) {
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
+    NvtxRange range_("lbm_batch_step");
     if (!b || nsteps < 0) return LBM_EINVAL;
     for (lbm_ctx* c : b->ctx)
         if (c->sticky != LBM_OK) return c->sticky;
@@ -1489,6 +1522,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
 }
 
 lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows) {
+    NvtxRange range_("lbm_batch_tune");
     if (!b) return LBM_EINVAL;
     bool timed = false;  // only ping-pong groups can be timed without changing the state
     for (auto& g : b->groups) timed = timed || !g.aa;
@@ -1733,6 +1767,7 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
 }
 
 lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
+    NvtxRange range_("lbm_server_advance");
     if (!s) return LBM_EINVAL;
     if (cudaSetDevice(s->device) != cudaSuccess) return LBM_ECUDA;
     // admission in arrival order while a request fits the memory budget and, with a cap, the

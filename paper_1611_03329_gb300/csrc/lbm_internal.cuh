@@ -103,6 +103,10 @@ struct BatchLattice {
 // scheduled while the stream's previous kernel drains, and waits for it before loading).
 cudaError_t launch_step(const KParams& p, bool outflow, const Planes& pl, bool pdl,
                         cudaStream_t st);
+// One time step with two x-adjacent sites per thread (step_pair_kernel): D3Q19, no node
+// walls, no enthalpy model, nx even, 32-bit plane offsets (KParams::off32).
+cudaError_t launch_step_pair(const KParams& p, bool outflow, const Planes& pl, bool pdl,
+                             cudaStream_t st);
 // AA pattern (FP32, D3Q19, no outflow; one copy).  Pull step (local = false): pl.in is the
 // permuted table of the copy (logical plane q at physical opp(q)), pl.out the identity table.
 // Local step (local = true): pl = (in: identity, out: permuted), pw.in = the permuted table.
