@@ -316,6 +316,10 @@ def run_cpu_plan():
     return 0
 
 
+# The step kernel the library picks for the headline channel (D3Q19, even nx, ping-pong).
+DEFAULT_KERNEL = "paired"
+
+
 def _run_config_extra(ws, kernel, scheme):
     """The run-specific config keys, identical in both arms for the same workload."""
     return {"parallelism": f"replicas{ws}" if ws > 1 else "single", "step_kernel": kernel,
@@ -340,7 +344,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(extra=_run_config_extra(ws, "plain", "pingpong")),
+            "config": _config(extra=_run_config_extra(ws, DEFAULT_KERNEL, "pingpong")),
             "cpu_baseline": {"value": round(mlups, 4), "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(mlups, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -642,8 +646,9 @@ def run_ours(args):
     ns = wnx * wny * wnz
     with torch.cuda.stream(stream):
         lat = gb.Lattice(pb, stream=stream.cuda_stream)
-        if args.kernel != "plain":
+        if args.kernel != "auto":
             lat.set_step_kernel(args.kernel)
+        kernel = lat.step_kernel  # the kernel that runs
         aa = lat.lattice()["scheme"] == 1
         lat.step(args.warmup)
         lat.sync()
@@ -714,11 +719,11 @@ def run_ours(args):
         "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}[args.storage],
         "data": "synthetic",
         "config": _config(args.workload, args.storage, q=q,
-                          extra=_run_config_extra(ws, args.kernel, args.scheme)),
+                          extra=_run_config_extra(ws, kernel, args.scheme)),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "traffic": (profiled_traffic()
-                                 if (args.workload, args.storage, q, args.kernel) == ("channel", "fp32", 19, "plain")
+                                 if (args.workload, args.storage, q, kernel) == ("channel", "fp32", 19, "paired")
                                  else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
@@ -729,10 +734,11 @@ def run_ours(args):
                                  "below peak)"),
                      "kernel": ("aa_pull_kernel<true> / aa_local_kernel<true> alternating (AA, one "
                                 "copy in place, porosity field)" if aa else
-                                ("tma_step_kernel" if args.kernel == "tma" else "step_kernel") +
+                                {"tma": "tma_step_kernel", "paired": "step_pair_kernel"}.get(kernel, "step_kernel") +
                                 (f"<false,true,D3Q{q}> (fused stream-collide, outflow)"
                                  if args.workload == "channel" else
-                                 f"<true,false,D3Q{q}> (fused stream-collide, porosity field)"))},
+                                 f"<true,false,D3Q{q}> (fused stream-collide, porosity field)") +
+                                (", two x-adjacent sites per thread" if kernel == "paired" else ""))},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_mlups, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(nblob),
@@ -769,8 +775,9 @@ def main(argv=None):
                     help="flow lattice of the channel / cavity workloads (the headline is D3Q19)")
     ap.add_argument("--scheme", choices=("pingpong", "aa", "auto"), default="pingpong",
                     help="population scheme: two copies, or one copy updated in place (AA)")
-    ap.add_argument("--kernel", choices=("plain", "tma"), default="plain",
-                    help="step kernel: per-thread loads, or populations staged by TMA")
+    ap.add_argument("--kernel", choices=("auto", "plain", "paired", "tma"), default="auto",
+                    help="step kernel: the library's choice (auto), one site per thread, two "
+                         "x-adjacent sites per thread, or populations staged by TMA")
     ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")
     ap.add_argument("--max-steps", type=int, default=None,
                     help="serve / sweep: step limit per solve (default 50000 / 200000)")

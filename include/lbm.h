@@ -242,7 +242,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 /* Step kernels.  Both compute the same site update (Eqs. 9-10, 34-35 with the boundary rules
  * of lbm_step) and give bit-identical populations; they differ in how the streamed
  * populations reach the collision.
- *  LBM_KERNEL_PLAIN : one thread per site, each pull a load through the L1 (default).
+ *  LBM_KERNEL_PLAIN : one thread per site, each pull a load through the L1.
  *  LBM_KERNEL_TMA   : persistent blocks over tiles of 64 x 4 sites of one z-plane; for
  *                     tiles inside the y and z ranges the Tensor Memory Accelerator copies,
  *                     a few tiles ahead, one box per population plane (shifted by -e_i) into
@@ -256,7 +256,8 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  *                     e_x = 0 are read and written as aligned 2-element accesses and the
  *                     collision runs on the paired FP32 instructions of sm_100 (two sites per
  *                     instruction).  Needs the D3Q19 lattice, the ping-pong scheme, an even
- *                     nx, fewer than ~82 M sites, no node walls and no enthalpy model. */
+ *                     nx, fewer than ~82 M sites, no node walls and no enthalpy model.
+ * lbm_create selects LBM_KERNEL_PAIRED where it applies, else LBM_KERNEL_PLAIN. */
 #define LBM_KERNEL_PLAIN 0
 #define LBM_KERNEL_TMA 1
 #define LBM_KERNEL_PAIRED 2
@@ -401,13 +402,27 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
  * and before the contexts' own streams). */
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
 
-/* Time the batched step at 32, 64, 128 and 256 threads per block and 1, 2 and 4 z-planes
- * per block and keep the fastest shape (written to *block_threads and *rows when non-NULL).
- * The timed launches write only the buffers that the next step overwrites, so the lattices'
- * state is unchanged; AA lattices, updated in place, are therefore not timed, and a batch of
- * AA lattices only takes 32 threads x 4 planes (measured fastest for them) without timing.
+/* Autotuner of the batched step.  (1) Block shape: time the step at 32, 64, 128 and 256
+ * threads per block and 1, 2 and 4 z-planes per block and keep the fastest (written to
+ * *block_threads and *rows when non-NULL); the timed launches write only the buffers that the
+ * next step overwrites, so the lattices' state is unchanged.  AA lattices, updated in place,
+ * are not timed, and a batch of AA lattices only takes 32 threads x 4 planes (measured fastest
+ * for them).  (2) Streaming scheme: every group of ping-pong lattices that could run the AA
+ * scheme is timed both ways at the chosen shape -- AA on scratch, each lattice's second copy
+ * filled with its state and stepped in place -- and moves to AA (lbm_batch_set_scheme) only if
+ * that is more than 3 % faster (lbm_batch_scheme_times reports the last trial).
  * Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows);
+
+/* Move every ping-pong member that can run the AA scheme (FP32, D3Q19, no outflow face, no
+ * node walls, no enthalpy model) to it: its current copy is permuted into its second copy,
+ * which becomes the only one, and the first is freed -- half the population memory, the same
+ * populations, bit-identical later steps.  LBM_SCHEME_PINGPONG is accepted and changes
+ * nothing (AA members are not moved back).  Synchronises.  LBM_EINVAL for another scheme. */
+lbm_status lbm_batch_set_scheme(lbm_batch* b, int scheme);
+
+/* Milliseconds per step of the last group the tuner timed both ways (0 before any trial). */
+lbm_status lbm_batch_scheme_times(const lbm_batch* b, double* pp_ms, double* aa_ms);
 
 /* Set the block shape of the batched step: threads (32, 64, 128 or 256) and z-planes per
  * block (1..64). */

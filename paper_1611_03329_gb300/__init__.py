@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "lbm_server_clock", "lbm_server_destroy", "lbm_server_set_fill", "lbm_set_step_kernel",
     "lbm_get_step_kernel", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
     "lbm_set_launch", "lbm_test_tma_extra_wait", "lbm_server_set_output",
-    "lbm_server_set_policy",
+    "lbm_server_set_policy", "lbm_batch_set_scheme", "lbm_batch_scheme_times",
 )
 
 ADMIT_POLICIES = {"fifo": 0, "backfill": 1}
@@ -199,6 +199,8 @@ def lib():
         L.lbm_batch_step.argtypes = [vp, C.c_int]
         L.lbm_batch_tune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.lbm_batch_set_block.argtypes = [vp, C.c_int, C.c_int]
+        L.lbm_batch_set_scheme.argtypes = [vp, C.c_int]
+        L.lbm_batch_scheme_times.argtypes = [vp, dp, dp]
         L.lbm_batch_last_error.argtypes = [vp]
         L.lbm_batch_last_error.restype = C.c_char_p
         L.lbm_batch_destroy.argtypes = [vp]
@@ -492,6 +494,17 @@ class Batch:
     def set_block(self, threads: int, rows: int = 1):
         self._check(lib().lbm_batch_set_block(self._h, int(threads), int(rows)),
                     "lbm_batch_set_block")
+
+    def set_scheme(self, scheme: str):
+        """lbm_batch_set_scheme: move the members that can run AA to it ("aa")."""
+        self._check(lib().lbm_batch_set_scheme(self._h, SCHEMES[scheme]), "lbm_batch_set_scheme")
+
+    def scheme_times(self):
+        """(ping-pong ms, AA ms) per step of the tuner's last scheme trial."""
+        pp, aa = C.c_double(), C.c_double()
+        self._check(lib().lbm_batch_scheme_times(self._h, C.byref(pp), C.byref(aa)),
+                    "lbm_batch_scheme_times")
+        return pp.value, aa.value
 
     def sync(self):
         for l in self.lattices:

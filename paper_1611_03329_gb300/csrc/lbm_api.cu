@@ -537,13 +537,13 @@ int plane_off(const lbm_ctx* c, const void* base, const void* plane) {
 
 // Plane tables of an AA context's single copy: `in_perm` / `out_perm` select the swapped
 // layout (logical plane q at physical plane opp(q)) for the input / output side.
-lbm::Planes aa_planes(const lbm_ctx* c, bool in_perm, bool out_perm) {
+lbm::Planes aa_planes_at(const lbm_ctx* c, void* copy, bool in_perm, bool out_perm) {
     lbm::Planes pl;
-    pl.base_in = c->pop[0];
-    pl.base_out = c->pop[0];
+    pl.base_in = copy;
+    pl.base_out = copy;
     for (int q = 0; q < lbm::kQ + lbm::kQT; ++q) {
         const int pp = lbm::aa_swapped_plane(q);
-        char* base = static_cast<char*>(c->pop[0]);
+        char* base = static_cast<char*>(copy);
         pl.in[q] = base + (size_t)(in_perm ? pp : q) * (size_t)c->sq * c->elem;
         pl.out[q] = base + (size_t)(out_perm ? pp : q) * (size_t)c->sq * c->elem;
         pl.off_in[q] = plane_off(c, pl.base_in, pl.in[q]);
@@ -554,6 +554,10 @@ lbm::Planes aa_planes(const lbm_ctx* c, bool in_perm, bool out_perm) {
     pl.tin = nullptr;
     pl.tout = nullptr;
     return pl;
+}
+
+lbm::Planes aa_planes(const lbm_ctx* c, bool in_perm, bool out_perm) {
+    return aa_planes_at(c, c->pop[0], in_perm, out_perm);
 }
 
 // Planes of a step that reads copy `from` and writes the other copy.
@@ -706,6 +710,42 @@ lbm_status residual_collect(lbm_ctx* c, double* r_u, double* r_T) {
     return LBM_OK;
 }
 
+// Whether the paired step kernel can run a context.
+bool pair_eligible(const lbm_ctx* c) {
+    return flow_q(c) == 19 && !c->lat.enthalpy && !c->lat.node_walls && !c->aa &&
+           c->prm.nx % 2 == 0 && c->kp.off32;
+}
+
+// A ping-pong context moved to the AA scheme (aa_eligible lattices): the AA layout at rest
+// holds logical plane q at physical plane opp(q), so the current copy's planes are copied,
+// permuted, into the other copy, which becomes the single copy; the current copy is freed.
+// The populations are not changed, only where they are kept.
+lbm_status convert_to_aa(lbm_ctx* c) {
+    if (c->aa) return LBM_OK;
+    if (!aa_eligible(&c->prm, c->lat))
+        return fail(c, LBM_EINVAL, "this lattice cannot run the AA scheme");
+    void* src = c->pop[c->cur];
+    void* dst = c->pop[c->cur ^ 1];
+    const size_t plane = (size_t)c->sq * c->elem;
+    for (int q = 0; q < lbm::kQ + lbm::kQT; ++q)
+        LBM_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + (size_t)lbm::aa_swapped_plane(q) * plane,
+                                 static_cast<const char*>(src) + (size_t)q * plane,
+                                 (size_t)c->ns * c->elem, cudaMemcpyDeviceToDevice, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    LBM_CUDA(cudaFree(src));
+    c->pop[0] = dst;
+    c->pop[1] = nullptr;
+    c->cur = 0;
+    c->aa = true;
+    c->aa_phase = 0;
+    c->lat.scheme = LBM_SCHEME_AA;
+    if (c->step_kernel == LBM_KERNEL_PAIRED) c->step_kernel = LBM_KERNEL_PLAIN;
+    c->pl[0] = aa_planes(c, true, false);
+    c->pl[1] = aa_planes(c, false, true);
+    c->pw = aa_planes(c, true, true);
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -776,6 +816,8 @@ lbm_status lbm_create(const lbm_params* p, void* stream, lbm_ctx** out) {
     }
     if (st == LBM_OK) {
         fill_kparams(c);
+        // the paired kernel where it applies (bit-identical, faster in every measured case)
+        if (pair_eligible(c)) c->step_kernel = LBM_KERNEL_PAIRED;
         if (c->aa) {
             c->pl[0] = aa_planes(c, true, false);
             c->pl[1] = aa_planes(c, false, true);
@@ -1195,12 +1237,10 @@ lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
         return LBM_OK;
     }
     if (kernel == LBM_KERNEL_PAIRED) {
-        if (flow_q(c) != 19 || c->lat.enthalpy || c->lat.node_walls || c->aa)
+        if (!pair_eligible(c))
             return fail(c, LBM_EINVAL, "the paired step kernel takes D3Q19 ping-pong lattices "
-                                       "without node walls or enthalpy");
-        if (c->prm.nx % 2 != 0 || !c->kp.off32)
-            return fail(c, LBM_EINVAL, "the paired step kernel needs an even nx and fewer "
-                                       "than ~82 M sites");
+                                       "without node walls or enthalpy, with an even nx and "
+                                       "fewer than ~82 M sites");
         c->step_kernel = kernel;
         return LBM_OK;
     }
@@ -1289,6 +1329,7 @@ struct lbm_batch {
     std::map<int, cudaGraphExec_t> graphs;  // captured n-step sequences
     cudaEvent_t ev = nullptr;
     bool tuned = false;
+    double last_pp_ms = 0.0, last_aa_ms = 0.0;  // the tuner's last scheme trial (per step)
     char err[256] = {0};
 };
 
@@ -1392,6 +1433,105 @@ lbm_status batch_upload(lbm_batch* b) {
     return LBM_OK;
 }
 
+// Whether a ping-pong group could run the AA scheme (every member is eligible).
+bool group_aa_eligible(const lbm_batch* b, const lbm_batch::Group& g) {
+    if (g.aa) return false;
+    for (int k : g.members)
+        if (!aa_eligible(&b->ctx[k]->prm, b->ctx[k]->lat)) return false;
+    return true;
+}
+
+// Milliseconds per step of one group at the batch's block shape: the ping-pong kernel in its
+// state-preserving form (flip 0 writes only the non-current copies), or, with `aa`, the AA
+// kernel run on scratch: each member's non-current copy, filled with its current state, is
+// stepped in place as an AA copy, so the state stays untouched.
+lbm_status time_group(lbm_batch* b, lbm_batch::Group& g, bool aa, float* ms_per_step) {
+    const int nwarm = 2, ntime = 6;
+    lbm::BatchLattice* dtab = g.dtab;
+    unsigned short* dblk = g.dblk;
+    std::vector<lbm::BatchLattice> tab;
+    std::vector<unsigned short> blk;
+    if (aa) {
+        tab = g.htab;
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            lbm_ctx* c = b->ctx[g.members[k]];
+            void* scratch = c->pop[c->cur ^ 1];
+            LBM_BCUDA(cudaMemcpyAsync(scratch, c->pop[c->cur],
+                                      (size_t)(lbm::kQ + lbm::kQT) * c->sq * c->elem,
+                                      cudaMemcpyDeviceToDevice, b->stream));
+            tab[k].pl[0] = aa_planes_at(c, scratch, true, false);
+            tab[k].pl[1] = aa_planes_at(c, scratch, false, true);
+            tab[k].cur = 0;
+        }
+        LBM_BCUDA(cudaMalloc(&dtab, sizeof(lbm::BatchLattice) * tab.size()));
+        LBM_BCUDA(cudaMemcpyAsync(dtab, tab.data(), sizeof(lbm::BatchLattice) * tab.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+    }
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    for (int t = 0; t < nwarm + ntime && e == cudaSuccess; ++t) {
+        if (t == nwarm) e = cudaEventRecord(t0, b->stream);
+        if (e != cudaSuccess) break;
+        e = aa ? lbm::launch_batch_aa(dtab, dblk, g.nblocks, b->block_threads, b->rows, g.het,
+                                      t & 1, b->stream)
+               : lbm::launch_batch_step(dtab, dblk, g.nblocks, b->block_threads, b->rows,
+                                        g.storage, g.het, g.outflow, g.enthalpy, g.off32, 0,
+                                        b->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (aa) cudaFree(dtab);
+    if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "timing a group", e);
+    *ms_per_step = ms / ntime;
+    return LBM_OK;
+}
+
+// (Re)build the batch's kernel-variant groups and their device tables.
+lbm_status batch_group(lbm_batch* b) {
+    // group the lattices by kernel variant
+    lbm_status st = LBM_OK;
+    const int n = (int)b->ctx.size();
+    for (auto& g : b->groups) {
+        cudaFree(g.dtab);
+        cudaFree(g.dblk);
+    }
+    b->groups.clear();
+    for (int k = 0; k < n; ++k) {
+        lbm_ctx* c = b->ctx[k];
+        const int stg = c->prm.storage;
+        const bool het = c->lat.has_phi_field != 0, outf = c->outflow;
+        const bool ent = c->lat.enthalpy != 0, aa = c->aa, o32 = c->kp.off32 != 0;
+        lbm_batch::Group* grp = nullptr;
+        for (auto& gr : b->groups)
+            if (gr.storage == stg && gr.het == het && gr.outflow == outf && gr.enthalpy == ent &&
+                gr.aa == aa && gr.off32 == o32)
+                grp = &gr;
+        if (!grp) {
+            b->groups.emplace_back();
+            grp = &b->groups.back();
+            grp->storage = stg;
+            grp->het = het;
+            grp->outflow = outf;
+            grp->enthalpy = ent;
+            grp->aa = aa;
+            grp->off32 = o32;
+        }
+        grp->members.push_back(k);
+    }
+    for (auto& g : b->groups) {
+        if (st != LBM_OK) break;
+        size_t bytes = sizeof(lbm::BatchLattice) * g.members.size();
+        g.htab.resize(g.members.size());
+        if (cudaMalloc(&g.dtab, bytes) != cudaSuccess) st = LBM_ENOMEM;
+    }
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1434,35 +1574,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
     if (e != cudaSuccess) st = LBM_ECUDA;
-    // group the lattices by kernel variant
-    for (int k = 0; k < n && st == LBM_OK; ++k) {
-        lbm_ctx* c = b->ctx[k];
-        const int stg = c->prm.storage;
-        const bool het = c->lat.has_phi_field != 0, outf = c->outflow;
-        const bool ent = c->lat.enthalpy != 0, aa = c->aa, o32 = c->kp.off32 != 0;
-        lbm_batch::Group* grp = nullptr;
-        for (auto& gr : b->groups)
-            if (gr.storage == stg && gr.het == het && gr.outflow == outf && gr.enthalpy == ent &&
-                gr.aa == aa && gr.off32 == o32)
-                grp = &gr;
-        if (!grp) {
-            b->groups.emplace_back();
-            grp = &b->groups.back();
-            grp->storage = stg;
-            grp->het = het;
-            grp->outflow = outf;
-            grp->enthalpy = ent;
-            grp->aa = aa;
-            grp->off32 = o32;
-        }
-        grp->members.push_back(k);
-    }
-    for (auto& g : b->groups) {
-        if (st != LBM_OK) break;
-        size_t bytes = sizeof(lbm::BatchLattice) * g.members.size();
-        g.htab.resize(g.members.size());
-        if (cudaMalloc(&g.dtab, bytes) != cudaSuccess) st = LBM_ENOMEM;
-    }
+    if (st == LBM_OK) st = batch_group(b);
     if (st != LBM_OK) {
         lbm_batch_destroy(b);
         return st;
@@ -1575,7 +1687,56 @@ lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows) {
     if (block_threads) *block_threads = best;
     if (rows) *rows = best_rows;
     if (st != LBM_OK) return st;
+    // streaming scheme: a ping-pong group whose lattices could run the AA scheme is timed both
+    // ways at the chosen shape; it moves to AA only when that is faster by more than 3 %
+    if ((st = batch_upload(b)) != LBM_OK) return st;
+    bool moved = false;
+    for (auto& g : b->groups) {
+        if (!group_aa_eligible(b, g)) continue;
+        float pp = 0.0f, aa = 0.0f;
+        if ((st = time_group(b, g, false, &pp)) != LBM_OK) return st;
+        if ((st = time_group(b, g, true, &aa)) != LBM_OK) return st;
+        b->last_pp_ms = pp;
+        b->last_aa_ms = aa;
+        if (aa < 0.97f * pp) {
+            for (int k : g.members)
+                if ((st = convert_to_aa(b->ctx[k])) != LBM_OK) return st;
+            moved = true;
+        }
+    }
+    if (moved) {
+        LBM_BCUDA(cudaStreamSynchronize(b->stream));
+        if ((st = batch_group(b)) != LBM_OK) return st;
+        batch_clear_graphs(b);
+    }
     return batch_join(b, false);
+}
+
+lbm_status lbm_batch_set_scheme(lbm_batch* b, int scheme) {
+    if (!b || (scheme != LBM_SCHEME_AA && scheme != LBM_SCHEME_PINGPONG)) return LBM_EINVAL;
+    if (scheme == LBM_SCHEME_PINGPONG) return LBM_OK;  // ping-pong members stay as they are
+    LBM_BCUDA(cudaSetDevice(b->device));
+    lbm_status st = batch_join(b, true);
+    if (st != LBM_OK) return st;
+    LBM_BCUDA(cudaStreamSynchronize(b->stream));
+    bool moved = false;
+    for (lbm_ctx* c : b->ctx)
+        if (!c->aa && aa_eligible(&c->prm, c->lat)) {
+            if ((st = convert_to_aa(c)) != LBM_OK) return st;
+            moved = true;
+        }
+    if (moved) {
+        if ((st = batch_group(b)) != LBM_OK) return st;
+        batch_clear_graphs(b);
+    }
+    return batch_join(b, false);
+}
+
+lbm_status lbm_batch_scheme_times(const lbm_batch* b, double* pp_ms, double* aa_ms) {
+    if (!b) return LBM_EINVAL;
+    if (pp_ms) *pp_ms = b->last_pp_ms;
+    if (aa_ms) *aa_ms = b->last_aa_ms;
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_set_block(lbm_batch* b, int block_threads, int rows) {

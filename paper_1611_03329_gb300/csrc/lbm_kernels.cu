@@ -826,10 +826,17 @@ __device__ __forceinline__ void collide_g(const KParams& p, const Medium& md, fl
 // |M_k|^2 come precomputed in KParams.  PU (one site): the velocity is prescribed (pu, a node
 // wall) instead of solved from Eqs. 27-28, and the conserved momentum becomes
 // rho0 pu + rho0 F / 2 after the collision.  ENTH (one site): the enthalpy model.
-template <class V, bool FULL, bool ENTH = false, bool PU = false>
+// GOut: called as gout(g, dT) with the post-collision D3Q7 populations as soon as they are
+// final (the thermal collision needs only T and u), so that a caller can store them before
+// the D3Q19 relaxation runs and its registers are free; NoGStore leaves them in g.
+struct NoGStore {
+    template <class V>
+    __device__ __forceinline__ void operator()(const V*, V) const {}
+};
+template <class V, bool FULL, bool ENTH = false, bool PU = false, class GOut = NoGStore>
 __device__ __forceinline__ MacroT<V> collide_t(const KParams& p, const MediumT<V>& md, V* f, V* g,
                                                float pux = 0.0f, float puy = 0.0f,
-                                               float puz = 0.0f) {
+                                               float puz = 0.0f, GOut gout = GOut{}) {
     static_assert(std::is_same<V, L1>::value || !(ENTH || PU), "paired sites: standard model");
     // temperature (Eq. 39, or Eqs. B7-B9 with the enthalpy model) and body force (Eq. 5)
     const V n0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);  // sigma (T - T0)
@@ -897,6 +904,9 @@ __device__ __forceinline__ MacroT<V> collide_t(const KParams& p, const MediumT<V
     mac.T = T;
     mac.dT = dT;
     if (!FULL) return mac;
+
+    collide_g_t<V, ENTH>(p, md, g, n0, T, fl, ux, uy, uz);
+    gout(static_cast<const V*>(g), dT);
 
     if (rest) {  // f_eq(rho, 0) in deviation form: w_i (rho - rho0)
 #pragma unroll
@@ -1017,14 +1027,15 @@ __device__ __forceinline__ MacroT<V> collide_t(const KParams& p, const MediumT<V
 
     }  // flow collision
 
-    collide_g_t<V, ENTH>(p, md, g, n0, T, fl, ux, uy, uz);
     return mac;
 }
-template <bool FULL, bool ENTH = false, bool PU = false>
+template <bool FULL, bool ENTH = false, bool PU = false, class GOut = NoGStore>
 __device__ __forceinline__ Macro collide(const KParams& p, const Medium& md, float* f, float* g,
-                                         float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
+                                         float pux = 0.0f, float puy = 0.0f, float puz = 0.0f,
+                                         GOut gout = GOut{}) {
     const MacroT<L1> m = collide_t<L1, FULL, ENTH, PU>(p, md, reinterpret_cast<L1*>(f),
-                                                       reinterpret_cast<L1*>(g), pux, puy, puz);
+                                                       reinterpret_cast<L1*>(g), pux, puy, puz,
+                                                       gout);
     return {m.rho.v, m.ux.v, m.uy.v, m.uz.v, m.T.v, m.dT.v};
 }
 
@@ -1157,11 +1168,17 @@ __device__ __forceinline__ Macro collide15(const KParams& p, const Medium& md, f
 }
 
 // The collision of the flow lattice L (PU: with the velocity prescribed as pu).
-template <bool FULL, bool ENTH, class L, bool PU = false>
+template <bool FULL, bool ENTH, class L, bool PU = false, class GOut = NoGStore>
 __device__ __forceinline__ Macro collide_on(const KParams& p, const Medium& md, float* f, float* g,
-                                            float pux = 0.0f, float puy = 0.0f, float puz = 0.0f) {
-    if constexpr (L::kQ == 15) return collide15<FULL, PU>(p, md, f, g, pux, puy, puz);
-    else return collide<FULL, ENTH, PU>(p, md, f, g, pux, puy, puz);
+                                            float pux = 0.0f, float puy = 0.0f, float puz = 0.0f,
+                                            GOut gout = GOut{}) {
+    if constexpr (L::kQ == 15) {
+        const Macro m = collide15<FULL, PU>(p, md, f, g, pux, puy, puz);
+        if (FULL) gout(reinterpret_cast<const L1*>(g), L1{m.dT});
+        return m;
+    } else {
+        return collide<FULL, ENTH, PU>(p, md, f, g, pux, puy, puz, gout);
+    }
 }
 
 // ---- node walls (non-equilibrium extrapolation) -------------------------------------------------
@@ -1353,12 +1370,13 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
         pl.hout[5 * p.nyz + yz] = g[2];
     }
     const Medium md = medium_at<HET>(p, s);
-    const Macro m = collide_on<true, ENTH, L>(p, md, f, g);
+    collide_on<true, ENTH, L>(p, md, f, g, 0.0f, 0.0f, 0.0f, [&](const L1* gg, L1 dT) {
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, gg[i].v, dT.v);
+        if constexpr (S::kScaled) pl.tout[s] = dT.v;
+    });
 #pragma unroll
     for (int i = 0; i < L::kQ; ++i) stp<S>(pl, p, i, s, f[i]);
-#pragma unroll
-    for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, g[i], m.dT);
-    if constexpr (S::kScaled) pl.tout[s] = m.dT;
 }
 
 // Programmatic dependent launch: a step kernel launched with it may be scheduled while the
@@ -1493,6 +1511,105 @@ __device__ __forceinline__ void gather_pair_interior(const Planes& pl, const KPa
     }
 }
 
+// The x faces' rules of gather_pair_x: site a (lane .x) on the x-low face, site b (lane .y) on
+// the x-high face, as xsel_fix_f and outflow_anchor apply them to a single site.
+template <bool OUTF, int... I>
+__device__ __forceinline__ void pair_x_fix_f(const KParams& p, bool cxm, bool cxp, bool xout,
+                                             const float* hf, L2* f,
+                                             std::integer_sequence<int, I...>) {
+    const bool vlo = (p.vel_mask & 1u) && !(p.wall_mask & 1u);
+    const bool vhi = (p.vel_mask & 2u) && !(p.wall_mask & 2u);
+    bool via[kQ];
+    (([&] {
+         constexpr int ex = D3Q19::ex(I);
+         via[I] = false;
+         if constexpr (ex == 1) {
+             if (cxm && vlo) f[I].v.x = bounce_moving<D3Q19, I>(p, 0, f[I].v.x);
+         } else if constexpr (ex == -1) {
+             if (cxp) {
+                 if (xout) {
+                     if constexpr (OUTF) {
+                         f[I].v.y = outflow_blend(p, hf[D3Q19::slot(I)], f[I].v.y);
+                         via[I] = true;
+                     }
+                 } else if (vhi) {
+                     f[I].v.y = bounce_moving<D3Q19, I>(p, 1, f[I].v.y);
+                 }
+             }
+         }
+     }()),
+     ...);
+    if (OUTF && cxp && xout) {
+        float fb[kQ];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) fb[i] = f[i].v.y;
+        outflow_anchor<D3Q19>(fb, via);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) f[i].v.y = fb[i];
+    }
+}
+
+// Pull of a pair whose rows need no y/z face rule (yz_fast) but whose site a may lie on the
+// x-low face or site b on the x-high face: the planes with e_x = 0 stay paired, the shifted
+// planes select per site as gather_xsel does, and the x faces' rules apply to the site on the
+// face (the same operations on each site as gather_xsel).
+template <bool OUTF, class S>
+__device__ __forceinline__ void gather_pair_x(const Planes& pl, const KParams& p, int xa, int y,
+                                              int z, int sa, L2* f, L2* g) {
+    const AxisOff o = axis_offsets(p, xa, y, z);  // site a; site b differs only along +x
+    const bool cxm = (o.cross & 1u) != 0u;        // site a on a non-periodic x-low face
+    const int sb = sa + 1;
+    bool cxp = false;                              // site b on a non-periodic x-high face
+    int xpb = 1;
+    if (xa + 1 == p.nx - 1) {
+        if (p.per_mask & 2u) xpb = 1 - p.nx;
+        else { xpb = 0; cxp = true; }
+    }
+    const bool xout = OUTF && !(p.wall_mask & 2u) && !(p.vel_mask & 2u);
+    const bool bnc_b = cxp && !xout;  // site b's -x pulls bounce back
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int oyz = axis_off(D3Q19::ey(i), o.ym, o.yp) + axis_off(D3Q19::ez(i), o.zm, o.zp);
+        if (D3Q19::ex(i) == 0) {
+            f[i] = ldp2<S>(pl, p, i, sa + oyz);
+        } else if (D3Q19::ex(i) == 1) {
+            f[i] = pair(ldp_either<S>(pl, p, i, D3Q19::opp(i), cxm, cxm ? sa : sa + o.xm + oyz),
+                        ldp<S>(pl, p, i, sa + oyz));
+        } else {
+            f[i] = pair(ldp<S>(pl, p, i, sa + 1 + oyz),
+                        ldp_either<S>(pl, p, i, D3Q19::opp(i), bnc_b, bnc_b ? sb : sb + xpb + oyz));
+        }
+    }
+    const bool gout = OUTF && cxp && p.heat_kind[1] == 3;
+#pragma unroll
+    for (int i = 0; i < kQT; ++i) {
+        const int oyz = axis_off(ey7(i), o.ym, o.yp) + axis_off(ez7(i), o.zm, o.zp);
+        if (ex7(i) == 0) {
+            g[i] = ldg2<S>(pl, p, i, sa + oyz);
+        } else if (ex7(i) == 1) {
+            g[i] = pair(ldg_either<S>(pl, p, i, opp7(i), cxm, cxm ? sa : sa + o.xm + oyz),
+                        ldg_dev<S>(pl, p, i, sa + oyz));
+        } else {
+            const bool bb = cxp && !gout;
+            g[i] = pair(ldg_dev<S>(pl, p, i, sa + 1 + oyz),
+                        ldg_either<S>(pl, p, i, opp7(i), bb, bb ? sb : sb + xpb + oyz));
+        }
+    }
+    float hf[kOutSlots];
+    if constexpr (OUTF) {
+        const int yz = y + p.ny * z;
+#pragma unroll
+        for (int k = 0; k < kOutSlots; ++k) hf[k] = cxp ? __ldg(pl.hin + k * p.nyz + yz) : 0.0f;
+    }
+    if (!(cxm || cxp)) return;
+    pair_x_fix_f<OUTF>(p, cxm, cxp, xout, hf, f, std::make_integer_sequence<int, kQ>{});
+    if (cxm && p.heat_kind[0] == 2) g[1].v.x = -g[1].v.x + p.heat_abb[0];
+    if (cxp) {
+        if (gout) g[2].v.y = outflow_blend(p, hf[5], g[2].v.y);
+        else if (p.heat_kind[1] == 2) g[2].v.y = -g[2].v.y + p.heat_abb[1];
+    }
+}
+
 // The gather mode of a warp of pairs (warp_gather_mode over both sites of every lane).
 __device__ __forceinline__ int warp_pair_mode(const KParams& p, int xa, int y, int z, bool active) {
     const bool quiet = site_no_cross(p, xa, y, z) && site_no_cross(p, xa + 1, y, z);
@@ -1501,8 +1618,12 @@ __device__ __forceinline__ int warp_pair_mode(const KParams& p, int xa, int y, i
     return kGatherAny;
 }
 
+// Registers (measured on the 256x64x64 channel and the 256^3 field cavity, GB300): uncapped
+// the kernel takes ~128 and runs 14 warps per SM, latency-bound; 96 (16-bit) and 104 (FP32)
+// give 20 warps at little spilling for a uniform medium; with a porosity field the 16-bit
+// instance is fastest at 112 and the FP32 one uncapped (it spills heavily below that).
 template <bool HET, bool OUTF, class S>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __maxnreg__(HET ? (S::kScaled ? 112 : 128) : (S::kScaled ? 96 : 104))
     step_pair_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int xa = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -1515,6 +1636,8 @@ __global__ void __launch_bounds__(kBlock)
     L2 f[kQ], g[kQT];
     if (mode == kGatherInterior) {
         gather_pair_interior<S>(pl, p, xa, y, z, sa, f, g);
+    } else if (mode == kGatherX) {
+        gather_pair_x<OUTF, S>(pl, p, xa, y, z, sa, f, g);
     } else {
         float fa[kQ], ga[kQT], fb[kQ], gb[kQT];
         gather_site<OUTF, S>(pl, p, xa, y, z, sa, mode, fa, ga);
@@ -1534,12 +1657,13 @@ __global__ void __launch_bounds__(kBlock)
         pl.hout[5 * p.nyz + yz] = g[2].v.y;
     }
     const MediumT<L2> md = medium_pair<HET>(p, sa);
-    const MacroT<L2> m = collide_t<L2, true>(p, md, f, g);
+    collide_t<L2, true>(p, md, f, g, 0.0f, 0.0f, 0.0f, [&](const L2* gg, L2 dT) {
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) stg2<S>(pl, p, i, sa, gg[i], dT);
+        if constexpr (S::kScaled) *reinterpret_cast<float2*>(pl.tout + sa) = dT.v;
+    });
 #pragma unroll
     for (int i = 0; i < kQ; ++i) stp2<S>(pl, p, i, sa, f[i]);
-#pragma unroll
-    for (int i = 0; i < kQT; ++i) stg2<S>(pl, p, i, sa, g[i], m.dT);
-    if constexpr (S::kScaled) *reinterpret_cast<float2*>(pl.tout + sa) = m.dT.v;
 }
 
 // ---- AA pattern: one population copy, updated in place (FP32, D3Q19, no outflow) ----------

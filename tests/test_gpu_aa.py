@@ -200,3 +200,55 @@ def test_batch_of_aa_lattices_only(gb):
         assert np.array_equal(a.populations()[0], s_.populations()[0])
         assert np.array_equal(a.populations()[1], s_.populations()[1])
     batch.close()
+
+
+def test_batch_moves_lattices_to_aa(gb):
+    """lbm_batch_set_scheme("aa"): the eligible ping-pong members move to the one-copy scheme
+    (their current copy permuted into the second, the first freed); an outflow channel stays
+    ping-pong.  Every lattice keeps stepping bit-identically to the same problem stepped alone
+    with ping-pong copies."""
+    pbs = [dict(cavity_problem(12, Ra=1e4, Da=1e-2, phi=0.7, Pr=0.71), ny=10, nz=9),
+           _hetero(10), channel_problem(24, 8, 6, Da=1e-2)]
+    alone = [gb.Lattice(pb) for pb in pbs]
+    batched = [gb.Lattice(pb) for pb in pbs]
+    for a, b in zip(alone, batched):
+        a.step(3)
+        b.step(3)
+    batch = gb.Batch(batched)
+    batch.step(2)
+    batch.set_scheme("aa")
+    assert [b.lattice()["scheme"] for b in batched] == [1, 1, 0]
+    batch.step(5)
+    batch.step(4)
+    for a in alone:
+        a.step(11)
+    for a, b in zip(alone, batched):
+        fa, ga = a.populations()
+        fb, gbb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gbb)
+    batch.close()
+
+
+def test_tuner_chooses_the_scheme_by_timing(gb):
+    """lbm_batch_tune times eligible ping-pong groups both ways (AA on scratch copies) and
+    keeps ping-pong unless AA is more than 3 % faster; the state is untouched either way."""
+    pbs = [cavity_problem(24, Ra=1e5, Da=1e-2, phi=0.8, Pr=0.71) for _ in range(3)]
+    alone = [gb.Lattice(pb) for pb in pbs]
+    batched = [gb.Lattice(pb) for pb in pbs]
+    batch = gb.Batch(batched)
+    batch.step(7)
+    for a in alone:
+        a.step(7)
+    batch.tune()
+    pp, aa = batch.scheme_times()
+    assert pp > 0.0 and aa > 0.0
+    want = 1 if aa < 0.97 * pp else 0
+    assert all(b.lattice()["scheme"] == want for b in batched)
+    batch.step(9)
+    for a in alone:
+        a.step(9)
+    for a, b in zip(alone, batched):
+        fa, ga = a.populations()
+        fb, gbb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gbb)
+    batch.close()

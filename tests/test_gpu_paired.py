@@ -64,8 +64,9 @@ def test_paired_kernel_is_bit_identical(gb, orc, name, storage):
     pb = dict(CASES[name], storage=storage)
     lp, o, f, g = _state(orc, pb, seed=len(name))
     one, two = gb.Lattice(pb), gb.Lattice(pb)
+    one.set_step_kernel("plain")
     two.set_step_kernel("paired")
-    assert two.step_kernel == "paired"
+    assert one.step_kernel == "plain" and two.step_kernel == "paired"
     for lat in (one, two):
         lat.set_populations(f, g)
     for n in (1, 2, 17):
@@ -93,6 +94,7 @@ def test_paired_kernel_long_channel_run_matches_oracle(gb, orc):
     1e-5 of the oracle, and bit-identical to the one-site kernel."""
     pb = channel_problem(64, 16, 16)
     one, two = gb.Lattice(pb), gb.Lattice(pb)
+    one.set_step_kernel("plain")
     two.set_step_kernel("paired")
     one.step(2000)
     two.step(2000)
@@ -102,6 +104,13 @@ def test_paired_kernel_long_channel_run_matches_oracle(gb, orc):
     _, ug, Tg = two.macros()
     _, uo, To = o.macros()
     assert orc.field_error(ug, uo) < 1e-5 and orc.field_error(Tg, To) < 1e-5
+
+
+def test_paired_kernel_is_the_default_where_it_applies(gb):
+    assert gb.Lattice(channel_problem(34, 10, 7, Da=1e-2)).step_kernel == "paired"
+    assert gb.Lattice(dict(cavity_problem(9, Ra=1e4, Da=1e-2, phi=0.6), ny=8)).step_kernel == "plain"
+    assert gb.Lattice(dict(cavity_problem(8, Ra=1e4, Da=1e-2, phi=0.6), q=15)).step_kernel == "plain"
+    assert gb.Lattice(dict(cavity_problem(8, Ra=1e4, Da=1e-2, phi=0.6), scheme="aa")).step_kernel == "plain"
 
 
 def test_paired_kernel_rules(gb):

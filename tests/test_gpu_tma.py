@@ -60,6 +60,7 @@ def _state(orc, pb, seed):
 
 def _pair(gb, pb, f, g):
     plain, tma = gb.Lattice(pb), gb.Lattice(pb)
+    plain.set_step_kernel("plain")
     tma.set_step_kernel("tma")
     assert plain.step_kernel == "plain" and tma.step_kernel == "tma"
     plain.set_populations(f, g)
