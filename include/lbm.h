@@ -281,6 +281,14 @@ int lbm_get_step_kernel(const lbm_ctx* ctx);
  * Results do not depend on either.  Errors: LBM_EINVAL (a value out of range; nothing changed). */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int block_threads, int dependent_launch);
 
+/* Bounds-checked build (the library compiled with -DLBM_BOUNDS_CHECK, e.g.
+ * `python -m paper_1611_03329_gb300.build --checked`, liblbm_gb300_checked.so): every site
+ * index of a population, temperature-plane, porosity or outflow-history access of the site
+ * kernels (step, paired, batched, AA, macros) is checked; an index out of range is replaced by
+ * 0 and the first one met is kept.  *first_bad receives it (-1: none) for the current device.
+ * The ordinary build returns LBM_EINVAL (nothing is checked there). */
+lbm_status lbm_bounds_report(long long* first_bad);
+
 /* TEST ONLY: makes every pipeline stage of the TMA step kernel wait for `bytes` (0 .. 4096)
  * more than its loads bring, so that its bounded waits run out and the failure path of
  * LBM_KERNEL_TMA can be exercised without a fault; 0 (the default) turns it off.  Takes effect

@@ -41,6 +41,7 @@ ABI_SYMBOLS = (
     "lbm_get_step_kernel", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
     "lbm_set_launch", "lbm_test_tma_extra_wait", "lbm_server_set_output",
     "lbm_server_set_policy", "lbm_batch_set_scheme", "lbm_batch_scheme_times",
+    "lbm_bounds_report",
 )
 
 ADMIT_POLICIES = {"fifo": 0, "backfill": 1}
@@ -213,6 +214,7 @@ def lib():
         L.lbm_server_poll.argtypes = [vp, C.POINTER(LbmResult), C.c_int, C.POINTER(C.c_int)]
         L.lbm_server_set_output.argtypes = [vp, C.c_longlong, fp, fp]
         L.lbm_server_set_policy.argtypes = [vp, C.c_int]
+        L.lbm_bounds_report.argtypes = [C.POINTER(C.c_longlong)]
         L.lbm_server_set_fill.argtypes = [vp, C.c_longlong]
         L.lbm_server_clock.argtypes = [vp]
         L.lbm_server_clock.restype = C.c_double
@@ -631,3 +633,13 @@ def algorithmic_bytes_per_site(pb: dict) -> int:
 
 def nan_safe(x: float) -> float:
     return x if math.isfinite(x) else float("nan")
+
+
+def bounds_report():
+    """lbm_bounds_report: the first out-of-range site index the bounds-checked library met
+    (-1: none); raises LbmError(LBM_EINVAL) on the ordinary build."""
+    v = C.c_longlong(-1)
+    st = lib().lbm_bounds_report(C.byref(v))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_bounds_report: not a bounds-checked build")
+    return v.value

@@ -1268,6 +1268,13 @@ lbm_status lbm_set_step_kernel(lbm_ctx* c, int kernel) {
 
 int lbm_get_step_kernel(const lbm_ctx* c) { return c ? c->step_kernel : -1; }
 
+lbm_status lbm_bounds_report(long long* first_bad) {
+    if (!first_bad) return LBM_EINVAL;
+    int checked = 0;
+    if (lbm::bounds_report(first_bad, &checked) != cudaSuccess) return LBM_ECUDA;
+    return checked ? LBM_OK : LBM_EINVAL;
+}
+
 lbm_status lbm_set_launch(lbm_ctx* c, int block_threads, int dependent_launch) {
     lbm_status st = usable(c);
     if (st != LBM_OK) return st;

@@ -162,6 +162,10 @@ cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, co
                             int blocks, int extra_tx, int* err, bool pdl, cudaStream_t st);
 
 int reduction_blocks();
+// The bounds-checked build's record (-DLBM_BOUNDS_CHECK): *checked = 1 and *first_bad = the
+// first out-of-range site index a kernel of lbm_kernels.cu met (-1: none); *checked = 0 in the
+// ordinary build.
+cudaError_t bounds_report(long long* first_bad, int* checked);
 // Physical plane of logical D3Q19 + D3Q7 plane q in the AA scheme's swapped layout: the plane
 // of the opposite velocity.
 int aa_swapped_plane(int q);

@@ -164,6 +164,23 @@ using StoreF32o = Off32<StoreF32>;
 using StoreF16o = Off32<StoreF16>;
 using StoreBF16o = Off32<StoreBF16>;
 
+// Optional bounds checks (compile with -DLBM_BOUNDS_CHECK): every site index of a population,
+// temperature-plane, porosity or outflow-history access is checked; an index out of range is
+// recorded (the first one met, in g_bounds_bad) and replaced by 0, so the kernel goes on
+// without touching memory outside its buffers.  Without the macro the check is the identity.
+#ifdef LBM_BOUNDS_CHECK
+__device__ unsigned long long g_bounds_bad;  // 0, or 1 + the first out-of-range index met
+__device__ __forceinline__ int chk(int i, long long n) {
+    if ((unsigned long long)(long long)i >= (unsigned long long)n) {
+        atomicCAS(&g_bounds_bad, 0ull, 1ull + (unsigned long long)(unsigned)i);
+        return 0;
+    }
+    return i;
+}
+#else
+__device__ __forceinline__ int chk(int i, long long) { return i; }
+#endif
+
 // Weight that multiplies the stored value of plane q (q < 19: f, else g).
 template <class S>
 __device__ __forceinline__ float plane_scale(const KParams& p, int q) {
@@ -191,6 +208,7 @@ __device__ __forceinline__ typename S::T* plane_out(const Planes& pl, const KPar
 template <class S>
 __device__ __forceinline__ const typename S::T* at_in(const Planes& pl, const KParams& p, int q,
                                                       int idx) {
+    idx = chk(idx, p.ns);
     if constexpr (S::kOff32)
         return static_cast<const typename S::T*>(pl.base_in) + (unsigned)(pl.off_in[q] + idx);
     else
@@ -198,6 +216,7 @@ __device__ __forceinline__ const typename S::T* at_in(const Planes& pl, const KP
 }
 template <class S>
 __device__ __forceinline__ typename S::T* at_out(const Planes& pl, const KParams& p, int q, int idx) {
+    idx = chk(idx, p.ns);
     if constexpr (S::kOff32)
         return static_cast<typename S::T*>(pl.base_out) + (unsigned)(pl.off_out[q] + idx);
     else
@@ -206,6 +225,7 @@ __device__ __forceinline__ typename S::T* at_out(const Planes& pl, const KParams
 template <class S>
 __device__ __forceinline__ const typename S::T* at_in_either(const Planes& pl, const KParams& p,
                                                              int I, int J, bool other, int idx) {
+    idx = chk(idx, p.ns);
     if constexpr (S::kOff32)
         return static_cast<const typename S::T*>(pl.base_in) +
                (unsigned)((other ? pl.off_in[J] : pl.off_in[I]) + idx);
@@ -236,7 +256,7 @@ __device__ __forceinline__ float ldg_dev(const Planes& pl, const KParams& p, int
         // explicit roundings (no contraction left to the compiler): the staged-load kernel
         // repeats this arithmetic and must give the same bits
         const float sc = i == 0 ? p.om0 : p.om1;
-        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx),
+        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + chk(idx, p.ns)),
                                        S::ld(at_in<S>(pl, p, kQ + i, idx))));
     }
 }
@@ -355,7 +375,7 @@ __device__ __forceinline__ Medium medium_at(const KParams& p, int s) {
         m.c_forch = {p.c_forch};
         m.zeta_alpha = {p.zeta_alpha};
     } else {
-        const float ph = __ldg(p.phi_field + s);
+        const float ph = __ldg(p.phi_field + chk(s, p.ns));
         const float ph3 = __fmul_rn(__fmul_rn(ph, ph), ph);
         const float omp = __fsub_rn(1.0f, ph);
         const float Fp = p.F_phi < 0.0f ? __fmul_rn(1.75f, rsqrtf(__fmul_rn(150.0f, ph3))) : p.F_phi;
@@ -477,7 +497,7 @@ __device__ __forceinline__ float pull_f(const Planes& pl, const KParams& p, cons
         // wall or velocity face, taken above)
         *via = true;
         const float inner = ldp<S>(pl, p, I, n.s + oyz);
-        const float old = __ldg(pl.hin + L::slot(I) * p.nyz + n.y + p.ny * n.z);
+        const float old = __ldg(pl.hin + L::slot(I) * p.nyz + chk(n.y + p.ny * n.z, p.nyz));
         return outflow_blend(p, old, inner);
     }
     return bb;  // not reached for validated boundary sets
@@ -496,7 +516,7 @@ __device__ __forceinline__ float pull_g(const Planes& pl, const KParams& p, cons
     if constexpr (OUTF && ex == -1) {
         if (kind == 3) {  // g_I(N-2, t+1) = g*_I(N-1, t)
             const float inner = ldg_dev<S>(pl, p, I, n.s);
-            return outflow_blend(p, __ldg(pl.hin + 5 * p.nyz + n.y + p.ny * n.z), inner);
+            return outflow_blend(p, __ldg(pl.hin + 5 * p.nyz + chk(n.y + p.ny * n.z, p.nyz)), inner);
         }
     }
     const float bb = ldg_dev<S>(pl, p, opp7(I), n.s);
@@ -550,7 +570,7 @@ __device__ __forceinline__ void x_face_f(const Planes& pl, const KParams& p, int
                  if (out) {
                      const float inner = ldp<S>(pl, p, I, s + axis_off(L::ey(I), oym, oyp) +
                                                               axis_off(L::ez(I), ozm, ozp));
-                     f[I] = outflow_blend(p, __ldg(pl.hin + L::slot(I) * p.nyz + yz), inner);
+                     f[I] = outflow_blend(p, __ldg(pl.hin + L::slot(I) * p.nyz + chk(yz, p.nyz)), inner);
                      via[I] = true;
                  } else {
                      const float bb = ldp<S>(pl, p, L::opp(I), s);
@@ -583,7 +603,7 @@ __device__ __forceinline__ void x_face_fixup(const Planes& pl, const KParams& p,
     if (cxp) {
         const int kind = p.heat_kind[1];
         if (OUTF && kind == 3) {
-            g[2] = outflow_blend(p, __ldg(pl.hin + 5 * p.nyz + yz), ldg_dev<S>(pl, p, 2, s));
+            g[2] = outflow_blend(p, __ldg(pl.hin + 5 * p.nyz + chk(yz, p.nyz)), ldg_dev<S>(pl, p, 2, s));
         } else {
             const float bb = ldg_dev<S>(pl, p, 1, s);
             g[2] = kind == 2 ? -bb + p.heat_abb[1] : bb;
@@ -666,7 +686,7 @@ __device__ __forceinline__ float ldg_either(const Planes& pl, const KParams& p, 
         return ldp_either<S>(pl, p, kQ + I, kQ + J, other, idx);
     } else {
         const float sc = I == 0 ? p.om0 : p.om1;
-        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + idx),
+        return __fmul_rn(sc, __fmaf_rn(p.sigma, __ldg(pl.tin + chk(idx, p.ns)),
                                        S::ld(at_in_either<S>(pl, p, kQ + I, kQ + J, other, idx))));
     }
 }
@@ -746,7 +766,7 @@ __device__ __forceinline__ void gather_sel(const Planes& pl, const KParams& p, i
         const bool xo = (o.cross & 2u) != 0u;
         const int yz = y + p.ny * z;
 #pragma unroll
-        for (int k = 0; k < kOutSlots; ++k) hf[k] = xo ? __ldg(pl.hin + k * p.nyz + yz) : 0.0f;
+        for (int k = 0; k < kOutSlots; ++k) hf[k] = xo ? __ldg(pl.hin + k * p.nyz + chk(yz, p.nyz)) : 0.0f;
     }
     if (o.cross == 0u) return;  // no face rule at this site
     bool via[L::kQ];
@@ -1324,7 +1344,7 @@ __device__ __forceinline__ void gather_xsel(const Planes& pl, const KParams& p, 
     if constexpr (OUTF) {
         const int yz = y + p.ny * z;
 #pragma unroll
-        for (int k = 0; k < kOutSlots; ++k) hf[k] = cxp ? __ldg(pl.hin + k * p.nyz + yz) : 0.0f;
+        for (int k = 0; k < kOutSlots; ++k) hf[k] = cxp ? __ldg(pl.hin + k * p.nyz + chk(yz, p.nyz)) : 0.0f;
     }
     if (!(cxm || cxp)) return;
     bool via[L::kQ];
@@ -1362,18 +1382,18 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
                                             int s, float* f, float* g) {
     if (OUTF && x == p.nx - 1) {
         const int yz = y + p.ny * z;
-        pl.hout[0 * p.nyz + yz] = f[2];
-        pl.hout[1 * p.nyz + yz] = f[8];
-        pl.hout[2 * p.nyz + yz] = f[10];
-        pl.hout[3 * p.nyz + yz] = f[12];
-        pl.hout[4 * p.nyz + yz] = f[14];
-        pl.hout[5 * p.nyz + yz] = g[2];
+        pl.hout[0 * p.nyz + chk(yz, p.nyz)] = f[2];
+        pl.hout[1 * p.nyz + chk(yz, p.nyz)] = f[8];
+        pl.hout[2 * p.nyz + chk(yz, p.nyz)] = f[10];
+        pl.hout[3 * p.nyz + chk(yz, p.nyz)] = f[12];
+        pl.hout[4 * p.nyz + chk(yz, p.nyz)] = f[14];
+        pl.hout[5 * p.nyz + chk(yz, p.nyz)] = g[2];
     }
     const Medium md = medium_at<HET>(p, s);
     collide_on<true, ENTH, L>(p, md, f, g, 0.0f, 0.0f, 0.0f, [&](const L1* gg, L1 dT) {
 #pragma unroll
         for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, gg[i].v, dT.v);
-        if constexpr (S::kScaled) pl.tout[s] = dT.v;
+        if constexpr (S::kScaled) pl.tout[chk(s, p.ns)] = dT.v;
     });
 #pragma unroll
     for (int i = 0; i < L::kQ; ++i) stp<S>(pl, p, i, s, f[i]);
@@ -1450,6 +1470,7 @@ __device__ __forceinline__ void st2_raw(typename S::T* a, float2 v) {
 // Plane q (flow) at the aligned pair idx, idx + 1, as ldp reads each.
 template <class S>
 __device__ __forceinline__ L2 ldp2(const Planes& pl, const KParams& p, int q, int idx) {
+    idx = chk(idx + 1, p.ns) - 1;  // both elements of the pair in range
     const L2 v{ld2_raw<S>(at_in<S>(pl, p, q, idx))};
     if constexpr (S::kScaled) return v * K<L2>(plane_scale<S>(p, q));
     else return v;
@@ -1460,18 +1481,21 @@ __device__ __forceinline__ L2 ldg2(const Planes& pl, const KParams& p, int i, in
     if constexpr (!S::kScaled) {
         return ldp2<S>(pl, p, kQ + i, idx);
     } else {
+        idx = chk(idx + 1, p.ns) - 1;
         const L2 st{ld2_raw<S>(at_in<S>(pl, p, kQ + i, idx))};
-        const L2 tin{__ldg(reinterpret_cast<const float2*>(pl.tin + idx))};
+        const L2 tin{__ldg(reinterpret_cast<const float2*>(pl.tin + chk(idx, p.ns - 1)))};
         return K<L2>(i == 0 ? p.om0 : p.om1) * fma(K<L2>(p.sigma), tin, st);
     }
 }
 template <class S>
 __device__ __forceinline__ void stp2(const Planes& pl, const KParams& p, int q, int idx, L2 v) {
+    idx = chk(idx + 1, p.ns) - 1;
     if constexpr (S::kScaled) v = v * K<L2>(plane_inv_scale<S>(p, q));
     st2_raw<S>(at_out<S>(pl, p, q, idx), v.v);
 }
 template <class S>
 __device__ __forceinline__ void stg2(const Planes& pl, const KParams& p, int i, int idx, L2 v, L2 dT) {
+    idx = chk(idx + 1, p.ns) - 1;
     if constexpr (!S::kScaled) {
         stp2<S>(pl, p, kQ + i, idx, v);
     } else {
@@ -1599,7 +1623,7 @@ __device__ __forceinline__ void gather_pair_x(const Planes& pl, const KParams& p
     if constexpr (OUTF) {
         const int yz = y + p.ny * z;
 #pragma unroll
-        for (int k = 0; k < kOutSlots; ++k) hf[k] = cxp ? __ldg(pl.hin + k * p.nyz + yz) : 0.0f;
+        for (int k = 0; k < kOutSlots; ++k) hf[k] = cxp ? __ldg(pl.hin + k * p.nyz + chk(yz, p.nyz)) : 0.0f;
     }
     if (!(cxm || cxp)) return;
     pair_x_fix_f<OUTF>(p, cxm, cxp, xout, hf, f, std::make_integer_sequence<int, kQ>{});
@@ -1649,18 +1673,18 @@ __global__ void __maxnreg__(HET ? (S::kScaled ? 112 : 128) : (S::kScaled ? 96 : 
     }
     if (OUTF && xa + 1 == p.nx - 1) {  // site b on the outflow face: its pre-collision pulls
         const int yz = y + p.ny * z;
-        pl.hout[0 * p.nyz + yz] = f[2].v.y;
-        pl.hout[1 * p.nyz + yz] = f[8].v.y;
-        pl.hout[2 * p.nyz + yz] = f[10].v.y;
-        pl.hout[3 * p.nyz + yz] = f[12].v.y;
-        pl.hout[4 * p.nyz + yz] = f[14].v.y;
-        pl.hout[5 * p.nyz + yz] = g[2].v.y;
+        pl.hout[0 * p.nyz + chk(yz, p.nyz)] = f[2].v.y;
+        pl.hout[1 * p.nyz + chk(yz, p.nyz)] = f[8].v.y;
+        pl.hout[2 * p.nyz + chk(yz, p.nyz)] = f[10].v.y;
+        pl.hout[3 * p.nyz + chk(yz, p.nyz)] = f[12].v.y;
+        pl.hout[4 * p.nyz + chk(yz, p.nyz)] = f[14].v.y;
+        pl.hout[5 * p.nyz + chk(yz, p.nyz)] = g[2].v.y;
     }
     const MediumT<L2> md = medium_pair<HET>(p, sa);
     collide_t<L2, true>(p, md, f, g, 0.0f, 0.0f, 0.0f, [&](const L2* gg, L2 dT) {
 #pragma unroll
         for (int i = 0; i < kQT; ++i) stg2<S>(pl, p, i, sa, gg[i], dT);
-        if constexpr (S::kScaled) *reinterpret_cast<float2*>(pl.tout + sa) = dT.v;
+        if constexpr (S::kScaled) *reinterpret_cast<float2*>(pl.tout + chk(sa + 1, p.ns) - 1) = dT.v;
     });
 #pragma unroll
     for (int i = 0; i < kQ; ++i) stp2<S>(pl, p, i, sa, f[i]);
@@ -2276,6 +2300,20 @@ cudaError_t with_storage(int storage, Fn&& fn) {
 #ifndef LBM_DEVICE_ONLY
 // ---- launch wrappers ---------------------------------------------------------------------------
 int reduction_blocks() { return kRedBlocks; }
+
+cudaError_t bounds_report(long long* first_bad, int* checked) {
+#ifdef LBM_BOUNDS_CHECK
+    *checked = 1;
+    unsigned long long v = 0;
+    const cudaError_t e = cudaMemcpyFromSymbol(&v, g_bounds_bad, sizeof(v));
+    *first_bad = v ? (long long)(v - 1) : -1;
+    return e;
+#else
+    *checked = 0;
+    *first_bad = -1;
+    return cudaSuccess;
+#endif
+}
 
 int aa_swapped_plane(int q) { return q < kQ ? opp19(q) : kQ + opp7(q - kQ); }
 
