@@ -548,10 +548,26 @@ def _latency_summary(results):
                         for s in sorted({r.get("storage") for r in results})}}
 
 
+# Request streams of the serving workload: "wide" spans lattices that fill the GPU alone
+# (up to 192^3 and the 256 x 64 x 64 channel); "small" holds only lattices far too small to
+# fill it (16^3 - 48^3 cavities, channels of section 12^2 - 24^2), the case continuous
+# batching is for.
+SERVE_MIXES = {
+    "wide": {"n": 24, "mix": {"rate": 20.0}, "text": "porous cavities 32^3-192^3, 4WxWxW "
+             "channels (W 32, 64) and, one in ten, melting cavities (enthalpy model); "
+             "Poisson 20/s"},
+    "small": {"n": 96, "mix": {"rate": 400.0, "edges": (16, 24, 32, 40, 48),
+                               "widths": (12, 16, 24)},
+              "text": "porous cavities 16^3-48^3, 4WxWxW channels (W 12, 16, 24) and, one in "
+                      "ten, melting cavities (enthalpy model); Poisson 400/s"},
+}
+
+
 def run_serve(args, gb):
     from lbm_inputs import serving_mix
 
-    reqs = serving_mix(args.requests, seed=5)
+    reqs = serving_mix(args.requests or SERVE_MIXES[args.serve_mix]["n"], seed=5,
+                       **SERVE_MIXES[args.serve_mix]["mix"])
     tol, max_steps, chunk = 1e-6, args.max_steps or 50000, 100
     runs = {}
     runs["fifo"] = _latency_summary(_serve_stream(gb, reqs, 0, chunk, tol, max_steps,
@@ -600,9 +616,8 @@ def run_ours(args):
                 "value": runs[best]["mlups"], "unit": UNIT, "n_gpus": ws, "steps": None,
                 "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32-math, fp32 or fp16 storage per request", "data": "synthetic",
-                "config": {"workload": f"{n} requests, Poisson 20/s (seed 5): porous cavities "
-                                       "32^3-192^3, 4WxWxW channels (W 32, 64) and, one "
-                                       "in ten, melting cavities (enthalpy model)",
+                "config": {"workload": f"{n} requests (seed 5, mix '{args.serve_mix}'): "
+                                       + SERVE_MIXES[args.serve_mix]["text"],
                            "tol": tol, "max_steps": max_steps, "chunk": 100,
                            "admission": "by device footprint (80% of free memory)"
                                         + (f", at most {args.fill} sites admitted" if args.fill else ""),
@@ -778,7 +793,10 @@ def main(argv=None):
     ap.add_argument("--kernel", choices=("auto", "plain", "paired", "tma"), default="auto",
                     help="step kernel: the library's choice (auto), one site per thread, two "
                          "x-adjacent sites per thread, or populations staged by TMA")
-    ap.add_argument("--requests", type=int, default=24, help="serve: number of requests")
+    ap.add_argument("--requests", type=int, default=None,
+                    help="serve: number of requests (default 24 wide, 96 small)")
+    ap.add_argument("--serve-mix", choices=tuple(SERVE_MIXES), default="wide",
+                    help="serve: request stream (lattices up to 192^3, or only small ones)")
     ap.add_argument("--max-steps", type=int, default=None,
                     help="serve / sweep: step limit per solve (default 50000 / 200000)")
     ap.add_argument("--sweep-edge", type=int, default=128, help="sweep: cavity edge")

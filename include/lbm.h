@@ -449,7 +449,9 @@ lbm_status lbm_footprint(const lbm_params* p, int has_phi_field, unsigned long l
 /* ---- serving loop ------------------------------------------------------------------------
  * A server takes solve requests as they arrive, admits them in arrival order while their
  * device footprint fits its memory budget, keeps their populations resident and advances all
- * admitted lattices together with batched launches (lbm_batch_*) in chunks of `chunk` steps.
+ * admitted lattices together in chunks of `chunk` steps: lattices below 512 K sites in one
+ * batched launch per step (lbm_batch_*), larger ones, which fill the GPU on their own, with
+ * their own step kernel (lbm_step), all queued on the server's stream.
  * After every chunk each lattice's steady-state residual (lbm_residual; one synchronisation of
  * the server's stream for all of them) is checked; a request
  * finishes when both residuals fall below its tolerance, when it reaches its step limit, or

@@ -1972,17 +1972,29 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
         if (st != LBM_OK) server_finish(s, s->active.size() - 1, LBM_REQ_FAILED);
     }
     if (!s->active.empty()) {
+        // a lattice of at least kBatchMaxSites sites steps alone (its own step kernel, the
+        // paired one where it applies, as dependent launches); the smaller ones, whose steps
+        // are too short to fill the GPU, advance together in one batched launch per step
+        constexpr long long kBatchMaxSites = 512 * 1024;
+        auto small = [&](const lbm_server::Req* r) {
+            return (long long)r->p.nx * r->p.ny * r->p.nz < kBatchMaxSites;
+        };
         if (s->dirty) {
             lbm_batch_destroy(s->batch);
             s->batch = nullptr;
             std::vector<lbm_ctx*> ctxs;
-            for (auto* r : s->active) ctxs.push_back(r->ctx);
-            lbm_status st = lbm_batch_create(ctxs.data(), (int)ctxs.size(), s->stream, &s->batch);
-            if (st != LBM_OK) return st;
+            for (auto* r : s->active)
+                if (small(r)) ctxs.push_back(r->ctx);
+            if (!ctxs.empty()) {
+                lbm_status st = lbm_batch_create(ctxs.data(), (int)ctxs.size(), s->stream, &s->batch);
+                if (st != LBM_OK) return st;
+            }
             s->dirty = false;
         }
-        lbm_status st = lbm_batch_step(s->batch, s->chunk);
-        if (st != LBM_OK) return st;
+        lbm_status st = LBM_OK;
+        for (auto* r : s->active)
+            if (!small(r) && (st = lbm_step(r->ctx, s->chunk)) != LBM_OK) return st;
+        if (s->batch && (st = lbm_batch_step(s->batch, s->chunk)) != LBM_OK) return st;
         // every residual queued behind the chunk, then one synchronisation for all of them
         std::vector<lbm_status> launched(s->active.size());
         for (size_t k = 0; k < s->active.size(); ++k) launched[k] = residual_launch(s->active[k]->ctx);
