@@ -84,7 +84,9 @@ enum {
  * time step reads and writes (each population once each way):
  *  LBM_STORE_FP32     : FP32 deviations f_i - w_i rho0 and g_i - omega_i sigma T0 (208 B/site;
  *                       D3Q15: 176 B/site);
- *  LBM_STORE_FP16_DEV : FP16 scaled deviations, rounded to nearest: (f_i - w_i rho0) / w_i, and
+ *  LBM_STORE_FP16_DEV : FP16 scaled deviations, rounded to nearest: 64 (f_i - w_i rho0) for the
+ *                       D3Q19 planes (a power of two: the kernels convert without multiplying
+ *                       and collide in these units), and
  *                       for the D3Q7 planes (g_i - omega_i sigma T_x) / omega_i against the
  *                       site's own temperature T_x, whose deviation T_x - T0 is kept in an FP32
  *                       temperature plane (26 x 2 B + 4 B, read and written: 112 B/site);

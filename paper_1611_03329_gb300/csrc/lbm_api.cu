@@ -401,8 +401,13 @@ void fill_kparams(lbm_ctx* c) {
     double U = L.U_out > 0.0 ? L.U_out : 0.0;
     k.out_a = (float)(1.0 / (1.0 + U));
     k.out_b = (float)(U / (1.0 + U));
+    // populations in units of 1 / fu (a power of two: every scaled constant is the FP32 one
+    // times fu exactly)
+    const double fu = p.storage == LBM_STORE_FP32 ? 1.0 : lbm::kFlowUnit;
     k.rho0 = (float)L.rho0;
-    k.inv_rho0 = (float)(1.0 / L.rho0);
+    k.frho0 = (float)(fu * L.rho0);
+    k.inv_fu = (float)(1.0 / fu);
+    k.inv_rho0 = (float)(1.0 / (fu * L.rho0));
     k.sigma = (float)L.sigma;
     k.inv_sigma = (float)(1.0 / L.sigma);
     k.T0 = (float)L.T0;
@@ -427,8 +432,8 @@ void fill_kparams(lbm_ctx* c) {
         k.aeps = a(seps, 252.0);
         k.beps = b(seps, 252.0);
         k.aq = a(sq, 40.0);
-        k.aqc = (float)(sq / 40.0 * c23);
-        k.bqc = (float)((1.0 - 0.5 * sq) / 40.0 * c23);
+        k.aqc = (float)(fu * (sq / 40.0 * c23));
+        k.bqc = (float)(fu * ((1.0 - 0.5 * sq) / 40.0 * c23));
         k.anu36 = a(snu, 36.0);
         k.bnu36 = b(snu, 36.0);
         k.api72 = a(spi, 72.0);
@@ -440,7 +445,7 @@ void fill_kparams(lbm_ctx* c) {
         k.anu4 = a(snu, 4.0);
         k.bnu4 = b(snu, 4.0);
         k.am8 = a(sm, 8.0);
-        k.rho0_10 = (float)(L.rho0 / 10.0);
+        k.rho0_10 = (float)(fu * (L.rho0 / 10.0));
         // D3Q15 (Eq. A1 row norms: e 18, eps 360, q 40, 3p_xx 12, p_ww 4, p_xy.. 8, m_xyz 8)
         const double c73 = 7.0 / 3.0 * L.rho0;  // q_eq = -7/3 rho0 u (Eq. 15)
         k.ae15 = a(se, 18.0);
@@ -973,7 +978,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const double* T_field, const double*
 static double plane_scale(const lbm_ctx* c, int q) {
     if (c->prm.storage == LBM_STORE_FP32) return 1.0;
     const lbm_lattice& L = c->lat;
-    if (q < lbm::kQ) return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);  // D3Q19 only
+    if (q < lbm::kQ) return 1.0 / lbm::kFlowUnit;  // D3Q19 only
     return q == lbm::kQ ? 1.0 - L.varpi : L.varpi / 6.0;
 }
 
@@ -1053,7 +1058,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* g) {
 namespace {
 struct StateHeader {  // 128 bytes at the start of a state blob
     char magic[8];    // "LBMSTATE"
-    int version;      // 1
+    int version;      // 2 (the 16-bit flow planes hold deviations in units of 1 / kFlowUnit)
     int nx, ny, nz;
     int q, storage, scheme;
     long long steps;
@@ -1066,7 +1071,7 @@ StateHeader state_header(const lbm_ctx* c) {
     StateHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "LBMSTATE", 8);
-    h.version = 1;
+    h.version = 2;
     h.nx = c->prm.nx;
     h.ny = c->prm.ny;
     h.nz = c->prm.nz;

@@ -13,6 +13,12 @@ constexpr int kQT = 7;   // D3Q7 temperature populations (Eq. 12, first seven co
 constexpr int kOutSlots = 6;  // populations entering across the x-high face: 5 f + 1 g
 constexpr int kBlock = 256;   // threads per block of the site kernels
 constexpr int kStepMinBlocks = 4;  // resident blocks per SM the step kernel is compiled for
+// The 16-bit formats store each D3Q19 deviation f_i - w_i rho0 multiplied by kFlowUnit (a
+// power of two, so the scaling is exact): the kernels decode and encode those planes by
+// conversion alone and run the flow collision in these units, with the constants that meet
+// the populations (KParams frho0, inv_rho0, rho0_10, aqc, bqc) scaled to match.  FP32
+// storage uses the unit 1.
+constexpr double kFlowUnit = 64.0;
 
 // Everything a site kernel needs, passed by value (__grid_constant__).
 struct KParams {
@@ -38,6 +44,10 @@ struct KParams {
 
     // fluid and lattice
     float rho0, inv_rho0, sigma, inv_sigma, T0, varpi;
+    // the flow populations' unit (kFlowUnit for 16-bit storage, else 1): frho0 = unit * rho0,
+    // inv_fu = 1 / unit; inv_rho0 holds 1 / (unit rho0), and rho0_10, aqc, bqc (below) the
+    // unit as a factor
+    float frho0, inv_fu;
     float s_e, s_eps, s_q, s_nu, s_pi, s_m;        // Lambda (Eq. 22), s_rho = s_j = 1
     float zeta_e, zeta_nu, zeta_alpha;              // Q (Eq. 38), zeta_T = 1
     // collision factors: a = s_k / |M_k|^2, b = (1 - s_k/2) / |M_k|^2 for the rows of Eq. A2

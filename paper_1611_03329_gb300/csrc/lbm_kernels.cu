@@ -119,10 +119,12 @@ static_assert(opp19(7) == 10 && opp19(8) == 9 && opp19(12) == 13 && opp19(16) ==
 static_assert(ex19(opp19(13)) == -ex19(13) && ez19(opp19(13)) == -ez19(13), "opp19 sign");
 
 // ---- population storage ------------------------------------------------------------------
-// FP32 planes hold the deviation f - w_i rho0 (g - omega_i sigma T0) itself; the 16-bit
-// formats hold it divided by the weight, (f - w_i rho0) / w_i and (g - omega_i sigma T0) /
-// omega_i, so that every plane carries values of the order of the Mach number.  Arithmetic is
-// FP32 in every case; 16-bit values are rounded to nearest on store.
+// FP32 planes hold the deviation f - w_i rho0 (g - omega_i sigma T0) itself.  The 16-bit
+// formats hold kFlowUnit (f - w_i rho0) for the D3Q19 planes (a power of two, so the loads
+// and stores are conversions only and the flow collision runs in these units; the factor
+// keeps the smallest deviations out of the FP16 subnormal range) and (g - omega_i sigma T_x) /
+// omega_i for the D3Q7 planes, against the site's own temperature T_x kept in an FP32 plane
+// (ldg_dev).  Arithmetic is FP32 in every case; 16-bit values are rounded to nearest on store.
 // kStrided: plane q is addressed as plane 0 + q * sq (the planes of a copy are contiguous)
 // instead of through its own pointer.  Fewer pointer loads from the parameter block (which go
 // through the address-divergence pipe) for more integer adds; the 16-bit step measured 13 %
@@ -181,17 +183,6 @@ __device__ __forceinline__ int chk(int i, long long n) {
 __device__ __forceinline__ int chk(int i, long long) { return i; }
 #endif
 
-// Weight that multiplies the stored value of plane q (q < 19: f, else g).
-template <class S>
-__device__ __forceinline__ float plane_scale(const KParams& p, int q) {
-    if constexpr (!S::kScaled) return 1.0f;
-    else return q < kQ ? w19(q) : (q == kQ ? p.om0 : p.om1);
-}
-template <class S>
-__device__ __forceinline__ float plane_inv_scale(const KParams& p, int q) {
-    if constexpr (!S::kScaled) return 1.0f;
-    else return q < kQ ? 1.0f / w19(q) : (q == kQ ? p.iom0 : p.iom1);
-}
 // Start of plane q of the planes being read / written.
 template <class S>
 __device__ __forceinline__ const typename S::T* plane_in(const Planes& pl, const KParams& p, int q) {
@@ -222,6 +213,17 @@ __device__ __forceinline__ typename S::T* at_out(const Planes& pl, const KParams
     else
         return plane_out<S>(pl, p, q) + idx;
 }
+// Element idx + d of plane q of the planes being read, addressed from element idx: elements
+// next to each other share one address computation.  The bounds-checked build checks idx + d.
+template <class S>
+__device__ __forceinline__ const typename S::T* at_in_rel(const Planes& pl, const KParams& p, int q,
+                                                          int idx, int d) {
+#ifdef LBM_BOUNDS_CHECK
+    return at_in<S>(pl, p, q, idx + d);
+#else
+    return at_in<S>(pl, p, q, idx) + d;
+#endif
+}
 template <class S>
 __device__ __forceinline__ const typename S::T* at_in_either(const Planes& pl, const KParams& p,
                                                              int I, int J, bool other, int idx) {
@@ -232,17 +234,16 @@ __device__ __forceinline__ const typename S::T* at_in_either(const Planes& pl, c
     else
         return (other ? plane_in<S>(pl, p, J) : plane_in<S>(pl, p, I)) + idx;
 }
-// Deviation of plane q at site index idx of the planes being read / written.
+// Deviation of plane q at site index idx of the planes being read / written, in the flow unit
+// of the format (kFlowUnit for a 16-bit D3Q19 plane): decoding and encoding are conversions
+// only.  D3Q7 planes go through these only in FP32 (16-bit: ldg_dev / stg_dev).
 template <class S>
 __device__ __forceinline__ float ldp(const Planes& pl, const KParams& p, int q, int idx) {
-    const float v = S::ld(at_in<S>(pl, p, q, idx));
-    if constexpr (S::kScaled) return __fmul_rn(v, plane_scale<S>(p, q));
-    else return v;
+    return S::ld(at_in<S>(pl, p, q, idx));
 }
 template <class S>
 __device__ __forceinline__ void stp(const Planes& pl, const KParams& p, int q, int idx, float v) {
-    if constexpr (S::kScaled) S::st(at_out<S>(pl, p, q, idx), __fmul_rn(v, plane_inv_scale<S>(p, q)));
-    else S::st(at_out<S>(pl, p, q, idx), v);
+    S::st(at_out<S>(pl, p, q, idx), v);
 }
 // D3Q7 population i at site idx as the deviation g_i - omega_i sigma T0.  The 16-bit formats
 // store (g_i - omega_i sigma T_x) / omega_i against the site's own temperature T_x, whose
@@ -416,7 +417,7 @@ __device__ __forceinline__ float bounce_moving(const KParams& p, int face, float
     const float eu = __fadd_rn(__fadd_rn((float)L::ex(I) * p.face_u[face][0],
                                          (float)L::ey(I) * p.face_u[face][1]),
                                (float)L::ez(I) * p.face_u[face][2]);
-    return __fmaf_rn(__fmul_rn(6.0f * L::w(I), p.rho0), eu, bb);
+    return __fmaf_rn(__fmul_rn(6.0f * L::w(I), p.frho0), eu, bb);
 }
 // The same for a pull of I that crosses the velocity faces vm (non-zero): the lowest-numbered
 // one applies.  The candidate faces are those along I's non-zero components, known at compile
@@ -444,7 +445,7 @@ __device__ __forceinline__ float bounce_moving_on(const KParams& p, unsigned vm,
         if (!found) { u0 = p.face_u[fz][0]; u1 = p.face_u[fz][1]; u2 = p.face_u[fz][2]; }
     }
     const float eu = __fadd_rn(__fadd_rn((float)ex * u0, (float)ey * u1), (float)ez * u2);
-    return __fmaf_rn(__fmul_rn(6.0f * L::w(I), p.rho0), eu, bb);
+    return __fmaf_rn(__fmul_rn(6.0f * L::w(I), p.frho0), eu, bb);
 }
 // Face a D3Q7 velocity crosses (each has one non-zero component): x-low, x-high, y-low, ...
 constexpr int face7(int i) {
@@ -675,9 +676,7 @@ __device__ __forceinline__ void gather_interior(const Planes& pl, const KParams&
 template <class S>
 __device__ __forceinline__ float ldp_either(const Planes& pl, const KParams& p, int I, int J,
                                             bool other, int idx) {
-    const float v = S::ld(at_in_either<S>(pl, p, I, J, other, idx));
-    if constexpr (S::kScaled) return __fmul_rn(v, plane_scale<S>(p, I));
-    else return v;
+    return S::ld(at_in_either<S>(pl, p, I, J, other, idx));
 }
 template <class S>
 __device__ __forceinline__ float ldg_either(const Planes& pl, const KParams& p, int I, int J,
@@ -917,7 +916,7 @@ __device__ __forceinline__ MacroT<V> collide_t(const KParams& p, const MediumT<V
     }
 
     MacroT<V> mac;
-    mac.rho = K<V>(p.rho0) + rho;
+    mac.rho = K<V>(p.rho0) + rho * K<V>(p.inv_fu);
     mac.ux = ux;
     mac.uy = uy;
     mac.uz = uz;
@@ -960,7 +959,7 @@ __device__ __forceinline__ MacroT<V> collide_t(const KParams& p, const MediumT<V
 
     // equilibria (Eq. 21, beta1 = 3, beta2 = -11/2, beta3 = -1/2) and forcing (Eq. 23), with
     // the velocity scaled by rho0 / phi once: w = rho0 u / phi
-    const V r0p = K<V>(p.rho0) * md.inv_phi;
+    const V r0p = K<V>(p.frho0) * md.inv_phi;
     const V wx = r0p * ux, wy = r0p * uy, wz = r0p * uz;
     const V pxx = wx * ux, pyy = wy * uy, pzz = wz * uz;  // rho0 u_a^2 / phi
     const V fxx = wx * Fx, fyy = wy * Fy, fzz = wz * Fz;  // rho0 u_a F_a / phi
@@ -980,9 +979,9 @@ __device__ __forceinline__ MacroT<V> collide_t(const KParams& p, const MediumT<V
                        K<V>(__fmul_rn(-11.0f, p.beps)) * uF);
     V djx = K<V>(p.rho0_10) * Fx, djy = K<V>(p.rho0_10) * Fy, djz = K<V>(p.rho0_10) * Fz;
     if constexpr (PU) {
-        djx = K<V>(0.1f) * fma(K<V>(p.rho0), fma(K<V>(0.5f), Fx, ux), -jx);
-        djy = K<V>(0.1f) * fma(K<V>(p.rho0), fma(K<V>(0.5f), Fy, uy), -jy);
-        djz = K<V>(0.1f) * fma(K<V>(p.rho0), fma(K<V>(0.5f), Fz, uz), -jz);
+        djx = K<V>(0.1f) * fma(K<V>(p.frho0), fma(K<V>(0.5f), Fx, ux), -jx);
+        djy = K<V>(0.1f) * fma(K<V>(p.frho0), fma(K<V>(0.5f), Fy, uy), -jy);
+        djz = K<V>(0.1f) * fma(K<V>(p.frho0), fma(K<V>(0.5f), Fz, uz), -jz);
     }
     const V dqx = fma(K<V>(-p.aq), qx, -fma(K<V>(p.aqc), ux, K<V>(p.bqc) * Fx));
     const V dqy = fma(K<V>(-p.aq), qy, -fma(K<V>(p.aqc), uy, K<V>(p.bqc) * Fy));
@@ -1403,6 +1402,17 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
 // previous kernel of the stream drains.  Each thread first waits until that kernel has
 // completed and its writes are visible (a no-op for an ordinary launch), then allows the next
 // step's grid to be scheduled in turn.
+// Row block and slab of a step-kernel block.  Blocks start roughly in launch order, and the
+// blocks that hold a face of the lattice (the slabs z = 0 and z = nz - 1, the first and last
+// row block of each slab) gather the slowest.  The last slab and the last row block of each
+// slab are launched first, so that a step ends on interior blocks and its drain is short.  The
+// map is a rotation of the block indices: every block of the grid still runs once.
+__device__ __forceinline__ int step_row_block() {
+    return blockIdx.y == 0 ? (int)gridDim.y - 1 : (int)blockIdx.y - 1;
+}
+__device__ __forceinline__ int step_slab() {
+    return blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1;
+}
 __device__ __forceinline__ void dependent_launch_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -1418,8 +1428,8 @@ __global__ void __maxnreg__(HET ? 72 : 64)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int y = step_row_block() * blockDim.y + threadIdx.y;
+    const int z = step_slab();
     const bool valid = x < p.nx && y < p.ny;
     const unsigned nb = (NEE && valid) ? nee_bits(p, x, y, z) : 0u;  // node-wall site
     const bool streams = valid && nb == 0u;
@@ -1471,9 +1481,7 @@ __device__ __forceinline__ void st2_raw(typename S::T* a, float2 v) {
 template <class S>
 __device__ __forceinline__ L2 ldp2(const Planes& pl, const KParams& p, int q, int idx) {
     idx = chk(idx + 1, p.ns) - 1;  // both elements of the pair in range
-    const L2 v{ld2_raw<S>(at_in<S>(pl, p, q, idx))};
-    if constexpr (S::kScaled) return v * K<L2>(plane_scale<S>(p, q));
-    else return v;
+    return L2{ld2_raw<S>(at_in<S>(pl, p, q, idx))};
 }
 // D3Q7 population i at the aligned pair idx, idx + 1, as ldg_dev reads each.
 template <class S>
@@ -1490,7 +1498,6 @@ __device__ __forceinline__ L2 ldg2(const Planes& pl, const KParams& p, int i, in
 template <class S>
 __device__ __forceinline__ void stp2(const Planes& pl, const KParams& p, int q, int idx, L2 v) {
     idx = chk(idx + 1, p.ns) - 1;
-    if constexpr (S::kScaled) v = v * K<L2>(plane_inv_scale<S>(p, q));
     st2_raw<S>(at_out<S>(pl, p, q, idx), v.v);
 }
 template <class S>
@@ -1505,32 +1512,65 @@ __device__ __forceinline__ void stg2(const Planes& pl, const KParams& p, int i, 
 }
 __device__ __forceinline__ L2 pair(float a, float b) { return {make_float2(a, b)}; }
 
-// Pull of the pair when no pull of either site crosses a non-periodic face.
+// Plane q's values at elements idx + d and idx + d + 1, as ldp reads each, both addressed from
+// element idx.
+template <class S>
+__device__ __forceinline__ L2 ldp2_rel(const Planes& pl, const KParams& p, int q, int idx, int d) {
+    return pair(S::ld(at_in_rel<S>(pl, p, q, idx, d)), S::ld(at_in_rel<S>(pl, p, q, idx, d + 1)));
+}
+// D3Q7 population i of a 16-bit format from its stored pair st and the temperature deviations
+// T of its two source sites, as ldg_dev decodes each.
+template <class S>
+__device__ __forceinline__ L2 g_decode(const KParams& p, int i, L2 st, L2 T) {
+    return K<L2>(i == 0 ? p.om0 : p.om1) * fma(K<L2>(p.sigma), T, st);
+}
+
+// Pull of the pair when no pull of either site crosses a face and no x pull wraps (x_a > 0,
+// x_a + 2 < nx; warp_pair_mode sends the other pairs to gather_pair_x): the two sources of a
+// plane with e_x = +-1 are the elements next to the pair's own and share its address; the
+// thermal pulls of a 16-bit format take their source temperatures from the pair's own
+// temperature row and the elements beside it.
 template <class S>
 __device__ __forceinline__ void gather_pair_interior(const Planes& pl, const KParams& p, int xa,
                                                      int y, int z, int sa, L2* f, L2* g) {
     const AxisOff o = axis_offsets(p, xa, y, z);  // site a; site b differs only along +x
-    const int xpb = (xa + 1 == p.nx - 1) ? 1 - p.nx : 1;  // periodic wrap of site b's +x source
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-        const int oyz = axis_off(D3Q19::ey(i), o.ym, o.yp) + axis_off(D3Q19::ez(i), o.zm, o.zp);
-        if (D3Q19::ex(i) == 0) {
-            f[i] = ldp2<S>(pl, p, i, sa + oyz);
-        } else if (D3Q19::ex(i) == 1) {  // sources x - 1: sa + xm (a), sa (b)
-            f[i] = pair(ldp<S>(pl, p, i, sa + o.xm + oyz), ldp<S>(pl, p, i, sa + oyz));
-        } else {  // sources x + 1: sa + 1 (a), sa + 1 + xpb (b)
-            f[i] = pair(ldp<S>(pl, p, i, sa + 1 + oyz), ldp<S>(pl, p, i, sa + 1 + xpb + oyz));
-        }
+        const int row = sa + axis_off(D3Q19::ey(i), o.ym, o.yp) + axis_off(D3Q19::ez(i), o.zm, o.zp);
+        if (D3Q19::ex(i) == 0) f[i] = ldp2<S>(pl, p, i, row);
+        else if (D3Q19::ex(i) == 1) f[i] = ldp2_rel<S>(pl, p, i, row, -1);  // sources x - 1
+        else f[i] = ldp2_rel<S>(pl, p, i, row, 1);                          // sources x + 1
     }
+    if constexpr (!S::kScaled) {
 #pragma unroll
-    for (int i = 0; i < kQT; ++i) {
-        const int oyz = axis_off(ey7(i), o.ym, o.yp) + axis_off(ez7(i), o.zm, o.zp);
-        if (ex7(i) == 0) {
-            g[i] = ldg2<S>(pl, p, i, sa + oyz);
-        } else if (ex7(i) == 1) {
-            g[i] = pair(ldg_dev<S>(pl, p, i, sa + o.xm + oyz), ldg_dev<S>(pl, p, i, sa + oyz));
-        } else {
-            g[i] = pair(ldg_dev<S>(pl, p, i, sa + 1 + oyz), ldg_dev<S>(pl, p, i, sa + 1 + xpb + oyz));
+        for (int i = 0; i < kQT; ++i) {
+            const int row = sa + axis_off(ey7(i), o.ym, o.yp) + axis_off(ez7(i), o.zm, o.zp);
+            if (ex7(i) == 0) g[i] = ldp2<S>(pl, p, kQ + i, row);
+            else g[i] = ldp2_rel<S>(pl, p, kQ + i, row, ex7(i) == 1 ? -1 : 1);
+        }
+    } else {
+        // temperatures: the pair's own (x_a, x_a + 1) and the sites beside it (x_a - 1, x_a + 2)
+        const float* tr = pl.tin + chk(sa, p.ns - 1);
+        const L2 Ts{__ldg(reinterpret_cast<const float2*>(tr))};
+#ifdef LBM_BOUNDS_CHECK
+        const float Tm = __ldg(pl.tin + chk(sa - 1, p.ns)), Tp = __ldg(pl.tin + chk(sa + 2, p.ns));
+#else
+        const float Tm = __ldg(tr - 1), Tp = __ldg(tr + 2);
+#endif
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) {
+            const int row = sa + axis_off(ey7(i), o.ym, o.yp) + axis_off(ez7(i), o.zm, o.zp);
+            if (ex7(i) == 0) {
+                const L2 st{ld2_raw<S>(at_in<S>(pl, p, kQ + i, chk(row + 1, p.ns) - 1))};
+                const L2 T = i == 0 ? Ts
+                                    : L2{__ldg(reinterpret_cast<const float2*>(pl.tin + chk(row, p.ns - 1)))};
+                g[i] = g_decode<S>(p, i, st, T);
+            } else {
+                const int d = ex7(i) == 1 ? -1 : 1;
+                const L2 st = pair(S::ld(at_in_rel<S>(pl, p, kQ + i, row, d)),
+                                   S::ld(at_in_rel<S>(pl, p, kQ + i, row, d + 1)));
+                g[i] = g_decode<S>(p, i, st, ex7(i) == 1 ? pair(Tm, Ts.v.x) : pair(Ts.v.y, Tp));
+            }
         }
     }
 }
@@ -1634,9 +1674,11 @@ __device__ __forceinline__ void gather_pair_x(const Planes& pl, const KParams& p
     }
 }
 
-// The gather mode of a warp of pairs (warp_gather_mode over both sites of every lane).
+// The gather mode of a warp of pairs: interior when no pull of any lane crosses a face and no
+// x pull wraps (x_a > 0, x_a + 2 < nx); x-select when every lane's y/z pulls need no rule
+// (this includes the pairs at the ends of a periodic x axis); else the general select.
 __device__ __forceinline__ int warp_pair_mode(const KParams& p, int xa, int y, int z, bool active) {
-    const bool quiet = site_no_cross(p, xa, y, z) && site_no_cross(p, xa + 1, y, z);
+    const bool quiet = yz_fast(p, y, z) && xa > 0 && xa + 2 < p.nx;
     if (__all_sync(0xffffffffu, !active || quiet)) return kGatherInterior;
     if (__all_sync(0xffffffffu, !active || yz_fast(p, y, z))) return kGatherX;
     return kGatherAny;
@@ -1651,8 +1693,8 @@ __global__ void __maxnreg__(HET ? (S::kScaled ? 112 : 128) : (S::kScaled ? 96 : 
     step_pair_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int xa = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int y = step_row_block() * blockDim.y + threadIdx.y;
+    const int z = step_slab();
     const bool valid = xa < p.nx && y < p.ny;  // nx even: x + 1 < nx as well
     const int mode = warp_pair_mode(p, xa, y, z, valid);
     if (!valid) return;
@@ -1816,8 +1858,8 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     aa_pull_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int y = step_row_block() * blockDim.y + threadIdx.y;
+    const int z = step_slab();
     const bool valid = x < p.nx && y < p.ny;
     const int mode = warp_gather_mode(p, x, y, z, valid);
     if (valid) aa_pull_site<HET>(p, pl, x, y, z, mode);
@@ -1830,8 +1872,8 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
                     const __grid_constant__ Planes pw) {
     dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+    const int y = step_row_block() * blockDim.y + threadIdx.y;
+    const int z = step_slab();
     if (x < p.nx && y < p.ny) aa_local_site<HET>(p, pl, pw, x, y, z);
 }
 
@@ -2010,7 +2052,7 @@ __global__ void init_eq_kernel(const __grid_constant__ KParams p, const __grid_c
         double eu = L::ex(i) * ux + L::ey(i) * uy + L::ez(i) * uz;
         double w = L::wd(i);
         double rel = rho0 * (3.0 * eu + 4.5 * eu * eu / phi - 1.5 * usq / phi);  // dev / w
-        S::st(static_cast<typename S::T*>(pl.out[i]) + s, (float)(S::kScaled ? rel : w * rel));
+        S::st(static_cast<typename S::T*>(pl.out[i]) + s, (float)(S::kScaled ? kFlowUnit * w * rel : w * rel));
     }
     double varpi = p.varpi, sigma = p.sigma, T0 = p.T0, csT2 = varpi / 3.0;
     if (p.enthalpy) {
@@ -2144,7 +2186,7 @@ __global__ void __launch_bounds__(kRedThreads)
     double v[2] = {0.0, 0.0};
     for (int s = blockIdx.x * kRedThreads + threadIdx.x; s < p.ns; s += gridDim.x * kRedThreads) {
 #pragma unroll
-        for (int i = 0; i < L::kQ; ++i) v[0] += (double)ldp<S>(pl, p, i, s);
+        for (int i = 0; i < L::kQ; ++i) v[0] += (double)ldp<S>(pl, p, i, s) * (double)p.inv_fu;
 #pragma unroll
         for (int i = 0; i < kQT; ++i) v[1] += (double)ldg_dev<S>(pl, p, i, s);
     }

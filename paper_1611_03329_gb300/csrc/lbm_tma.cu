@@ -164,8 +164,7 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             const T* src = reinterpret_cast<const T*>(stage + i * C::kPlane);
-            f[i] = to_f32(src[r * (ex19(i) ? 72 : 64) + tx + box_col(ex19(i))]) *
-                   plane_scale<S>(p, i);
+            f[i] = to_f32(src[r * (ex19(i) ? 72 : 64) + tx + box_col(ex19(i))]);
         }
 #pragma unroll
         for (int j = 0; j < kQT; ++j) {
@@ -176,7 +175,7 @@ __device__ __forceinline__ void tma_site(const KParams& p, const Planes& pl,
                     stage + (kQ + kQT) * C::kPlane + j * C::kTSlot);
                 g[j] = __fmul_rn(j == 0 ? p.om0 : p.om1, __fmaf_rn(p.sigma, tsrc[at], v));
             } else {
-                g[j] = v * plane_scale<S>(p, kQ + j);
+                g[j] = v;
             }
         }
         const int nxy = p.nx * p.ny;
