@@ -1404,14 +1404,20 @@ __device__ __forceinline__ void finish_site(const Planes& pl, const KParams& p, 
 // step's grid to be scheduled in turn.
 // Row block and slab of a step-kernel block.  Blocks start roughly in launch order, and the
 // blocks that hold a face of the lattice (the slabs z = 0 and z = nz - 1, the first and last
-// row block of each slab) gather the slowest.  The last slab and the last row block of each
-// slab are launched first, so that a step ends on interior blocks and its drain is short.  The
-// map is a rotation of the block indices: every block of the grid still runs once.
+// row block of each slab) gather the slowest.  With ROT the last slab and the last row block
+// of each slab are launched first, so that a step ends on interior blocks and its drain is
+// shorter; the map is a rotation of the block indices, every block still runs once.  Measured
+// on the 256 x 64 x 64 channel: FP32 +0.9 %, FP16 -1.6 % (its state partly stays in L2, which
+// the launch order also decides), so the 16-bit formats keep the plain order.
+template <bool ROT>
 __device__ __forceinline__ int step_row_block() {
-    return blockIdx.y == 0 ? (int)gridDim.y - 1 : (int)blockIdx.y - 1;
+    if constexpr (ROT) return blockIdx.y == 0 ? (int)gridDim.y - 1 : (int)blockIdx.y - 1;
+    else return (int)blockIdx.y;
 }
+template <bool ROT>
 __device__ __forceinline__ int step_slab() {
-    return blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1;
+    if constexpr (ROT) return blockIdx.z == 0 ? (int)gridDim.z - 1 : (int)blockIdx.z - 1;
+    else return (int)blockIdx.z;
 }
 __device__ __forceinline__ void dependent_launch_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -1428,8 +1434,8 @@ __global__ void __maxnreg__(HET ? 72 : 64)
     step_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = step_row_block() * blockDim.y + threadIdx.y;
-    const int z = step_slab();
+    const int y = step_row_block<!S::kScaled>() * blockDim.y + threadIdx.y;
+    const int z = step_slab<!S::kScaled>();
     const bool valid = x < p.nx && y < p.ny;
     const unsigned nb = (NEE && valid) ? nee_bits(p, x, y, z) : 0u;  // node-wall site
     const bool streams = valid && nb == 0u;
@@ -1693,8 +1699,8 @@ __global__ void __maxnreg__(HET ? (S::kScaled ? 112 : 128) : (S::kScaled ? 96 : 
     step_pair_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int xa = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = step_row_block() * blockDim.y + threadIdx.y;
-    const int z = step_slab();
+    const int y = step_row_block<!S::kScaled>() * blockDim.y + threadIdx.y;
+    const int z = step_slab<!S::kScaled>();
     const bool valid = xa < p.nx && y < p.ny;  // nx even: x + 1 < nx as well
     const int mode = warp_pair_mode(p, xa, y, z, valid);
     if (!valid) return;
@@ -1858,8 +1864,8 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
     aa_pull_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
     dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = step_row_block() * blockDim.y + threadIdx.y;
-    const int z = step_slab();
+    const int y = step_row_block<true>() * blockDim.y + threadIdx.y;
+    const int z = step_slab<true>();
     const bool valid = x < p.nx && y < p.ny;
     const int mode = warp_gather_mode(p, x, y, z, valid);
     if (valid) aa_pull_site<HET>(p, pl, x, y, z, mode);
@@ -1872,8 +1878,8 @@ __global__ void __launch_bounds__(kBlock, HET ? kStepMinBlocks - 1 : kStepMinBlo
                     const __grid_constant__ Planes pw) {
     dependent_launch_prologue();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = step_row_block() * blockDim.y + threadIdx.y;
-    const int z = step_slab();
+    const int y = step_row_block<true>() * blockDim.y + threadIdx.y;
+    const int z = step_slab<true>();
     if (x < p.nx && y < p.ny) aa_local_site<HET>(p, pl, pw, x, y, z);
 }
 
