@@ -386,9 +386,8 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
  * on the thread by an earlier call is neither reported nor cleared.
  * It allocates nothing: its partial sums live in a static 320 KiB device array that every
  * GPU loading the library holds until exit.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array: calls whose kernels overlap on the GPU race and must
- * be serialised.  Errors: LBM_EINVAL (NULL pointer or ns out of range), LBM_ECUDA. */
+ * array's device address (cudaGetSymbolAddress).  All calls share the array: calls whose
+ * kernels overlap on the GPU race and must be serialised.  Errors: LBM_EINVAL (NULL pointer or ns out of range), LBM_ECUDA. */
 lbm_status lbm_residual_noalloc(const float* u, const float* T, const float* u_prev,
                                 const float* T_prev, long long ns, double* out, void* stream);
 
