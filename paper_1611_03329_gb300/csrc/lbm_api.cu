@@ -691,7 +691,7 @@ lbm_status residual_launch(lbm_ctx* c) {
         pu = cu;
         pT = cT;
     }
-    int nr = lbm::reduction_blocks();
+    const int nr = lbm::residual_blocks(c->ns);
     LBM_CUDA(lbm::launch_residual(cu, cT, pu, pT, c->ns, c->partials, nr, c->dres, c->stream));
     LBM_CUDA(cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * 5, cudaMemcpyDeviceToHost,
                              c->stream));

@@ -172,6 +172,9 @@ cudaError_t launch_step_tma(const KParams& p, bool outflow, const Planes& pl, co
                             int blocks, int extra_tx, int* err, bool pdl, cudaStream_t st);
 
 int reduction_blocks();
+// Blocks of the residual reduction over ns sites: reduction_blocks(), or fewer for a small
+// lattice (at least 2,048 sites per block), so that its launch takes a few blocks, not 608.
+int residual_blocks(long long ns);
 // The bounds-checked build's record (-DLBM_BOUNDS_CHECK): *checked = 1 and *first_bad = the
 // first out-of-range site index a kernel of lbm_kernels.cu met (-1: none); *checked = 0 in the
 // ordinary build.

@@ -2348,6 +2348,10 @@ cudaError_t with_storage(int storage, Fn&& fn) {
 #ifndef LBM_DEVICE_ONLY
 // ---- launch wrappers ---------------------------------------------------------------------------
 int reduction_blocks() { return kRedBlocks; }
+int residual_blocks(long long ns) {
+    const long long b = (ns + 2047) / 2048;
+    return b < 1 ? 1 : (b > kRedBlocks ? kRedBlocks : (int)b);
+}
 
 cudaError_t bounds_report(long long* first_bad, int* checked) {
 #ifdef LBM_BOUNDS_CHECK
