@@ -452,7 +452,10 @@ lbm_status lbm_footprint(const lbm_params* p, int has_phi_field, unsigned long l
  * device footprint fits its memory budget, keeps their populations resident and advances all
  * admitted lattices together in chunks of `chunk` steps: lattices below 512 K sites in one
  * batched launch per step (lbm_batch_*), larger ones, which fill the GPU on their own, with
- * their own step kernel (lbm_step), all queued on the server's stream.
+ * their own step kernel (lbm_step), all queued on the server's stream.  The block shape of the
+ * batched step is tuned (as stage (1) of lbm_batch_tune, leaving the state unchanged) on the
+ * first batch of at least 8 lattices and again whenever a batch has twice the lattices of the
+ * one last tuned; other batches reuse the last shape.
  * After every chunk each lattice's steady-state residual (lbm_residual; one synchronisation of
  * the server's stream for all of them) is checked; a request
  * finishes when both residuals fall below its tolerance, when it reaches its step limit, or

@@ -1645,9 +1645,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     return batch_join(b, false);
 }
 
-lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows) {
-    NvtxRange range_("lbm_batch_tune");
-    if (!b) return LBM_EINVAL;
+// Stage (1) of lbm_batch_tune: the block shape, timed without changing the lattices' state.
+static lbm_status batch_tune_shape(lbm_batch* b, int* block_threads, int* rows) {
     bool timed = false;  // only ping-pong groups can be timed without changing the state
     for (auto& g : b->groups) timed = timed || !g.aa;
     if (!timed) {
@@ -1699,6 +1698,17 @@ lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows) {
     if (block_threads) *block_threads = best;
     if (rows) *rows = best_rows;
     if (st != LBM_OK) return st;
+    return batch_join(b, false);
+}
+
+lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows) {
+    NvtxRange range_("lbm_batch_tune");
+    if (!b) return LBM_EINVAL;
+    lbm_status st = batch_tune_shape(b, block_threads, rows);
+    if (st != LBM_OK) return st;
+    bool timed = false;  // a batch of AA lattices only: no scheme to choose
+    for (auto& g : b->groups) timed = timed || !g.aa;
+    if (!timed) return LBM_OK;
     // streaming scheme: a ping-pong group whose lattices could run the AA scheme is timed both
     // ways at the chosen shape; it moves to AA only when that is faster by more than 3 %
     if ((st = batch_upload(b)) != LBM_OK) return st;
@@ -1820,6 +1830,10 @@ struct lbm_server {
     std::vector<Req*> active;
     std::vector<lbm_result> done;
     lbm_batch* batch = nullptr;
+    // block shape of the batched step (0: not tuned yet) and the lattice count of the batch it
+    // was tuned on
+    int batch_threads = 0, batch_rows = 0;
+    size_t tuned_lattices = 0;
     bool dirty = true;
     long long next_id = 1;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
@@ -1992,6 +2006,18 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
                 if (small(r)) ctxs.push_back(r->ctx);
             if (!ctxs.empty()) {
                 lbm_status st = lbm_batch_create(ctxs.data(), (int)ctxs.size(), s->stream, &s->batch);
+                if (st != LBM_OK) return st;
+                // the block shape: tuned on a batch of at least kTuneMinLattices lattices and
+                // again whenever the batch has grown to twice the size it was tuned on (the
+                // timed launches leave the state unchanged, the streaming scheme is not
+                // changed); every other batch reuses the last shape
+                constexpr size_t kTuneMinLattices = 8;
+                if (ctxs.size() >= kTuneMinLattices && ctxs.size() >= 2 * s->tuned_lattices) {
+                    st = batch_tune_shape(s->batch, &s->batch_threads, &s->batch_rows);
+                    s->tuned_lattices = ctxs.size();
+                } else if (s->batch_threads > 0) {
+                    st = lbm_batch_set_block(s->batch, s->batch_threads, s->batch_rows);
+                }
                 if (st != LBM_OK) return st;
             }
             s->dirty = false;
