@@ -507,8 +507,12 @@ lbm_status lbm_server_create(unsigned long long budget_bytes, int chunk, void* s
                              lbm_server** out);
 
 /* Queue a request: problem p, medium m (NULL: lbm_set_medium defaults), residual tolerance
- * tol > 0 and step limit max_steps >= 1.  Returns its id.  LBM_EINVAL for an invalid
- * problem or one larger than the whole budget. */
+ * tol > 0 and step limit max_steps >= 1.  Returns its id.  Every lattice lbm_create takes is
+ * served: D3Q15 and node-wall lattices step alone, the others batch; p->scheme ==
+ * LBM_SCHEME_AA is kept (one population copy, counted as such against the budget), AUTO is
+ * served with two copies.  LBM_EINVAL for an invalid problem, an AA request the scheme does
+ * not take (after the storage rule of the serving loop), or one larger than the whole
+ * budget. */
 lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_medium* m,
                              double tol, long long max_steps, long long* id);
 

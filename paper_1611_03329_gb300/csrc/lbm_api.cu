@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -1805,6 +1806,7 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 struct lbm_server {
     struct Req {
         long long id = 0;
+        bool batchable = true;  // may join the batched launch (D3Q19, halfway walls)
         lbm_params p{};
         double phi = 1.0, K = 0.0, F_phi = 0.0, alpha_m = -1.0, phi_ref = 0.0;
         std::vector<float> phi_field;
@@ -1834,12 +1836,56 @@ struct lbm_server {
     // was tuned on
     int batch_threads = 0, batch_rows = 0;
     size_t tuned_lattices = 0;
+    // batched residual of the batched lattices: their table, block map and totals, pinned on
+    // the host and on the device, grown as needed
+    lbm::ResLattice* h_tab = nullptr;
+    lbm::ResLattice* d_tab = nullptr;
+    int2* h_blk = nullptr;
+    int2* d_blk = nullptr;
+    double* h_out = nullptr;
+    double* d_out = nullptr;
+    size_t tab_cap = 0, blk_cap = 0;
     bool dirty = true;
     long long next_id = 1;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 };
 
 namespace {
+
+// Room for n lattices and nblk blocks in the batched-residual buffers.
+lbm_status server_reserve(lbm_server* s, size_t n, size_t nblk) {
+    if (n > s->tab_cap) {
+        const size_t cap = n > 2 * s->tab_cap ? n : 2 * s->tab_cap;
+        cudaFreeHost(s->h_tab);
+        cudaFree(s->d_tab);
+        cudaFreeHost(s->h_out);
+        cudaFree(s->d_out);
+        s->h_tab = nullptr;
+        s->d_tab = nullptr;
+        s->h_out = nullptr;
+        s->d_out = nullptr;
+        s->tab_cap = 0;
+        if (cudaHostAlloc(&s->h_tab, cap * sizeof(lbm::ResLattice), cudaHostAllocDefault) != cudaSuccess ||
+            cudaMalloc(&s->d_tab, cap * sizeof(lbm::ResLattice)) != cudaSuccess ||
+            cudaHostAlloc(&s->h_out, cap * 5 * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
+            cudaMalloc(&s->d_out, cap * 5 * sizeof(double)) != cudaSuccess)
+            return LBM_ENOMEM;
+        s->tab_cap = cap;
+    }
+    if (nblk > s->blk_cap) {
+        const size_t cap = nblk > 2 * s->blk_cap ? nblk : 2 * s->blk_cap;
+        cudaFreeHost(s->h_blk);
+        cudaFree(s->d_blk);
+        s->h_blk = nullptr;
+        s->d_blk = nullptr;
+        s->blk_cap = 0;
+        if (cudaHostAlloc(&s->h_blk, cap * sizeof(int2), cudaHostAllocDefault) != cudaSuccess ||
+            cudaMalloc(&s->d_blk, cap * sizeof(int2)) != cudaSuccess)
+            return LBM_ENOMEM;
+        s->blk_cap = cap;
+    }
+    return LBM_OK;
+}
 
 void server_finish(lbm_server* s, size_t k, int status) {
     lbm_server::Req* r = s->active[k];
@@ -1918,18 +1964,22 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
     if (!s || !p || !(tol > 0.0) || max_steps < 1) return LBM_EINVAL;
     lbm_lattice L;
     if (derive(p, &L)) return LBM_EINVAL;
-    if (L.q == 15 || L.node_walls) return LBM_EINVAL;  // the serving loop batches D3Q19 lattices
-                                                       // with halfway walls
-    if (p->scheme == LBM_SCHEME_AA) return LBM_EINVAL;  // and ping-pong copies
     auto* r = new (std::nothrow) lbm_server::Req();
     if (!r) return LBM_ENOMEM;
     r->p = *p;
-    r->p.scheme = LBM_SCHEME_PINGPONG;
+    // the AA scheme when asked for; LBM_SCHEME_AUTO is served with two copies
+    if (p->scheme != LBM_SCHEME_AA) r->p.scheme = LBM_SCHEME_PINGPONG;
     // a 16-bit format cannot bring the residual below its floor: such a request is stored in
     // FP32, so that it converges at the accuracy it asked for
     if ((p->storage == LBM_STORE_FP16_DEV && tol < LBM_RESIDUAL_FLOOR_FP16) ||
         (p->storage == LBM_STORE_BF16_DEV && tol < LBM_RESIDUAL_FLOOR_BF16))
         r->p.storage = LBM_STORE_FP32;
+    if (r->p.scheme == LBM_SCHEME_AA && !aa_eligible(&r->p, L)) {
+        delete r;
+        return LBM_EINVAL;
+    }
+    // D3Q15 and node-wall lattices do not batch: they step alone (lbm_step)
+    r->batchable = L.q == 19 && !L.node_walls;
     if (m) {
         r->phi = m->phi;
         r->K = m->K;
@@ -1992,11 +2042,12 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
     }
     if (!s->active.empty()) {
         // a lattice of at least kBatchMaxSites sites steps alone (its own step kernel, the
-        // paired one where it applies, as dependent launches); the smaller ones, whose steps
-        // are too short to fill the GPU, advance together in one batched launch per step
+        // paired one where it applies, as dependent launches), and so does one the batched
+        // launch does not take (D3Q15, node walls); the other, smaller ones, whose steps are
+        // too short to fill the GPU, advance together in one batched launch per step
         constexpr long long kBatchMaxSites = 512 * 1024;
         auto small = [&](const lbm_server::Req* r) {
-            return (long long)r->p.nx * r->p.ny * r->p.nz < kBatchMaxSites;
+            return r->batchable && (long long)r->p.nx * r->p.ny * r->p.nz < kBatchMaxSites;
         };
         if (s->dirty) {
             lbm_batch_destroy(s->batch);
@@ -2026,13 +2077,88 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
         for (auto* r : s->active)
             if (!small(r) && (st = lbm_step(r->ctx, s->chunk)) != LBM_OK) return st;
         if (s->batch && (st = lbm_batch_step(s->batch, s->chunk)) != LBM_OK) return st;
-        // every residual queued behind the chunk, then one synchronisation for all of them
-        std::vector<lbm_status> launched(s->active.size());
-        for (size_t k = 0; k < s->active.size(); ++k) launched[k] = residual_launch(s->active[k]->ctx);
+        // every residual queued behind the chunk, then one synchronisation for all of them:
+        // the batched lattices' residuals in one launch per kernel variant (the sums of
+        // lbm_residual, bit for bit), the others one lattice at a time
+        const size_t na = s->active.size();
+        std::vector<lbm_status> launched(na, LBM_OK);
+        std::vector<int> slot(na, -1);  // entry in the batched residual's table
+        {
+            std::vector<std::pair<int, size_t>> items;  // (kernel variant, active index)
+            for (size_t k = 0; k < na; ++k) {
+                lbm_ctx* c = s->active[k]->ctx;
+                if (!small(s->active[k])) continue;
+                lbm_status sk = usable(c);
+                if (sk == LBM_OK) sk = aa_settle(c);
+                if (sk == LBM_OK) sk = ensure_mac(c);
+                if (sk != LBM_OK) {
+                    launched[k] = sk;
+                    continue;
+                }
+                const int variant = (c->kp.phi_field ? 1 : 0) | (c->outflow ? 2 : 0) |
+                                    (c->lat.enthalpy ? 4 : 0) | (c->prm.storage << 3);
+                items.emplace_back(variant, k);
+            }
+            std::stable_sort(items.begin(), items.end(),
+                             [](const std::pair<int, size_t>& a, const std::pair<int, size_t>& b) {
+                                 return a.first < b.first;
+                             });
+            size_t nblk = 0;
+            for (auto& it : items) nblk += (size_t)lbm::residual_blocks(s->active[it.second]->ctx->ns);
+            if (!items.empty()) {
+                if ((st = server_reserve(s, items.size(), nblk)) != LBM_OK) return st;
+                size_t b = 0, first = 0;  // first: start of the current variant's run
+                for (size_t i = 0; i < items.size(); ++i) {
+                    lbm_ctx* c = s->active[items[i].second]->ctx;
+                    if (items[i].first != items[first].first) first = i;
+                    lbm::ResLattice& R = s->h_tab[i];
+                    R.p = c->kp;
+                    R.pl = c->pl[c->cur];
+                    R.cu = c->mac + (size_t)(c->snap ^ 1) * 4 * c->ns;  // new fields
+                    R.cT = R.cu + 3 * c->ns;
+                    R.pu = c->have_prev ? c->mac + (size_t)c->snap * 4 * c->ns : nullptr;
+                    R.pT = R.pu ? R.pu + 3 * c->ns : nullptr;
+                    R.partials = c->partials;
+                    R.out = s->d_out + 5 * i;
+                    R.nr = lbm::residual_blocks(c->ns);
+                    R.pad_ = 0;
+                    for (int j = 0; j < R.nr; ++j) s->h_blk[b++] = make_int2((int)(i - first), j);
+                    slot[items[i].second] = (int)i;
+                }
+                const size_t n = items.size();
+                if (cudaMemcpyAsync(s->d_tab, s->h_tab, n * sizeof(lbm::ResLattice),
+                                    cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(s->d_blk, s->h_blk, nblk * sizeof(int2), cudaMemcpyHostToDevice,
+                                    s->stream) != cudaSuccess)
+                    return LBM_ECUDA;
+                // one launch per kernel variant, over its run of the table
+                size_t i0 = 0, b0 = 0;
+                while (i0 < n) {
+                    size_t i1 = i0, b1 = b0;
+                    while (i1 < n && items[i1].first == items[i0].first) b1 += (size_t)s->h_tab[i1++].nr;
+                    lbm_ctx* c = s->active[items[i0].second]->ctx;
+                    if (lbm::launch_batch_residual(s->d_tab + i0, s->d_blk + b0, (int)(b1 - b0),
+                                                   c->kp.phi_field != nullptr, c->outflow,
+                                                   c->prm.storage, c->lat.enthalpy != 0,
+                                                   s->stream) != cudaSuccess)
+                        return LBM_ECUDA;
+                    i0 = i1;
+                    b0 = b1;
+                }
+                if (lbm::launch_batch_residual_finish(s->d_tab, (int)n, s->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(s->h_out, s->d_out, n * 5 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+                    return LBM_ECUDA;
+            }
+        }
+        for (size_t k = 0; k < na; ++k)
+            if (slot[k] < 0 && launched[k] == LBM_OK) launched[k] = residual_launch(s->active[k]->ctx);
         if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
-        std::vector<int> status(s->active.size(), -1);
-        for (size_t k = 0; k < s->active.size(); ++k) {
+        std::vector<int> status(na, -1);
+        for (size_t k = 0; k < na; ++k) {
             lbm_server::Req* r = s->active[k];
+            if (slot[k] >= 0 && launched[k] == LBM_OK)
+                std::memcpy(r->ctx->hres, s->h_out + 5 * (size_t)slot[k], 5 * sizeof(double));
             st = launched[k] == LBM_OK ? residual_collect(r->ctx, &r->r_u, &r->r_T) : launched[k];
             if (st == LBM_EUNSTABLE) status[k] = LBM_REQ_UNSTABLE;
             else if (st != LBM_OK) status[k] = LBM_REQ_FAILED;
@@ -2102,10 +2228,14 @@ void lbm_server_destroy(lbm_server* s) {
         delete r;
     }
     for (auto* r : s->queue) delete r;
-    if (s->own_stream && s->stream) {
-        cudaStreamSynchronize(s->stream);
-        cudaStreamDestroy(s->stream);
-    }
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    cudaFreeHost(s->h_tab);
+    cudaFree(s->d_tab);
+    cudaFreeHost(s->h_blk);
+    cudaFree(s->d_blk);
+    cudaFreeHost(s->h_out);
+    cudaFree(s->d_out);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
 

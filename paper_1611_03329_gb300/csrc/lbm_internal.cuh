@@ -192,6 +192,30 @@ cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk
 // pull step when (cur ^ flip) is 0, else a local step; cur holds its AA phase.
 cudaError_t launch_batch_aa(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                             int block_threads, int rows, bool het, int flip, cudaStream_t st);
+// One lattice of a batched residual: its parameters and the planes of its current copy, the
+// macroscopic fields written now (cu: u as 3 x ns, cT) and those of the previous residual (pu,
+// pT; nullptr on the first one, when the new fields are compared with themselves), its
+// partial sums (5 per block, residual_blocks(ns) blocks) and its 5 totals (device).
+struct ResLattice {
+    KParams p;
+    Planes pl;
+    float* cu;
+    float* cT;
+    const float* pu;
+    const float* pT;
+    double* partials;
+    double* out;
+    int nr;
+    int pad_;
+};
+// Residual sums of the n lattices of tab, all with the same medium kind (het), outflow,
+// storage and thermal model (enthalpy): for each, the macroscopic fields (as launch_macros
+// computes them) and the sums of launch_residual over residual_blocks(ns) blocks, bit for
+// bit.  blk maps each of the nblocks blocks to (lattice in tab, block within the lattice).
+cudaError_t launch_batch_residual(const ResLattice* tab, const int2* blk, int nblocks, bool het,
+                                  bool outflow, int storage, bool enthalpy, cudaStream_t st);
+// The totals of the n lattices of tab from their partial sums (finalize of launch_residual).
+cudaError_t launch_batch_residual_finish(const ResLattice* tab, int n, cudaStream_t st);
 // x-extent of a site-kernel block for a lattice of width nx within block_threads threads.
 int block_x(int nx, int block_threads);  // number of partial sums the reductions write (<= partials size)
 

@@ -2199,9 +2199,10 @@ __global__ void __launch_bounds__(kRedThreads)
     block_reduce_store<2>(v, partials + 2 * blockIdx.x);
 }
 
+// Totals of nparts partial sums (NV values each) in a fixed order, by one block.
 template <int NV>
-__global__ void __launch_bounds__(kRedThreads)
-    finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+__device__ __forceinline__ void finalize_sums(const double* __restrict__ partials, int nparts,
+                                              double* __restrict__ out) {
     double v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = 0.0;
@@ -2209,6 +2210,28 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
         for (int k = 0; k < NV; ++k) v[k] += partials[NV * b + k];
     block_reduce_store<NV>(v, out);
+}
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads)
+    finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+    finalize_sums<NV>(partials, nparts, out);
+}
+
+// Residual sums of one site against the previous fields: v += (|u - u_prev|^2, |u|^2,
+// (T - T_prev)^2, T^2, non-finite values).
+__device__ __forceinline__ void residual_site(double (&v)[5], const float (&u)[3],
+                                              const float (&up)[3], float T, float Tp) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double x = u[a], d = x - (double)up[a];
+        v[0] += d * d;
+        v[1] += x * x;
+        if (!isfinite(x)) v[4] += 1.0;
+    }
+    const double t = T, dt = t - (double)Tp;
+    v[2] += dt * dt;
+    v[3] += t * t;
+    if (!isfinite(t)) v[4] += 1.0;
 }
 
 __global__ void __launch_bounds__(kRedThreads)
@@ -2218,19 +2241,54 @@ __global__ void __launch_bounds__(kRedThreads)
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (long long s = (long long)blockIdx.x * kRedThreads + threadIdx.x; s < ns;
          s += (long long)gridDim.x * kRedThreads) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double x = u[a * ns + s], d = x - (double)up[a * ns + s];
-            v[0] += d * d;
-            v[1] += x * x;
-            if (!isfinite(x)) v[4] += 1.0;
-        }
-        double t = T[s], dt = t - (double)Tp[s];
-        v[2] += dt * dt;
-        v[3] += t * t;
-        if (!isfinite(t)) v[4] += 1.0;
+        const float uu[3] = {u[s], u[ns + s], u[2 * ns + s]};
+        const float pu[3] = {up[s], up[ns + s], up[2 * ns + s]};
+        residual_site(v, uu, pu, T[s], Tp[s]);
     }
     block_reduce_store<5>(v, partials + 5 * blockIdx.x);
+}
+
+// Batched residual (lbm_server): block b of the list takes lattice blk[b].x and, within it,
+// the sites residual_kernel's block blk[b].y takes (the same stride over the same number of
+// blocks), computes their macroscopic fields as macros_kernel does, stores them as the new
+// snapshot and adds them up with residual_site: every lattice's partial sums are those of
+// launch_macros + launch_residual, bit for bit.
+template <bool HET, bool OUTF, class S, bool ENTH>
+__global__ void __launch_bounds__(kRedThreads)
+    batch_residual_kernel(const ResLattice* __restrict__ tab, const int2* __restrict__ blk) {
+    const int2 lb = blk[blockIdx.x];
+    const ResLattice& R = tab[lb.x];
+    const KParams& p = R.p;
+    const long long ns = p.ns, nxy = (long long)p.nx * p.ny;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long s = (long long)lb.y * kRedThreads + threadIdx.x; s < ns;
+         s += (long long)R.nr * kRedThreads) {
+        const int z = (int)(s / nxy), rem = (int)(s - (long long)z * nxy);
+        const int y = rem / p.nx, x = rem - y * p.nx;
+        const Nbr n = neighbourhood(p, x, y, z);
+        float f[kQ], g[kQT];
+        gather_general<OUTF, S, D3Q19>(R.pl, p, n, f, g);
+        const Medium md = medium_at<HET>(p, n.s);
+        const Macro m = collide_on<false, ENTH, D3Q19>(p, md, f, g);
+        const float uu[3] = {m.ux, m.uy, m.uz};
+        R.cu[s] = m.ux;
+        R.cu[ns + s] = m.uy;
+        R.cu[2 * ns + s] = m.uz;
+        R.cT[s] = m.T;
+        if (R.pu) {
+            const float pu[3] = {R.pu[s], R.pu[ns + s], R.pu[2 * ns + s]};
+            residual_site(v, uu, pu, m.T, R.pT[s]);
+        } else {  // first residual: the fields against themselves
+            residual_site(v, uu, uu, m.T, m.T);
+        }
+    }
+    block_reduce_store<5>(v, R.partials + 5 * lb.y);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    batch_residual_finish_kernel(const ResLattice* __restrict__ tab) {
+    const ResLattice& R = tab[blockIdx.x];
+    finalize_sums<5>(R.partials, R.nr, R.out);
 }
 
 // Temperature at a site from the streamed D3Q7 populations (Eq. 39).
@@ -2631,6 +2689,31 @@ cudaError_t launch_nusselt(const KParams& p, bool outflow, const Planes& pl, int
         nusselt_finalize_kernel<<<1, kRedThreads, 0, st>>>(profile, n1, out);
         return cudaGetLastError();
     });
+}
+
+cudaError_t launch_batch_residual(const ResLattice* tab, const int2* blk, int nblocks, bool het,
+                                  bool outflow, int storage, bool enthalpy, cudaStream_t st) {
+    if (nblocks < 1) return cudaSuccess;
+    if (enthalpy) {  // FP32, uniform medium, no outflow (the model's rules)
+        batch_residual_kernel<false, false, StoreF32, true><<<nblocks, kRedThreads, 0, st>>>(tab, blk);
+        return cudaGetLastError();
+    }
+    auto go = [&](auto tag) {
+        using S = decltype(tag);
+        auto k = het ? (outflow ? batch_residual_kernel<true, true, S, false>
+                                : batch_residual_kernel<true, false, S, false>)
+                     : (outflow ? batch_residual_kernel<false, true, S, false>
+                                : batch_residual_kernel<false, false, S, false>);
+        k<<<nblocks, kRedThreads, 0, st>>>(tab, blk);
+        return cudaGetLastError();
+    };
+    return with_storage(storage, go);
+}
+
+cudaError_t launch_batch_residual_finish(const ResLattice* tab, int n, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    batch_residual_finish_kernel<<<n, kRedThreads, 0, st>>>(tab);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const float* u, const float* T, const float* up, const float* Tp,

@@ -247,3 +247,44 @@ def test_served_requests_match_oracle(gb, orc):
         Tg = T.reshape(To.shape)
         assert orc.field_error(ug, uo) < TOL_FIELD, k
         assert orc.field_error(Tg, To) < TOL_FIELD, k
+
+
+def test_served_variants_match_oracle(gb, orc):
+    """A D3Q15 cavity and a node-wall cavity (stepped alone by the server) and an AA cavity
+    (batched in its own group), served together with a ping-pong cavity: each request's final
+    u and T equal an oracle run of the same problem for the same steps, within 1e-5."""
+    nee = cavity_problem(11, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71, L=10)
+    nee.update(ny=10, nz=9, flow_bc=[4] * 6, heat_bc=[4, 4, 5, 5, 5, 5])
+    mix = [dict(cavity_problem(12, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71), q=15, ny=10),
+           nee,
+           dict(cavity_problem(12, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71), ny=10, scheme="aa"),
+           cavity_problem(10, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71)]
+    limits = [400, 300, 500, 300]
+    srv = gb.Server(chunk=100)
+    outs, ids = {}, {}
+    for k, pb in enumerate(mix):
+        ns = int(pb["nx"]) * int(pb["ny"]) * int(pb["nz"])
+        rid = srv.submit(pb, tol=1e-14, max_steps=limits[k])
+        u = np.zeros(3 * ns, np.float32)
+        T = np.zeros(ns, np.float32)
+        srv.set_output(rid, u, T)
+        outs[rid] = (u, T)
+        ids[rid] = k
+    results = []
+    for _ in range(100):
+        na, nq = srv.advance()
+        results += srv.poll()
+        if na == 0 and nq == 0:
+            break
+    results += srv.poll()
+    srv.close()
+    assert sorted(r["id"] for r in results) == sorted(ids)
+    for r in results:
+        k = ids[r["id"]]
+        assert r["status"] == "max_steps" and r["steps"] == limits[k]
+        o = orc.Oracle(orc.map_problem(mix[k]))
+        o.step(r["steps"])
+        _, uo, To = o.macros()
+        u, T = outs[r["id"]]
+        assert orc.field_error(u.reshape(uo.shape), uo) < TOL_FIELD, k
+        assert orc.field_error(T.reshape(To.shape), To) < TOL_FIELD, k

@@ -168,3 +168,88 @@ def test_backfill_lets_small_requests_pass(gb, policy):
         assert res[ic]["t_admit"] >= res[ib]["t_admit"]
     for r in res.values():
         assert r["status"] == "max_steps"
+
+
+NEE, NEE_T, NEE_A = 4, 4, 5
+
+
+def _variant_requests():
+    nee = cavity_problem(11, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71, L=10)
+    nee.update(ny=10, nz=9, flow_bc=[NEE] * 6, heat_bc=[NEE_T, NEE_T, NEE_A, NEE_A, NEE_A, NEE_A])
+    return [
+        dict(cavity_problem(12, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71), q=15, ny=10),  # D3Q15
+        nee,                                                                         # node walls
+        dict(cavity_problem(14, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71), ny=12, scheme="aa"),
+        cavity_problem(16, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71),
+        channel_problem(40, 10, 10, Da=1e-2),
+    ]
+
+
+def test_d3q15_node_wall_and_aa_requests_are_served(gb):
+    """D3Q15 and node-wall lattices step alone, an AA lattice batches in its own group: each
+    result is the same alone and in the mix, and the AA request holds one population copy."""
+    pbs = _variant_requests()
+    srv = gb.Server(chunk=100)
+    ids = [srv.submit(pb, tol=1e-6, max_steps=1500) for pb in pbs]
+    done = _drain(srv)
+    srv.close()
+    assert sorted(r["id"] for r in done) == sorted(ids)
+    mixed = {r["id"]: r for r in done}
+    for rid, pb in zip(ids, pbs):
+        solo = gb.Server(chunk=100)
+        solo.submit(pb, tol=1e-6, max_steps=1500)
+        (r,) = _drain(solo)
+        solo.close()
+        _same(mixed[rid], r)
+        assert r["status"] in ("converged", "max_steps"), r["status"]
+    aa, pp = mixed[ids[2]], None
+    solo = gb.Server(chunk=100)
+    solo.submit(dict(pbs[2], scheme="pingpong"), tol=1e-6, max_steps=1500)
+    (pp,) = _drain(solo)
+    solo.close()
+    assert aa["bytes"] < pp["bytes"]
+    _same(aa, {**pp, "storage": aa["storage"]})  # the AA scheme changes no result
+
+
+def test_aa_request_the_scheme_does_not_take_is_rejected(gb):
+    srv = gb.Server(chunk=100)
+    with pytest.raises(gb.LbmError):  # an outflow face: AA does not apply
+        srv.submit(dict(channel_problem(40, 10, 10, Da=1e-2), scheme="aa"), tol=1e-6)
+    with pytest.raises(gb.LbmError):  # 16-bit storage kept (tolerance above its floor)
+        srv.submit(dict(cavity_problem(12, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71), scheme="aa",
+                        storage="fp16"), tol=1e-3)
+    srv.close()
+
+
+def test_served_residuals_equal_lbm_residual(gb):
+    """The server takes the residuals of its batched lattices in one launch per kernel variant
+    (uniform and field media, outflow, 16-bit storage, the enthalpy model): each equals, bit for
+    bit, what lbm_residual gives for the same lattice after the same chunks."""
+    from lbm_inputs import porosity_field
+
+    phi = porosity_field(12, 10, 8, seed=9).astype(np.float32).astype(np.float64)
+    melt = dict(nx=12, ny=6, nz=12, mapping="cavity", Ra=1e5, Pr=0.71, phi=1.0, enthalpy=True,
+                T_m=0.5, St=1.0, flow_bc=[1] * 6, heat_bc=[2, 2, 1, 1, 1, 1],
+                face_T=[1.0, 0.0, 0, 0, 0, 0], T_init=0.0, T0=0.5)
+    pbs = [cavity_problem(12, Ra=1e5, Da=1e-2, phi=0.8, Pr=0.71),
+           dict(cavity_problem(12, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71, phi_field=phi), ny=10, nz=8),
+           channel_problem(32, 8, 6, Da=1e-2),
+           dict(cavity_problem(14, Ra=1e4, Da=1e-2, phi=0.7, Pr=0.71), storage="fp16"),
+           melt]
+    steps = 300
+    srv = gb.Server(chunk=100)
+    # tolerances none of them reaches in 300 steps; the FP16 one above its format's residual
+    # floor, so that it is served in FP16
+    ids = [srv.submit(pb, tol=2.5e-4 if pb.get("storage") == "fp16" else 1e-14, max_steps=steps)
+           for pb in pbs]
+    done = {r["id"]: r for r in _drain(srv)}
+    srv.close()
+    for rid, pb in zip(ids, pbs):
+        lat = gb.Lattice(pb)
+        for _ in range(steps // 100):
+            lat.step(100)
+            ru, rT = lat.residual()
+        lat.close()
+        r = done[rid]
+        assert r["steps"] == steps and r["storage"] == pb.get("storage", "fp32")
+        assert r["r_u"] == ru and r["r_T"] == rT, (pb.get("storage"), r["r_u"], ru, r["r_T"], rT)
