@@ -146,7 +146,13 @@ def test_declined_combinations(gb):
     lat = gb.Lattice(pb)
     with pytest.raises(gb.LbmError):
         gb.Batch([lat])
-    srv = gb.Server()
-    with pytest.raises(gb.LbmError):
-        srv.submit(pb)
+    srv = gb.Server(chunk=100)  # the serving loop takes it and steps it alone
+    rid = srv.submit(pb, tol=1e-14, max_steps=200)
+    done = []
+    for _ in range(10):
+        na, nq = srv.advance()
+        done += srv.poll()
+        if na == 0 and nq == 0:
+            break
     srv.close()
+    assert [r["id"] for r in done] == [rid] and done[0]["status"] == "max_steps"
