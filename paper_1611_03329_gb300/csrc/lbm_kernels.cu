@@ -1425,7 +1425,8 @@ __device__ __forceinline__ void dependent_launch_prologue() {
 }
 
 // 3D launch: threadIdx.x + blockIdx.x * blockDim.x -> x, the same for y, blockIdx.z -> z.
-// blockDim.x is a multiple of 32, so every warp lies in one x-row and votes as a whole.
+// blockDim.x is the smallest power of two >= nx up to the block size (block_x_of): a warp
+// holds one or more whole rows, or part of one, and votes as a whole over its lanes' sites.
 // Registers: 64 per thread (32 resident warps per SM with 64-thread blocks); 72 with a porosity
 // field, whose medium terms need more (28 warps; at 80 the field kernel lost 4 % on the 256^3
 // cavity).
@@ -2376,9 +2377,11 @@ inline unsigned blocks_for(long long n, int threads) {
 }
 
 // Block of p.block_threads (32..kBlock) threads: blockDim.x = the smallest power of two >= nx
-// within that size, the rest along y.
+// within that size, the rest along y.  A row narrower than a warp shares the warp with the
+// next rows (a 16-wide lattice fills its warps instead of leaving half the lanes idle); the
+// warp votes of the gathers test every lane's own site, so they hold for any rows.
 int block_x_of(int nx, int nt) {
-    int bx = 32;
+    int bx = 1;
     while (bx < nx && bx < nt) bx *= 2;
     return bx;
 }
