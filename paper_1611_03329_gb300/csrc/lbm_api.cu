@@ -1327,6 +1327,7 @@ struct lbm_batch {
         bool het = false, outflow = false, enthalpy = false;
         bool aa = false;  // AA-scheme lattices (one copy each, stepped by batch_aa_kernel)
         bool off32 = false;  // the members' planes are addressed by 32-bit offsets
+        bool pair = false;   // two x-adjacent sites per thread (batch_pair_kernel)
         std::vector<int> members;           // indices into ctx
         lbm::BatchLattice* dtab = nullptr;  // device table
         // host mirror in pageable memory: an asynchronous copy from it stages the data before
@@ -1365,6 +1366,17 @@ void batch_clear_graphs(lbm_batch* b) {
     b->graphs.clear();
 }
 
+// Block layout of one lattice of a batch (x-extent, blocks along x and y; pair: nx / 2 pairs
+// per row); returns its number of blocks.
+int batch_layout(const lbm_ctx* c, bool pair, int block_threads, int rows, lbm::BatchLattice* L) {
+    const int nx = pair ? c->prm.nx / 2 : c->prm.nx;
+    L->bx = lbm::block_x(nx, block_threads);
+    const int by = block_threads / L->bx;
+    L->gx = (nx + L->bx - 1) / L->bx;
+    L->gy = (c->prm.ny + by - 1) / by;
+    return L->gx * L->gy * ((c->prm.nz + rows - 1) / rows);
+}
+
 // Host tables of every group from the contexts' current state and the block size.
 void batch_fill_tables(lbm_batch* b) {
     for (auto& g : b->groups) {
@@ -1376,15 +1388,21 @@ void batch_fill_tables(lbm_batch* b) {
             L.pl[0] = c->pl[0];
             L.pl[1] = c->pl[1];
             L.cur = c->aa ? c->aa_phase : c->cur;  // AA: 0 pull step next, 1 local step next
-            L.bx = lbm::block_x(c->prm.nx, b->block_threads);
-            const int by = b->block_threads / L.bx;
-            L.gx = (c->prm.nx + L.bx - 1) / L.bx;
-            L.gy = (c->prm.ny + by - 1) / by;
             L.block_begin = off;
-            off += L.gx * L.gy * ((c->prm.nz + b->rows - 1) / b->rows);
+            off += batch_layout(c, g.pair, b->block_threads, b->rows, &L);
         }
         g.nblocks = off;
     }
+}
+
+// The block -> lattice map of a table whose block_begin fields are set (nblocks blocks).
+std::vector<unsigned short> batch_block_map(const std::vector<lbm::BatchLattice>& tab, int nblocks) {
+    std::vector<unsigned short> blk((size_t)nblocks, 0);
+    for (size_t k = 0; k < tab.size(); ++k) {
+        const int end = k + 1 < tab.size() ? tab[k + 1].block_begin : nblocks;
+        for (int i = tab[k].block_begin; i < end; ++i) blk[(size_t)i] = (unsigned short)k;
+    }
+    return blk;
 }
 
 // Order the batch stream after every context's pending work (and the reverse at the end).
@@ -1411,7 +1429,7 @@ lbm_status batch_launch_steps(lbm_batch* b, int nsteps, bool tuning) {
             }
             LBM_BCUDA(lbm::launch_batch_step(g.dtab, g.dblk, g.nblocks, b->block_threads, b->rows,
                                              g.storage, g.het, g.outflow, g.enthalpy, g.off32,
-                                             tuning ? 0 : (t & 1), b->stream));
+                                             g.pair, tuning ? 0 : (t & 1), b->stream));
         }
     return LBM_OK;
 }
@@ -1424,11 +1442,7 @@ lbm_status batch_upload(lbm_batch* b) {
                                   sizeof(lbm::BatchLattice) * g.members.size(),
                                   cudaMemcpyHostToDevice, b->stream));
         if (g.dblk_threads == b->block_threads && g.dblk_rows == b->rows && g.dblk) continue;
-        g.hblk.assign((size_t)g.nblocks, 0);
-        for (size_t k = 0; k < g.htab.size(); ++k) {
-            const int end = k + 1 < g.htab.size() ? g.htab[k + 1].block_begin : g.nblocks;
-            for (int blk = g.htab[k].block_begin; blk < end; ++blk) g.hblk[blk] = (unsigned short)k;
-        }
+        g.hblk = batch_block_map(g.htab, g.nblocks);
         if ((size_t)g.nblocks > g.dblk_cap) {
             // the map is sized once per layout; kernels of earlier launches may still read
             // the old one, so wait for them before freeing it
@@ -1462,6 +1476,7 @@ lbm_status time_group(lbm_batch* b, lbm_batch::Group& g, bool aa, float* ms_per_
     const int nwarm = 2, ntime = 6;
     lbm::BatchLattice* dtab = g.dtab;
     unsigned short* dblk = g.dblk;
+    int nblocks = g.nblocks;
     std::vector<lbm::BatchLattice> tab;
     std::vector<unsigned short> blk;
     if (aa) {
@@ -1476,6 +1491,18 @@ lbm_status time_group(lbm_batch* b, lbm_batch::Group& g, bool aa, float* ms_per_
             tab[k].pl[1] = aa_planes_at(c, scratch, false, true);
             tab[k].cur = 0;
         }
+        if (g.pair) {  // the AA kernel takes one site per thread: a layout of its own
+            int off = 0;
+            for (size_t k = 0; k < g.members.size(); ++k) {
+                tab[k].block_begin = off;
+                off += batch_layout(b->ctx[g.members[k]], false, b->block_threads, b->rows, &tab[k]);
+            }
+            nblocks = off;
+            blk = batch_block_map(tab, nblocks);
+            LBM_BCUDA(cudaMalloc(&dblk, sizeof(unsigned short) * blk.size()));
+            LBM_BCUDA(cudaMemcpyAsync(dblk, blk.data(), sizeof(unsigned short) * blk.size(),
+                                      cudaMemcpyHostToDevice, b->stream));
+        }
         LBM_BCUDA(cudaMalloc(&dtab, sizeof(lbm::BatchLattice) * tab.size()));
         LBM_BCUDA(cudaMemcpyAsync(dtab, tab.data(), sizeof(lbm::BatchLattice) * tab.size(),
                                   cudaMemcpyHostToDevice, b->stream));
@@ -1486,11 +1513,11 @@ lbm_status time_group(lbm_batch* b, lbm_batch::Group& g, bool aa, float* ms_per_
     for (int t = 0; t < nwarm + ntime && e == cudaSuccess; ++t) {
         if (t == nwarm) e = cudaEventRecord(t0, b->stream);
         if (e != cudaSuccess) break;
-        e = aa ? lbm::launch_batch_aa(dtab, dblk, g.nblocks, b->block_threads, b->rows, g.het,
+        e = aa ? lbm::launch_batch_aa(dtab, dblk, nblocks, b->block_threads, b->rows, g.het,
                                       t & 1, b->stream)
-               : lbm::launch_batch_step(dtab, dblk, g.nblocks, b->block_threads, b->rows,
-                                        g.storage, g.het, g.outflow, g.enthalpy, g.off32, 0,
-                                        b->stream);
+               : lbm::launch_batch_step(dtab, dblk, nblocks, b->block_threads, b->rows,
+                                        g.storage, g.het, g.outflow, g.enthalpy, g.off32, g.pair,
+                                        0, b->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -1499,6 +1526,7 @@ lbm_status time_group(lbm_batch* b, lbm_batch::Group& g, bool aa, float* ms_per_
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (aa) cudaFree(dtab);
+    if (dblk != g.dblk) cudaFree(dblk);
     if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "timing a group", e);
     *ms_per_step = ms / ntime;
     return LBM_OK;
@@ -1519,10 +1547,11 @@ lbm_status batch_group(lbm_batch* b) {
         const int stg = c->prm.storage;
         const bool het = c->lat.has_phi_field != 0, outf = c->outflow;
         const bool ent = c->lat.enthalpy != 0, aa = c->aa, o32 = c->kp.off32 != 0;
+        const bool pr = pair_eligible(c);  // two sites per thread where the paired kernel applies
         lbm_batch::Group* grp = nullptr;
         for (auto& gr : b->groups)
             if (gr.storage == stg && gr.het == het && gr.outflow == outf && gr.enthalpy == ent &&
-                gr.aa == aa && gr.off32 == o32)
+                gr.aa == aa && gr.off32 == o32 && gr.pair == pr)
                 grp = &gr;
         if (!grp) {
             b->groups.emplace_back();
@@ -1533,6 +1562,7 @@ lbm_status batch_group(lbm_batch* b) {
             grp->enthalpy = ent;
             grp->aa = aa;
             grp->off32 = o32;
+            grp->pair = pr;
         }
         grp->members.push_back(k);
     }

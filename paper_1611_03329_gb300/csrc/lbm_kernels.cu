@@ -1691,20 +1691,10 @@ __device__ __forceinline__ int warp_pair_mode(const KParams& p, int xa, int y, i
     return kGatherAny;
 }
 
-// Registers (measured on the 256x64x64 channel and the 256^3 field cavity, GB300): uncapped
-// the kernel takes ~128 and runs 14 warps per SM, latency-bound; 96 (16-bit) and 104 (FP32)
-// give 20 warps at little spilling for a uniform medium; with a porosity field the 16-bit
-// instance is fastest at 112 and the FP32 one uncapped (it spills heavily below that).
+// The update of the pair (xa, xa + 1) at row y, slab z in the gather mode of its warp.
 template <bool HET, bool OUTF, class S>
-__global__ void __maxnreg__(HET ? (S::kScaled ? 112 : 128) : (S::kScaled ? 96 : 104))
-    step_pair_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
-    dependent_launch_prologue();
-    const int xa = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = step_row_block<!S::kScaled>() * blockDim.y + threadIdx.y;
-    const int z = step_slab<!S::kScaled>();
-    const bool valid = xa < p.nx && y < p.ny;  // nx even: x + 1 < nx as well
-    const int mode = warp_pair_mode(p, xa, y, z, valid);
-    if (!valid) return;
+__device__ __forceinline__ void pair_update(const Planes& pl, const KParams& p, int xa, int y,
+                                            int z, int mode) {
     const int sa = xa + p.nx * (y + p.ny * z);
     L2 f[kQ], g[kQT];
     if (mode == kGatherInterior) {
@@ -1737,6 +1727,22 @@ __global__ void __maxnreg__(HET ? (S::kScaled ? 112 : 128) : (S::kScaled ? 96 : 
     });
 #pragma unroll
     for (int i = 0; i < kQ; ++i) stp2<S>(pl, p, i, sa, f[i]);
+}
+
+// Registers (measured on the 256x64x64 channel and the 256^3 field cavity, GB300): uncapped
+// the kernel takes ~128 and runs 14 warps per SM, latency-bound; 96 (16-bit) and 104 (FP32)
+// give 20 warps at little spilling for a uniform medium; with a porosity field the 16-bit
+// instance is fastest at 112 and the FP32 one uncapped (it spills heavily below that).
+template <bool HET, bool OUTF, class S>
+__global__ void __maxnreg__(HET ? (S::kScaled ? 112 : 128) : (S::kScaled ? 96 : 104))
+    step_pair_kernel(const __grid_constant__ KParams p, const __grid_constant__ Planes pl) {
+    dependent_launch_prologue();
+    const int xa = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = step_row_block<!S::kScaled>() * blockDim.y + threadIdx.y;
+    const int z = step_slab<!S::kScaled>();
+    const bool valid = xa < p.nx && y < p.ny;  // nx even: x + 1 < nx as well
+    const int mode = warp_pair_mode(p, xa, y, z, valid);
+    if (valid) pair_update<HET, OUTF, S>(pl, p, xa, y, z, mode);
 }
 
 // ---- AA pattern: one population copy, updated in place (FP32, D3Q19, no outflow) ----------
@@ -1972,6 +1978,37 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
             gather_site<OUTF, S>(pl, p, x, y, z, s, mode, f, g);
             finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
         }
+    }
+}
+
+// Batched step with two x-adjacent sites per thread: the lattices of a group that the paired
+// kernel takes (D3Q19, even nx, no node walls, no enthalpy model, 32-bit plane offsets).  The
+// block -> pair mapping is that of batch_step_kernel over nx / 2 pairs per row; each pair is
+// updated by pair_update, as step_pair_kernel updates it, bit for bit.  Its parameters come
+// from the lattice table in global memory, not from the constant bank, and take registers of
+// their own: 128 per thread (16 warps per SM) keeps its spills to a few bytes (at the single
+// kernel's 96-104 it spilled 200-400 bytes).
+template <bool HET, bool OUTF, class S>
+__global__ void __maxnreg__(128)
+    batch_pair_kernel(const BatchLattice* __restrict__ tab,
+                      const unsigned short* __restrict__ blk_lat, int flip, int rows) {
+    const BatchLattice* L = tab + __ldg(blk_lat + blockIdx.x);
+    const KParams& p = L->p;
+    const Planes& pl = L->pl[L->cur ^ flip];
+    const int bx = L->bx, gx = L->gx, gy = L->gy;
+    const int local = (int)blockIdx.x - L->block_begin;
+    const int by = blockDim.x / bx;
+    const int tx = threadIdx.x & (bx - 1), ty = threadIdx.x / bx;
+    const int bxi = local % gx, rest = local / gx;
+    const int xa = 2 * (bxi * bx + tx);
+    const int y = (rest % gy) * by + ty;
+    const int z0 = (rest / gy) * rows;
+    const bool valid = xa < p.nx && y < p.ny;
+    for (int r = 0; r < rows; ++r) {
+        const int z = z0 + r;
+        if (z >= p.nz) break;  // uniform over the block
+        const int mode = warp_pair_mode(p, xa, y, z, valid);
+        if (valid) pair_update<HET, OUTF, S>(pl, p, xa, y, z, mode);
     }
 }
 
@@ -2434,8 +2471,20 @@ int block_x(int nx, int block_threads) { return block_x_of(nx, block_threads); }
 
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
-                              bool enthalpy, bool off32, int flip, cudaStream_t st) {
+                              bool enthalpy, bool off32, bool pair, int flip, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
+    if (pair) {  // 32-bit plane offsets, no enthalpy model (pair_eligible)
+        auto go = [&](auto tag) {
+            using S = decltype(tag);
+            auto k = het ? (outflow ? batch_pair_kernel<true, true, S> : batch_pair_kernel<true, false, S>)
+                         : (outflow ? batch_pair_kernel<false, true, S> : batch_pair_kernel<false, false, S>);
+            k<<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+            return cudaGetLastError();
+        };
+        if (storage == 1) return go(StoreF16o{});
+        if (storage == 2) return go(StoreBF16o{});
+        return go(StoreF32o{});
+    }
     if (enthalpy) {
         batch_step_kernel<false, false, StoreF32, true>
             <<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
