@@ -366,7 +366,7 @@ def run_batch(args, gb, torch):
     lats = [gb.Lattice(pb, stream=stream.cuda_stream) for pb in pbs]
     sites = sum(l.ns for l in lats)
     batch = gb.Batch(lats, stream=stream.cuda_stream)
-    block = batch.tune()  # (threads per block, z-planes per block)
+    block = batch.tune() + batch.launch_groups()  # shape, then (fused, per-lattice) groups
     chunk = max(1, min(args.steps, 500))
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -647,6 +647,7 @@ def run_ours(args):
                 "config": _config("batch64", args.storage, scheme=args.scheme,
                                   extra={"sites": sites, "block_threads": block[0],
                                          "planes_per_block": block[1],
+                                         "groups_fused": block[2], "groups_per_lattice": block[3],
                                          "unstable_lattices": unstable}),
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak[0],
                              "unit": "GB/s", "frac": round(achieved / peak[0], 4),

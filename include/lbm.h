@@ -419,7 +419,9 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
  * for them).  (2) Streaming scheme: every group of ping-pong lattices that could run the AA
  * scheme is timed both ways at the chosen shape -- AA on scratch, each lattice's second copy
  * filled with its state and stepped in place -- and moves to AA (lbm_batch_set_scheme) only if
- * that is more than 3 % faster (lbm_batch_scheme_times reports the last trial).
+ * that is more than 3 % faster (lbm_batch_scheme_times reports the last trial).  (3) Launch:
+ * every ping-pong group is timed fused and per lattice (lbm_batch_set_launch_mode), without
+ * changing the state, and runs per lattice where that is more than 3 % faster.
  * Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows);
 
@@ -432,6 +434,18 @@ lbm_status lbm_batch_set_scheme(lbm_batch* b, int scheme);
 
 /* Milliseconds per step of the last group the tuner timed both ways (0 before any trial). */
 lbm_status lbm_batch_scheme_times(const lbm_batch* b, double* pp_ms, double* aa_ms);
+
+/* How a batch group's lattices are stepped.  LBM_BATCH_FUSED: one launch per step for all of
+ * them (replayed from a graph).  LBM_BATCH_PER_LATTICE: each lattice's own single-lattice step
+ * kernel, launched directly, one launch per lattice and step -- faster for lattices that fill
+ * the GPU alone, whose kernel then reads its parameters from the constant bank and takes fewer
+ * registers.  Results are the same either way.  lbm_batch_tune (stage 3) times both for every
+ * ping-pong group and keeps the per-lattice launch where it is more than 3 % faster;
+ * lbm_batch_set_launch_mode sets every ping-pong group (AA groups are always fused). */
+enum { LBM_BATCH_FUSED = 0, LBM_BATCH_PER_LATTICE = 1 };
+lbm_status lbm_batch_set_launch_mode(lbm_batch* b, int mode);
+/* Number of groups stepped by the fused launch and per lattice. */
+lbm_status lbm_batch_launch_groups(const lbm_batch* b, int* fused, int* per_lattice);
 
 /* Set the block shape of the batched step: threads (32, 64, 128 or 256) and z-planes per
  * block (1..64). */

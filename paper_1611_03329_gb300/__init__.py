@@ -41,6 +41,7 @@ ABI_SYMBOLS = (
     "lbm_get_step_kernel", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
     "lbm_set_launch", "lbm_test_tma_extra_wait", "lbm_server_set_output",
     "lbm_server_set_policy", "lbm_batch_set_scheme", "lbm_batch_scheme_times",
+    "lbm_batch_set_launch_mode", "lbm_batch_launch_groups",
     "lbm_bounds_report",
 )
 
@@ -49,6 +50,7 @@ RESIDUAL_FLOOR = {"fp16": 2e-4, "bf16": 2e-3}  # LBM_RESIDUAL_FLOOR_FP16 / _BF16
 
 # Population schemes (LBM_SCHEME_*).
 SCHEMES = {"pingpong": 0, "aa": 1, "auto": 2}
+BATCH_LAUNCH = {"fused": 0, "per_lattice": 1}  # LBM_BATCH_FUSED / _PER_LATTICE
 
 # Step kernels (LBM_KERNEL_*).
 STEP_KERNELS = {"plain": 0, "tma": 1, "paired": 2}
@@ -202,6 +204,8 @@ def lib():
         L.lbm_batch_set_block.argtypes = [vp, C.c_int, C.c_int]
         L.lbm_batch_set_scheme.argtypes = [vp, C.c_int]
         L.lbm_batch_scheme_times.argtypes = [vp, dp, dp]
+        L.lbm_batch_set_launch_mode.argtypes = [vp, C.c_int]
+        L.lbm_batch_launch_groups.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.lbm_batch_last_error.argtypes = [vp]
         L.lbm_batch_last_error.restype = C.c_char_p
         L.lbm_batch_destroy.argtypes = [vp]
@@ -507,6 +511,19 @@ class Batch:
         self._check(lib().lbm_batch_scheme_times(self._h, C.byref(pp), C.byref(aa)),
                     "lbm_batch_scheme_times")
         return pp.value, aa.value
+
+    def set_launch_mode(self, mode: str):
+        """lbm_batch_set_launch_mode: "fused" (one launch per step for a group) or
+        "per_lattice" (each lattice's own step kernel)."""
+        self._check(lib().lbm_batch_set_launch_mode(self._h, BATCH_LAUNCH[mode]),
+                    "lbm_batch_set_launch_mode")
+
+    def launch_groups(self):
+        """(fused groups, per-lattice groups): lbm_batch_launch_groups."""
+        nf, ns = C.c_int(), C.c_int()
+        self._check(lib().lbm_batch_launch_groups(self._h, C.byref(nf), C.byref(ns)),
+                    "lbm_batch_launch_groups")
+        return nf.value, ns.value
 
     def sync(self):
         for l in self.lattices:

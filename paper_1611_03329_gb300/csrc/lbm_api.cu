@@ -1328,6 +1328,9 @@ struct lbm_batch {
         bool aa = false;  // AA-scheme lattices (one copy each, stepped by batch_aa_kernel)
         bool off32 = false;  // the members' planes are addressed by 32-bit offsets
         bool pair = false;   // two x-adjacent sites per thread (batch_pair_kernel)
+        // each member stepped by its own single-lattice kernel (launched directly, not from
+        // the graph), chosen by the tuner where that is faster than the fused launch
+        bool solo = false;
         std::vector<int> members;           // indices into ctx
         lbm::BatchLattice* dtab = nullptr;  // device table
         // host mirror in pageable memory: an asynchronous copy from it stages the data before
@@ -1417,10 +1420,28 @@ lbm_status batch_join(lbm_batch* b, bool into_batch) {
     return LBM_OK;
 }
 
+// The steps of a group whose members run their own single-lattice kernels: all nsteps of one
+// member, then the next (the members are independent; consecutive steps of one lattice find
+// much of its state still in L2), step t of a member reading its copy cur ^ (t & 1) (tuning:
+// always cur, so that only the other copy is written).
+lbm_status batch_launch_solo(lbm_batch* b, lbm_batch::Group& g, int nsteps, bool tuning) {
+    for (int k : g.members) {
+        lbm_ctx* c = b->ctx[k];
+        for (int t = 0; t < nsteps; ++t) {
+            const lbm::Planes& pl = c->pl[c->cur ^ (tuning ? 0 : (t & 1))];
+            LBM_BCUDA(g.pair ? lbm::launch_step_pair(c->kp, c->outflow, pl, c->pdl, b->stream)
+                             : lbm::launch_step(c->kp, c->outflow, pl, c->pdl, b->stream));
+        }
+    }
+    return LBM_OK;
+}
+
+// The fused launches of nsteps steps (the solo groups are left to batch_launch_solo).
 // tuning: launches that leave the state unchanged, so AA groups (updated in place) are left out
 lbm_status batch_launch_steps(lbm_batch* b, int nsteps, bool tuning) {
     for (int t = 0; t < nsteps; ++t)
         for (auto& g : b->groups) {
+            if (g.solo) continue;
             if (g.aa) {
                 if (!tuning)
                     LBM_BCUDA(lbm::launch_batch_aa(g.dtab, g.dblk, g.nblocks, b->block_threads,
@@ -1527,6 +1548,29 @@ lbm_status time_group(lbm_batch* b, lbm_batch::Group& g, bool aa, float* ms_per_
     if (t1) cudaEventDestroy(t1);
     if (aa) cudaFree(dtab);
     if (dblk != g.dblk) cudaFree(dblk);
+    if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "timing a group", e);
+    *ms_per_step = ms / ntime;
+    return LBM_OK;
+}
+
+// Milliseconds per step of a group's members stepped by their own kernels (tuning launches:
+// the state is unchanged).
+lbm_status time_solo(lbm_batch* b, lbm_batch::Group& g, float* ms_per_step) {
+    const int nwarm = 2, ntime = 6;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    lbm_status st = LBM_OK;
+    if (e == cudaSuccess) st = batch_launch_solo(b, g, nwarm, true);
+    if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(t0, b->stream);
+    if (e == cudaSuccess && st == LBM_OK) st = batch_launch_solo(b, g, ntime, true);
+    if (e == cudaSuccess && st == LBM_OK) e = cudaEventRecord(t1, b->stream);
+    if (e == cudaSuccess && st == LBM_OK) e = cudaEventSynchronize(t1);
+    float ms = 0.0f;
+    if (e == cudaSuccess && st == LBM_OK) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (st != LBM_OK) return st;
     if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "timing a group", e);
     *ms_per_step = ms / ntime;
     return LBM_OK;
@@ -1650,8 +1694,10 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     lbm_status st = batch_join(b, true);
     if (st != LBM_OK) return st;
     if ((st = batch_upload(b)) != LBM_OK) return st;
+    bool fused = false;
+    for (auto& g : b->groups) fused = fused || !g.solo;
     auto it = b->graphs.find(nsteps);
-    if (it == b->graphs.end()) {
+    if (fused && it == b->graphs.end()) {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         LBM_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -1667,7 +1713,9 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
         if (e != cudaSuccess) return batch_fail(b, LBM_ECUDA, "cudaGraphInstantiate", e);
         it = b->graphs.emplace(nsteps, exec).first;
     }
-    LBM_BCUDA(cudaGraphLaunch(it->second, b->stream));
+    if (fused) LBM_BCUDA(cudaGraphLaunch(it->second, b->stream));
+    for (auto& g : b->groups)
+        if (g.solo && (st = batch_launch_solo(b, g, nsteps, false)) != LBM_OK) return st;
     for (lbm_ctx* c : b->ctx) {
         if (c->aa) c->aa_phase ^= (nsteps & 1);
         else c->cur ^= (nsteps & 1);
@@ -1762,7 +1810,39 @@ lbm_status lbm_batch_tune(lbm_batch* b, int* block_threads, int* rows) {
         if ((st = batch_group(b)) != LBM_OK) return st;
         batch_clear_graphs(b);
     }
+    // launch: a ping-pong group runs each member's own single-lattice kernel where that is more
+    // than 3 % faster than the fused launch (lattices that fill the GPU alone, with a kernel
+    // that reads its parameters from the constant bank and so takes fewer registers)
+    if ((st = batch_upload(b)) != LBM_OK) return st;
+    bool changed = false;
+    for (auto& g : b->groups) {
+        if (g.aa) continue;
+        float fused = 0.0f, solo = 0.0f;
+        if ((st = time_group(b, g, false, &fused)) != LBM_OK) return st;
+        if ((st = time_solo(b, g, &solo)) != LBM_OK) return st;
+        const bool want = solo < 0.97f * fused;
+        changed = changed || want != g.solo;
+        g.solo = want;
+    }
+    if (changed) batch_clear_graphs(b);
     return batch_join(b, false);
+}
+
+lbm_status lbm_batch_set_launch_mode(lbm_batch* b, int mode) {
+    if (!b || (mode != LBM_BATCH_FUSED && mode != LBM_BATCH_PER_LATTICE)) return LBM_EINVAL;
+    for (auto& g : b->groups)
+        if (!g.aa) g.solo = mode == LBM_BATCH_PER_LATTICE;
+    batch_clear_graphs(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_launch_groups(const lbm_batch* b, int* fused, int* per_lattice) {
+    if (!b) return LBM_EINVAL;
+    int nf = 0, ns = 0;
+    for (auto& g : b->groups) (g.solo ? ns : nf) += 1;
+    if (fused) *fused = nf;
+    if (per_lattice) *per_lattice = ns;
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_set_scheme(lbm_batch* b, int scheme) {

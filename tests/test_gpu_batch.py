@@ -89,6 +89,56 @@ def test_tune_keeps_state(gb):
     batch.close()
 
 
+def test_per_lattice_launch_equals_individual_steps(gb):
+    """Groups stepped by each lattice's own kernel (lbm_batch_set_launch_mode): the same
+    populations as the lattices stepped alone, across graph-free odd and even step counts, a
+    switch back to the fused launch and an individual step in between."""
+    alone, batched = _pair(gb)
+    batch = gb.Batch(batched)
+    batch.set_launch_mode("per_lattice")
+    nf, ns = batch.launch_groups()
+    assert nf == 0 and ns >= 4  # every group is a ping-pong group here
+    batch.step(37)
+    batch.step(20)
+    for a in alone:
+        a.step(57)
+    _same(alone, batched)
+    batched[1].step(3)
+    alone[1].step(3)
+    batch.set_launch_mode("fused")
+    assert batch.launch_groups() == (ns, 0)
+    batch.step(9)
+    batch.set_launch_mode("per_lattice")
+    batch.step(4)
+    for a in alone:
+        a.step(13)
+    _same(alone, batched)
+    batch.close()
+
+
+def test_tuner_chooses_the_launch_by_timing_and_keeps_state(gb):
+    """Stage 3 of the tuner times every ping-pong group fused and per lattice without changing
+    the state; large lattices (which fill the GPU alone) and small ones batch differently,
+    and either way the populations follow the individual steps."""
+    pbs = [dict(cavity_problem(96, Ra=1e5, Da=1e-2, phi=0.8, Pr=0.71), storage="fp16"),
+           dict(cavity_problem(128, Ra=1e4, Da=1e-3, phi=0.6, Pr=0.71), storage="fp16")]
+    batched = [gb.Lattice(pb) for pb in pbs]
+    alone = [gb.Lattice(pb) for pb in pbs]
+    batch = gb.Batch(batched)
+    before = [b.populations() for b in batched]
+    batch.tune()
+    for (f0, g0), b in zip(before, batched):
+        f1, g1 = b.populations()
+        assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    nf, ns = batch.launch_groups()
+    assert nf + ns == 1  # one FP16 paired group
+    batch.step(7)
+    for a in alone:
+        a.step(7)
+    _same(alone, batched)
+    batch.close()
+
+
 def test_batch_diagnostics_follow_the_contexts(gb):
     """After batched steps every per-context call sees the new state."""
     pb = cavity_problem(16, Ra=1e5, Da=1e-2, phi=0.8, Pr=0.71)
