@@ -745,9 +745,10 @@ def run_ours(args):
                                  else None),
                      "peak_source": peak_src,
                      "algorithmic_bytes_per_site": bytes_site, "sites_per_launch": ns,
-                     "limiter": ("memory latency and the drain of each launch (ncu: DRAM "
-                                 "traffic equals the algorithmic bytes, long-scoreboard stalls "
-                                 "first)" if args.storage == "fp32" else
+                     "limiter": ("DRAM and memory latency (ncu: long-scoreboard stalls first; "
+                                 "alternating sweep directions serve part of each step's reads "
+                                 "from L2, so DRAM traffic is below the algorithmic bytes)"
+                                 if args.storage == "fp32" else
                                  "instruction issue (ncu on the channel: issue-bound, DRAM well "
                                  "below peak)"),
                      "kernel": ("aa_pull_kernel<true> / aa_local_kernel<true> alternating (AA, one "

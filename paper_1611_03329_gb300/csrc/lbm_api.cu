@@ -930,6 +930,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     }
     for (int t = 0; t < nsteps; ++t) {
         int nxt = c->cur ^ 1;
+        c->kp.reverse = c->cur;  // alternate sweep directions (sweep_block)
         if (c->step_kernel == LBM_KERNEL_PAIRED)
             LBM_CUDA(lbm::launch_step_pair(c->kp, c->outflow, c->pl[c->cur], c->pdl, c->stream));
         else if (c->step_kernel == LBM_KERNEL_TMA)
@@ -1427,10 +1428,13 @@ lbm_status batch_join(lbm_batch* b, bool into_batch) {
 lbm_status batch_launch_solo(lbm_batch* b, lbm_batch::Group& g, int nsteps, bool tuning) {
     for (int k : g.members) {
         lbm_ctx* c = b->ctx[k];
+        lbm::KParams kp = c->kp;
         for (int t = 0; t < nsteps; ++t) {
-            const lbm::Planes& pl = c->pl[c->cur ^ (tuning ? 0 : (t & 1))];
-            LBM_BCUDA(g.pair ? lbm::launch_step_pair(c->kp, c->outflow, pl, c->pdl, b->stream)
-                             : lbm::launch_step(c->kp, c->outflow, pl, c->pdl, b->stream));
+            const int from = c->cur ^ (tuning ? 0 : (t & 1));
+            kp.reverse = from;  // alternate sweep directions, as lbm_step
+            const lbm::Planes& pl = c->pl[from];
+            LBM_BCUDA(g.pair ? lbm::launch_step_pair(kp, c->outflow, pl, c->pdl, b->stream)
+                             : lbm::launch_step(kp, c->outflow, pl, c->pdl, b->stream));
         }
     }
     return LBM_OK;

@@ -30,6 +30,7 @@ struct KParams {
     long long ns;   // sites
     long long sq;   // elements between consecutive population planes (>= ns, padded)
     int off32;      // every element offset within a population copy fits an int
+    int reverse;    // step kernels: sweep the blocks in reverse order (set on alternate steps)
 
     // boundaries (face bits: 1 << face, faces x-low, x-high, y-low, y-high, z-low, z-high)
     unsigned per_mask;    // periodic faces (flow and heat)
