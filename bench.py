@@ -97,8 +97,8 @@ KERNEL_SOURCES = ("paper_1611_03329_gb300/csrc/lbm_kernels.cu",
 # figure describes the kernel whose sources had this hash and is reported only while they
 # still do.
 STEP_TRAFFIC = {"kernel_source_sha256":
-                "0c6da162577cf990e8b889447579124364fc201d1d76c123cb61e413c4bdfb68",
-                "dram_bytes_per_launch": 216688282}
+                "5862eebee2c15869905033f4231ff117de12327e147ed37d1237dbceac2167cc",
+                "dram_bytes_per_launch": 173549261}
 
 
 def kernel_source_hash() -> str:
