@@ -386,15 +386,17 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r_u, double* r_T);
  * on the thread by an earlier call is neither reported nor cleared.
  * It allocates nothing: its partial sums live in a static 320 KiB device array that every
  * GPU loading the library holds until exit.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress).  All calls share the array: calls whose
+ * array's device address (cudaGetSymbolAddress), so make that first call on each device
+ * before any stream capture begins.  All calls share the array: calls whose
  * kernels overlap on the GPU race and must be serialised.  Errors: LBM_EINVAL (NULL pointer or ns out of range), LBM_ECUDA. */
 lbm_status lbm_residual_noalloc(const float* u, const float* T, const float* u_prev,
                                 const float* T_prev, long long ns, double* out, void* stream);
 
 /* ---- batched launches -----------------------------------------------------------------
  * A batch advances many independent lattices (contexts) with one fused launch per time step
- * and kernel variant (storage format, uniform or field medium, outflow or not, ping-pong or
- * AA scheme; an AA lattice takes its own pull or local step in the shared launch): the step of
+ * and kernel variant (storage format, uniform or field medium, outflow or not, D3Q19 or D3Q15
+ * flow lattice, halfway or node walls, ping-pong or AA scheme; an AA lattice takes its own
+ * pull or local step in the shared launch): the step of
  * Sec. 3 at every site of every lattice, exactly as lbm_step computes it, so a lattice's
  * results are identical alone and in a batch.  Multi-step sequences are recorded once per
  * step count as a CUDA graph and replayed.  The contexts keep owning their state; after

@@ -1329,6 +1329,8 @@ struct lbm_batch {
         bool aa = false;  // AA-scheme lattices (one copy each, stepped by batch_aa_kernel)
         bool off32 = false;  // the members' planes are addressed by 32-bit offsets
         bool pair = false;   // two x-adjacent sites per thread (batch_pair_kernel)
+        int qf = 19;         // flow lattice: D3Q19 or D3Q15
+        bool nee = false;    // node walls (non-equilibrium extrapolation)
         // each member stepped by its own single-lattice kernel (launched directly, not from
         // the graph), chosen by the tuner where that is faster than the fused launch
         bool solo = false;
@@ -1454,7 +1456,8 @@ lbm_status batch_launch_steps(lbm_batch* b, int nsteps, bool tuning) {
             }
             LBM_BCUDA(lbm::launch_batch_step(g.dtab, g.dblk, g.nblocks, b->block_threads, b->rows,
                                              g.storage, g.het, g.outflow, g.enthalpy, g.off32,
-                                             g.pair, tuning ? 0 : (t & 1), b->stream));
+                                             g.pair, g.qf, g.nee, tuning ? 0 : (t & 1),
+                                             b->stream));
         }
     return LBM_OK;
 }
@@ -1542,7 +1545,7 @@ lbm_status time_group(lbm_batch* b, lbm_batch::Group& g, bool aa, float* ms_per_
                                       t & 1, b->stream)
                : lbm::launch_batch_step(dtab, dblk, nblocks, b->block_threads, b->rows,
                                         g.storage, g.het, g.outflow, g.enthalpy, g.off32, g.pair,
-                                        0, b->stream);
+                                        g.qf, g.nee, 0, b->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -1596,10 +1599,12 @@ lbm_status batch_group(lbm_batch* b) {
         const bool het = c->lat.has_phi_field != 0, outf = c->outflow;
         const bool ent = c->lat.enthalpy != 0, aa = c->aa, o32 = c->kp.off32 != 0;
         const bool pr = pair_eligible(c);  // two sites per thread where the paired kernel applies
+        const int qf = flow_q(c);
+        const bool nee = c->lat.node_walls != 0;
         lbm_batch::Group* grp = nullptr;
         for (auto& gr : b->groups)
             if (gr.storage == stg && gr.het == het && gr.outflow == outf && gr.enthalpy == ent &&
-                gr.aa == aa && gr.off32 == o32 && gr.pair == pr)
+                gr.aa == aa && gr.off32 == o32 && gr.pair == pr && gr.qf == qf && gr.nee == nee)
                 grp = &gr;
         if (!grp) {
             b->groups.emplace_back();
@@ -1611,6 +1616,8 @@ lbm_status batch_group(lbm_batch* b) {
             grp->aa = aa;
             grp->off32 = o32;
             grp->pair = pr;
+            grp->qf = qf;
+            grp->nee = nee;
         }
         grp->members.push_back(k);
     }
@@ -1637,7 +1644,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, void* stream, lbm_batch
     }
     for (int k = 0; k < n; ++k) {
         lbm_ctx* c = ctxs[k];
-        if (!c || c->sticky != LBM_OK || c->lat.q == 15 || c->lat.node_walls) {  // step alone
+        if (!c || c->sticky != LBM_OK) {
             delete b;
             return LBM_EINVAL;
         }

@@ -183,12 +183,14 @@ cudaError_t bounds_report(long long* first_bad, int* checked);
 // Physical plane of logical D3Q19 + D3Q7 plane q in the AA scheme's swapped layout: the plane
 // of the opposite velocity.
 int aa_swapped_plane(int q);
-// One time step of every lattice of a batch group (same storage, medium kind and outflow):
-// lattice l reads its planes pl[cur ^ flip]; blk_lat maps each of the nblocks blocks to its
-// lattice.  pair: two x-adjacent sites per thread (the group's layout counts nx / 2 per row).
+// One time step of every lattice of a batch group (same storage, medium kind, outflow, flow
+// lattice qf (19 or 15) and node walls): lattice l reads its planes pl[cur ^ flip]; blk_lat
+// maps each of the nblocks blocks to its lattice.  pair: two x-adjacent sites per thread (the
+// group's layout counts nx / 2 per row).
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
-                              bool enthalpy, bool off32, bool pair, int flip, cudaStream_t st);
+                              bool enthalpy, bool off32, bool pair, int qf, bool nee, int flip,
+                              cudaStream_t st);
 // One time step of the AA lattices of a batch group (FP32, D3Q19, no outflow): lattice l runs a
 // pull step when (cur ^ flip) is 0, else a local step; cur holds its AA phase.
 cudaError_t launch_batch_aa(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,

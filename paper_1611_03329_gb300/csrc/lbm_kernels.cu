@@ -1942,16 +1942,17 @@ __global__ void __launch_bounds__(kBlock) aa_normalize_kernel(const __grid_const
 // Batched step: one flat grid over the blocks of many lattices.  blk_lat[b] names the lattice
 // of block b; the lattice's parameters and planes are read in place through the read-only
 // cache (uniform over the block).  A block covers `rows` consecutive z-planes of one
-// (x-segment, y-band) column, so the lookup is paid once per `rows` site updates.
-template <bool HET, bool OUTF, class S, bool ENTH = false>
+// (x-segment, y-band) column, so the lookup is paid once per `rows` site updates.  L and NEE
+// as in step_kernel: the D3Q15 flow lattice, node walls (a node-wall site takes nee_site).
+template <bool HET, bool OUTF, class S, bool ENTH = false, class L = D3Q19, bool NEE = false>
 __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     batch_step_kernel(const BatchLattice* __restrict__ tab,
                       const unsigned short* __restrict__ blk_lat, int flip, int rows) {
-    const BatchLattice* L = tab + __ldg(blk_lat + blockIdx.x);
-    const KParams& p = L->p;
-    const Planes& pl = L->pl[L->cur ^ flip];
-    const int bx = L->bx, gx = L->gx, gy = L->gy;
-    const int local = (int)blockIdx.x - L->block_begin;
+    const BatchLattice* B = tab + __ldg(blk_lat + blockIdx.x);
+    const KParams& p = B->p;
+    const Planes& pl = B->pl[B->cur ^ flip];
+    const int bx = B->bx, gx = B->gx, gy = B->gy;
+    const int local = (int)blockIdx.x - B->block_begin;
     const int by = blockDim.x / bx;
     const int tx = threadIdx.x & (bx - 1), ty = threadIdx.x / bx;
     const int bxi = local % gx, rest = local / gx;
@@ -1962,15 +1963,25 @@ __global__ void __launch_bounds__(kBlock, kStepMinBlocks - 1)
     for (int r = 0; r < rows; ++r) {
         const int z = z0 + r;
         if (z >= p.nz) break;  // uniform over the block
+        const unsigned nb = (NEE && valid) ? nee_bits(p, x, y, z) : 0u;  // node-wall site
         // every lane of the warp reaches the votes; only the valid lanes update a site (the
         // site update itself holds no warp-wide vote)
-        const int mode = warp_gather_mode(p, x, y, z, valid);
-        if (valid) {
-            float f[kQ], g[kQT];
-            const int s = x + p.nx * (y + p.ny * z);
-            gather_site<OUTF, S>(pl, p, x, y, z, s, mode, f, g);
-            finish_site<HET, OUTF, S, ENTH>(pl, p, x, y, z, s, f, g);
+        const int mode = warp_gather_mode(p, x, y, z, valid && nb == 0u);
+        if (!valid) continue;
+        float f[L::kQ], g[kQT];
+        const int s = x + p.nx * (y + p.ny * z);
+        if constexpr (NEE) {
+            if (nb) {
+                nee_site<HET, true, S, L>(pl, p, x, y, z, s, nb, f, g);
+#pragma unroll
+                for (int i = 0; i < L::kQ; ++i) stp<S>(pl, p, i, s, f[i]);
+#pragma unroll
+                for (int i = 0; i < kQT; ++i) stg_dev<S>(pl, p, i, s, g[i], 0.0f);
+                continue;
+            }
         }
+        gather_site<OUTF, S, L>(pl, p, x, y, z, s, mode, f, g);
+        finish_site<HET, OUTF, S, ENTH, L>(pl, p, x, y, z, s, f, g);
     }
 }
 
@@ -2464,8 +2475,25 @@ int block_x(int nx, int block_threads) { return block_x_of(nx, block_threads); }
 
 cudaError_t launch_batch_step(const BatchLattice* tab, const unsigned short* blk_lat, int nblocks,
                               int block_threads, int rows, int storage, bool het, bool outflow,
-                              bool enthalpy, bool off32, bool pair, int flip, cudaStream_t st) {
+                              bool enthalpy, bool off32, bool pair, int qf, bool nee, int flip,
+                              cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
+    if (nee) {  // node walls: FP32 storage, no outflow (validated on the host)
+        auto k = qf == 15 ? (het ? batch_step_kernel<true, false, StoreF32, false, D3Q15, true>
+                                 : batch_step_kernel<false, false, StoreF32, false, D3Q15, true>)
+                          : (het ? batch_step_kernel<true, false, StoreF32, false, D3Q19, true>
+                                 : batch_step_kernel<false, false, StoreF32, false, D3Q19, true>);
+        k<<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+        return cudaGetLastError();
+    }
+    if (qf == 15) {  // D3Q15 flow lattice: FP32 storage (validated on the host)
+        auto k = het ? (outflow ? batch_step_kernel<true, true, StoreF32, false, D3Q15>
+                                : batch_step_kernel<true, false, StoreF32, false, D3Q15>)
+                     : (outflow ? batch_step_kernel<false, true, StoreF32, false, D3Q15>
+                                : batch_step_kernel<false, false, StoreF32, false, D3Q15>);
+        k<<<nblocks, block_threads, 0, st>>>(tab, blk_lat, flip, rows);
+        return cudaGetLastError();
+    }
     if (pair) {  // 32-bit plane offsets, no enthalpy model (pair_eligible)
         auto go = [&](auto tag) {
             using S = decltype(tag);

@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device by the first call made on
+// that device; that first call belongs before any stream capture begins.
 std::mutex g_setup_mutex;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 

@@ -13,7 +13,8 @@ stepped alone on the GPU.  Tolerances are those of the single-lattice parity tes
 import numpy as np
 import pytest
 
-from lbm_inputs import (cavity_problem, channel_problem, porosity_field, random_macros,
+from lbm_inputs import (cavity_problem, channel_problem, paper_channel, porosity_field,
+                        random_macros,
                         uniform)
 
 pytestmark = pytest.mark.gpu
@@ -114,6 +115,80 @@ def test_batch_steps_match_oracle(gb, orc):
         assert ef < 4 * TOL_STEP and eg < 4 * TOL_STEP, (name, ef, eg)
         assert lat.steps == 20
     batch.close()
+
+
+def _node_walls(pb):
+    nee, nee_t, nee_a = 4, 4, 5  # LBM_FLOW_NEE, LBM_HEAT_NEE_DIRICHLET, LBM_HEAT_NEE_ADIABATIC
+    return dict(pb, flow_bc=[nee] * 6, heat_bc=[nee_t, nee_t, nee_a, nee_a, nee_a, nee_a])
+
+
+# the paper-fidelity lattices of Secs. 3.1.1 and 4: D3Q15 with halfway walls (a field medium,
+# the outflow channel), node walls by non-equilibrium extrapolation on D3Q19 and D3Q15 (a
+# ragged cavity, the paper's transpiring channel, a field medium), beside a D3Q19 lattice
+VARIANT_CASES = {
+    "d3q15_hetero": dict(cavity_problem(12, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71,
+                                        phi_field=porosity_field(12, 10, 8, seed=5)
+                                        .astype(np.float32).astype(np.float64)),
+                         ny=10, nz=8, q=15),
+    "d3q15_channel": dict(channel_problem(19, 10, 7, Da=1e-2), q=15),
+    "nee_cavity": dict(_node_walls(cavity_problem(13, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71, L=12)),
+                       ny=11, nz=9),
+    "nee_d3q15_channel": dict(paper_channel(12, nx=5, nz=4, walls="nee"), q=15),
+    "nee_hetero": dict(_node_walls(cavity_problem(10, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71, L=9,
+                                                  phi_field=porosity_field(10, 9, 8, seed=6)
+                                                  .astype(np.float32).astype(np.float64))),
+                       ny=9, nz=8),
+    "d3q19_cavity": dict(cavity_problem(11, Ra=1e4, Da=1e-2, phi=0.7, Pr=0.71), ny=9, nz=8),
+}
+
+
+def test_batch_d3q15_and_node_walls_match_oracle(gb, orc):
+    """D3Q15 and node-wall lattices advance in the batched launch (groups of their own): every
+    population after one batched step and after 19 more (two graph replays) against the oracle,
+    and bit for bit the same as the lattice stepped alone by lbm_step."""
+    names = sorted(VARIANT_CASES)
+    lats, solos, runs = [], [], []
+    for k, name in enumerate(names):
+        pb = VARIANT_CASES[name]
+        lp, o, f, g = _random_state(orc, pb, seed=90 + 5 * k)
+        lat, solo = gb.Lattice(pb), gb.Lattice(pb)
+        for x in (lat, solo):
+            x.set_populations(f, g)
+        o.set_populations(f, g)
+        lats.append(lat)
+        solos.append(solo)
+        runs.append((lp, o))
+    assert sum(l.lattice()["q"] == 15 for l in lats) == 3
+    assert sum(l.lattice()["node_walls"] == 1 for l in lats) == 3
+    batch = gb.Batch(lats)
+
+    def errors(lp, lat, o):
+        fa, ga = lat.populations()
+        fb, gbo = o.populations()
+        w = (orc.tables15()["w15"] if lp.q == 15 else orc.tables()["w19"]).reshape(-1, 1, 1, 1)
+        _, om = _weights(orc, lp)
+        return (np.abs(fa - fb).max() / np.abs(fb - w * lp.rho0).max(),
+                np.abs(ga - gbo).max() / np.abs(gbo - om).max())
+
+    batch.step(1)
+    for name, lat, (lp, o) in zip(names, lats, runs):
+        o.step(1)
+        ef, eg = errors(lp, lat, o)
+        assert ef < TOL_STEP and eg < TOL_STEP, (name, ef, eg)
+    batch.step(12)
+    batch.step(7)
+    for name, lat, solo, (lp, o) in zip(names, lats, solos, runs):
+        o.step(19)
+        ef, eg = errors(lp, lat, o)
+        assert ef < 4 * TOL_STEP and eg < 4 * TOL_STEP, (name, ef, eg)
+        assert lat.steps == 20
+        solo.step(20)
+        fa, ga = lat.populations()
+        fs, gs = solo.populations()
+        assert np.array_equal(fa, fs) and np.array_equal(ga, gs), name
+    batch.close()
+    for x in lats + solos:
+        x.close()
 
 
 def test_batch_enthalpy_and_fp16_one_step(gb, orc):

@@ -143,9 +143,6 @@ def test_declined_combinations(gb):
         with pytest.raises(gb.LbmError):
             gb.derive_lattice(bad)
     assert gb.derive_lattice(pb)["q"] == 15
-    lat = gb.Lattice(pb)
-    with pytest.raises(gb.LbmError):
-        gb.Batch([lat])
     srv = gb.Server(chunk=100)  # the serving loop takes it and steps it alone
     rid = srv.submit(pb, tol=1e-14, max_steps=200)
     done = []
