@@ -524,7 +524,8 @@ lbm_status lbm_server_create(unsigned long long budget_bytes, int chunk, void* s
 
 /* Queue a request: problem p, medium m (NULL: lbm_set_medium defaults), residual tolerance
  * tol > 0 and step limit max_steps >= 1.  Returns its id.  Every lattice lbm_create takes is
- * served: D3Q15 and node-wall lattices step alone, the others batch; p->scheme ==
+ * served: lattices below 512 K sites batch (D3Q15 and node-wall ones too), larger ones step
+ * alone; p->scheme ==
  * LBM_SCHEME_AA is kept (one population copy, counted as such against the budget), AUTO is
  * served with two copies.  LBM_EINVAL for an invalid problem, an AA request the scheme does
  * not take (after the storage rule of the serving loop), or one larger than the whole

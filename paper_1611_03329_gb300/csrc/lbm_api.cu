@@ -1927,7 +1927,9 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 struct lbm_server {
     struct Req {
         long long id = 0;
-        bool batchable = true;  // may join the batched launch (D3Q19, halfway walls)
+        // residual taken in the batched residual launch (D3Q19, halfway walls); the others
+        // take lbm_residual's launches
+        bool batched_residual = true;
         lbm_params p{};
         double phi = 1.0, K = 0.0, F_phi = 0.0, alpha_m = -1.0, phi_ref = 0.0;
         std::vector<float> phi_field;
@@ -2099,8 +2101,8 @@ lbm_status lbm_server_submit(lbm_server* s, const lbm_params* p, const lbm_mediu
         delete r;
         return LBM_EINVAL;
     }
-    // D3Q15 and node-wall lattices do not batch: they step alone (lbm_step)
-    r->batchable = L.q == 19 && !L.node_walls;
+    // D3Q15 and node-wall lattices batch, but take their residuals one lattice at a time
+    r->batched_residual = L.q == 19 && !L.node_walls;
     if (m) {
         r->phi = m->phi;
         r->K = m->K;
@@ -2163,12 +2165,12 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
     }
     if (!s->active.empty()) {
         // a lattice of at least kBatchMaxSites sites steps alone (its own step kernel, the
-        // paired one where it applies, as dependent launches), and so does one the batched
-        // launch does not take (D3Q15, node walls); the other, smaller ones, whose steps are
-        // too short to fill the GPU, advance together in one batched launch per step
+        // paired one where it applies, as dependent launches); the other, smaller ones, whose
+        // steps are too short to fill the GPU, advance together in one batched launch per
+        // step and kernel variant
         constexpr long long kBatchMaxSites = 512 * 1024;
         auto small = [&](const lbm_server::Req* r) {
-            return r->batchable && (long long)r->p.nx * r->p.ny * r->p.nz < kBatchMaxSites;
+            return (long long)r->p.nx * r->p.ny * r->p.nz < kBatchMaxSites;
         };
         if (s->dirty) {
             lbm_batch_destroy(s->batch);
@@ -2199,8 +2201,8 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
             if (!small(r) && (st = lbm_step(r->ctx, s->chunk)) != LBM_OK) return st;
         if (s->batch && (st = lbm_batch_step(s->batch, s->chunk)) != LBM_OK) return st;
         // every residual queued behind the chunk, then one synchronisation for all of them:
-        // the batched lattices' residuals in one launch per kernel variant (the sums of
-        // lbm_residual, bit for bit), the others one lattice at a time
+        // the batched D3Q19 halfway-wall lattices' residuals in one launch per kernel variant
+        // (the sums of lbm_residual, bit for bit), the others one lattice at a time
         const size_t na = s->active.size();
         std::vector<lbm_status> launched(na, LBM_OK);
         std::vector<int> slot(na, -1);  // entry in the batched residual's table
@@ -2208,7 +2210,7 @@ lbm_status lbm_server_advance(lbm_server* s, int* n_active, int* n_queued) {
             std::vector<std::pair<int, size_t>> items;  // (kernel variant, active index)
             for (size_t k = 0; k < na; ++k) {
                 lbm_ctx* c = s->active[k]->ctx;
-                if (!small(s->active[k])) continue;
+                if (!small(s->active[k]) || !s->active[k]->batched_residual) continue;
                 lbm_status sk = usable(c);
                 if (sk == LBM_OK) sk = aa_settle(c);
                 if (sk == LBM_OK) sk = ensure_mac(c);

@@ -325,8 +325,8 @@ def test_served_requests_match_oracle(gb, orc):
 
 
 def test_served_variants_match_oracle(gb, orc):
-    """A D3Q15 cavity and a node-wall cavity (stepped alone by the server) and an AA cavity
-    (batched in its own group), served together with a ping-pong cavity: each request's final
+    """A D3Q15 cavity, a node-wall cavity and an AA cavity (each batched in a group of its
+    own), served together with a ping-pong cavity: each request's final
     u and T equal an oracle run of the same problem for the same steps, within 1e-5."""
     nee = cavity_problem(11, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71, L=10)
     nee.update(ny=10, nz=9, flow_bc=[4] * 6, heat_bc=[4, 4, 5, 5, 5, 5])

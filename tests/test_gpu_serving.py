@@ -186,8 +186,8 @@ def _variant_requests():
 
 
 def test_d3q15_node_wall_and_aa_requests_are_served(gb):
-    """D3Q15 and node-wall lattices step alone, an AA lattice batches in its own group: each
-    result is the same alone and in the mix, and the AA request holds one population copy."""
+    """D3Q15, node-wall and AA lattices batch in groups of their own: each result is the same
+    alone and in the mix, and the AA request holds one population copy."""
     pbs = _variant_requests()
     srv = gb.Server(chunk=100)
     ids = [srv.submit(pb, tol=1e-6, max_steps=1500) for pb in pbs]
@@ -223,8 +223,9 @@ def test_aa_request_the_scheme_does_not_take_is_rejected(gb):
 
 def test_served_residuals_equal_lbm_residual(gb):
     """The server takes the residuals of its batched lattices in one launch per kernel variant
-    (uniform and field media, outflow, 16-bit storage, the enthalpy model): each equals, bit for
-    bit, what lbm_residual gives for the same lattice after the same chunks."""
+    (uniform and field media, outflow, 16-bit storage, the enthalpy model), and those of its
+    batched D3Q15 and node-wall lattices one at a time: each equals, bit for bit, what
+    lbm_residual gives for the same lattice after the same chunks."""
     from lbm_inputs import porosity_field
 
     phi = porosity_field(12, 10, 8, seed=9).astype(np.float32).astype(np.float64)
@@ -235,7 +236,10 @@ def test_served_residuals_equal_lbm_residual(gb):
            dict(cavity_problem(12, Ra=1e5, Da=1e-2, phi=0.6, Pr=0.71, phi_field=phi), ny=10, nz=8),
            channel_problem(32, 8, 6, Da=1e-2),
            dict(cavity_problem(14, Ra=1e4, Da=1e-2, phi=0.7, Pr=0.71), storage="fp16"),
-           melt]
+           melt,
+           dict(cavity_problem(11, Ra=1e4, Da=1e-2, phi=0.7, Pr=0.71), q=15),
+           dict(cavity_problem(11, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71, L=10),
+                flow_bc=[4] * 6, heat_bc=[4, 4, 5, 5, 5, 5])]
     steps = 300
     srv = gb.Server(chunk=100)
     # tolerances none of them reaches in 300 steps; the FP16 one above its format's residual
