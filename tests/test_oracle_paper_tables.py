@@ -1,0 +1,71 @@
+"""The oracle against the Nusselt numbers the paper prints for the porous cavity (Sec. 4.2,
+Tables 1 and 3; the values sit in tests/golden/cavity_nusselt_tables.txt with their table).
+
+The paper's values come from 64^3 lattices.  The oracle runs the cheapest entries on 12^3 and
+16^3 lattices with the paper's own set-up (node walls by non-equilibrium extrapolation, Pr =
+0.71, Ma = 0.1, the relaxation rates of Sec. 4, hot wall x = 0, cold wall x = L, gravity along
+-z) to steady state and compares the convective part Nu_3D - 1 of the hot wall's Nusselt
+number (Eq. 55).  Tolerance: 10 % of the paper's Nu_3D - 1, twice the largest spread between
+the paper's values and the independent boundary-element values it prints beside them in Table
+1 (5 %: 0.0095 against 0.010 at Ra* = 50, Da = 0.1), which leaves room for the coarse
+lattices' discretisation error.  A model without buoyancy (Nu_3D = 1), a buoyancy, Darcy
+drag or diffusivity wrong by a factor of two, or a lost porosity dependence of the Ergun
+inertia term (Table 3's phi = 0.4 against 0.8) each moves Nu_3D - 1 far outside it.
+"""
+import os
+
+import pytest
+
+from lbm_inputs import cavity_problem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cavity_nusselt_tables.txt")
+NEE, NEE_T, NEE_A = 4, 4, 5  # node-wall flow, node-wall Dirichlet and adiabatic heat kinds
+TOL = 0.10
+
+
+def _table():
+    rows = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if not line.strip() or line.lstrip().startswith("#"):
+                continue
+            table, model, phi, da, ra_star, nu, _ = line.split()
+            rows[(table, float(phi), float(da), float(ra_star))] = float(nu)
+    return rows
+
+
+def _steady_nusselt(orc, n, phi, da, ra_star, brinkman_darcy, max_steps):
+    pb = cavity_problem(n, Ra=ra_star / da, Da=da, phi=phi, Pr=0.71,
+                        F_phi=0.0 if brinkman_darcy else -1.0, L=n - 1)
+    pb.update(flow_bc=[NEE] * 6, heat_bc=[NEE_T, NEE_T, NEE_A, NEE_A, NEE_A, NEE_A])
+    o = orc.Oracle(orc.map_problem(pb))
+    prev = None
+    while o.steps < max_steps:
+        o.step(1000)
+        _, _, T = o.macros()
+        if prev is not None and orc.residual(T, prev) < 1e-9:
+            break
+        prev = T.copy()
+    assert o.steps < max_steps, "no steady state"
+    return orc.nusselt(T, 0, 1.0, n - 1, node_wall=True)[0]
+
+
+def test_golden_file_holds_the_printed_tables():
+    rows = _table()
+    assert len(rows) == 18
+    assert rows[("table1", 0.8, 1e-2, 50.0)] == 1.2162
+    assert rows[("table3", 0.4, 1e-1, 50.0)] == 1.0029
+
+
+@pytest.mark.parametrize("table, phi, da, ra_star, n", [
+    ("table1", 0.8, 1e-1, 50.0, 12),
+    ("table1", 0.8, 1e-1, 100.0, 12),
+    ("table3", 0.4, 1e-1, 50.0, 12),
+    ("table3", 0.8, 1e-1, 100.0, 12),
+    ("table1", 0.8, 1e-2, 50.0, 16),
+])
+def test_cavity_nusselt_matches_paper(orc, table, phi, da, ra_star, n):
+    paper = _table()[(table, phi, da, ra_star)]
+    nu = _steady_nusselt(orc, n, phi, da, ra_star, brinkman_darcy=table == "table1",
+                         max_steps=40000)
+    assert abs((nu - 1.0) / (paper - 1.0) - 1.0) < TOL, (nu, paper)
