@@ -9,8 +9,14 @@ number (Eq. 55).  Tolerance: 10 % of the paper's Nu_3D - 1, twice the largest sp
 the paper's values and the independent boundary-element values it prints beside them in Table
 1 (5 %: 0.0095 against 0.010 at Ra* = 50, Da = 0.1), which leaves room for the coarse
 lattices' discretisation error.  A model without buoyancy (Nu_3D = 1), a buoyancy, Darcy
-drag or diffusivity wrong by a factor of two, or a lost porosity dependence of the Ergun
-inertia term (Table 3's phi = 0.4 against 0.8) each moves Nu_3D - 1 far outside it.
+drag or diffusivity wrong by a factor of two, or a lost porosity dependence (Table 3's phi =
+0.4 against 0.8) each moves Nu_3D - 1 far outside it.
+
+The Forchheimer term (Eq. 4 with the Ergun coefficient of Eq. 6) is pinned by the pair of
+entries that differ in it alone (phi = 0.8, Da = 1e-2, Ra* = 50: Table 1 without it, Table 3
+with it): the paper's ratio of their Nu_3D - 1 is 1.081, and the oracle's, taken on the same
+lattice so that most of the discretisation error cancels, must reproduce that 8.1 % effect to
+within a quarter of itself.
 """
 import os
 
@@ -34,7 +40,17 @@ def _table():
     return rows
 
 
-def _steady_nusselt(orc, n, phi, da, ra_star, brinkman_darcy, max_steps):
+_CACHE = {}
+
+
+def _steady_nusselt(orc, n, phi, da, ra_star, brinkman_darcy, max_steps=40000):
+    key = (n, phi, da, ra_star, brinkman_darcy)
+    if key not in _CACHE:
+        _CACHE[key] = _run(orc, n, phi, da, ra_star, brinkman_darcy, max_steps)
+    return _CACHE[key]
+
+
+def _run(orc, n, phi, da, ra_star, brinkman_darcy, max_steps):
     pb = cavity_problem(n, Ra=ra_star / da, Da=da, phi=phi, Pr=0.71,
                         F_phi=0.0 if brinkman_darcy else -1.0, L=n - 1)
     pb.update(flow_bc=[NEE] * 6, heat_bc=[NEE_T, NEE_T, NEE_A, NEE_A, NEE_A, NEE_A])
@@ -43,7 +59,7 @@ def _steady_nusselt(orc, n, phi, da, ra_star, brinkman_darcy, max_steps):
     while o.steps < max_steps:
         o.step(1000)
         _, _, T = o.macros()
-        if prev is not None and orc.residual(T, prev) < 1e-9:
+        if prev is not None and orc.residual(T, prev) < 1e-7:  # Nu_3D then settled to ~1e-6
             break
         prev = T.copy()
     assert o.steps < max_steps, "no steady state"
@@ -63,9 +79,19 @@ def test_golden_file_holds_the_printed_tables():
     ("table3", 0.4, 1e-1, 50.0, 12),
     ("table3", 0.8, 1e-1, 100.0, 12),
     ("table1", 0.8, 1e-2, 50.0, 16),
+    ("table3", 0.8, 1e-2, 50.0, 16),
+    ("table3", 0.4, 1e-2, 50.0, 16),
 ])
 def test_cavity_nusselt_matches_paper(orc, table, phi, da, ra_star, n):
     paper = _table()[(table, phi, da, ra_star)]
-    nu = _steady_nusselt(orc, n, phi, da, ra_star, brinkman_darcy=table == "table1",
-                         max_steps=40000)
+    nu = _steady_nusselt(orc, n, phi, da, ra_star, brinkman_darcy=table == "table1")
     assert abs((nu - 1.0) / (paper - 1.0) - 1.0) < TOL, (nu, paper)
+
+
+def test_forchheimer_effect_matches_paper(orc):
+    rows = _table()
+    paper = (rows[("table1", 0.8, 1e-2, 50.0)] - 1.0) / (rows[("table3", 0.8, 1e-2, 50.0)] - 1.0)
+    ours = ((_steady_nusselt(orc, 16, 0.8, 1e-2, 50.0, brinkman_darcy=True) - 1.0) /
+            (_steady_nusselt(orc, 16, 0.8, 1e-2, 50.0, brinkman_darcy=False) - 1.0))
+    assert paper > 1.05  # the term matters at this entry
+    assert abs((ours - 1.0) / (paper - 1.0) - 1.0) < 0.25, (ours, paper)
