@@ -14,7 +14,15 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def orc():
+    # LBM_ORACLE_UNDER_TEST: a directory holding a copy of the oracle package with one planted
+    # mistake (tests/test_oracle_mutants.py), which the pins must then reject
+    alt = os.environ.get("LBM_ORACLE_UNDER_TEST")
+    if alt:
+        sys.path.insert(0, alt)
     import oracle
+
+    if alt:
+        assert os.path.dirname(os.path.dirname(os.path.abspath(oracle.__file__))) == alt
 
     oracle.lib()
     return oracle

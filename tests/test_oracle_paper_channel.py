@@ -26,11 +26,16 @@ def E(a, ref):
     return math.sqrt(float(np.sum((a - ref) ** 2)) / float(np.sum(ref ** 2)))
 
 
-def steady(orc, ny, Re, Da):
-    o = orc.Oracle(orc.map_problem(paper_channel(ny, Re=Re, Da=Da)))
-    o.step(max(2000, int(40 * ny / (0.01 * Re))))  # 40 advective times of the injection
-    _, u, T = o.macros()
-    return u[:, 0, :, 0], T[0, :, 0]
+_STEADY = {}
+
+
+def steady(orc, ny, Re, Da, full=False):
+    if (ny, Re, Da) not in _STEADY:
+        o = orc.Oracle(orc.map_problem(paper_channel(ny, Re=Re, Da=Da)))
+        o.step(max(2000, int(40 * ny / (0.01 * Re))))  # 40 advective times of the injection
+        _STEADY[(ny, Re, Da)] = o.macros()
+    _, u, T = _STEADY[(ny, Re, Da)]
+    return T if full else (u[:, 0, :, 0], T[0, :, 0])
 
 
 @pytest.mark.parametrize("Re,Da", [(10.0, 1e-2), (5.0, 1e-1)])
@@ -67,3 +72,45 @@ def test_closed_form_is_a_solution():
     alpha = nu
     rT = u1 * (T[2:] - T[:-2]) / (2 * h) - alpha * (T[2:] - 2 * T[1:-1] + T[:-2]) / h ** 2
     assert np.abs(rT).max() < 1e-5 * u1 * np.abs(np.gradient(T, h)).max()
+
+
+
+def _exact_flux(pe):
+    """Heat flux into the fluid at the hot plate, in units of dT / H, of Eq. 49's profile
+    T = (exp(Pe y) - 1) / (exp(Pe) - 1), Pe = Pr Re."""
+    return pe * math.exp(pe) / (math.exp(pe) - 1.0)
+
+
+def test_wall_heat_flux_formula_second_order(orc):
+    """Eq. 53's discretisations, applied to Eq. 49's exact temperatures at the nodes of a
+    halfway-wall lattice (y = (j + 1/2) / H) and of a node-wall lattice (y = j / H), converge
+    to the plate's exact heat flux at second order.  The profile is exponential, so a formula
+    that is exact only for linear profiles (a one-sided first-order difference) fails."""
+    pe = 10.0
+    for node in (False, True):
+        errs = []
+        for H in (32, 64, 128):
+            ny = H + 1 if node else H
+            y = np.arange(ny) / H if node else (np.arange(ny) + 0.5) / H
+            T = ((np.exp(pe * y) - 1.0) / (math.exp(pe) - 1.0)).reshape(1, ny, 1)
+            T = np.broadcast_to(T, (2, ny, 3))
+            nu = orc.nusselt(T, 3, 1.0, H, node_wall=node)[0]
+            errs.append(abs(nu / _exact_flux(pe) - 1.0))
+        for e0, e1 in zip(errs, errs[1:]):
+            assert math.log2(e0 / e1) > 1.8, (node, errs)
+
+
+def test_node_wall_heat_flux_converges(orc):
+    """The paper's channel with node walls (the paper's boundary scheme): the hot plate's heat
+    flux from the oracle's steady field approaches Eq. 49's at second order on the last
+    halving (H = 32 -> 64)."""
+    Re, Da = 10.0, 1e-2
+    errs = []
+    for H in (16, 32, 64):
+        ny = H + 1
+        o = orc.Oracle(orc.map_problem(paper_channel(ny, Re=Re, Da=Da, walls="nee")))
+        o.step(max(2000, int(40 * ny / (0.01 * Re))))
+        _, _, T = o.macros()
+        errs.append(abs(orc.nusselt(T, 3, 1.0, H, node_wall=True)[0] / _exact_flux(Re) - 1.0))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.05, errs
+    assert math.log2(errs[1] / errs[2]) > 1.8, errs
