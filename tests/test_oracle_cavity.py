@@ -98,3 +98,17 @@ def test_heterogeneous_medium_conserves_mass(orc):
     o2.step(200)
     u2 = o2.macros()[1]
     assert np.abs(u - u2).max() > 1e-3 * np.abs(u2).max()
+
+
+def test_hot_fluid_rises(orc):
+    """Buoyancy (Eq. 5) lifts warm fluid against gravity: in the cavity heated from the x-low
+    wall, with gravity along -z, the fluid next to the hot wall moves up and the fluid next to
+    the cold wall moves down (the mirror symmetries and the Nusselt numbers are the same for
+    either sign, so this is the pin on it)."""
+    pb = cavity_problem(10, Ra=1e4, Da=1e-2, phi=0.8, Pr=0.71)
+    o = orc.Oracle(orc.map_problem(pb))
+    o.step(600)
+    _, u, T = o.macros()  # u[3][z][y][x]
+    uz = u[2]
+    assert uz[:, :, 0].mean() > 1e-5 and uz[:, :, -1].mean() < -1e-5, (uz[:, :, 0].mean(),
+                                                                      uz[:, :, -1].mean())

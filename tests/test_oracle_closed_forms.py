@@ -121,13 +121,16 @@ def test_shear_wave_decay(orc, phi, K):
     assert rate == pytest.approx(want, rel=5e-3)
 
 
-@pytest.mark.parametrize("sigma,ux", [(1.0, 0.0), (2.0, 0.02)])
-def test_temperature_wave(orc, sigma, ux):
+@pytest.mark.parametrize("sigma,ux,phi,alpha_m", [(1.0, 0.0, 1.0, -1.0), (2.0, 0.02, 1.0, -1.0),
+                                                  (1.5, 0.0, 0.4, 0.01)])
+def test_temperature_wave(orc, sigma, ux, phi, alpha_m):
     """sigma dT/dt + u.grad T = alpha_e lap T (Eq. 3): a cosine mode decays at
-    alpha_e k^2 / sigma and travels at u / sigma, with alpha_e from Eq. 41."""
+    alpha_e k^2 / sigma and travels at u / sigma, with alpha_e from Eq. 41; with a solid
+    matrix of diffusivity alpha_m, alpha_e = phi alpha_f + (1 - phi) alpha_m (Sec. 2)."""
     N = 32
     k = 2 * math.pi / N
-    pb = dict(nx=N, ny=1, nz=1, mapping="lattice", nu_e=0.05, alpha_f=0.04, sigma=sigma)
+    pb = dict(nx=N, ny=1, nz=1, mapping="lattice", nu_e=0.05, alpha_f=0.04, sigma=sigma,
+              phi=phi, alpha_m=alpha_m)
     lp = orc.map_problem(pb)
     o = orc.Oracle(lp)
     x = np.arange(N)
@@ -141,7 +144,8 @@ def test_temperature_wave(orc, sigma, ux):
     z1, z2 = np.sum(T1 * np.exp(-1j * k * x)), np.sum(T2 * np.exp(-1j * k * x))
     rate = -math.log(abs(z2) / abs(z1)) / 300
     speed = -np.angle(z2 / z1) / 300 / k
-    assert rate == pytest.approx(lp.alpha_f * k * k / sigma, rel=5e-3)
+    alpha_e = phi * 0.04 + (1.0 - phi) * alpha_m if alpha_m >= 0 else 0.04
+    assert rate == pytest.approx(alpha_e * k * k / sigma, rel=5e-3)
     assert speed == pytest.approx(ux / sigma, abs=1e-5)
 
 

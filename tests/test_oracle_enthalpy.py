@@ -28,6 +28,18 @@ def test_enthalpy_state_relations(orc):
         assert t == pytest.approx(T, abs=1e-14) and f in (0.0, 1.0)
 
 
+def test_latent_heat_scales_with_porosity(orc):
+    """Eqs. B5 and B8: the effective enthalpy is sigma c_pl T + phi f_l L_a, only the pore
+    fraction phi of a site melting, so at the melting point a site of porosity phi holding
+    En_e = sigma c_pl T_m + phi f L_a is at T_m with liquid fraction f."""
+    lp = _params(orc, T_s=0.5, T_l=0.5, St=0.5)
+    for phi in (1.0, 0.4):
+        for f in (0.25, 0.75):
+            En = lp.sigma_s * lp.c_pl * 0.5 + phi * f * lp.L_a
+            t, fl = orc.enthalpy_state(lp, En, phi)
+            assert t == pytest.approx(0.5, abs=1e-12) and fl == pytest.approx(f, abs=1e-12)
+
+
 def test_geq_b12_has_the_moments_of_b6(orc):
     """N g_eq (Eq. B12) = n_eq (Eq. B6)."""
     lp = _params(orc, c_pl=1.3, c_ps=0.7, varpi=0.4)

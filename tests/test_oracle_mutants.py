@@ -6,9 +6,10 @@ handed to the pins through LBM_ORACLE_UNDER_TEST (read by the `orc` fixture of c
 the oracle itself is never modified.  Each entry names the pin file expected to reject it
 first, so a pin that loses its power shows up here.
 
-One planted slip is known to pass every pin and is therefore not listed: the advection speed
-of the convective outflow (reading 19 of the design notes; the blend (old + U inner) / (1 + U)
-with U replaced by 1).  Every steady state is a fixed point of the blend for any U, and the
+One kind of planted slip is known to pass every pin and is therefore not listed: the
+advection speed of the convective outflow, for the flow and the temperature populations alike
+(reading 19 of the design notes; the blend (old + U inner) / (1 + U) with U replaced by 1, or
+the inner value taken alone).  Every steady state is a fixed point of the blend for any U, and the
 pins (the exact uniform stream, the flux balance of the walled channel) are steady; the speed
 shapes only the transient, for which the paper gives nothing to compare with.
 """
@@ -125,6 +126,60 @@ MUTANTS = [
      "q = 2.0 * (T_wall - t0) * L / dT",
      "Eq. 53 on a halfway wall from a one-sided first-order gradient",
      "test_oracle_paper_channel.py", "formula"),
+    ("geq_enthalpy_half", "lbm_oracle.c",
+     "geq[i] = L->varpi * L->c_ref * T / 6.0 + 0.5 * eu * L->c_pl * T;",
+     "geq[i] = L->varpi * L->c_ref * T / 6.0 + eu * L->c_pl * T;",
+     "Eq. B12: the 1/2 of the advective part",
+     "test_oracle_enthalpy.py", "geq_b12"),
+    ("latent_heat_porosity_dropped", "lbm_oracle.c",
+     "double El = L->sigma_l * L->c_pl * L->T_l + phi * L->L_a;",
+     "double El = L->sigma_l * L->c_pl * L->T_l + L->L_a;",
+     "Eq. B8: phi of the latent heat",
+     "test_oracle_enthalpy.py", "latent"),
+    ("matrix_diffusivity_swapped", "lbm_oracle.c",
+     ": phi * L->alpha_f + (1.0 - phi) * L->alpha_m;",
+     ": phi * L->alpha_m + (1.0 - phi) * L->alpha_f;",
+     "alpha_e = phi alpha_f + (1 - phi) alpha_m with the two diffusivities exchanged",
+     "test_oracle_closed_forms.py", "temperature_wave"),
+    ("buoyancy_sign", "__init__.py",
+     "buoy[gaxis] = -gsign * gbeta", "buoy[gaxis] = gsign * gbeta",
+     "Eq. 5: buoyancy along gravity instead of against it",
+     "test_oracle_cavity.py", "hot_fluid"),
+    ("cavity_buoyancy_scale", "__init__.py",
+     "gbeta = (Ma * math.sqrt(CS2)) ** 2 / (dT * L)", "gbeta = Ma ** 2 * CS2 / dT",
+     "Eq. 56: u_c^2 = g beta dT L without the L",
+     "test_oracle_paper_tables.py", "halfway"),
+    ("darcy_number_scale", "__init__.py",
+     "K = float(Da) * L * L if Da is not None else math.inf",
+     "K = float(Da) * L if Da is not None else math.inf",
+     "Da = K / L^2 read as K / L",
+     "test_oracle_cavity.py", "x_mirror_symmetry"),
+    ("channel_viscosity_mapping", "__init__.py",
+     "inv_s_nu = 0.5 + J * L * u0 / (CS2 * Re)", "inv_s_nu = 0.5 + J * L * u0 / Re",
+     "Eq. 51: c_s^2 dropped",
+     "test_oracle_d3q15.py", "paper_channel_second_order"),
+    ("stilde15_coefficient", "lbm_oracle.c",
+     "S[1] = 2.0 * rho0 * uF / phi;", "S[1] = 1.0 * rho0 * uF / phi;",
+     "Eq. 17: the energy-moment coefficient of D3Q15",
+     "test_oracle_d3q15.py", "forcing_is_the_derivative"),
+    ("meq15_coefficient", "lbm_oracle.c",
+     "meq[4] = -7.0 / 3.0 * rho0 * ux;", "meq[4] = -2.0 / 3.0 * rho0 * ux;",
+     "Eq. 15: the D3Q15 heat-flux moment with the D3Q19 coefficient",
+     "test_oracle_d3q15.py", "equilibrium_moments"),
+    ("node_wall_density", "lbm_oracle.c",
+     "double rhob = out > 0.0 ? L->rho0 : m[0];", "double rhob = m[0];",
+     "node walls: the withdrawing wall takes the fluid node's density",
+     "test_oracle_nee.py", "steady_mass"),
+    ("node_wall_flow_sign", "lbm_oracle.c",
+     "for (int i = 0; i < D->q; ++i) f[i] += eb[i] - ef[i];",
+     "for (int i = 0; i < D->q; ++i) f[i] += ef[i] - eb[i];",
+     "node walls: the equilibrium parts exchanged with the wrong sign",
+     "test_oracle_nee.py", "couette_between_node_walls"),
+    ("node_wall_thermal_sign", "lbm_oracle.c",
+     "for (int i = 0; i < Q7; ++i) g[i] += gb[i] - gf[i];",
+     "for (int i = 0; i < Q7; ++i) g[i] += gf[i] - gb[i];",
+     "node walls: the thermal equilibrium parts exchanged with the wrong sign",
+     "test_oracle_nee.py", "conduction_between_node_walls"),
 ]
 
 
