@@ -9,7 +9,7 @@ in the few plain definitions below (parameter mapping, Nusselt numbers, residual
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against the lattice
 definitions, closed forms, invariants and symmetries that the paper and the mathematics
 fix, and against the cavity Nusselt numbers the paper prints; ``tests/test_oracle_mutants.py``
-plants 35 plausible slips in a copy of the oracle and checks that a pin rejects each.  The
+plants 37 plausible slips in a copy of the oracle and checks that a pin rejects each.  The
 Nusselt discretisation (Eq. 53) is pinned by the exact conduction value and, at second order,
 by the exponential temperature profile of the paper's channel.  Parity unpinned, in part:
 the advection speed of the convective outflow (a reading; the paper has no outflow).  Its

@@ -178,3 +178,25 @@ def test_channel_outflow_mass_balance(orc):
     flux = u[0].sum(axis=(0, 1))
     assert np.ptp(flux) / flux.mean() < 1e-6
     assert np.abs(rho[:, :, -1] - 1.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("p,Fphi", [(0.45, 0.0), (0.8, -1.0)])
+def test_porosity_field_medium(orc, p, Fphi):
+    """A porosity field sets each site's medium from Eq. 6: K = K_ref [p^3 / (1 - p)^2] /
+    [p_ref^3 / (1 - p_ref)^2] (Kozeny-Carman about the reference porosity) and, for Ergun's
+    inertia, F_phi = 1.75 / sqrt(150 p^3).  A field uniform at p in a forced periodic box
+    must then flow at the uniform Darcy-Forchheimer velocity of that K and F_phi."""
+    nu_e, K_ref, p_ref, a = 0.1, 0.5, 0.6, 2e-4
+    field = np.full((2, 2, 2), p)
+    pb = dict(nx=2, ny=2, nz=2, mapping="lattice", nu_e=nu_e, phi=p_ref, K=K_ref, F_phi=Fphi,
+              accel=[a, 0, 0], phi_field=field, phi_ref=p_ref)
+    o = _run(orc, pb, 3000)
+    _, u, _ = o.macros()
+    K = K_ref * (p ** 3 / (1 - p) ** 2) / (p_ref ** 3 / (1 - p_ref) ** 2)
+    nu = nu_e
+    if Fphi < 0:
+        c = 1.75 / math.sqrt(150 * p ** 3) / math.sqrt(K)
+        ue = (-nu / K + math.sqrt((nu / K) ** 2 + 4 * c * a)) / (2 * c)
+    else:
+        ue = K * a / nu
+    assert u[0].mean() == pytest.approx(ue, rel=1e-9)

@@ -180,6 +180,16 @@ MUTANTS = [
      "for (int i = 0; i < Q7; ++i) g[i] += gf[i] - gb[i];",
      "node walls: the thermal equilibrium parts exchanged with the wrong sign",
      "test_oracle_nee.py", "conduction_between_node_walls"),
+    ("kozeny_carman_exponent", "lbm_oracle.c",
+     "double kc = p * p * p / ((1.0 - p) * (1.0 - p));",
+     "double kc = p * p / ((1.0 - p) * (1.0 - p));",
+     "Eq. 6: phi^2 in place of phi^3 in the Kozeny-Carman permeability",
+     "test_oracle_closed_forms.py", "porosity_field"),
+    ("ergun_field_exponent", "lbm_oracle.c",
+     "*Fphi = L->F_phi < 0 ? 1.75 / sqrt(150.0 * p * p * p) : L->F_phi;",
+     "*Fphi = L->F_phi < 0 ? 1.75 / sqrt(150.0 * p * p) : L->F_phi;",
+     "Eq. 6: phi^2 in place of phi^3 in Ergun's coefficient of a field site",
+     "test_oracle_closed_forms.py", "porosity_field"),
 ]
 
 
