@@ -9,11 +9,12 @@ in the few plain definitions below (parameter mapping, Nusselt numbers, residual
 Pins: every function here is checked by ``tests/test_oracle_*.py`` against the lattice
 definitions, closed forms, invariants and symmetries that the paper and the mathematics
 fix, and against the cavity Nusselt numbers the paper prints; ``tests/test_oracle_mutants.py``
-plants 37 plausible slips in a copy of the oracle and checks that a pin rejects each.  The
+plants 41 plausible slips in a copy of the oracle and checks that a pin rejects each.  The
 Nusselt discretisation (Eq. 53) is pinned by the exact conduction value and, at second order,
 by the exponential temperature profile of the paper's channel.  Parity unpinned, in part:
 the advection speed of the convective outflow (a reading; the paper has no outflow).  Its
-steady states, which the pins check, are the same for every speed.
+steady states, which the pins check, are the same for every speed; and the corner convention
+of node walls (which face's velocity a corner site takes), which the paper leaves open.
 """
 from __future__ import annotations
 

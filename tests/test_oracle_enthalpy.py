@@ -127,6 +127,22 @@ def test_solid_cells_do_not_flow(orc):
     assert np.abs(u[:, liquid]).max() > 1e-5
 
 
+def test_flow_gate_is_at_half_liquid(orc):
+    """The flow gate of the enthalpy model (a reading: App. B gives the thermal model only) at
+    one site: under a body force a mushy site with f_l just below 1/2 keeps no velocity and its
+    flow populations rest at f_eq(rho, 0); just above 1/2 it flows."""
+    lp = _params(orc, T_m=0.5, St=0.5, accel=[1e-4, 0.0, 0.0], K=10.0, phi=1.0)
+    f = orc.feq19(1.0, np.zeros(3), 1.0, 1.0)
+    for fl, flows in ((0.45, False), (0.55, True)):
+        En = lp.sigma_s * lp.c_pl * 0.5 + fl * lp.L_a
+        g = orc.geq7_enthalpy(lp, En, 0.5, np.zeros(3))
+        fo, _, mac = orc.collide_site(lp, f, g)
+        if flows:
+            assert mac[1] > 1e-6
+        else:
+            assert np.abs(mac[1:4]).max() == 0.0 and np.allclose(fo, f, atol=1e-15)
+
+
 def test_gate_margin_records_the_distance_of_f_l_from_one_half(orc):
     """Oracle.gate_margin: in a closed adiabatic box at rest with a uniform mushy enthalpy
     (f_l = 0.3 or 0.62 by Eq. B9) nothing changes, so after a step every site's margin is

@@ -11,7 +11,10 @@ advection speed of the convective outflow, for the flow and the temperature popu
 (reading 19 of the design notes; the blend (old + U inner) / (1 + U) with U replaced by 1, or
 the inner value taken alone).  Every steady state is a fixed point of the blend for any U, and the
 pins (the exact uniform stream, the flux balance of the walled channel) are steady; the speed
-shapes only the transient, for which the paper gives nothing to compare with.
+shapes only the transient, for which the paper gives nothing to compare with.  Nor is the
+corner convention of node walls (a corner site takes the velocity of its lowest-numbered wall
+face, reading 26): the paper leaves it open, and no pin has two differently moving walls
+meeting at a corner.
 """
 import os
 import shutil
@@ -190,6 +193,24 @@ MUTANTS = [
      "*Fphi = L->F_phi < 0 ? 1.75 / sqrt(150.0 * p * p) : L->F_phi;",
      "Eq. 6: phi^2 in place of phi^3 in Ergun's coefficient of a field site",
      "test_oracle_closed_forms.py", "porosity_field"),
+    ("outflow_anchor_dropped", "lbm_oracle.c",
+     "if (via[i]) f[i] += D->w[i] * (L->rho0 - rho) / wsum;", "if (via[i]) f[i] += 0.0;",
+     "reading 19: the outlet's pressure anchor left out",
+     "test_oracle_closed_forms.py", "outflow_mass_balance"),
+    ("enthalpy_diffusivity_swapped", "lbm_oracle.c",
+     "(fl * L->alpha_l + (1.0 - fl) * L->alpha_s)", "(fl * L->alpha_s + (1.0 - fl) * L->alpha_l)",
+     "Eq. B11: the liquid and solid diffusivities exchanged",
+     "test_oracle_enthalpy.py", "two_region_melting"),
+    ("velocity_sum_range", "lbm_oracle.c",
+     "for (int i = 0; i < D->q; ++i) s += D->e[a * D->q + i] * f[i];",
+     "for (int i = 0; i < 9; ++i) s += D->e[a * D->q + i] * f[i];",
+     "Eq. 28 with its printed upper limit 8 taken literally",
+     "test_oracle_lattice.py", "velocity_solves_eq26"),
+    ("enthalpy_flow_gate", "lbm_oracle.c",
+     "if (L->enthalpy && (L->flow_off || fl < 0.5)) {",
+     "if (L->enthalpy && (L->flow_off || fl < 0.05)) {",
+     "reading 22: the flow gate at f_l = 0.05 instead of 1/2",
+     "test_oracle_enthalpy.py", "flow_gate"),
 ]
 
 
